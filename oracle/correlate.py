@@ -48,7 +48,8 @@ def cell_bins(N, L, r_edges, n_mur, r_perp_cut, w):
     """
     dx = L / N
     dx2 = dx * dx
-    e2 = np.asarray(r_edges, dtype=np.float64) ** 2
+    e = np.asarray(r_edges, dtype=np.float64)
+    e2 = e * e
     o = np.arange(-w, w + 1, dtype=np.int64)
     c = o[:, None, None]
     b = o[None, :, None]

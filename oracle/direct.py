@@ -86,3 +86,34 @@ def window_C(pts_a, w_a, pts_b, w_b, L, N, assign, w, r_max):
     if Qa == 0.0 or Qb == 0.0:
         return None
     return float(N) ** 3 * D / (Qa * Qb) - 1.0
+
+
+def _window_D_chunk(args):
+    return window_D(*args)[0]
+
+
+def window_C_parallel(pts_a, w_a, pts_b, w_b, L, N, assign, w, r_max, workers=None):
+    """window_C with the a-points split over a spawn-started process pool
+    (D is a sum over a-points, so the chunks add). Safe to call from a
+    process that already uses CUDA."""
+    import multiprocessing as mp
+    import os
+    pa = np.asarray(pts_a, dtype=np.float64)
+    na = pa.shape[0]
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    if workers == 1 or na < 2000:
+        return window_C(pts_a, w_a, pts_b, w_b, L, N, assign, w, r_max)
+    bounds = np.linspace(0, na, workers * 2 + 1).astype(int)
+    wa = None if w_a is None else np.asarray(w_a, dtype=np.float64)
+    jobs = [(pa[b0:b1], None if wa is None else wa[b0:b1], pts_b, w_b, L, N, assign, w, r_max)
+            for b0, b1 in zip(bounds[:-1], bounds[1:]) if b1 > b0]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        parts = pool.map(_window_D_chunk, jobs)
+    D = np.sum(parts, axis=0)
+    _, _, _, qa, _ = omesh.corners(pa, w_a, L, N, assign)
+    _, _, _, qb, _ = omesh.corners(np.asarray(pts_b, dtype=np.float64), w_b, L, N, assign)
+    Qa = float(qa.sum()) / TWO32
+    Qb = float(qb.sum()) / TWO32
+    if Qa == 0.0 or Qb == 0.0:
+        return None
+    return float(N) ** 3 * D / (Qa * Qb) - 1.0

@@ -49,7 +49,8 @@ def min_image(d: np.ndarray, L: float) -> np.ndarray:
 
 def _bin_pairs(d, s_edges, n_mu):
     """(s bin, mu bin, valid) for separation vectors d [m, 3]."""
-    e2 = np.asarray(s_edges, dtype=np.float64) ** 2
+    e = np.asarray(s_edges, dtype=np.float64)
+    e2 = e * e
     s2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
     k = np.searchsorted(e2, s2, side="right") - 1
     valid = (k >= 0) & (k < len(e2) - 1)
@@ -129,3 +130,27 @@ def xi_ss(ddq, w, n_gal, L, s_edges, n_mu):
     dd = ddq.astype(np.float64) / TWO32
     with np.errstate(invalid="ignore", divide="ignore"):
         return dd / rr - 1.0, rr
+
+
+def find_pairs_kdtree(pos, w, L, s_edges, n_mu):
+    """find_pairs for large catalogues: the candidate pairs i < j closer than
+    s_max come from scipy's periodic k-d tree (a library neighbour search,
+    slightly enlarged radius); binning, midpoints and weights are then the
+    same definitions as find_pairs. Output sorted by (i, j)."""
+    from scipy.spatial import cKDTree
+    pos = np.asarray(pos, dtype=np.float64)
+    wt = None if w is None else np.asarray(w, dtype=np.float32).astype(np.float64)
+    tree = cKDTree(pos, boxsize=L)
+    cand = tree.query_pairs(float(s_edges[-1]) * (1.0 + 1e-9), output_type="ndarray")
+    if cand.size == 0:
+        cand = np.zeros((0, 2), dtype=np.int64)
+    I = np.minimum(cand[:, 0], cand[:, 1]).astype(np.int64)
+    J = np.maximum(cand[:, 0], cand[:, 1]).astype(np.int64)
+    o = np.lexsort((J, I))
+    I, J = I[o], J[o]
+    d = min_image(pos[J] - pos[I], L)
+    k, m, valid = _bin_pairs(d, s_edges, n_mu)
+    I, J, d, k, m = I[valid], J[valid], d[valid], k[valid], m[valid]
+    return {"i": I, "j": J, "sbin": k.astype(np.int64), "mubin": m.astype(np.int64),
+            "mid": wrap(pos[I] + 0.5 * d, L),
+            "weight": np.ones(I.size) if wt is None else wt[I] * wt[J]}

@@ -101,3 +101,15 @@ def test_weighted_counts_exact():
     # weights all one: RR is N(N-1)/2 times the volume fraction
     _, rr = op.xi_ss(np.zeros(1, np.int64), np.ones(300, np.float32), 300, L, (0.0, 3.0), 1)
     assert math.isclose(rr[0], 300 * 299 / 2 * (4 / 3 * math.pi * 27) / L ** 3)
+
+
+def test_kdtree_pairs_equal_brute_force():
+    L = 80.0
+    cat = synth.make_catalogue_box(L, 1500, seed=12)
+    w = synth.make_weights(cat.n, 3)
+    edges = (0.0, 1.0, 2.5, 4.0, 6.0)
+    a = op.find_pairs(cat.pos, w, L, edges, 3)
+    b = op.find_pairs_kdtree(cat.pos, w, L, edges, 3)
+    oa = np.lexsort((a["j"], a["i"]))
+    for k in ("i", "j", "sbin", "mubin", "mid", "weight"):
+        np.testing.assert_array_equal(a[k][oa], b[k])
