@@ -1,0 +1,236 @@
+/*
+ * pairgal.h -- C ABI of libpairgal.so, the GB300 (sm_103a) pair-galaxy
+ * cross-correlation library after Yuan, Eisenstein & Garrison (2017),
+ * "Using galaxy pairs to investigate the three-point correlation function in
+ * the squeezed limit".
+ *
+ * The method (Sec. 2.1-2.2): close galaxy pairs, binned by separation s and
+ * line-of-sight cosine mu, are objects at their midpoints; each bin's pair
+ * field is deposited on a periodic mesh and cross-correlated with the galaxy
+ * mesh by 3D FFTs. Binning the correlation by (r, mu_r) gives
+ *   xi_pg(s, mu; r, mu_r), xi_gg(r, mu_r), b_pg = xi_pg / xi_gg   (eq. bpg_initial,
+ *   with W the indicator of one (r, mu_r) shell; eq. bpg_final is the same
+ *   estimator written in real space),
+ *   xi(d_w) = sum C_gg^2 / sum C_gg over the shell                  (eq. xi_dw),
+ *   Q_eff from eq. Qeff_notsq and the strict-squeezed form eq. Qeff, with
+ *   xi(d_p) = xi(s, mu) = DD / RR - 1 from the pair counts           (eq. 2PCF_d_collapsed).
+ *
+ * Conventions for every entry point:
+ *  - Positions are FP64, [n][3] row-major (x, y, z), Mpc/h, any real value
+ *    (they are wrapped into [0, L)). The line of sight is z.
+ *  - "device" pointers are CUDA device memory of the current device; "host"
+ *    pointers are ordinary or pinned host memory. The caller owns every input
+ *    and output buffer; the library never frees them.
+ *  - Mesh arrays are [z][y][x] with x contiguous; mesh node i sits at i * L/N.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = the legacy
+ *    default stream) unless it returns host results, in which case it
+ *    synchronises that stream before returning.
+ *  - No call throws; each returns a pg_status. A plan is not thread safe;
+ *    separate plans may run on separate streams.
+ *  - Empty bins (no pairs, no galaxies, or no mesh cells) give NaN outputs
+ *    with PG_OK; callers inspect dd and n_cells.
+ */
+#ifndef PAIRGAL_H
+#define PAIRGAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PG_OK = 0,
+  PG_ERR_INVALID_ARG = 1,   /* bad sizes, edges, NaN/Inf input, NULL where required */
+  PG_ERR_UNSUPPORTED = 2,   /* valid request this build does not handle (e.g. mesh_n) */
+  PG_ERR_OOM = 3,           /* device allocation failed */
+  PG_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed */
+  PG_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+  PG_ERR_UNIMPLEMENTED = 6,
+  PG_ERR_CAPACITY = 7       /* an output buffer is smaller than the result */
+} pg_status;
+
+/* Returns a static, NUL-terminated description of a status code. */
+const char* pg_status_string(pg_status s);
+
+/* Problem statement (Sec. 2.1, Sec. 3.3-3.6). Edge arrays are HOST memory and
+ * are copied by pg_plan_create. */
+typedef struct pg_params {
+  double box_L;             /* periodic box side, Mpc/h, > 0 */
+  int32_t mesh_n;           /* N: power of two, 32..1024 (Sec. 3.5 mesh) */
+  int32_t assign;           /* 0 = NGP, 1 = CIC mass assignment (Sec. 3.5) */
+  int32_t n_s;              /* pair separation bins, 1..64 */
+  const double* s_edges;    /* [n_s+1] ascending, s_edges[0] >= 0, s_edges[n_s] < L/2 */
+  int32_t n_mu;             /* equal bins of mu = |dz|/s on [0, 1], 1..64 */
+  int32_t n_r;              /* correlation radius bins, 1..64 */
+  const double* r_edges;    /* [n_r+1] ascending, r_edges[0] >= 0, r_edges[n_r] < L/2 */
+  int32_t n_mur;            /* equal bins of mu_r = |r_z|/r on [0, 1], 1..64 */
+  double rsd_factor;        /* Mpc/h per km/s: z' = z + rsd_factor * v_z (eq. RSD); 0 = real space */
+  double r_perp_cut;        /* aggregates exclude cells with r_perp < cut (Sec. 3.6(b)); 0 = off */
+  int32_t precision;        /* 0 = FP32 FFT + FP64 reductions, 1 = FP64 throughout */
+  int32_t bins_per_batch;   /* pair meshes resident at once; 0 = chosen from N */
+} pg_params;
+
+typedef struct pg_plan pg_plan;
+
+/* Host output buffers (caller-owned; any pointer may be NULL to skip it).
+ * P = n_s*n_mu pair bins (index s_bin*n_mu + mu_bin); Q = n_r*n_mur
+ * correlation bins (index r_bin*n_mur + mur_bin). */
+typedef struct pg_result {
+  int64_t* dd;          /* [P] number of pairs per (s, mu) bin */
+  double* dd_w;         /* [P] sum of w_i*w_j (exact: summed as Q32.32 integers) */
+  double* xi_ss;        /* [P] xi(s, mu) = DD/RR - 1, RR = ((sum w)^2 - sum w^2)/2 * V_bin/L^3 */
+  double* xi_pg;        /* [P][Q] mean of C_pg over the bin's cells */
+  double* xi_gg;        /* [Q] mean of C_gg */
+  double* b_pg;         /* [P][Q] xi_pg / xi_gg */
+  double* q_eff;        /* [P][Q] eq. Qeff_notsq with xi(d_p) = xi_ss, xi(d_w) = xi_dw */
+  double* q_eff_sq;     /* [P][Q] eq. Qeff (strictly squeezed) */
+  double* xi_dw;        /* [Q] sum C_gg^2 / sum C_gg over the bin (eq. xi_dw) */
+  double* b_pg_agg;     /* [P] sum C_pg / sum C_gg over all cells with r in [r_0, r_nr), r_perp >= cut */
+  double* q_eff_agg;    /* [P] eq. Qeff_notsq with b_pg_agg and xi_dw_agg */
+  double* xi_dw_agg;    /* [1] */
+  int64_t* n_cells;     /* [Q] mesh offsets in each (r, mu_r) bin */
+  int64_t* n_cells_agg; /* [1] */
+  double* sum_pg;       /* [P][Q] sum of C_pg over the bin (raw) */
+  double* sum_pg_agg;   /* [P] */
+  double* sum_gg;       /* [Q] */
+  double* sum2_gg;      /* [Q] sum of C_gg^2 */
+  double* sum_gg_agg;   /* [2] sum C_gg, sum C_gg^2 over the aggregate cells */
+} pg_result;
+
+/* Validates *params, copies the edges and builds the data-independent plan
+ * state (FFT twiddles, the (r, mu_r) cell lists of the offset window) on the
+ * current device. Device workspace grows on first use (see pg_plan_reserve).
+ * Errors: PG_ERR_INVALID_ARG, PG_ERR_UNSUPPORTED, PG_ERR_OOM, PG_ERR_CUDA. */
+pg_status pg_plan_create(const pg_params* params, pg_plan** out);
+
+/* Frees the plan and its device workspace (synchronises the device first). */
+void pg_plan_destroy(pg_plan* plan);
+
+/* Allocates workspace for catalogues up to n_gal_max galaxies and
+ * n_pairs_max pairs so that later calls allocate nothing. */
+pg_status pg_plan_reserve(pg_plan* plan, int64_t n_gal_max, int64_t n_pairs_max);
+
+/* Device bytes currently held by the plan. */
+size_t pg_workspace_bytes(const pg_plan* plan);
+
+/* The full forward path (Sec. 2.1-2.2, 3.2-3.6) for one catalogue:
+ * positions -> (s, mu) pairs -> per-bin midpoint meshes and the galaxy mesh
+ * -> FFT cross-correlation -> (r, mu_r) binning -> ratios.
+ *   d_pos [n_gal][3] FP64 device; d_vel [n_gal][3] FP32 km/s device or NULL
+ *   (needed when rsd_factor != 0); d_w [n_gal] FP32 device or NULL (unit
+ *   weights; weights must be >= 0). Results are written to *host_out; the
+ *   stream is synchronised before return.
+ * Errors: PG_ERR_INVALID_ARG (n_gal < 0, NULL positions, non-finite
+ * positions), PG_ERR_OOM, PG_ERR_CUDA. n_gal = 0 gives NaN outputs. */
+pg_status pg_forward(pg_plan* plan, int64_t n_gal, const double* d_pos,
+                     const float* d_vel, const float* d_w,
+                     pg_result* host_out, void* stream);
+
+/* pg_forward with HOST inputs: copies them to plan-owned device buffers on
+ * `stream` first (pinned host memory makes the copies asynchronous). */
+pg_status pg_forward_host(pg_plan* plan, int64_t n_gal, const double* h_pos,
+                          const float* h_vel, const float* h_w,
+                          pg_result* host_out, void* stream);
+
+/* Low-level form of the estimator for two arbitrary point sets (Sec. 2.1,
+ * eq. bpg_initial): deposits set a and set b, correlates them, and bins
+ * C_ab(r) = (1/N^3) sum_x delta_b(x) delta_a(x + r) by (r, mu_r).
+ * Positions are device [n][3] FP64 already inside [0, L); weights device FP64
+ * or NULL. Writes host arrays h_sum[Q], h_sum2[Q] (sum C, sum C^2 per bin),
+ * h_agg[2] (over the aggregate cells) and h_ncells[Q]; any may be NULL. */
+pg_status pg_correlate_points(pg_plan* plan,
+                              int64_t n_a, const double* d_pts_a, const double* d_w_a,
+                              int64_t n_b, const double* d_pts_b, const double* d_w_b,
+                              double* h_sum, double* h_sum2, double* h_agg,
+                              int64_t* h_ncells, void* stream);
+
+/* ---- stage entry points (each row of the path on its own) -------------- */
+
+/* Sec. 3.2, eq. RSD: wraps positions into [0, L) and, when rsd_factor != 0,
+ * shifts z to wrap(z + rsd_factor * v_z). d_in [n][3] FP64, d_vel [n][3]
+ * FP32 or NULL, d_out [n][3] FP64 (may alias d_in). */
+pg_status pg_transform_positions(int64_t n, double box_L, double rsd_factor,
+                                 const double* d_in, const float* d_vel,
+                                 double* d_out, void* stream);
+
+/* Sec. 3.3 (all pairs closer than s_max, every pair of a triplet kept) and
+ * Sec. 2.1 (a pair sits at its midpoint): cell-list enumeration of all
+ * unordered pairs of the wrapped positions d_pos [n][3] with s in
+ * [s_edges[0], s_edges[n_s]), binned by (s, mu). For a pair of input indices
+ * i < j: d = min-image(x_j - x_i), midpoint wrap(x_i + d/2), weight w_i*w_j.
+ * Outputs (device, caller-owned): d_dd[P] int64 pair counts, d_ddq[P] int64
+ * sums of llrint(w_i w_j 2^32). If capacity > 0 the pairs are also written,
+ * grouped by bin in ascending bin order (order inside a bin unspecified):
+ * d_bin[cap] int32, d_i[cap], d_j[cap] int32, d_mid[cap][3] FP64,
+ * d_wp[cap] FP64. *h_n_pairs (host) receives the total; PG_ERR_CAPACITY if it
+ * exceeds capacity (counts are still valid). Uses `plan` for its binning and
+ * box; the plan's mesh is not used. Synchronises the stream. */
+pg_status pg_find_pairs(pg_plan* plan, int64_t n, const double* d_pos,
+                        const float* d_w, int64_t* d_dd, int64_t* d_ddq,
+                        int64_t capacity, int32_t* d_bin, int32_t* d_i,
+                        int32_t* d_j, double* d_mid, double* d_wp,
+                        int64_t* h_n_pairs, void* stream);
+
+/* Sec. 3.5: NGP/CIC mass assignment of n points (device [n][3] FP64 in
+ * [0, L)) with weights (device FP64 or NULL = 1) into a dense device mesh
+ * d_mesh[N][N][N] int64 of Q32.32 node weights llrint(((w wx) wy) wz 2^32),
+ * ADDED to its current contents (zero it first for a fresh mesh). Exact and
+ * order independent. */
+pg_status pg_deposit_dense(int64_t n, const double* d_pts, const double* d_w,
+                           double box_L, int32_t mesh_n, int32_t assign,
+                           int64_t* d_mesh, void* stream);
+
+/* Sec. 3.6 (the transforms the estimator is built on): forward real-to-
+ * complex 3D DFT F(k) = sum_x f(x) exp(-2 pi i k.x / N) of a dense mesh
+ * d_in[N][N][N] (FP32 if precision 0, FP64 if 1) into the half spectrum
+ * d_out[N][N][N/2+1] (complex64 / complex128 interleaved, kx contiguous),
+ * through the same pass kernels as the estimator. Needs a plan with this
+ * mesh_n and precision (its workspace is used). */
+pg_status pg_fft_r2c_3d(pg_plan* plan, const void* d_in, void* d_out, void* stream);
+
+/* Inverse of the above, unnormalised: f(x) = sum_k F(k) exp(+2 pi i k.x / N)
+ * over the Hermitian-completed spectrum. d_in is not modified. */
+pg_status pg_fft_c2r_3d(pg_plan* plan, const void* d_in, void* d_out, void* stream);
+
+/* ---- measurement ---------------------------------------------------------- */
+
+/* Kernel families of the path, in the order of pg_plan_last_stats. */
+enum {
+  PG_FAM_POSITIONS = 0,   /* wrap, RSD, finiteness check, weight sums */
+  PG_FAM_CELLS,           /* cell-list counting sort */
+  PG_FAM_PAIRS,           /* pair counting, pair list, grouping by bin */
+  PG_FAM_DEPOSIT,         /* line flags, line numbering, Q32.32 deposit */
+  PG_FAM_FFT_X_R2C,       /* x pass, real to complex */
+  PG_FAM_FFT_Y_FWD,       /* y pass forward (writes the dense spectra) */
+  PG_FAM_FFT_Z_FWD,       /* z pass forward of the galaxy spectrum */
+  PG_FAM_FFT_Z_CORR,      /* z pass: forward, times conj(F_g), inverse, window */
+  PG_FAM_FFT_Y_INV,       /* y pass inverse on the window */
+  PG_FAM_FFT_X_C2R,       /* x pass complex to real on the window */
+  PG_FAM_BIN,             /* (r, mu_r) sums */
+  PG_FAM_RATIOS,          /* xi, b_pg, Q_eff */
+  PG_N_FAMILIES
+};
+
+typedef struct pg_kernel_stat {
+  char name[24];          /* family name */
+  int64_t launches;       /* kernel launches in the last profiled call */
+  double ms;              /* their summed duration: CUDA events on the call's stream */
+  double bytes;           /* algorithmic bytes they must move (reads + writes) */
+} pg_kernel_stat;
+
+/* Enables (1) or disables (0) per-family event timing on later calls of
+ * pg_forward / pg_forward_host on this plan. */
+pg_status pg_plan_set_profiling(pg_plan* plan, int32_t enable);
+
+/* Statistics of the last pg_forward / pg_forward_host call: out[PG_N_FAMILIES]
+ * (host; times are 0 unless profiling was enabled) and *total_launches, the
+ * number of kernels that call launched (always counted). Either may be NULL. */
+pg_status pg_plan_last_stats(const pg_plan* plan, pg_kernel_stat* out, int64_t* total_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAIRGAL_H */

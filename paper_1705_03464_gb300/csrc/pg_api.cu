@@ -1,0 +1,952 @@
+// C ABI of libpairgal: plans, workspace and the forward pipeline.
+//
+// pg_forward runs the path of Sec. 2.1-2.2 and 3.2-3.6 on one device stream:
+//   positions (eq. RSD) -> cell list -> (s, mu) pairs and DD -> galaxy mesh ->
+//   galaxy spectrum -> galaxy auto-correlation window -> for each batch of
+//   pair bins: midpoint meshes -> spectra -> cross-spectrum with the galaxy
+//   spectrum and inverse (z, then y, then x on the |r| <= r_max window) ->
+//   (r, mu_r) sums -> ratios.
+// Host code only sizes buffers, builds plan geometry (twiddle table, cell
+// lists of the window) and launches kernels; every step of the path runs on
+// the device.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "pg_internal.cuh"
+
+using namespace pg;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t want, size_t* total) {
+    if (want <= bytes) return cudaSuccess;
+    if (p) { cudaFree(p); *total -= bytes; p = nullptr; bytes = 0; }
+    if (want == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) { p = nullptr; return e; }
+    bytes = want;
+    *total += want;
+    return cudaSuccess;
+  }
+  void release(size_t* total) {
+    if (p) { cudaFree(p); *total -= bytes; }
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+pg_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return PG_OK;
+  if (e == cudaErrorMemoryAllocation) return PG_ERR_OOM;
+  return PG_ERR_CUDA;
+}
+
+#define PG_TRY(expr)                            \
+  do {                                          \
+    cudaError_t e_ = (expr);                    \
+    if (e_ != cudaSuccess) {                    \
+      (void)cudaGetLastError();                 \
+      return from_cuda(e_);                     \
+    }                                           \
+  } while (0)
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+struct pg_plan {
+  pg_params prm;
+  std::vector<double> s_edges, r_edges;
+  int device = 0;
+  int N = 0, M1 = 0, P = 0;       // mesh, half-spectrum length, row pitch
+  int w = 0, W = 0;               // window half size, side
+  int nPB = 0, nQ = 0, nL = 0;    // pair bins, (r, mu_r) bins, lists (nQ + 1)
+  int nbmax = 1;                  // pair meshes per batch
+  double dx = 0.0;
+  PairGeom geom;
+  size_t total = 0;
+  int64_t n_cells_listed = 0;
+  std::vector<int64_t> h_list_off;
+
+  // plan geometry
+  DevBuf tw, cells, list_off, s_edges_d;
+  // catalogue
+  DevBuf in_pos, in_vel, in_w, x, y, z, gw, flag, wpart, wsum;
+  DevBuf cell_id, ccount, cstart, ccursor, perm, xs, ys, zs, ws, ctmp, ctot;
+  // pairs
+  DevBuf dd, ddq, pcursor, ubin, ui, uj, umx, umy, umz, uwp;
+  DevBuf pbin, px, py, pz, pw, bcursor;
+  // meshes
+  DevBuf flags, lidx, seg_total, line_base, n_lines, stmp, line_y, line_bin, lines_q, qsum, scale;
+  DevBuf spec, S, Fg, Wz, Wy, Cwin, sums_pg, sums_gg, pg_valid, tmpfft;
+  // outputs
+  DevBuf out;
+  int64_t cap_gal = -1, cap_pairs = -1, cap_lines = -1;
+
+  // measurement: event pairs around each launch site of a profiled call
+  bool prof_on = false;
+  std::vector<cudaEvent_t> events;
+  struct Rec { int fam; int ev0, ev1; long long launches; };
+  std::vector<Rec> recs;
+  int next_event = 0;
+  double fam_bytes[PG_N_FAMILIES] = {};
+  pg_kernel_stat stats[PG_N_FAMILIES] = {};
+  int64_t last_launches = 0;
+};
+
+std::atomic<long long>& pg::launch_counter() {
+  static std::atomic<long long> c{0};
+  return c;
+}
+
+namespace {
+
+size_t csize(const pg_plan* p) { return p->prm.precision ? sizeof(double2) : sizeof(float2); }
+size_t rsize(const pg_plan* p) { return p->prm.precision ? sizeof(double) : sizeof(float); }
+
+const char* kFamNames[PG_N_FAMILIES] = {"positions", "cells", "pairs", "deposit", "fft_x_r2c",
+                                        "fft_y_fwd", "fft_z_fwd", "fft_z_corr", "fft_y_inv",
+                                        "fft_x_c2r", "bin", "ratios"};
+
+// Times the launches issued inside its scope (one kernel family) with a pair
+// of CUDA events on the call's stream, and books the family's algorithmic
+// bytes. Costs nothing when profiling is off.
+struct ProfScope {
+  pg_plan* p;
+  int fam;
+  cudaStream_t s;
+  int ev0 = -1;
+  long long l0 = 0;
+  ProfScope(pg_plan* p_, int fam_, cudaStream_t s_, double bytes) : p(p_), fam(fam_), s(s_) {
+    p->fam_bytes[fam] += bytes;
+    l0 = launch_counter().load();
+    if (!p->prof_on) return;
+    ev0 = take();
+    if (ev0 >= 0) cudaEventRecord(p->events[ev0], s);
+  }
+  int take() {
+    if (p->next_event >= (int)p->events.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      p->events.push_back(e);
+    }
+    return p->next_event++;
+  }
+  ~ProfScope() {
+    long long l1 = launch_counter().load();
+    if (!p->prof_on || ev0 < 0) {
+      p->stats[fam].launches += l1 - l0;
+      return;
+    }
+    int ev1 = take();
+    if (ev1 < 0) return;
+    cudaEventRecord(p->events[ev1], s);
+    p->recs.push_back({fam, ev0, ev1, l1 - l0});
+  }
+};
+
+void prof_begin(pg_plan* p) {
+  p->recs.clear();
+  p->next_event = 0;
+  for (int f = 0; f < PG_N_FAMILIES; ++f) {
+    p->fam_bytes[f] = 0.0;
+    memset(&p->stats[f], 0, sizeof(pg_kernel_stat));
+    strncpy(p->stats[f].name, kFamNames[f], sizeof(p->stats[f].name) - 1);
+  }
+}
+
+// After the call's final synchronisation.
+void prof_end(pg_plan* p) {
+  for (const auto& r : p->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->events[r.ev0], p->events[r.ev1]) == cudaSuccess)
+      p->stats[r.fam].ms += ms;
+    p->stats[r.fam].launches += r.launches;
+  }
+  for (int f = 0; f < PG_N_FAMILIES; ++f) p->stats[f].bytes = p->fam_bytes[f];
+}
+
+cudaError_t ensure_gal(pg_plan* p, int64_t n) {
+  if (n <= p->cap_gal) return cudaSuccess;
+  int64_t c = std::max<int64_t>(n, 1);
+  size_t* t = &p->total;
+  PG_CUDA_TRY(p->x.ensure(8 * c, t));
+  PG_CUDA_TRY(p->y.ensure(8 * c, t));
+  PG_CUDA_TRY(p->z.ensure(8 * c, t));
+  PG_CUDA_TRY(p->gw.ensure(8 * c, t));
+  PG_CUDA_TRY(p->cell_id.ensure(4 * c, t));
+  PG_CUDA_TRY(p->perm.ensure(4 * c, t));
+  PG_CUDA_TRY(p->xs.ensure(8 * c, t));
+  PG_CUDA_TRY(p->ys.ensure(8 * c, t));
+  PG_CUDA_TRY(p->zs.ensure(8 * c, t));
+  PG_CUDA_TRY(p->ws.ensure(4 * c, t));
+  p->cap_gal = c;
+  return cudaSuccess;
+}
+
+cudaError_t ensure_pairs(pg_plan* p, int64_t np) {
+  if (np <= p->cap_pairs) return cudaSuccess;
+  int64_t c = std::max<int64_t>(np + np / 8, 1024);
+  size_t* t = &p->total;
+  PG_CUDA_TRY(p->ubin.ensure(4 * c, t));
+  PG_CUDA_TRY(p->ui.ensure(4 * c, t));
+  PG_CUDA_TRY(p->uj.ensure(4 * c, t));
+  PG_CUDA_TRY(p->umx.ensure(8 * c, t));
+  PG_CUDA_TRY(p->umy.ensure(8 * c, t));
+  PG_CUDA_TRY(p->umz.ensure(8 * c, t));
+  PG_CUDA_TRY(p->uwp.ensure(8 * c, t));
+  PG_CUDA_TRY(p->pbin.ensure(4 * c, t));
+  PG_CUDA_TRY(p->px.ensure(8 * c, t));
+  PG_CUDA_TRY(p->py.ensure(8 * c, t));
+  PG_CUDA_TRY(p->pz.ensure(8 * c, t));
+  PG_CUDA_TRY(p->pw.ensure(8 * c, t));
+  p->cap_pairs = c;
+  return cudaSuccess;
+}
+
+cudaError_t ensure_lines(pg_plan* p, int64_t nl) {
+  if (nl <= p->cap_lines) return cudaSuccess;
+  int64_t c = std::max<int64_t>(nl, 64);
+  size_t* t = &p->total;
+  PG_CUDA_TRY(p->line_y.ensure(4 * c, t));
+  PG_CUDA_TRY(p->line_bin.ensure(4 * c, t));
+  PG_CUDA_TRY(p->lines_q.ensure(8 * (size_t)c * p->N, t));
+  PG_CUDA_TRY(p->spec.ensure(csize(p) * (size_t)c * p->P, t));
+  p->cap_lines = c;
+  return cudaSuccess;
+}
+
+// Buffers whose size depends only on the plan.
+cudaError_t ensure_fixed(pg_plan* p) {
+  size_t* t = &p->total;
+  const int64_t NN = (int64_t)p->N * p->N;
+  const int64_t ncell = (int64_t)p->geom.nc * p->geom.nc * p->geom.nc;
+  const int nb = p->nbmax;
+  PG_CUDA_TRY(p->flag.ensure(64, t));
+  PG_CUDA_TRY(p->wpart.ensure(sizeof(double) * 2 * 256, t));
+  PG_CUDA_TRY(p->wsum.ensure(sizeof(double) * 2, t));
+  PG_CUDA_TRY(p->ccount.ensure(4 * (ncell + 1), t));
+  PG_CUDA_TRY(p->cstart.ensure(4 * (ncell + 1), t));
+  PG_CUDA_TRY(p->ccursor.ensure(4 * (ncell + 1), t));
+  PG_CUDA_TRY(p->ctmp.ensure(8 * scan_tmp_elems(ncell + 1, 1), t));
+  PG_CUDA_TRY(p->ctot.ensure(8, t));
+  PG_CUDA_TRY(p->dd.ensure(8 * p->nPB, t));
+  PG_CUDA_TRY(p->ddq.ensure(8 * p->nPB, t));
+  PG_CUDA_TRY(p->pcursor.ensure(8, t));
+  PG_CUDA_TRY(p->bcursor.ensure(8 * p->nPB, t));
+  PG_CUDA_TRY(p->flags.ensure((size_t)nb * NN, t));
+  PG_CUDA_TRY(p->lidx.ensure(4 * (size_t)nb * NN, t));
+  PG_CUDA_TRY(p->seg_total.ensure(8 * nb, t));
+  PG_CUDA_TRY(p->line_base.ensure(8 * nb, t));
+  PG_CUDA_TRY(p->n_lines.ensure(8, t));
+  PG_CUDA_TRY(p->stmp.ensure(8 * scan_tmp_elems(NN, nb), t));
+  PG_CUDA_TRY(p->qsum.ensure(8 * nb, t));
+  PG_CUDA_TRY(p->scale.ensure(8 * nb, t));
+  const size_t plane = csize(p) * (size_t)NN * p->P;
+  PG_CUDA_TRY(p->S.ensure(plane * nb, t));
+  PG_CUDA_TRY(p->Fg.ensure(plane, t));
+  PG_CUDA_TRY(p->Wz.ensure(csize(p) * (size_t)p->W * p->N * p->P * nb, t));
+  PG_CUDA_TRY(p->Wy.ensure(csize(p) * (size_t)p->W * p->W * p->P * nb, t));
+  PG_CUDA_TRY(p->Cwin.ensure(rsize(p) * (size_t)p->W * p->W * p->W * nb, t));
+  PG_CUDA_TRY(p->sums_pg.ensure(sizeof(double) * 2 * (size_t)p->nPB * p->nL, t));
+  PG_CUDA_TRY(p->sums_gg.ensure(sizeof(double) * 2 * (size_t)p->nL, t));
+  PG_CUDA_TRY(p->pg_valid.ensure(p->nPB, t));
+  // outputs: doubles [P*Q]*5 + [P]*6 + [Q]*4 + 4, int64 [P] + [Q] + 1
+  const size_t nd = (size_t)p->nPB * p->nQ * 5 + (size_t)p->nPB * 6 + (size_t)p->nQ * 4 + 8;
+  const size_t ni = (size_t)p->nPB + p->nQ + 2;
+  PG_CUDA_TRY(p->out.ensure(sizeof(double) * nd + sizeof(int64_t) * ni, t));
+  return cudaSuccess;
+}
+
+// Geometry of the (r, mu_r) bins over the offset window [-w, w]^3, with the
+// same FP64 comparisons as the binning definition: R2 = a^2+b^2+c^2,
+// r^2 = R2 dx^2 against squared edges, mu_r = |c|/sqrt(R2), bin =
+// min(n_mur - 1, floor(n_mur mu_r)). List Q holds the aggregate support.
+void build_cell_lists(const pg_plan* p, std::vector<int32_t>& cells, std::vector<int64_t>& off) {
+  const int w = p->w, W = p->W, nQ = p->nQ, nmur = p->prm.n_mur;
+  const double dx2 = p->dx * p->dx;
+  std::vector<double> e2(p->r_edges.size());
+  for (size_t i = 0; i < e2.size(); ++i) e2[i] = p->r_edges[i] * p->r_edges[i];
+  const double cut2 = p->prm.r_perp_cut * p->prm.r_perp_cut;
+  std::vector<std::vector<int32_t>> lists(nQ + 1);
+  for (int c = -w; c <= w; ++c)
+    for (int b = -w; b <= w; ++b)
+      for (int a = -w; a <= w; ++a) {
+        const int64_t R2 = (int64_t)a * a + (int64_t)b * b + (int64_t)c * c;
+        const double r2 = (double)R2 * dx2;
+        if (r2 < e2[0] || !(r2 < e2[p->nQ / nmur])) continue;
+        int k = 0;
+        while (k + 1 < (int)e2.size() - 1 && !(r2 < e2[k + 1])) ++k;
+        const double mu = R2 > 0 ? (double)std::abs(c) / sqrt((double)R2) : 0.0;
+        int m = (int)floor((double)nmur * mu);
+        if (m > nmur - 1) m = nmur - 1;
+        const int32_t cell = ((c + w) * W + (b + w)) * W + (a + w);
+        lists[k * nmur + m].push_back(cell);
+        if (cut2 <= 0.0 || (double)((int64_t)a * a + (int64_t)b * b) * dx2 >= cut2) lists[nQ].push_back(cell);
+      }
+  off.assign(nQ + 2, 0);
+  for (int q = 0; q <= nQ; ++q) off[q + 1] = off[q] + (int64_t)lists[q].size();
+  cells.clear();
+  cells.reserve(off[nQ + 1]);
+  for (int q = 0; q <= nQ; ++q) cells.insert(cells.end(), lists[q].begin(), lists[q].end());
+}
+
+template <typename R>
+cudaError_t build_twiddles(pg_plan* p) {
+  using C = typename CT<R>::C;
+  const int N = p->N;
+  std::vector<C> h(N);
+  for (int j = 0; j < N; ++j) {
+    const double a = 2.0 * M_PI * (double)j / (double)N;
+    h[j].x = (R)cos(a);
+    h[j].y = (R)(-sin(a));
+  }
+  // exact values at the quarter points
+  h[0].x = 1; h[0].y = 0;
+  if (N % 4 == 0) {
+    h[N / 4].x = 0; h[N / 4].y = -1;
+    h[N / 2].x = -1; h[N / 2].y = 0;
+    h[3 * N / 4].x = 0; h[3 * N / 4].y = 1;
+  }
+  PG_CUDA_TRY(p->tw.ensure(sizeof(C) * N, &p->total));
+  return cudaMemcpy(p->tw.p, h.data(), sizeof(C) * N, cudaMemcpyHostToDevice);
+}
+
+// Deposits one set of points (bins [bin0, bin0 + nb) of a bin-sorted list, or
+// one galaxy set when pbin == null) into compact lines and returns the line
+// count; leaves per-mesh scale = N^3 / Q in p->scale.
+cudaError_t deposit_batch(pg_plan* p, int64_t n, const double* x, const double* y,
+                          const double* z, const double* w, const int32_t* pbin, int bin0,
+                          int nb, int64_t* n_lines_out, cudaStream_t s) {
+  const int64_t NN = (int64_t)p->N * p->N;
+  DepGeom g{p->N, p->dx, p->prm.assign};
+  int64_t nl = 0;
+  {
+    // flags + scan + numbering: NN bytes written and read, NN int32 written
+    ProfScope ps(p, PG_FAM_DEPOSIT, s, (double)nb * NN * 6 + 32.0 * n);
+    PG_CUDA_TRY(cudaMemsetAsync(p->flags.p, 0, (size_t)nb * NN, s));
+    PG_CUDA_TRY(launch_mark_lines(g, n, x, y, z, pbin, bin0, p->flags.as<uint8_t>(), s));
+    PG_CUDA_TRY(scan_u8_i32(p->flags.as<uint8_t>(), p->lidx.as<int32_t>(), NN, nb,
+                            p->seg_total.as<int64_t>(), p->stmp.as<int64_t>(), s));
+    PG_CUDA_TRY(launch_line_bases(nb, p->seg_total.as<int64_t>(), p->line_base.as<int64_t>(),
+                                  p->n_lines.as<int64_t>(), s));
+  }
+  PG_CUDA_TRY(cudaMemcpyAsync(&nl, p->n_lines.p, 8, cudaMemcpyDeviceToHost, s));
+  PG_CUDA_TRY(cudaStreamSynchronize(s));
+  PG_CUDA_TRY(ensure_lines(p, nl));
+  {
+    ProfScope ps(p, PG_FAM_DEPOSIT, s, (double)nl * p->N * 8 + 40.0 * n * (p->prm.assign ? 8 : 1));
+    PG_CUDA_TRY(launch_line_compact(p->N, nb, p->flags.as<uint8_t>(), p->lidx.as<int32_t>(),
+                                    p->line_base.as<int64_t>(), p->line_y.as<int32_t>(),
+                                    p->line_bin.as<int32_t>(), s));
+    PG_CUDA_TRY(cudaMemsetAsync(p->lines_q.p, 0, (size_t)nl * p->N * 8, s));
+    PG_CUDA_TRY(cudaMemsetAsync(p->qsum.p, 0, 8 * (size_t)nb, s));
+    PG_CUDA_TRY(launch_deposit_lines(g, n, x, y, z, w, pbin, bin0, p->lidx.as<int32_t>(),
+                                     p->line_base.as<int64_t>(),
+                                     p->lines_q.as<unsigned long long>(),
+                                     p->qsum.as<unsigned long long>(), s));
+    PG_CUDA_TRY(launch_field_scale(nb, p->qsum.as<unsigned long long>(), p->N, p->scale.as<double>(), s));
+  }
+  *n_lines_out = nl;
+  return cudaSuccess;
+}
+
+// Spectrum of deposited lines: x pass then y pass into S (nb meshes).
+template <typename R>
+cudaError_t lines_to_S(pg_plan* p, int nb, int64_t nl, typename CT<R>::C* S, int64_t S_stride,
+                       cudaStream_t s) {
+  using C = typename CT<R>::C;
+  const C* tw = p->tw.as<C>();
+  const double cs = (double)sizeof(C), M1 = p->M1, N = p->N;
+  {
+    ProfScope ps(p, PG_FAM_FFT_X_R2C, s, (double)nl * (N * 8.0 + M1 * cs));
+    PG_CUDA_TRY(FftPasses<R>::x_r2c_lines(p->N, p->lines_q.as<int64_t>(), p->line_bin.as<int32_t>(),
+                                          p->scale.as<double>(), nl, p->spec.as<C>(), p->P, tw, s));
+  }
+  ProfScope ps(p, PG_FAM_FFT_Y_FWD, s, (double)nl * M1 * cs + (double)nb * N * N * M1 * cs);
+  return FftPasses<R>::y_fwd(p->N, nb, p->spec.as<C>(), p->P, p->lidx.as<int32_t>(),
+                             p->seg_total.as<int64_t>(), p->line_base.as<int64_t>(),
+                             p->line_y.as<int32_t>(), S, S_stride, tw, s);
+}
+
+// Correlation window of nb meshes against Fg (or Fg with itself) and its bin
+// sums into `sums` ([nb][nL][2]).
+template <typename R>
+cudaError_t correlate_window(pg_plan* p, int nb, bool gg, double* sums, cudaStream_t s) {
+  using C = typename CT<R>::C;
+  const C* tw = p->tw.as<C>();
+  const int64_t S_stride = (int64_t)p->N * p->N * p->P;
+  const int64_t Wz_stride = (int64_t)p->W * p->N * p->P;
+  const int64_t Wy_stride = (int64_t)p->W * p->W * p->P;
+  const int64_t Cw_stride = (int64_t)p->W * p->W * p->W;
+  const double inv_n3 = 1.0 / ((double)p->N * p->N * p->N);
+  const double cs = (double)sizeof(C), M1 = p->M1, N = p->N, W = p->W;
+  {
+    // reads each mesh's spectrum once and F_g once (later meshes of the batch
+    // find F_g in L2); writes the z window of each mesh
+    ProfScope ps(p, PG_FAM_FFT_Z_CORR, s,
+                 (gg ? 0.0 : nb * N * N * M1 * cs) + N * N * M1 * cs + nb * W * N * M1 * cs);
+    PG_CUDA_TRY(FftPasses<R>::z_corr(p->N, nb, p->S.as<C>(), S_stride, p->Fg.as<C>(), gg, p->w,
+                                     p->Wz.as<C>(), Wz_stride, p->P, tw, s));
+  }
+  {
+    ProfScope ps(p, PG_FAM_FFT_Y_INV, s, nb * (W * N * M1 * cs + W * W * M1 * cs));
+    PG_CUDA_TRY(FftPasses<R>::y_inv_win(p->N, nb, p->Wz.as<C>(), Wz_stride, p->w, p->Wy.as<C>(),
+                                        Wy_stride, p->P, tw, s));
+  }
+  {
+    ProfScope ps(p, PG_FAM_FFT_X_C2R, s, nb * (W * W * M1 * cs + W * W * W * (double)sizeof(R)));
+    PG_CUDA_TRY(FftPasses<R>::x_c2r_win(p->N, nb, p->Wy.as<C>(), Wy_stride, p->w, p->Cwin.as<R>(),
+                                        Cw_stride, p->P, inv_n3, tw, s));
+  }
+  ProfScope ps(p, PG_FAM_BIN, s, nb * (double)p->n_cells_listed * (4.0 + (double)sizeof(R)));
+  return launch_bin_sums<R>(nb, p->nL, p->Cwin.as<R>(), Cw_stride, p->cells.as<int32_t>(),
+                            p->list_off.as<int64_t>(), sums, s);
+}
+
+// Galaxy spectrum into Fg from points (SoA), then the galaxy window sums.
+template <typename R>
+cudaError_t galaxy_pass(pg_plan* p, int64_t n, const double* x, const double* y, const double* z,
+                        const double* w, bool do_gg, cudaStream_t s) {
+  using C = typename CT<R>::C;
+  int64_t nl = 0;
+  PG_CUDA_TRY(deposit_batch(p, n, x, y, z, w, nullptr, 0, 1, &nl, s));
+  PG_CUDA_TRY(lines_to_S<R>(p, 1, nl, p->Fg.as<C>(), 0, s));
+  {
+    ProfScope ps(p, PG_FAM_FFT_Z_FWD, s, 2.0 * p->N * p->N * p->M1 * (double)sizeof(C));
+    PG_CUDA_TRY(FftPasses<R>::z_fwd(p->N, p->Fg.as<C>(), p->P, p->tw.as<C>(), s));
+  }
+  if (do_gg) PG_CUDA_TRY(correlate_window<R>(p, 1, true, p->sums_gg.as<double>(), s));
+  return cudaSuccess;
+}
+
+struct OutPtrs {
+  double *dd_w, *xi_ss, *xi_pg, *xi_gg, *b_pg, *q_eff, *q_eff_sq, *xi_dw, *b_pg_agg, *q_eff_agg,
+      *xi_dw_agg, *sum_pg, *sum_pg_agg, *sum_gg, *sum2_gg, *sum_gg_agg;
+  int64_t *dd, *n_cells, *n_cells_agg;
+};
+
+OutPtrs out_layout(pg_plan* p) {
+  const size_t PQ = (size_t)p->nPB * p->nQ, P = p->nPB, Q = p->nQ;
+  double* d = p->out.as<double>();
+  OutPtrs o;
+  o.xi_pg = d; d += PQ;
+  o.b_pg = d; d += PQ;
+  o.q_eff = d; d += PQ;
+  o.q_eff_sq = d; d += PQ;
+  o.sum_pg = d; d += PQ;
+  o.dd_w = d; d += P;
+  o.xi_ss = d; d += P;
+  o.b_pg_agg = d; d += P;
+  o.q_eff_agg = d; d += P;
+  o.sum_pg_agg = d; d += P;
+  d += P;
+  o.xi_gg = d; d += Q;
+  o.xi_dw = d; d += Q;
+  o.sum_gg = d; d += Q;
+  o.sum2_gg = d; d += Q;
+  o.xi_dw_agg = d; d += 1;
+  o.sum_gg_agg = d; d += 2;
+  d += 5;
+  int64_t* i = reinterpret_cast<int64_t*>(d);
+  o.dd = i; i += P;
+  o.n_cells = i; i += Q;
+  o.n_cells_agg = i;
+  return o;
+}
+
+cudaError_t copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (!dst) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+}
+
+// a1-a3 on device positions; leaves the bin-sorted pair list in p->p*, counts
+// in p->dd / p->ddq and the host copy of the counts in hdd.
+cudaError_t positions_and_pairs(pg_plan* p, int64_t n, const double* d_pos, const float* d_vel,
+                                const float* d_w, std::vector<unsigned long long>& hdd,
+                                int64_t* np_out, int* nonfinite, cudaStream_t s) {
+  PG_CUDA_TRY(ensure_gal(p, n));
+  {
+    ProfScope ps(p, PG_FAM_POSITIONS, s, 24.0 * n * 2 + (d_vel ? 12.0 * n : 0.0) + (d_w ? 4.0 * n : 0.0));
+    PG_CUDA_TRY(cudaMemsetAsync(p->flag.p, 0, 4, s));
+    PG_CUDA_TRY(launch_check_finite(n, d_pos, p->flag.as<int32_t>(), s));
+    PG_CUDA_TRY(launch_transform(n, p->prm.box_L, p->prm.rsd_factor, d_pos, d_vel, nullptr,
+                                 p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), s));
+    PG_CUDA_TRY(launch_wsum(n, d_w, p->wpart.as<double>(), p->wsum.as<double>(), s));
+  }
+  CellList cl{p->cell_id.as<int32_t>(), p->ccount.as<int32_t>(), p->cstart.as<int32_t>(),
+              p->ccursor.as<int32_t>(), p->perm.as<int32_t>(), p->xs.as<double>(),
+              p->ys.as<double>(), p->zs.as<double>(), p->ws.as<float>(), p->ctmp.as<int64_t>(),
+              p->ctot.as<int64_t>()};
+  {
+    ProfScope ps(p, PG_FAM_CELLS, s, 24.0 * n * 2 + 16.0 * n);
+    PG_CUDA_TRY(launch_cells(p->geom, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(),
+                             d_w, cl, s));
+  }
+  PG_CUDA_TRY(cudaMemsetAsync(p->dd.p, 0, 8 * p->nPB, s));
+  PG_CUDA_TRY(cudaMemsetAsync(p->ddq.p, 0, 8 * p->nPB, s));
+  PairOut po{};
+  po.dd = p->dd.as<unsigned long long>();
+  po.ddq = p->ddq.as<unsigned long long>();
+  {
+    ProfScope ps(p, PG_FAM_PAIRS, s, 28.0 * n);
+    PG_CUDA_TRY(launch_pairs(p->geom, n, cl, d_w != nullptr, false, po, s));
+  }
+  hdd.assign(p->nPB, 0ull);
+  int32_t hflag = 0;
+  PG_CUDA_TRY(cudaMemcpyAsync(hdd.data(), p->dd.p, 8 * p->nPB, cudaMemcpyDeviceToHost, s));
+  PG_CUDA_TRY(cudaMemcpyAsync(&hflag, p->flag.p, 4, cudaMemcpyDeviceToHost, s));
+  PG_CUDA_TRY(cudaStreamSynchronize(s));
+  *nonfinite = hflag;
+  int64_t np = 0;
+  for (auto v : hdd) np += (int64_t)v;
+  *np_out = np;
+  PG_CUDA_TRY(ensure_pairs(p, np));
+  PG_CUDA_TRY(cudaMemsetAsync(p->pcursor.p, 0, 8, s));
+  po.cursor = p->pcursor.as<unsigned long long>();
+  po.capacity = p->cap_pairs;
+  po.bin = p->ubin.as<int32_t>(); po.i = p->ui.as<int32_t>(); po.j = p->uj.as<int32_t>();
+  po.mx = p->umx.as<double>(); po.my = p->umy.as<double>(); po.mz = p->umz.as<double>();
+  po.wp = p->uwp.as<double>();
+  ProfScope ps(p, PG_FAM_PAIRS, s, 28.0 * n + 2.0 * 44.0 * np);
+  PG_CUDA_TRY(launch_pairs(p->geom, n, cl, d_w != nullptr, true, po, s));
+  std::vector<unsigned long long> off(p->nPB, 0ull);
+  for (int b = 1; b < p->nPB; ++b) off[b] = off[b - 1] + hdd[b - 1];
+  PG_CUDA_TRY(cudaMemcpyAsync(p->bcursor.p, off.data(), 8 * p->nPB, cudaMemcpyHostToDevice, s));
+  PG_CUDA_TRY(launch_pair_scatter(np, po, p->bcursor.as<unsigned long long>(), p->pbin.as<int32_t>(),
+                                  nullptr, nullptr, nullptr, p->px.as<double>(), p->py.as<double>(),
+                                  p->pz.as<double>(), p->pw.as<double>(), s));
+  // the scatter reads the host offsets before this function's vector dies
+  return cudaStreamSynchronize(s);
+}
+
+template <typename R>
+pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* d_vel,
+                       const float* d_w, pg_result* out, cudaStream_t s) {
+  std::vector<unsigned long long> hdd;
+  int64_t np = 0;
+  int nonfinite = 0;
+  prof_begin(p);
+  const long long launches0 = launch_counter().load();
+  PG_TRY(positions_and_pairs(p, n, d_pos, d_vel, d_w, hdd, &np, &nonfinite, s));
+  if (nonfinite) return PG_ERR_INVALID_ARG;
+  // galaxy weights widened to FP64 for the deposit
+  const double* gw = nullptr;
+  if (d_w) {
+    PG_TRY(launch_widen_f32(n, d_w, p->gw.as<double>(), s));
+    gw = p->gw.as<double>();
+  }
+  const bool have_gal = n > 0;
+  if (have_gal) {
+    PG_TRY((galaxy_pass<R>(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, true, s)));
+  }
+  std::vector<unsigned char> valid(p->nPB, 0);
+  for (int b = 0; b < p->nPB; ++b) valid[b] = (have_gal && hdd[b] > 0) ? 1 : 0;
+  PG_TRY(cudaMemcpyAsync(p->pg_valid.p, valid.data(), p->nPB, cudaMemcpyHostToDevice, s));
+  // pair bins in batches of contiguous bin ranges
+  std::vector<int64_t> off(p->nPB + 1, 0);
+  for (int b = 0; b < p->nPB; ++b) off[b + 1] = off[b] + (int64_t)hdd[b];
+  using C = typename CT<R>::C;
+  const int64_t S_stride = (int64_t)p->N * p->N * p->P;
+  int b0 = 0;
+  while (have_gal && b0 < p->nPB) {
+    while (b0 < p->nPB && hdd[b0] == 0) ++b0;
+    if (b0 >= p->nPB) break;
+    int b1 = std::min(p->nPB, b0 + p->nbmax);
+    const int nb = b1 - b0;
+    const int64_t pn = off[b1] - off[b0];
+    int64_t nl = 0;
+    PG_TRY(deposit_batch(p, pn, p->px.as<double>() + off[b0], p->py.as<double>() + off[b0],
+                         p->pz.as<double>() + off[b0], p->pw.as<double>() + off[b0],
+                         p->pbin.as<int32_t>() + off[b0], b0, nb, &nl, s));
+    PG_TRY(lines_to_S<R>(p, nb, nl, p->S.as<C>(), S_stride, s));
+    PG_TRY(correlate_window<R>(p, nb, false, p->sums_pg.as<double>() + (size_t)b0 * p->nL * 2, s));
+    b0 = b1;
+  }
+  // ratios
+  OutPtrs o = out_layout(p);
+  RatioArgs ra{};
+  ra.P = p->nPB; ra.Q = p->nQ; ra.n_mu = p->prm.n_mu;
+  ra.s_edges = p->s_edges_d.as<double>();
+  ra.L = p->prm.box_L;
+  ra.dd = p->dd.as<unsigned long long>();
+  ra.ddq = p->ddq.as<unsigned long long>();
+  ra.wsum = p->wsum.as<double>();
+  ra.sum_pg = p->sums_pg.as<double>();
+  ra.pg_valid = p->pg_valid.as<unsigned char>();
+  ra.sum_gg = p->sums_gg.as<double>();
+  ra.gg_valid = have_gal ? 1 : 0;
+  ra.list_off = p->list_off.as<int64_t>();
+  ra.dd_w = o.dd_w; ra.xi_ss = o.xi_ss; ra.xi_pg = o.xi_pg; ra.xi_gg = o.xi_gg; ra.b_pg = o.b_pg;
+  ra.q_eff = o.q_eff; ra.q_eff_sq = o.q_eff_sq; ra.xi_dw = o.xi_dw; ra.b_pg_agg = o.b_pg_agg;
+  ra.q_eff_agg = o.q_eff_agg; ra.xi_dw_agg = o.xi_dw_agg; ra.o_sum_pg = o.sum_pg;
+  ra.o_sum_pg_agg = o.sum_pg_agg; ra.o_sum_gg = o.sum_gg; ra.o_sum2_gg = o.sum2_gg;
+  ra.o_sum_gg_agg = o.sum_gg_agg; ra.o_dd = o.dd; ra.n_cells = o.n_cells;
+  ra.n_cells_agg = o.n_cells_agg;
+  {
+    ProfScope ps(p, PG_FAM_RATIOS, s, 0.0);
+    PG_TRY(launch_ratios(ra, s));
+  }
+  if (out) {
+    const size_t PQ = sizeof(double) * p->nPB * p->nQ, Pd = sizeof(double) * p->nPB,
+                 Qd = sizeof(double) * p->nQ;
+    PG_TRY(copy_out(out->dd, o.dd, 8 * p->nPB, s));
+    PG_TRY(copy_out(out->dd_w, o.dd_w, Pd, s));
+    PG_TRY(copy_out(out->xi_ss, o.xi_ss, Pd, s));
+    PG_TRY(copy_out(out->xi_pg, o.xi_pg, PQ, s));
+    PG_TRY(copy_out(out->xi_gg, o.xi_gg, Qd, s));
+    PG_TRY(copy_out(out->b_pg, o.b_pg, PQ, s));
+    PG_TRY(copy_out(out->q_eff, o.q_eff, PQ, s));
+    PG_TRY(copy_out(out->q_eff_sq, o.q_eff_sq, PQ, s));
+    PG_TRY(copy_out(out->xi_dw, o.xi_dw, Qd, s));
+    PG_TRY(copy_out(out->b_pg_agg, o.b_pg_agg, Pd, s));
+    PG_TRY(copy_out(out->q_eff_agg, o.q_eff_agg, Pd, s));
+    PG_TRY(copy_out(out->xi_dw_agg, o.xi_dw_agg, 8, s));
+    PG_TRY(copy_out(out->n_cells, o.n_cells, 8 * p->nQ, s));
+    PG_TRY(copy_out(out->n_cells_agg, o.n_cells_agg, 8, s));
+    PG_TRY(copy_out(out->sum_pg, o.sum_pg, PQ, s));
+    PG_TRY(copy_out(out->sum_pg_agg, o.sum_pg_agg, Pd, s));
+    PG_TRY(copy_out(out->sum_gg, o.sum_gg, Qd, s));
+    PG_TRY(copy_out(out->sum2_gg, o.sum2_gg, Qd, s));
+    PG_TRY(copy_out(out->sum_gg_agg, o.sum_gg_agg, 16, s));
+  }
+  PG_TRY(cudaStreamSynchronize(s));
+  p->last_launches = launch_counter().load() - launches0;
+  if (p->prof_on) prof_end(p);
+  else
+    for (int f = 0; f < PG_N_FAMILIES; ++f) p->stats[f].bytes = p->fam_bytes[f];
+  return PG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* pg_status_string(pg_status s) {
+  switch (s) {
+    case PG_OK: return "ok";
+    case PG_ERR_INVALID_ARG: return "invalid argument";
+    case PG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case PG_ERR_OOM: return "device out of memory";
+    case PG_ERR_CUDA: return "CUDA error";
+    case PG_ERR_TIMEOUT: return "device wait timed out";
+    case PG_ERR_UNIMPLEMENTED: return "not implemented";
+    case PG_ERR_CAPACITY: return "output buffer too small";
+  }
+  return "unknown status";
+}
+
+pg_status pg_plan_create(const pg_params* prm, pg_plan** out) {
+  if (!prm || !out) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  const pg_params& q = *prm;
+  if (!(q.box_L > 0.0) || !isfinite(q.box_L)) return PG_ERR_INVALID_ARG;
+  if (q.n_s < 1 || q.n_s > 64 || q.n_mu < 1 || q.n_mu > 64 || q.n_r < 1 || q.n_r > 64 ||
+      q.n_mur < 1 || q.n_mur > 64 || !q.s_edges || !q.r_edges)
+    return PG_ERR_INVALID_ARG;
+  if (q.assign != 0 && q.assign != 1) return PG_ERR_INVALID_ARG;
+  if (q.precision != 0 && q.precision != 1) return PG_ERR_INVALID_ARG;
+  if (!is_pow2(q.mesh_n) || q.mesh_n < 32 || q.mesh_n > 1024) return PG_ERR_UNSUPPORTED;
+  for (int i = 0; i < q.n_s; ++i)
+    if (!(q.s_edges[i] < q.s_edges[i + 1]) || !(q.s_edges[0] >= 0.0)) return PG_ERR_INVALID_ARG;
+  for (int i = 0; i < q.n_r; ++i)
+    if (!(q.r_edges[i] < q.r_edges[i + 1]) || !(q.r_edges[0] >= 0.0)) return PG_ERR_INVALID_ARG;
+  if (!(q.s_edges[q.n_s] < 0.5 * q.box_L) || !(q.r_edges[q.n_r] < 0.5 * q.box_L))
+    return PG_ERR_INVALID_ARG;
+  if (!isfinite(q.rsd_factor) || !(q.r_perp_cut >= 0.0)) return PG_ERR_INVALID_ARG;
+  pg_plan* p = new (std::nothrow) pg_plan();
+  if (!p) return PG_ERR_OOM;
+  p->prm = q;
+  p->s_edges.assign(q.s_edges, q.s_edges + q.n_s + 1);
+  p->r_edges.assign(q.r_edges, q.r_edges + q.n_r + 1);
+  p->prm.s_edges = p->s_edges.data();
+  p->prm.r_edges = p->r_edges.data();
+  cudaGetDevice(&p->device);
+  p->N = q.mesh_n;
+  p->M1 = p->N / 2 + 1;
+  p->P = p->N / 2 + 2;
+  p->dx = q.box_L / (double)q.mesh_n;
+  const double r_max = q.r_edges[q.n_r];
+  p->w = (int)ceil(r_max / p->dx);
+  p->W = 2 * p->w + 1;
+  if (p->W > p->N || p->w >= p->N / 2) { delete p; return PG_ERR_INVALID_ARG; }
+  p->nPB = q.n_s * q.n_mu;
+  p->nQ = q.n_r * q.n_mur;
+  p->nL = p->nQ + 1;
+  const double plane = (double)(q.precision ? 16 : 8) * p->N * p->N * p->P;
+  int nb = q.bins_per_batch;
+  if (nb <= 0) nb = (int)std::max(1.0, std::min(16.0, 72e9 / plane));
+  if (q.precision == 1 && q.bins_per_batch <= 0) nb = 1;
+  p->nbmax = std::min(nb, std::min(p->nPB, 64));
+  // cell list for pairs: cells of side >= s_max (slightly larger, for rounding)
+  PairGeom& g = p->geom;
+  memset(&g, 0, sizeof(g));
+  g.L = q.box_L;
+  g.halfL = 0.5 * q.box_L;
+  const double smax = q.s_edges[q.n_s];
+  int nc = (int)floor(q.box_L / (smax * (1.0 + 1e-9)));
+  if (nc > 256) nc = 256;
+  if (nc < 3) nc = 1;
+  g.nc = nc;
+  g.cell_scale = (double)nc / q.box_L;
+  g.n_s = q.n_s;
+  g.n_mu = q.n_mu;
+  for (int i = 0; i <= q.n_s; ++i) g.e2[i] = q.s_edges[i] * q.s_edges[i];
+  cudaError_t e = q.precision ? build_twiddles<double>(p) : build_twiddles<float>(p);
+  std::vector<int32_t> cells;
+  build_cell_lists(p, cells, p->h_list_off);
+  p->n_cells_listed = (int64_t)cells.size();
+  if (e == cudaSuccess) e = p->cells.ensure(4 * std::max<size_t>(cells.size(), 1), &p->total);
+  if (e == cudaSuccess && !cells.empty())
+    e = cudaMemcpy(p->cells.p, cells.data(), 4 * cells.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = p->list_off.ensure(8 * p->h_list_off.size(), &p->total);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->list_off.p, p->h_list_off.data(), 8 * p->h_list_off.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = p->s_edges_d.ensure(8 * p->s_edges.size(), &p->total);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->s_edges_d.p, p->s_edges.data(), 8 * p->s_edges.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = ensure_fixed(p);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    pg_plan_destroy(p);
+    return from_cuda(e);
+  }
+  *out = p;
+  return PG_OK;
+}
+
+void pg_plan_destroy(pg_plan* p) {
+  if (!p) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  DevBuf* all[] = {&p->tw, &p->cells, &p->list_off, &p->s_edges_d, &p->in_pos, &p->in_vel, &p->in_w,
+                   &p->x, &p->y, &p->z, &p->gw, &p->flag, &p->wpart, &p->wsum, &p->cell_id, &p->ccount,
+                   &p->cstart, &p->ccursor, &p->perm, &p->xs, &p->ys, &p->zs, &p->ws, &p->ctmp,
+                   &p->ctot, &p->dd, &p->ddq, &p->pcursor, &p->ubin, &p->ui, &p->uj, &p->umx,
+                   &p->umy, &p->umz, &p->uwp, &p->pbin, &p->px, &p->py, &p->pz, &p->pw,
+                   &p->bcursor, &p->flags, &p->lidx, &p->seg_total, &p->line_base, &p->n_lines,
+                   &p->stmp, &p->line_y, &p->line_bin, &p->lines_q, &p->qsum, &p->scale, &p->spec,
+                   &p->S, &p->Fg, &p->Wz, &p->Wy, &p->Cwin, &p->sums_pg, &p->sums_gg,
+                   &p->pg_valid, &p->tmpfft, &p->out};
+  for (DevBuf* b : all) b->release(&p->total);
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  cudaSetDevice(cur);
+  delete p;
+}
+
+pg_status pg_plan_reserve(pg_plan* p, int64_t n_gal_max, int64_t n_pairs_max) {
+  if (!p || n_gal_max < 0 || n_pairs_max < 0) return PG_ERR_INVALID_ARG;
+  PG_TRY(ensure_gal(p, n_gal_max));
+  PG_TRY(ensure_pairs(p, n_pairs_max));
+  const int64_t NN = (int64_t)p->N * p->N;
+  const int64_t per = p->prm.assign ? 4 : 1;
+  PG_TRY(ensure_lines(p, std::min<int64_t>(NN * p->nbmax, std::max(per * n_gal_max, per * n_pairs_max))));
+  return PG_OK;
+}
+
+size_t pg_workspace_bytes(const pg_plan* p) { return p ? p->total : 0; }
+
+pg_status pg_plan_set_profiling(pg_plan* p, int32_t enable) {
+  if (!p) return PG_ERR_INVALID_ARG;
+  p->prof_on = enable != 0;
+  return PG_OK;
+}
+
+pg_status pg_plan_last_stats(const pg_plan* p, pg_kernel_stat* out, int64_t* total_launches) {
+  if (!p) return PG_ERR_INVALID_ARG;
+  if (out) memcpy(out, p->stats, sizeof(p->stats));
+  if (total_launches) *total_launches = p->last_launches;
+  return PG_OK;
+}
+
+pg_status pg_forward(pg_plan* p, int64_t n, const double* d_pos, const float* d_vel,
+                     const float* d_w, pg_result* out, void* stream) {
+  if (!p || n < 0 || (n > 0 && !d_pos)) return PG_ERR_INVALID_ARG;
+  if (p->prm.rsd_factor != 0.0 && n > 0 && !d_vel) return PG_ERR_INVALID_ARG;
+  if (n > INT32_MAX / 2) return PG_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return p->prm.precision ? forward_impl<double>(p, n, d_pos, d_vel, d_w, out, s)
+                          : forward_impl<float>(p, n, d_pos, d_vel, d_w, out, s);
+}
+
+pg_status pg_forward_host(pg_plan* p, int64_t n, const double* h_pos, const float* h_vel,
+                          const float* h_w, pg_result* out, void* stream) {
+  if (!p || n < 0 || (n > 0 && !h_pos)) return PG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t c = (size_t)std::max<int64_t>(n, 1);
+  PG_TRY(p->in_pos.ensure(24 * c, &p->total));
+  if (n > 0) PG_TRY(cudaMemcpyAsync(p->in_pos.p, h_pos, 24 * (size_t)n, cudaMemcpyHostToDevice, s));
+  const float* dv = nullptr;
+  const float* dw = nullptr;
+  if (h_vel) {
+    PG_TRY(p->in_vel.ensure(12 * c, &p->total));
+    if (n > 0) PG_TRY(cudaMemcpyAsync(p->in_vel.p, h_vel, 12 * (size_t)n, cudaMemcpyHostToDevice, s));
+    dv = p->in_vel.as<float>();
+  }
+  if (h_w) {
+    PG_TRY(p->in_w.ensure(4 * c, &p->total));
+    if (n > 0) PG_TRY(cudaMemcpyAsync(p->in_w.p, h_w, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    dw = p->in_w.as<float>();
+  }
+  return pg_forward(p, n, p->in_pos.as<double>(), dv, dw, out, stream);
+}
+
+pg_status pg_transform_positions(int64_t n, double L, double rsd, const double* d_in,
+                                 const float* d_vel, double* d_out, void* stream) {
+  if (n < 0 || !(L > 0.0) || (n > 0 && (!d_in || !d_out))) return PG_ERR_INVALID_ARG;
+  if (rsd != 0.0 && n > 0 && !d_vel) return PG_ERR_INVALID_ARG;
+  PG_TRY(launch_transform(n, L, rsd, d_in, d_vel, d_out, nullptr, nullptr, nullptr,
+                          static_cast<cudaStream_t>(stream)));
+  return PG_OK;
+}
+
+pg_status pg_find_pairs(pg_plan* p, int64_t n, const double* d_pos, const float* d_w,
+                        int64_t* d_dd, int64_t* d_ddq, int64_t capacity, int32_t* d_bin,
+                        int32_t* d_i, int32_t* d_j, double* d_mid, double* d_wp,
+                        int64_t* h_n_pairs, void* stream) {
+  if (!p || n < 0 || (n > 0 && !d_pos) || capacity < 0) return PG_ERR_INVALID_ARG;
+  if (capacity > 0 && (!d_bin || !d_i || !d_j || !d_mid || !d_wp)) return PG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PG_TRY(ensure_gal(p, n));
+  // positions are taken as given (already wrapped); split them to SoA
+  PG_TRY(launch_transform(n, p->prm.box_L, 0.0, d_pos, nullptr, nullptr, p->x.as<double>(),
+                          p->y.as<double>(), p->z.as<double>(), s));
+  CellList cl{p->cell_id.as<int32_t>(), p->ccount.as<int32_t>(), p->cstart.as<int32_t>(),
+              p->ccursor.as<int32_t>(), p->perm.as<int32_t>(), p->xs.as<double>(),
+              p->ys.as<double>(), p->zs.as<double>(), p->ws.as<float>(), p->ctmp.as<int64_t>(),
+              p->ctot.as<int64_t>()};
+  PG_TRY(launch_cells(p->geom, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), d_w, cl, s));
+  PG_TRY(cudaMemsetAsync(p->dd.p, 0, 8 * p->nPB, s));
+  PG_TRY(cudaMemsetAsync(p->ddq.p, 0, 8 * p->nPB, s));
+  PairOut po{};
+  po.dd = p->dd.as<unsigned long long>();
+  po.ddq = p->ddq.as<unsigned long long>();
+  PG_TRY(launch_pairs(p->geom, n, cl, d_w != nullptr, false, po, s));
+  std::vector<unsigned long long> hdd(p->nPB);
+  PG_TRY(cudaMemcpyAsync(hdd.data(), p->dd.p, 8 * p->nPB, cudaMemcpyDeviceToHost, s));
+  if (d_dd) PG_TRY(cudaMemcpyAsync(d_dd, p->dd.p, 8 * p->nPB, cudaMemcpyDeviceToDevice, s));
+  if (d_ddq) PG_TRY(cudaMemcpyAsync(d_ddq, p->ddq.p, 8 * p->nPB, cudaMemcpyDeviceToDevice, s));
+  PG_TRY(cudaStreamSynchronize(s));
+  int64_t np = 0;
+  for (auto v : hdd) np += (int64_t)v;
+  if (h_n_pairs) *h_n_pairs = np;
+  if (capacity == 0) return PG_OK;
+  if (np > capacity) return PG_ERR_CAPACITY;
+  PG_TRY(ensure_pairs(p, np));
+  PG_TRY(cudaMemsetAsync(p->pcursor.p, 0, 8, s));
+  po.cursor = p->pcursor.as<unsigned long long>();
+  po.capacity = p->cap_pairs;
+  po.bin = p->ubin.as<int32_t>(); po.i = p->ui.as<int32_t>(); po.j = p->uj.as<int32_t>();
+  po.mx = p->umx.as<double>(); po.my = p->umy.as<double>(); po.mz = p->umz.as<double>();
+  po.wp = p->uwp.as<double>();
+  PG_TRY(launch_pairs(p->geom, n, cl, d_w != nullptr, true, po, s));
+  std::vector<unsigned long long> off(p->nPB, 0ull);
+  for (int b = 1; b < p->nPB; ++b) off[b] = off[b - 1] + hdd[b - 1];
+  PG_TRY(cudaMemcpyAsync(p->bcursor.p, off.data(), 8 * p->nPB, cudaMemcpyHostToDevice, s));
+  PG_TRY(launch_pair_scatter(np, po, p->bcursor.as<unsigned long long>(), d_bin, d_i, d_j, d_mid,
+                             nullptr, nullptr, nullptr, d_wp, s));
+  PG_TRY(cudaStreamSynchronize(s));
+  return PG_OK;
+}
+
+pg_status pg_deposit_dense(int64_t n, const double* d_pts, const double* d_w, double L,
+                           int32_t N, int32_t assign, int64_t* d_mesh, void* stream) {
+  if (n < 0 || !(L > 0.0) || N < 1 || N > 4096 || (assign != 0 && assign != 1) || !d_mesh ||
+      (n > 0 && !d_pts))
+    return PG_ERR_INVALID_ARG;
+  DepGeom g{N, L / (double)N, assign};
+  PG_TRY(launch_deposit_dense(g, n, d_pts, d_w, reinterpret_cast<unsigned long long*>(d_mesh),
+                              static_cast<cudaStream_t>(stream)));
+  return PG_OK;
+}
+
+pg_status pg_fft_r2c_3d(pg_plan* p, const void* d_in, void* d_out, void* stream) {
+  if (!p || !d_in || !d_out) return PG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int N = p->N, P = N / 2 + 1;
+  if (p->prm.precision) {
+    using C = double2;
+    PG_TRY(FftPasses<double>::x_r2c_dense(N, (const double*)d_in, (C*)d_out, P, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<double>::y_fwd(N, 1, (C*)d_out, P, nullptr, nullptr, nullptr, nullptr, (C*)d_out, 0, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<double>::z_fwd(N, (C*)d_out, P, p->tw.as<C>(), s));
+  } else {
+    using C = float2;
+    PG_TRY(FftPasses<float>::x_r2c_dense(N, (const float*)d_in, (C*)d_out, P, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<float>::y_fwd(N, 1, (C*)d_out, P, nullptr, nullptr, nullptr, nullptr, (C*)d_out, 0, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<float>::z_fwd(N, (C*)d_out, P, p->tw.as<C>(), s));
+  }
+  return PG_OK;
+}
+
+pg_status pg_fft_c2r_3d(pg_plan* p, const void* d_in, void* d_out, void* stream) {
+  if (!p || !d_in || !d_out) return PG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int N = p->N, P = N / 2 + 1;
+  const size_t bytes = csize(p) * (size_t)N * N * P;
+  PG_TRY(p->tmpfft.ensure(bytes, &p->total));
+  PG_TRY(cudaMemcpyAsync(p->tmpfft.p, d_in, bytes, cudaMemcpyDeviceToDevice, s));
+  if (p->prm.precision) {
+    using C = double2;
+    C* t = p->tmpfft.as<C>();
+    PG_TRY(FftPasses<double>::z_inv_full(N, t, P, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<double>::y_inv_full(N, t, P, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<double>::x_c2r_full(N, t, P, (double*)d_out, p->tw.as<C>(), s));
+  } else {
+    using C = float2;
+    C* t = p->tmpfft.as<C>();
+    PG_TRY(FftPasses<float>::z_inv_full(N, t, P, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<float>::y_inv_full(N, t, P, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<float>::x_c2r_full(N, t, P, (float*)d_out, p->tw.as<C>(), s));
+  }
+  return PG_OK;
+}
+
+pg_status pg_correlate_points(pg_plan* p, int64_t n_a, const double* d_a, const double* d_wa,
+                              int64_t n_b, const double* d_b, const double* d_wb, double* h_sum,
+                              double* h_sum2, double* h_agg, int64_t* h_ncells, void* stream) {
+  if (!p || n_a <= 0 || n_b <= 0 || !d_a || !d_b) return PG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t nmax = std::max(n_a, n_b);
+  PG_TRY(ensure_gal(p, nmax));
+  // set b -> Fg; set a -> one "pair" mesh in S[0]
+  PG_TRY(launch_transform(n_b, p->prm.box_L, 0.0, d_b, nullptr, nullptr, p->x.as<double>(),
+                          p->y.as<double>(), p->z.as<double>(), s));
+  pg_status st = PG_OK;
+  auto run = [&](auto tag) -> cudaError_t {
+    using R = decltype(tag);
+    using C = typename CT<R>::C;
+    PG_CUDA_TRY((galaxy_pass<R>(p, n_b, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), d_wb, false, s)));
+    PG_CUDA_TRY(launch_transform(n_a, p->prm.box_L, 0.0, d_a, nullptr, nullptr, p->xs.as<double>(),
+                                 p->ys.as<double>(), p->zs.as<double>(), s));
+    int64_t nl = 0;
+    PG_CUDA_TRY(deposit_batch(p, n_a, p->xs.as<double>(), p->ys.as<double>(), p->zs.as<double>(),
+                              d_wa, nullptr, 0, 1, &nl, s));
+    PG_CUDA_TRY(lines_to_S<R>(p, 1, nl, p->S.as<C>(), 0, s));
+    return correlate_window<R>(p, 1, false, p->sums_pg.as<double>(), s);
+  };
+  cudaError_t e = p->prm.precision ? run(double{}) : run(float{});
+  if (e != cudaSuccess) { (void)cudaGetLastError(); return from_cuda(e); }
+  std::vector<double> sums(2 * p->nL);
+  PG_TRY(cudaMemcpyAsync(sums.data(), p->sums_pg.p, 16 * p->nL, cudaMemcpyDeviceToHost, s));
+  PG_TRY(cudaStreamSynchronize(s));
+  for (int q = 0; q < p->nQ; ++q) {
+    if (h_sum) h_sum[q] = sums[2 * q];
+    if (h_sum2) h_sum2[q] = sums[2 * q + 1];
+    if (h_ncells) h_ncells[q] = p->h_list_off[q + 1] - p->h_list_off[q];
+  }
+  if (h_agg) { h_agg[0] = sums[2 * p->nQ]; h_agg[1] = sums[2 * p->nQ + 1]; }
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// (r, mu_r) binning of the correlation window and the ratio outputs.
+//
+// Binning (Sec. 2.1, eq. bpg_initial with W the indicator of one shell): every
+// window cell belongs to at most one (r, mu_r) bin, and the plan holds, per
+// bin, the sorted list of its cells plus one extra list for the aggregate
+// support. One CTA sums one list of one mesh in FP64 (sum C and sum C^2) with
+// a fixed warp-shuffle tree, so the sums are deterministic.
+//
+// Ratios (Sec. 2.2 and Sec. 3.4): xi_pg, xi_gg, b_pg = xi_pg / xi_gg,
+// xi(d_w) = sum C_gg^2 / sum C_gg (eq. xi_dw), xi(s, mu) = DD/RR - 1
+// (eq. 2PCF_d_collapsed with the exact pair normalisation), Q_eff
+// (eq. Qeff_notsq) and the strict-squeezed Q_eff (eq. Qeff), all FP64.
+#include <math.h>
+
+#include "pg_internal.cuh"
+
+namespace pg {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_bin_sums(const R* __restrict__ Cwin, int64_t stride, const int32_t* __restrict__ cells,
+           const int64_t* __restrict__ list_off, double* __restrict__ out, int n_lists) {
+  const int l = blockIdx.x, b = blockIdx.y;
+  const R* cw = Cwin + (int64_t)b * stride;
+  const int64_t lo = list_off[l], hi = list_off[l + 1];
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+    double v = (double)cw[cells[i]];
+    s1 += v;
+    s2 += v * v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+  }
+  __shared__ double w1[kThreads / 32], w2[kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { w1[wid] = s1; w2[wid] = s2; }
+  __syncthreads();
+  if (wid == 0) {
+    s1 = lane < kThreads / 32 ? w1[lane] : 0.0;
+    s2 = lane < kThreads / 32 ? w2[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_down_sync(0xffffffffu, s1, o);
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      out[((int64_t)b * n_lists + l) * 2] = s1;
+      out[((int64_t)b * n_lists + l) * 2 + 1] = s2;
+    }
+  }
+}
+
+__device__ __forceinline__ double q_notsq(double b, double xi, double xw) {
+  // eq. Qeff_notsq
+  return ((1.0 + xi) * b - 2.0 - xw / (2.0 * xi)) / (2.0 * xi + 1.5 * xw);
+}
+__device__ __forceinline__ double q_sq(double b, double xi) {
+  // eq. Qeff
+  return ((1.0 + xi) * b - 2.0) / (2.0 * xi);
+}
+
+__global__ void __launch_bounds__(kThreads) k_ratios(RatioArgs a) {
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  const int P = a.P, Q = a.Q, L = Q + 1;
+  const double sw = a.wsum[0], sw2 = a.wsum[1];
+  const double npairs = 0.5 * (sw * sw - sw2);
+  const double L3 = a.L * a.L * a.L;
+  // per pair bin: counts and xi(s, mu)
+  for (int p = threadIdx.x; p < P; p += kThreads) {
+    const int ks = p / a.n_mu;
+    const double lo = a.s_edges[ks], hi = a.s_edges[ks + 1];
+    const double vb = (4.0 * M_PI / 3.0) * (hi * hi * hi - lo * lo * lo) / (double)a.n_mu;
+    const double rr = npairs * vb / L3;
+    const double ddw = (double)(long long)a.ddq[p] * (1.0 / 4294967296.0);
+    if (a.o_dd) a.o_dd[p] = (int64_t)a.dd[p];
+    if (a.dd_w) a.dd_w[p] = ddw;
+    if (a.xi_ss) a.xi_ss[p] = rr > 0.0 ? ddw / rr - 1.0 : nan;
+  }
+  // per correlation bin: galaxy terms
+  for (int q = threadIdx.x; q <= Q; q += kThreads) {
+    const int64_t n = a.list_off[q + 1] - a.list_off[q];
+    const double s1 = a.gg_valid ? a.sum_gg[2 * q] : nan;
+    const double s2 = a.gg_valid ? a.sum_gg[2 * q + 1] : nan;
+    if (q < Q) {
+      if (a.n_cells) a.n_cells[q] = n;
+      if (a.xi_gg) a.xi_gg[q] = n > 0 ? s1 / (double)n : nan;
+      if (a.xi_dw) a.xi_dw[q] = s2 / s1;
+      if (a.o_sum_gg) a.o_sum_gg[q] = s1;
+      if (a.o_sum2_gg) a.o_sum2_gg[q] = s2;
+    } else {
+      if (a.n_cells_agg) *a.n_cells_agg = n;
+      if (a.xi_dw_agg) *a.xi_dw_agg = s2 / s1;
+      if (a.o_sum_gg_agg) { a.o_sum_gg_agg[0] = s1; a.o_sum_gg_agg[1] = s2; }
+    }
+  }
+  // per (pair bin, correlation bin)
+  for (int t = threadIdx.x; t < P * L; t += kThreads) {
+    const int p = t / L, q = t % L;
+    const double ddw = (double)(long long)a.ddq[p] * (1.0 / 4294967296.0);
+    const int ks = p / a.n_mu;
+    const double lo = a.s_edges[ks], hi = a.s_edges[ks + 1];
+    const double vb = (4.0 * M_PI / 3.0) * (hi * hi * hi - lo * lo * lo) / (double)a.n_mu;
+    const double rr = npairs * vb / L3;
+    const double xi = rr > 0.0 ? ddw / rr - 1.0 : nan;
+    const double sp = a.pg_valid[p] ? a.sum_pg[((int64_t)p * L + q) * 2] : nan;
+    const double sg = a.gg_valid ? a.sum_gg[2 * q] : nan;
+    const double s2g = a.gg_valid ? a.sum_gg[2 * q + 1] : nan;
+    const double xw = s2g / sg;
+    if (q < Q) {
+      const int64_t n = a.list_off[q + 1] - a.list_off[q];
+      const double xpg = n > 0 ? sp / (double)n : nan;
+      const double xgg = n > 0 ? sg / (double)n : nan;
+      const double b = xpg / xgg;
+      const int64_t o = (int64_t)p * Q + q;
+      if (a.o_sum_pg) a.o_sum_pg[o] = sp;
+      if (a.xi_pg) a.xi_pg[o] = xpg;
+      if (a.b_pg) a.b_pg[o] = b;
+      if (a.q_eff) a.q_eff[o] = q_notsq(b, xi, xw);
+      if (a.q_eff_sq) a.q_eff_sq[o] = q_sq(b, xi);
+    } else {
+      const double b = sp / sg;
+      if (a.o_sum_pg_agg) a.o_sum_pg_agg[p] = sp;
+      if (a.b_pg_agg) a.b_pg_agg[p] = b;
+      if (a.q_eff_agg) a.q_eff_agg[p] = q_notsq(b, xi, xw);
+    }
+  }
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_bin_sums(int nb, int n_lists, const R* Cwin, int64_t Cwin_stride,
+                            const int32_t* cells, const int64_t* list_off, double* out,
+                            cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  dim3 g(n_lists, nb);
+  k_bin_sums<R><<<g, kThreads, 0, s>>>(Cwin, Cwin_stride, cells, list_off, out, n_lists);
+  return launched();
+}
+template cudaError_t launch_bin_sums<float>(int, int, const float*, int64_t, const int32_t*,
+                                            const int64_t*, double*, cudaStream_t);
+template cudaError_t launch_bin_sums<double>(int, int, const double*, int64_t, const int32_t*,
+                                             const int64_t*, double*, cudaStream_t);
+
+cudaError_t launch_ratios(const RatioArgs& a, cudaStream_t s) {
+  k_ratios<<<1, kThreads, 0, s>>>(a);
+  return launched();
+}
+
+}  // namespace pg

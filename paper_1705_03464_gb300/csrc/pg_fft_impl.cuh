@@ -1,0 +1,178 @@
+// Host launchers of the FFT passes: dispatch on the mesh size N and set the
+// dynamic shared-memory limits. Instantiated per precision.
+#pragma once
+
+#include "pg_fft_kernels.cuh"
+
+namespace pg {
+
+namespace fft {
+template <typename R> struct Cols;
+template <> struct Cols<float> { static constexpr int B = 16; };
+template <> struct Cols<double> { static constexpr int B = 8; };
+}  // namespace fft
+
+#define PG_DISPATCH_N(N, ...)                               \
+  switch (N) {                                              \
+    case 32: { constexpr int NN = 32; __VA_ARGS__; break; } \
+    case 64: { constexpr int NN = 64; __VA_ARGS__; break; } \
+    case 128: { constexpr int NN = 128; __VA_ARGS__; break; } \
+    case 256: { constexpr int NN = 256; __VA_ARGS__; break; } \
+    case 512: { constexpr int NN = 512; __VA_ARGS__; break; } \
+    case 1024: { constexpr int NN = 1024; __VA_ARGS__; break; } \
+    default: return cudaErrorInvalidValue;                  \
+  }
+
+template <typename K>
+static cudaError_t set_smem(K kern, size_t bytes) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R>
+int FftPasses<R>::cols() { return fft::Cols<R>::B; }
+
+template <typename R>
+cudaError_t FftPasses<R>::x_r2c_lines(int N, const int64_t* q, const int32_t* line_bin,
+                                      const double* scale, int64_t n_lines, C* spec, int P,
+                                      const C* tw, cudaStream_t s) {
+  if (n_lines <= 0) return cudaSuccess;
+  PG_DISPATCH_N(N, {
+    using X = fft::XPass<C, NN>;
+    auto k = fft::k_x_r2c_lines<C, NN>;
+    PG_CUDA_TRY(set_smem(k, X::smem_bytes()));
+    k<<<(unsigned)cdiv(n_lines, X::LB), X::THREADS, X::smem_bytes(), s>>>(q, line_bin, scale, n_lines, spec, P, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::x_r2c_dense(int N, const R* f, C* spec, int P, const C* tw, cudaStream_t s) {
+  const int64_t n_lines = (int64_t)N * N;
+  PG_DISPATCH_N(N, {
+    using X = fft::XPass<C, NN>;
+    auto k = fft::k_x_r2c_dense<C, NN>;
+    PG_CUDA_TRY(set_smem(k, X::smem_bytes()));
+    k<<<(unsigned)cdiv(n_lines, X::LB), X::THREADS, X::smem_bytes(), s>>>(f, n_lines, spec, P, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::y_fwd(int N, int nb, const C* spec, int P, const int32_t* idx,
+                                const int64_t* seg_total, const int64_t* line_base,
+                                const int32_t* line_y, C* S, int64_t S_stride, const C* tw,
+                                cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  constexpr int B = fft::Cols<R>::B;
+  PG_DISPATCH_N(N, {
+    using CP = fft::ColPass<C, NN, B>;
+    auto k = fft::k_y_fwd<C, NN, B>;
+    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
+    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN, nb);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(spec, P, idx, seg_total, line_base, line_y, S, S_stride, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::z_fwd(int N, C* S, int P, const C* tw, cudaStream_t s) {
+  constexpr int B = fft::Cols<R>::B;
+  PG_DISPATCH_N(N, {
+    using CP = fft::ColPass<C, NN, B>;
+    auto k = fft::k_z_fwd<C, NN, B>;
+    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
+    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, P, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::z_corr(int N, int nb, const C* S, int64_t S_stride, const C* Fg,
+                                 bool gg, int w, C* Wz, int64_t Wz_stride, int P, const C* tw,
+                                 cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  constexpr int B = fft::Cols<R>::B;
+  PG_DISPATCH_N(N, {
+    using CP = fft::ColPass<C, NN, B>;
+    auto k = fft::k_z_corr<C, NN, B>;
+    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
+    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(nb, S, S_stride, Fg, gg ? 1 : 0, w, Wz, Wz_stride, P, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::y_inv_win(int N, int nb, const C* Wz, int64_t Wz_stride, int w, C* Wy,
+                                    int64_t Wy_stride, int P, const C* tw, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  constexpr int B = fft::Cols<R>::B;
+  PG_DISPATCH_N(N, {
+    using CP = fft::ColPass<C, NN, B>;
+    auto k = fft::k_y_inv_win<C, NN, B>;
+    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
+    dim3 g((unsigned)cdiv(NN / 2 + 1, B), 2 * w + 1, nb);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(Wz, Wz_stride, w, Wy, Wy_stride, P, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::x_c2r_win(int N, int nb, const C* Wy, int64_t Wy_stride, int w, R* Cwin,
+                                    int64_t Cwin_stride, int P, double scale, const C* tw,
+                                    cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  const int64_t n_lines = (int64_t)(2 * w + 1) * (2 * w + 1);
+  PG_DISPATCH_N(N, {
+    using X = fft::XPass<C, NN>;
+    auto k = fft::k_x_c2r_win<C, NN>;
+    PG_CUDA_TRY(set_smem(k, X::smem_bytes()));
+    dim3 g((unsigned)cdiv(n_lines, X::LB), nb);
+    k<<<g, X::THREADS, X::smem_bytes(), s>>>(Wy, Wy_stride, w, Cwin, Cwin_stride, P, (R)scale, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::z_inv_full(int N, C* S, int P, const C* tw, cudaStream_t s) {
+  constexpr int B = fft::Cols<R>::B;
+  PG_DISPATCH_N(N, {
+    using CP = fft::ColPass<C, NN, B>;
+    auto k = fft::k_col_inv_full<C, NN, B, true>;
+    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
+    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, P, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::y_inv_full(int N, C* S, int P, const C* tw, cudaStream_t s) {
+  constexpr int B = fft::Cols<R>::B;
+  PG_DISPATCH_N(N, {
+    using CP = fft::ColPass<C, NN, B>;
+    auto k = fft::k_col_inv_full<C, NN, B, false>;
+    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
+    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, P, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::x_c2r_full(int N, const C* S, int P, R* out, const C* tw, cudaStream_t s) {
+  const int64_t n_lines = (int64_t)N * N;
+  PG_DISPATCH_N(N, {
+    using X = fft::XPass<C, NN>;
+    auto k = fft::k_x_c2r_full<C, NN>;
+    PG_CUDA_TRY(set_smem(k, X::smem_bytes()));
+    k<<<(unsigned)cdiv(n_lines, X::LB), X::THREADS, X::smem_bytes(), s>>>(S, P, out, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::set_smem_limits() { return cudaSuccess; }
+
+}  // namespace pg

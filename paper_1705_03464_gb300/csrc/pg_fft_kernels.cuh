@@ -1,0 +1,559 @@
+// FFT passes of the mesh cross-correlation (Sec. 2.1: F_p conj(F_g) and its
+// inverse, eqs. bpg_initial / bpg_intermediate), templated on the real type
+// R (float or double) and the mesh size N. Included by pg_fft_f32.cu and
+// pg_fft_f64.cu, which instantiate it once per precision.
+//
+// Layout. A mesh is [z][y][x], x contiguous. After the x pass a half spectrum
+// row holds kx = 0..N/2 with pitch P complex elements. The y and z passes work
+// on tiles of B consecutive kx columns x all N rows of one axis, staged in
+// shared memory as buf[n*B + c]; the x passes stage lines as buf[n*LD + line].
+//
+// Each length-N 1D transform is one Cooley-Tukey split N = N1*N2 (N1 = 32):
+// step 1 does the N1-point DFTs over j1 in registers and applies W_N^(j2 k1)
+// in place; step 2 does the N2-point DFTs over j2 in registers and leaves
+// X[k1 + N1 k2] in the registers of task (c, k1). The inverse runs the split
+// the other way round from registers (step A) back through shared memory
+// (step B), so the z pass goes forward -> multiply -> inverse without a
+// second round trip. Twiddles W_N^j come from an FP64-generated table.
+#pragma once
+
+#include "pg_internal.cuh"
+#include "pg_twiddle32.cuh"
+
+namespace pg {
+namespace fft {
+
+template <typename C> __device__ __forceinline__ C w32(int j);
+template <> __device__ __forceinline__ float2 w32<float2>(int j) { return c_w32f[j]; }
+template <> __device__ __forceinline__ double2 w32<double2>(int j) { return c_w32d[j]; }
+
+template <typename C> struct Real;
+template <> struct Real<float2> { using T = float; };
+template <> struct Real<double2> { using T = double; };
+
+template <typename C> __device__ __forceinline__ C make_c(typename Real<C>::T x, typename Real<C>::T y);
+template <> __device__ __forceinline__ float2 make_c<float2>(float x, float y) { return make_float2(x, y); }
+template <> __device__ __forceinline__ double2 make_c<double2>(double x, double y) { return make_double2(x, y); }
+
+__host__ __device__ constexpr int cbitrev(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+__host__ __device__ constexpr int clog2(int n) { return n <= 1 ? 0 : 1 + clog2(n >> 1); }
+
+// One radix-2 stage (butterflies of span LEN) of the in-register DFT.
+template <typename C, int RL, bool INV, int LEN>
+__device__ __forceinline__ void dft_stage(C (&a)[RL]) {
+  if constexpr (LEN <= RL) {
+    constexpr int half = LEN / 2;
+#pragma unroll
+    for (int i = 0; i < RL; i += LEN) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        C u = a[i + k];
+        C v = a[i + k + half];
+        if (k != 0) {
+          C w = w32<C>(k * (32 / LEN));
+          if (INV) w.y = -w.y;
+          v = cmul(v, w);
+        }
+        a[i + k] = cadd(u, v);
+        a[i + k + half] = csub(u, v);
+      }
+    }
+    dft_stage<C, RL, INV, LEN * 2>(a);
+  }
+}
+
+// In-register DFT of length RL (1..32), forward (exp(-i...)) or inverse:
+// bit-reversal permutation, then radix-2 decimation-in-time stages.
+template <typename C, int RL, bool INV>
+__device__ __forceinline__ void reg_dft(C (&a)[RL]) {
+  if constexpr (RL > 1) {
+    constexpr int bits = clog2(RL);
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+      const int j = cbitrev(i, bits);
+      if (j > i) { C t = a[i]; a[i] = a[j]; a[j] = t; }
+    }
+    dft_stage<C, RL, INV, 2>(a);
+  }
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ C twid(const C* __restrict__ tw, int j) {
+  C w = __ldg(&tw[j]);
+  if (INV) w.y = -w.y;
+  return w;
+}
+
+// Step 1 of the split on B columns held as buf[n*LD + c]: tasks (c, j2).
+template <typename C, int N1, int N2, int B, bool INV>
+__device__ __forceinline__ void step1(C* buf, int LD, const C* __restrict__ tw, int tws) {
+  for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+    const int c = t % B, j2 = t / B;
+    C a[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) a[j1] = buf[(N2 * j1 + j2) * LD + c];
+    reg_dft<C, N1, INV>(a);
+    if (N2 > 1 && j2 > 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) a[k1] = cmul(a[k1], twid<C, INV>(tw, j2 * k1 * tws));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) buf[(N2 * k1 + j2) * LD + c] = a[k1];
+  }
+}
+
+// Step 2: task (c, k1) reads its N2 values and leaves X[k1 + N1*k2] in a[k2].
+template <typename C, int N1, int N2, bool INV>
+__device__ __forceinline__ void step2(const C* buf, int LD, int c, int k1, C (&a)[N2]) {
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) a[j2] = buf[(N2 * k1 + j2) * LD + c];
+  reg_dft<C, N2, INV>(a);
+}
+
+// Step A (inverse split from registers): a[k2] = X[k1 + N1*k2] of task
+// (c, k1) -> buf[(n2*N1 + k1)*LD + c] = W_N^(-+k1 n2) sum_k2 X W_N2^(-+k2 n2).
+template <typename C, int N1, int N2, bool INV>
+__device__ __forceinline__ void stepA(C* buf, int LD, int c, int k1, C (&a)[N2],
+                                      const C* __restrict__ tw, int tws) {
+  reg_dft<C, N2, INV>(a);
+  if (N2 > 1 && k1 > 0) {
+#pragma unroll
+    for (int n2 = 1; n2 < N2; ++n2) a[n2] = cmul(a[n2], twid<C, INV>(tw, k1 * n2 * tws));
+  }
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) buf[(n2 * N1 + k1) * LD + c] = a[n2];
+}
+
+// Step B: task (c, n2) -> out[n1] = x[n2 + N2*n1].
+template <typename C, int N1, int N2, bool INV>
+__device__ __forceinline__ void stepB(const C* buf, int LD, int c, int n2, C (&a)[N1]) {
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) a[k1] = buf[(n2 * N1 + k1) * LD + c];
+  reg_dft<C, N1, INV>(a);
+}
+
+template <int N> struct Split {
+  static constexpr int N1 = N < 32 ? N : 32;
+  static constexpr int N2 = N / N1;
+};
+
+__device__ __forceinline__ int win_index(int n, int N, int w) {
+  // signed offset of mesh index n in (-N/2, N/2]; returns offset + w, or -1
+  if (n <= w) return n + w;
+  if (n >= N - w) return n - N + w;
+  return -1;
+}
+
+// ============================================================================
+// X pass, real-to-complex. Lines of N reals become M = N/2 complex values
+// z[m] = f[2m] + i f[2m+1]; after the M-point DFT,
+// X[k] = (Z[k] + conj Z[M-k])/2 + W_N^k (Z[k] - conj Z[M-k])/(2i), k = 0..M.
+// ============================================================================
+template <typename C, int N>
+struct XPass {
+  static constexpr int M = N / 2;
+  static constexpr int N1 = Split<M>::N1, N2 = Split<M>::N2;
+  static constexpr int LB = (256 / N1) < 8 ? 8 : (256 / N1);   // lines per CTA
+  static constexpr int LD = LB + 1;
+  static constexpr int THREADS = LB * N1;
+  static constexpr size_t smem_bytes() { return sizeof(C) * (size_t)(M + 1) * LD; }
+};
+
+template <typename C, int N, typename Loader>
+__device__ __forceinline__ void x_r2c_body(C* buf, int64_t l0, int64_t n_lines, C* __restrict__ spec,
+                                           int P, const C* __restrict__ tw, Loader load) {
+  using X = XPass<C, N>;
+  constexpr int M = X::M, LB = X::LB, LD = X::LD, N1 = X::N1, N2 = X::N2;
+  for (int idx = threadIdx.x; idx < LB * M; idx += blockDim.x) {
+    const int c = idx / M, m = idx % M;
+    const int64_t l = l0 + c;
+    C v;
+    v.x = 0; v.y = 0;
+    if (l < n_lines) v = load(l, m);
+    buf[m * LD + c] = v;
+  }
+  __syncthreads();
+  step1<C, N1, N2, LB, false>(buf, LD, tw, 2);
+  __syncthreads();
+  const int c = threadIdx.x % LB, k1 = threadIdx.x / LB;
+  C a[N2];
+  step2<C, N1, N2, false>(buf, LD, c, k1, a);
+  __syncthreads();
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) buf[(k1 + N1 * k2) * LD + c] = a[k2];
+  __syncthreads();
+  using RT = typename Real<C>::T;
+  for (int idx = threadIdx.x; idx < LB * (M + 1); idx += blockDim.x) {
+    const int cc = idx / (M + 1), k = idx % (M + 1);
+    const int64_t l = l0 + cc;
+    if (l >= n_lines) continue;
+    C zk = buf[(k % M) * LD + cc];
+    C zm = buf[((M - k) % M) * LD + cc];
+    C e = make_c<C>((zk.x + zm.x) * RT(0.5), (zk.y - zm.y) * RT(0.5));
+    // (Z[k] - conj Z[M-k]) / (2i)
+    C d = make_c<C>((zk.y + zm.y) * RT(0.5), -(zk.x - zm.x) * RT(0.5));
+    C w = __ldg(&tw[k]);
+    C o = cmul(d, w);
+    spec[l * P + k] = cadd(e, o);
+  }
+}
+
+
+template <typename C, int N>
+__global__ void __launch_bounds__(XPass<C, N>::THREADS)
+k_x_r2c_lines(const int64_t* __restrict__ q, const int32_t* __restrict__ line_bin,
+              const double* __restrict__ scale, int64_t n_lines, C* __restrict__ spec, int P,
+              const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  using RT = typename Real<C>::T;
+  const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
+  x_r2c_body<C, N>(buf, l0, n_lines, spec, P, tw, [&](int64_t l, int m) {
+    const longlong2 qq = reinterpret_cast<const longlong2*>(q + l * N)[m];
+    const double s = scale[line_bin[l]];
+    return make_c<C>((RT)((double)qq.x * s), (RT)((double)qq.y * s));
+  });
+}
+
+template <typename C, int N>
+__global__ void __launch_bounds__(XPass<C, N>::THREADS)
+k_x_r2c_dense(const typename Real<C>::T* __restrict__ f, int64_t n_lines, C* __restrict__ spec,
+              int P, const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
+  x_r2c_body<C, N>(buf, l0, n_lines, spec, P, tw, [&](int64_t l, int m) {
+    return reinterpret_cast<const C*>(f + l * N)[m];
+  });
+}
+
+// ============================================================================
+// Y pass forward over compact lines. CTA = (kx tile, z plane, mesh).
+// ============================================================================
+template <typename C, int N, int B>
+struct ColPass {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int THREADS = B * N1;
+  static constexpr size_t smem_bytes() { return sizeof(C) * (size_t)N * B; }
+};
+
+template <typename C, int B>
+__device__ __forceinline__ void zero_tile(C* buf, int rows) {
+  C z;
+  z.x = 0; z.y = 0;
+  for (int t = threadIdx.x; t < rows * B; t += blockDim.x) buf[t] = z;
+}
+
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+k_y_fwd(const C* __restrict__ spec, int P, const int32_t* __restrict__ idx,
+        const int64_t* __restrict__ seg_total, const int64_t* __restrict__ line_base,
+        const int32_t* __restrict__ line_y, C* __restrict__ S, int64_t S_stride,
+        const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  using CP = ColPass<C, N, B>;
+  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  const int kx0 = blockIdx.x * B;
+  const int z = blockIdx.y;
+  const int b = blockIdx.z;
+  const int ncol = min(B, M1 - kx0);
+  const int c = threadIdx.x % B;
+  if (idx) {
+    const int64_t NN = (int64_t)N * N;
+    const int32_t* ib = idx + (int64_t)b * NN;
+    const int64_t lo = ib[(int64_t)z * N];
+    const int64_t hi = (z + 1 < N) ? ib[(int64_t)(z + 1) * N] : seg_total[b];
+    zero_tile<C, B>(buf, N);
+    __syncthreads();
+    const int64_t base = line_base[b];
+    for (int64_t r = lo + threadIdx.x / B; r < hi; r += blockDim.x / B) {
+      const int64_t l = base + r;
+      const int y = line_y[l];
+      if (c < ncol) buf[y * B + c] = spec[l * P + kx0 + c];
+    }
+  } else {
+    for (int y = threadIdx.x / B; y < N; y += blockDim.x / B) {
+      const int64_t l = (int64_t)z * N + y;
+      C v;
+      v.x = 0; v.y = 0;
+      if (c < ncol) v = spec[l * P + kx0 + c];
+      buf[y * B + c] = v;
+    }
+  }
+  __syncthreads();
+  step1<C, N1, N2, B, false>(buf, B, tw, 1);
+  __syncthreads();
+  const int k1 = threadIdx.x / B;
+  C a[N2];
+  step2<C, N1, N2, false>(buf, B, c, k1, a);
+  if (c < ncol) {
+    C* out = S + (int64_t)b * S_stride + (int64_t)z * N * P + kx0 + c;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) out[(int64_t)(k1 + N1 * k2) * P] = a[k2];
+  }
+}
+
+// Column tile load of one (ky, kx tile) z-column: rows z at stride N*P.
+template <typename C, int N, int B>
+__device__ __forceinline__ void load_zcol(C* buf, const C* __restrict__ src, int P, int ncol) {
+  const int c = threadIdx.x % B;
+  for (int z = threadIdx.x / B; z < N; z += blockDim.x / B) {
+    C v;
+    v.x = 0; v.y = 0;
+    if (c < ncol) v = src[(int64_t)z * N * P + c];
+    buf[z * B + c] = v;
+  }
+}
+
+// Z pass forward in place (galaxy spectrum). CTA = (kx tile, ky).
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+k_z_fwd(C* __restrict__ S, int P, const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  using CP = ColPass<C, N, B>;
+  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  const int kx0 = blockIdx.x * B, ky = blockIdx.y;
+  const int ncol = min(B, M1 - kx0);
+  C* col = S + (int64_t)ky * P + kx0;
+  load_zcol<C, N, B>(buf, col, P, ncol);
+  __syncthreads();
+  step1<C, N1, N2, B, false>(buf, B, tw, 1);
+  __syncthreads();
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  C a[N2];
+  step2<C, N1, N2, false>(buf, B, c, k1, a);
+  if (c < ncol) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) col[(int64_t)(k1 + N1 * k2) * N * P + c] = a[k2];
+  }
+}
+
+// Z pass fused: forward z, multiply, inverse z, window rows. CTA = (kx tile, ky).
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+k_z_corr(int nb, const C* __restrict__ S, int64_t S_stride, const C* __restrict__ Fg, int gg,
+         int w, C* __restrict__ Wz, int64_t Wz_stride, int P, const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  using CP = ColPass<C, N, B>;
+  using RT = typename Real<C>::T;
+  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  const int kx0 = blockIdx.x * B, ky = blockIdx.y;
+  const int ncol = min(B, M1 - kx0);
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  const RT inv_n3 = (RT)(1.0 / ((double)N * (double)N * (double)N));
+  const C* gcol = Fg + (int64_t)ky * P + kx0 + c;
+  const bool dc_col = (kx0 + c == 0) && (ky == 0);
+  for (int b = 0; b < nb; ++b) {
+    C a[N2];
+    if (!gg) {
+      load_zcol<C, N, B>(buf, S + (int64_t)b * S_stride + (int64_t)ky * P + kx0, P, ncol);
+      __syncthreads();
+      step1<C, N1, N2, B, false>(buf, B, tw, 1);
+      __syncthreads();
+      step2<C, N1, N2, false>(buf, B, c, k1, a);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        C g;
+        g.x = 0; g.y = 0;
+        if (c < ncol) g = gcol[(int64_t)(k1 + N1 * k2) * N * P];
+        a[k2] = cscale(cmulc(a[k2], g), inv_n3);
+      }
+    } else {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        C g;
+        g.x = 0; g.y = 0;
+        if (c < ncol) g = gcol[(int64_t)(k1 + N1 * k2) * N * P];
+        a[k2].x = (g.x * g.x + g.y * g.y) * inv_n3;
+        a[k2].y = 0;
+      }
+    }
+    if (dc_col && k1 == 0) { a[0].x = 0; a[0].y = 0; }   // k = 0 mode
+    __syncthreads();
+    stepA<C, N1, N2, true>(buf, B, c, k1, a, tw, 1);
+    __syncthreads();
+    C* wout = Wz + (int64_t)b * Wz_stride + (int64_t)ky * P + kx0;
+    for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+      const int cc = t % B, n2 = t / B;
+      C x[N1];
+      stepB<C, N1, N2, true>(buf, B, cc, n2, x);
+      if (cc < ncol) {
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+          const int zw = win_index(n2 + N2 * n1, N, w);
+          if (zw >= 0) wout[(int64_t)zw * N * P + cc] = x[n1];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Inverse y on the window rows. CTA = (kx tile, zw, mesh).
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+k_y_inv_win(const C* __restrict__ Wz, int64_t Wz_stride, int w, C* __restrict__ Wy,
+            int64_t Wy_stride, int P, const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  using CP = ColPass<C, N, B>;
+  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  const int kx0 = blockIdx.x * B, zw = blockIdx.y, b = blockIdx.z;
+  const int W = 2 * w + 1;
+  const int ncol = min(B, M1 - kx0);
+  const int c = threadIdx.x % B;
+  const C* src = Wz + (int64_t)b * Wz_stride + (int64_t)zw * N * P + kx0;
+  for (int y = threadIdx.x / B; y < N; y += blockDim.x / B) {
+    C v;
+    v.x = 0; v.y = 0;
+    if (c < ncol) v = src[(int64_t)y * P + c];
+    buf[y * B + c] = v;
+  }
+  __syncthreads();
+  step1<C, N1, N2, B, true>(buf, B, tw, 1);
+  __syncthreads();
+  const int k1 = threadIdx.x / B;
+  C a[N2];
+  step2<C, N1, N2, true>(buf, B, c, k1, a);
+  if (c < ncol) {
+    C* out = Wy + (int64_t)b * Wy_stride + (int64_t)zw * W * P + kx0 + c;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int yw = win_index(k1 + N1 * k2, N, w);
+      if (yw >= 0) out[(int64_t)yw * P] = a[k2];
+    }
+  }
+}
+
+// ============================================================================
+// X pass, complex-to-real inverse (unnormalised) of half-spectrum lines:
+// Z[k] = (X[k] + conj X[M-k]) + i W_N^-k (X[k] - conj X[M-k]), k < M;
+// z = IDFT_M(Z) gives x[2m] = Re z[m], x[2m+1] = Im z[m].
+// ============================================================================
+template <typename C, int N, typename Store>
+__device__ __forceinline__ void x_c2r_body(C* buf, int64_t l0, int64_t n_lines, const C* __restrict__ src_of_line0,
+                                           int P, const C* __restrict__ tw, Store store) {
+  using X = XPass<C, N>;
+  constexpr int M = X::M, LB = X::LB, LD = X::LD, N1 = X::N1, N2 = X::N2;
+  for (int idx = threadIdx.x; idx < LB * (M + 1); idx += blockDim.x) {
+    const int cc = idx / (M + 1), k = idx % (M + 1);
+    const int64_t l = l0 + cc;
+    C v;
+    v.x = 0; v.y = 0;
+    if (l < n_lines) v = src_of_line0[(l - l0) * P + k];
+    buf[k * LD + cc] = v;
+  }
+  __syncthreads();
+  // build Z in place: task (line, k) for k in [0, M/2]
+  for (int idx = threadIdx.x; idx < LB * (M / 2 + 1); idx += blockDim.x) {
+    const int cc = idx / (M / 2 + 1), k = idx % (M / 2 + 1);
+    C xk = buf[k * LD + cc];
+    C xm = buf[(M - k) * LD + cc];
+    // for index k: E = X[k] + conj X[M-k], D = X[k] - conj X[M-k]
+    C e1 = make_c<C>(xk.x + xm.x, xk.y - xm.y);
+    C d1 = make_c<C>(xk.x - xm.x, xk.y + xm.y);
+    C w1 = twid<C, true>(tw, k);
+    C o1 = cmul(d1, w1);
+    C z1 = make_c<C>(e1.x - o1.y, e1.y + o1.x);   // E + i*O
+    // for index M-k: E' = X[M-k] + conj X[k], D' = X[M-k] - conj X[k]
+    C e2 = make_c<C>(xm.x + xk.x, xm.y - xk.y);
+    C d2 = make_c<C>(xm.x - xk.x, xm.y + xk.y);
+    C w2 = twid<C, true>(tw, M - k);
+    C o2 = cmul(d2, w2);
+    C z2 = make_c<C>(e2.x - o2.y, e2.y + o2.x);
+    buf[k * LD + cc] = z1;
+    if (k != 0 && k != M - k) buf[(M - k) * LD + cc] = z2;
+  }
+  __syncthreads();
+  step1<C, N1, N2, LB, true>(buf, LD, tw, 2);
+  __syncthreads();
+  const int c = threadIdx.x % LB, k1 = threadIdx.x / LB;
+  C a[N2];
+  step2<C, N1, N2, true>(buf, LD, c, k1, a);
+  const int64_t l = l0 + c;
+  if (l < n_lines) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int m = k1 + N1 * k2;
+      store(l, 2 * m, a[k2].x);
+      store(l, 2 * m + 1, a[k2].y);
+    }
+  }
+}
+
+// Window lines of one mesh: line = zw*W + yw, output x offsets |x| <= w.
+template <typename C, int N>
+__global__ void __launch_bounds__(XPass<C, N>::THREADS)
+k_x_c2r_win(const C* __restrict__ Wy, int64_t Wy_stride, int w, typename Real<C>::T* __restrict__ Cwin,
+            int64_t Cwin_stride, int P, typename Real<C>::T scale, const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  using RT = typename Real<C>::T;
+  const int W = 2 * w + 1;
+  const int64_t n_lines = (int64_t)W * W;
+  const int b = blockIdx.y;
+  const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
+  const C* src = Wy + (int64_t)b * Wy_stride + l0 * P;
+  RT* out = Cwin + (int64_t)b * Cwin_stride;
+  x_c2r_body<C, N>(buf, l0, n_lines, src, P, tw, [&](int64_t l, int n, RT v) {
+    const int xw = win_index(n, N, w);
+    if (xw >= 0) out[l * W + xw] = v * scale;
+  });
+}
+
+// Full C2R of all N^2 lines (stage entry point).
+template <typename C, int N>
+__global__ void __launch_bounds__(XPass<C, N>::THREADS)
+k_x_c2r_full(const C* __restrict__ S, int P, typename Real<C>::T* __restrict__ out,
+             const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  using RT = typename Real<C>::T;
+  const int64_t n_lines = (int64_t)N * N;
+  const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
+  x_c2r_body<C, N>(buf, l0, n_lines, S + l0 * P, P, tw, [&](int64_t l, int n, RT v) {
+    out[l * N + n] = v;
+  });
+}
+
+// Full inverse along z or y in place on a dense half spectrum (stage entry).
+template <typename C, int N, int B, bool ALONG_Z>
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+k_col_inv_full(C* __restrict__ S, int P, const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  using CP = ColPass<C, N, B>;
+  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  const int kx0 = blockIdx.x * B, other = blockIdx.y;
+  const int ncol = min(B, M1 - kx0);
+  const int c = threadIdx.x % B;
+  // ALONG_Z: column over z at fixed y = other; else over y at fixed z = other
+  const int64_t rs = ALONG_Z ? (int64_t)N * P : (int64_t)P;
+  C* col = S + (ALONG_Z ? (int64_t)other * P : (int64_t)other * N * P) + kx0;
+  for (int r = threadIdx.x / B; r < N; r += blockDim.x / B) {
+    C v;
+    v.x = 0; v.y = 0;
+    if (c < ncol) v = col[(int64_t)r * rs + c];
+    buf[r * B + c] = v;
+  }
+  __syncthreads();
+  step1<C, N1, N2, B, true>(buf, B, tw, 1);
+  __syncthreads();
+  const int k1 = threadIdx.x / B;
+  C a[N2];
+  step2<C, N1, N2, true>(buf, B, c, k1, a);
+  if (c < ncol) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) col[(int64_t)(k1 + N1 * k2) * rs + c] = a[k2];
+  }
+}
+
+}  // namespace fft
+}  // namespace pg

@@ -1,0 +1,209 @@
+// Internal declarations shared by the libpairgal translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/pairgal.h"
+
+#define PG_CUDA_TRY(expr)                                   \
+  do {                                                      \
+    cudaError_t e__ = (expr);                               \
+    if (e__ != cudaSuccess) return e__;                     \
+  } while (0)
+
+namespace pg {
+
+template <typename R> struct CT;
+template <> struct CT<float> { using C = float2; };
+template <> struct CT<double> { using C = double2; };
+
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// Kernel launches issued by this library (all threads, all plans); a launcher
+// calls launched() right after each <<<...>>> instead of cudaGetLastError().
+std::atomic<long long>& launch_counter();
+inline cudaError_t launched() {
+  launch_counter().fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---- scan (pg_scan.cu) -----------------------------------------------------
+// Exclusive scan of `nseg` independent segments of `len` elements each:
+// out[s*len + i] = sum_{j<i} in[s*len + j]; seg_total[s] = the segment sum.
+// `tmp` must hold scan_tmp_elems(len, nseg) int64 values.
+size_t scan_tmp_elems(int64_t len, int nseg);
+cudaError_t scan_u8_i32(const uint8_t* in, int32_t* out, int64_t len, int nseg,
+                        int64_t* seg_total, int64_t* tmp, cudaStream_t s);
+cudaError_t scan_i32_i32(const int32_t* in, int32_t* out, int64_t len, int nseg,
+                         int64_t* seg_total, int64_t* tmp, cudaStream_t s);
+
+// ---- positions and pairs (pg_pairs.cu, compiled without FMA contraction) ----
+cudaError_t launch_transform(int64_t n, double L, double rsd, const double* in_aos,
+                             const float* vel, double* out_aos, double* x, double* y,
+                             double* z, cudaStream_t s);
+cudaError_t launch_widen_f32(int64_t n, const float* in, double* out, cudaStream_t s);
+cudaError_t launch_check_finite(int64_t n, const double* aos, int32_t* flag, cudaStream_t s);
+cudaError_t launch_wsum(int64_t n, const float* w, double* partial, double* out2,
+                        cudaStream_t s);
+
+struct PairGeom {
+  double L, halfL;
+  int nc;                 // cells per side (1, or >= 3)
+  double cell_scale;      // nc / L
+  int n_s, n_mu;
+  double e2[65];          // squared s edges
+};
+
+struct CellList {
+  int32_t* cell_id;      // [n]
+  int32_t* count;        // [ncell + 1]
+  int32_t* start;        // [ncell + 1]
+  int32_t* cursor;       // [ncell]
+  int32_t* perm;         // [n] sorted slot -> input index
+  double* xs; double* ys; double* zs;   // [n] sorted positions
+  float* ws;             // [n] sorted weights (or unused)
+  int64_t* tmp;          // scan temp
+  int64_t* tot;          // [1]
+};
+
+cudaError_t launch_cells(const PairGeom& g, int64_t n, const double* x, const double* y,
+                         const double* z, const float* w, CellList& cl, cudaStream_t s);
+
+struct PairOut {
+  unsigned long long* dd;    // [P] counts
+  unsigned long long* ddq;   // [P] Q32.32 weight sums
+  unsigned long long* cursor;// [1] fill cursor of the unsorted list
+  int64_t capacity;
+  int32_t* bin; int32_t* i; int32_t* j;
+  double* mx; double* my; double* mz; double* wp;   // unsorted list
+};
+cudaError_t launch_pairs(const PairGeom& g, int64_t n, const CellList& cl, bool use_w,
+                         bool fill, PairOut& po, cudaStream_t s);
+// Groups the unsorted pair list by bin: slot = offset[bin] + atomic cursor.
+cudaError_t launch_pair_scatter(int64_t np, const PairOut& po, unsigned long long* bin_cursor,
+                                int32_t* sbin, int32_t* si, int32_t* sj, double* smid_aos,
+                                double* sx, double* sy, double* sz, double* sw,
+                                cudaStream_t s);
+
+// ---- mass assignment (pg_mesh.cu, compiled without FMA contraction) --------
+struct DepGeom {
+  int N;
+  double dx;              // L / N
+  int assign;             // 0 NGP, 1 CIC
+};
+// Points: SoA x,y,z (FP64, in [0,L)), weight FP64 or null; pbin: per point
+// bin index relative to the batch (null = all in bin 0).
+cudaError_t launch_mark_lines(const DepGeom& g, int64_t n, const double* x, const double* y,
+                              const double* z, const int32_t* pbin, int bin0,
+                              uint8_t* flags, cudaStream_t s);
+cudaError_t launch_line_compact(int N, int nb, const uint8_t* flags, const int32_t* idx,
+                                const int64_t* line_base, int32_t* line_y, int32_t* line_bin,
+                                cudaStream_t s);
+cudaError_t launch_line_bases(int nb, const int64_t* seg_total, int64_t* line_base,
+                              int64_t* n_lines_total, cudaStream_t s);
+cudaError_t launch_deposit_lines(const DepGeom& g, int64_t n, const double* x, const double* y,
+                                 const double* z, const double* w, const int32_t* pbin,
+                                 int bin0, const int32_t* idx, const int64_t* line_base,
+                                 unsigned long long* lines_q, unsigned long long* qsum,
+                                 cudaStream_t s);
+cudaError_t launch_deposit_dense(const DepGeom& g, int64_t n, const double* aos,
+                                 const double* w, unsigned long long* mesh, cudaStream_t s);
+cudaError_t launch_field_scale(int nb, const unsigned long long* qsum, int N, double* scale,
+                               cudaStream_t s);
+
+// ---- FFT passes (pg_fft_f32.cu / pg_fft_f64.cu) -----------------------------
+// Spectra are complex R pairs; P = row pitch in complex elements (>= N/2+1).
+template <typename R>
+struct FftPasses {
+  using C = typename CT<R>::C;
+  static int cols();   // B: kx columns per CTA in the y/z passes
+  // X pass, R2C of compact int64 Q32.32 lines: f = q * scale[line_bin].
+  static cudaError_t x_r2c_lines(int N, const int64_t* q, const int32_t* line_bin,
+                                 const double* scale, int64_t n_lines, C* spec, int P,
+                                 const C* tw, cudaStream_t s);
+  // X pass, R2C of a dense real mesh [N][N][N].
+  static cudaError_t x_r2c_dense(int N, const R* f, C* spec, int P, const C* tw,
+                                 cudaStream_t s);
+  // Y pass forward over the compact lines of nb meshes (idx == null: dense lines
+  // l = z*N + y of one mesh). S[b] = [z][ky][P].
+  static cudaError_t y_fwd(int N, int nb, const C* spec, int P, const int32_t* idx,
+                           const int64_t* seg_total, const int64_t* line_base,
+                           const int32_t* line_y, C* S, int64_t S_stride, const C* tw,
+                           cudaStream_t s);
+  // Z pass forward in place: S[z][ky][kx] -> F[kz][ky][kx].
+  static cudaError_t z_fwd(int N, C* S, int P, const C* tw, cudaStream_t s);
+  // Z pass fused: for each of nb meshes, forward z, times conj(Fg) / N^3
+  // (gg: P = |Fg|^2 / N^3 from Fg itself), k = 0 set to zero, inverse z, and
+  // only the |z| <= w rows written: Wz[b] = [2w+1][ky][P].
+  static cudaError_t z_corr(int N, int nb, const C* S, int64_t S_stride, const C* Fg,
+                            bool gg, int w, C* Wz, int64_t Wz_stride, int P, const C* tw,
+                            cudaStream_t s);
+  // Inverse y on the window rows: Wz[b][zw][ky] -> Wy[b][zw][yw], |y| <= w.
+  static cudaError_t y_inv_win(int N, int nb, const C* Wz, int64_t Wz_stride, int w, C* Wy,
+                               int64_t Wy_stride, int P, const C* tw, cudaStream_t s);
+  // Inverse x (C2R) on the window lines, x offsets |x| <= w, times `scale`:
+  // Cwin[b] = [zw][yw][xw] real, (2w+1)^3 per mesh.
+  static cudaError_t x_c2r_win(int N, int nb, const C* Wy, int64_t Wy_stride, int w,
+                               R* Cwin, int64_t Cwin_stride, int P, double scale,
+                               const C* tw, cudaStream_t s);
+  // Dense inverse passes for the stage entry point: full y, full x.
+  static cudaError_t z_inv_full(int N, C* S, int P, const C* tw, cudaStream_t s);
+  static cudaError_t y_inv_full(int N, C* S, int P, const C* tw, cudaStream_t s);
+  static cudaError_t x_c2r_full(int N, const C* S, int P, R* out, const C* tw,
+                                cudaStream_t s);
+  static cudaError_t set_smem_limits();
+};
+
+// ---- binning and ratios (pg_bin.cu) -----------------------------------------
+template <typename R>
+cudaError_t launch_bin_sums(int nb, int n_lists, const R* Cwin, int64_t Cwin_stride,
+                            const int32_t* cells, const int64_t* list_off, double* out,
+                            cudaStream_t s);
+
+struct RatioArgs {
+  int P, Q;                       // pair bins, (r, mu_r) bins
+  int n_mu;
+  const double* s_edges;          // device [n_s+1]
+  double L;
+  const unsigned long long* dd;   // [P]
+  const unsigned long long* ddq;  // [P]
+  const double* wsum;             // [2] sum w, sum w^2
+  const double* sum_pg;           // [P][Q+1][2]
+  const unsigned char* pg_valid;  // [P] 1 if the bin's mesh was correlated
+  const double* sum_gg;           // [Q+1][2]
+  int gg_valid;
+  const int64_t* list_off;        // [Q+2]
+  // outputs (device)
+  double *dd_w, *xi_ss, *xi_pg, *xi_gg, *b_pg, *q_eff, *q_eff_sq, *xi_dw, *b_pg_agg,
+      *q_eff_agg, *xi_dw_agg, *o_sum_pg, *o_sum_pg_agg, *o_sum_gg, *o_sum2_gg, *o_sum_gg_agg;
+  int64_t *o_dd, *n_cells, *n_cells_agg;
+};
+cudaError_t launch_ratios(const RatioArgs& a, cudaStream_t s);
+
+}  // namespace pg

@@ -1,0 +1,216 @@
+// Mass assignment (Sec. 3.5) into compact x-lines of Q32.32 int64 nodes.
+//
+// A pair bin touches few mesh lines (Sec. 2.1: a pair field is a sum of
+// deltas at the pair midpoints), so each bin's mesh is stored as the list of
+// (y, z) lines it touches: the lines are flagged, an exclusive scan of the
+// flags numbers them, and the deposit adds llrint(((w*wx)*wy)*wz*2^32) to the
+// node with a 64-bit integer atomic. Integer sums make every mesh exact and
+// independent of the order of the atomics. Compiled with -fmad=false.
+#include "pg_internal.cuh"
+
+namespace pg {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxBatch = 64;   // bins whose totals are summed in shared memory
+
+struct Foot {
+  int ix[2], iy[2], iz[2];
+  double wx[2], wy[2], wz[2];
+  int n;  // 1 (NGP) or 2 (CIC) nodes per axis
+};
+
+__device__ __forceinline__ void footprint(const DepGeom& g, double x, double y, double z, Foot& f) {
+  double u[3] = {__ddiv_rn(x, g.dx), __ddiv_rn(y, g.dx), __ddiv_rn(z, g.dx)};
+  int* idx[3] = {f.ix, f.iy, f.iz};
+  double* wt[3] = {f.wx, f.wy, f.wz};
+  if (g.assign == 0) {
+    f.n = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int i = (int)floor(__dadd_rn(u[a], 0.5));
+      i %= g.N;
+      if (i < 0) i += g.N;
+      idx[a][0] = i;
+      wt[a][0] = 1.0;
+    }
+  } else {
+    f.n = 2;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double i0 = floor(u[a]);
+      double fr = __dsub_rn(u[a], i0);
+      int i = (int)i0 % g.N;
+      if (i < 0) i += g.N;
+      idx[a][0] = i;
+      idx[a][1] = (i + 1 == g.N) ? 0 : i + 1;
+      wt[a][0] = __dsub_rn(1.0, fr);
+      wt[a][1] = fr;
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long node_q(const DepGeom& g, double w, double wx,
+                                                     double wy, double wz) {
+  double v = (g.assign == 0) ? w : __dmul_rn(__dmul_rn(__dmul_rn(w, wx), wy), wz);
+  return (unsigned long long)__double2ll_rn(__dmul_rn(v, 4294967296.0));
+}
+
+__constant__ DepGeom c_dep;
+
+__global__ void __launch_bounds__(kThreads)
+k_mark_lines(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+             const double* __restrict__ z, const int32_t* __restrict__ pbin, int bin0,
+             uint8_t* __restrict__ flags) {
+  int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= n) return;
+  const DepGeom& g = c_dep;
+  Foot f;
+  footprint(g, x[p], y[p], z[p], f);
+  const int b = pbin ? pbin[p] - bin0 : 0;
+  uint8_t* fl = flags + (int64_t)b * g.N * g.N;
+  for (int cz = 0; cz < f.n; ++cz)
+    for (int cy = 0; cy < f.n; ++cy) fl[(int64_t)f.iz[cz] * g.N + f.iy[cy]] = 1;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_line_compact(int N, int nb, const uint8_t* __restrict__ flags, const int32_t* __restrict__ idx,
+               const int64_t* __restrict__ line_base, int32_t* __restrict__ line_y,
+               int32_t* __restrict__ line_bin) {
+  const int64_t NN = (int64_t)N * N;
+  int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (t >= NN * nb) return;
+  if (!flags[t]) return;
+  int b = (int)(t / NN);
+  int64_t zy = t - (int64_t)b * NN;
+  int64_t l = line_base[b] + idx[t];
+  line_y[l] = (int32_t)(zy % N);
+  line_bin[l] = b;
+}
+
+__global__ void k_line_bases(int nb, const int64_t* __restrict__ seg_total,
+                             int64_t* __restrict__ line_base, int64_t* __restrict__ total) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t run = 0;
+  for (int b = 0; b < nb; ++b) { line_base[b] = run; run += seg_total[b]; }
+  *total = run;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_deposit_lines(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+                const double* __restrict__ z, const double* __restrict__ w,
+                const int32_t* __restrict__ pbin, int bin0, const int32_t* __restrict__ idx,
+                const int64_t* __restrict__ line_base, unsigned long long* __restrict__ lines_q,
+                unsigned long long* __restrict__ qsum) {
+  __shared__ unsigned long long sh_q[kMaxBatch];
+  for (int t = threadIdx.x; t < kMaxBatch; t += kThreads) sh_q[t] = 0ull;
+  __syncthreads();
+  int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const DepGeom& g = c_dep;
+  if (p < n) {
+    Foot f;
+    footprint(g, x[p], y[p], z[p], f);
+    const int b = pbin ? pbin[p] - bin0 : 0;
+    const double wp = w ? w[p] : 1.0;
+    const int64_t NN = (int64_t)g.N * g.N;
+    unsigned long long mine = 0ull;
+    for (int cz = 0; cz < f.n; ++cz)
+      for (int cy = 0; cy < f.n; ++cy) {
+        int64_t zy = (int64_t)f.iz[cz] * g.N + f.iy[cy];
+        int64_t line = line_base[b] + idx[(int64_t)b * NN + zy];
+        unsigned long long* row = lines_q + line * g.N;
+        for (int cx = 0; cx < f.n; ++cx) {
+          unsigned long long q = node_q(g, wp, f.wx[cx], f.wy[cy], f.wz[cz]);
+          if (q) atomicAdd(&row[f.ix[cx]], q);
+          mine += q;
+        }
+      }
+    // mesh total (rho_bar) per bin: block-local integer sums, then one global add
+    if (b < kMaxBatch) atomicAdd(&sh_q[b], mine);
+    else atomicAdd(&qsum[b], mine);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kMaxBatch; t += kThreads)
+    if (sh_q[t]) atomicAdd(&qsum[t], sh_q[t]);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_deposit_dense(int64_t n, const double* __restrict__ aos, const double* __restrict__ w,
+                unsigned long long* __restrict__ mesh) {
+  int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= n) return;
+  const DepGeom& g = c_dep;
+  Foot f;
+  footprint(g, aos[3 * p], aos[3 * p + 1], aos[3 * p + 2], f);
+  const double wp = w ? w[p] : 1.0;
+  for (int cz = 0; cz < f.n; ++cz)
+    for (int cy = 0; cy < f.n; ++cy)
+      for (int cx = 0; cx < f.n; ++cx) {
+        unsigned long long q = node_q(g, wp, f.wx[cx], f.wy[cy], f.wz[cz]);
+        int64_t node = ((int64_t)f.iz[cz] * g.N + f.iy[cy]) * g.N + f.ix[cx];
+        if (q) atomicAdd(&mesh[node], q);
+      }
+}
+
+// f = rho / rho_bar = q * N^3 / Q per mesh (FP64); 0 when the mesh is empty.
+__global__ void k_field_scale(int nb, const unsigned long long* __restrict__ qsum, double n3,
+                              double* __restrict__ scale) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  long long Q = (long long)qsum[b];
+  scale[b] = Q > 0 ? n3 / (double)Q : 0.0;
+}
+
+}  // namespace
+
+cudaError_t launch_mark_lines(const DepGeom& g, int64_t n, const double* x, const double* y,
+                              const double* z, const int32_t* pbin, int bin0, uint8_t* flags,
+                              cudaStream_t s) {
+  PG_CUDA_TRY(cudaMemcpyToSymbolAsync(c_dep, &g, sizeof(DepGeom), 0, cudaMemcpyHostToDevice, s));
+  if (n <= 0) return cudaSuccess;
+  k_mark_lines<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(n, x, y, z, pbin, bin0, flags);
+  return launched();
+}
+
+cudaError_t launch_line_compact(int N, int nb, const uint8_t* flags, const int32_t* idx,
+                                const int64_t* line_base, int32_t* line_y, int32_t* line_bin,
+                                cudaStream_t s) {
+  int64_t tot = (int64_t)N * N * nb;
+  k_line_compact<<<(unsigned)cdiv(tot, kThreads), kThreads, 0, s>>>(N, nb, flags, idx, line_base, line_y, line_bin);
+  return launched();
+}
+
+cudaError_t launch_line_bases(int nb, const int64_t* seg_total, int64_t* line_base,
+                              int64_t* n_lines_total, cudaStream_t s) {
+  k_line_bases<<<1, 32, 0, s>>>(nb, seg_total, line_base, n_lines_total);
+  return launched();
+}
+
+cudaError_t launch_deposit_lines(const DepGeom& g, int64_t n, const double* x, const double* y,
+                                 const double* z, const double* w, const int32_t* pbin, int bin0,
+                                 const int32_t* idx, const int64_t* line_base,
+                                 unsigned long long* lines_q, unsigned long long* qsum,
+                                 cudaStream_t s) {
+  PG_CUDA_TRY(cudaMemcpyToSymbolAsync(c_dep, &g, sizeof(DepGeom), 0, cudaMemcpyHostToDevice, s));
+  if (n <= 0) return cudaSuccess;
+  k_deposit_lines<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(n, x, y, z, w, pbin, bin0, idx,
+                                                                     line_base, lines_q, qsum);
+  return launched();
+}
+
+cudaError_t launch_deposit_dense(const DepGeom& g, int64_t n, const double* aos, const double* w,
+                                 unsigned long long* mesh, cudaStream_t s) {
+  PG_CUDA_TRY(cudaMemcpyToSymbolAsync(c_dep, &g, sizeof(DepGeom), 0, cudaMemcpyHostToDevice, s));
+  if (n <= 0) return cudaSuccess;
+  k_deposit_dense<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(n, aos, w, mesh);
+  return launched();
+}
+
+cudaError_t launch_field_scale(int nb, const unsigned long long* qsum, int N, double* scale,
+                               cudaStream_t s) {
+  double n3 = (double)N * (double)N * (double)N;
+  k_field_scale<<<(unsigned)cdiv(nb, 64), 64, 0, s>>>(nb, qsum, n3, scale);
+  return launched();
+}
+
+}  // namespace pg

@@ -1,0 +1,305 @@
+"""Thin Python binding of libpairgal (include/pairgal.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels. Device buffers are torch CUDA tensors (torch supplies memory and
+streams); host buffers are numpy arrays. The functions keep the C names.
+There is no fallback: if libpairgal.so is missing, importing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpairgal.so")
+
+PG_OK, PG_ERR_INVALID_ARG, PG_ERR_UNSUPPORTED, PG_ERR_OOM, PG_ERR_CUDA, \
+    PG_ERR_TIMEOUT, PG_ERR_UNIMPLEMENTED, PG_ERR_CAPACITY = range(8)
+
+
+class PairgalError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class pg_params(C.Structure):
+    _fields_ = [
+        ("box_L", C.c_double), ("mesh_n", C.c_int32), ("assign", C.c_int32),
+        ("n_s", C.c_int32), ("s_edges", C.POINTER(C.c_double)), ("n_mu", C.c_int32),
+        ("n_r", C.c_int32), ("r_edges", C.POINTER(C.c_double)), ("n_mur", C.c_int32),
+        ("rsd_factor", C.c_double), ("r_perp_cut", C.c_double),
+        ("precision", C.c_int32), ("bins_per_batch", C.c_int32),
+    ]
+
+
+_RESULT_FIELDS = [
+    ("dd", "i8", "P"), ("dd_w", "f8", "P"), ("xi_ss", "f8", "P"), ("xi_pg", "f8", "PQ"),
+    ("xi_gg", "f8", "Q"), ("b_pg", "f8", "PQ"), ("q_eff", "f8", "PQ"), ("q_eff_sq", "f8", "PQ"),
+    ("xi_dw", "f8", "Q"), ("b_pg_agg", "f8", "P"), ("q_eff_agg", "f8", "P"),
+    ("xi_dw_agg", "f8", "1"), ("n_cells", "i8", "Q"), ("n_cells_agg", "i8", "1"),
+    ("sum_pg", "f8", "PQ"), ("sum_pg_agg", "f8", "P"), ("sum_gg", "f8", "Q"),
+    ("sum2_gg", "f8", "Q"), ("sum_gg_agg", "f8", "2"),
+]
+
+
+class pg_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double),
+                ("bytes", C.c_double)]
+
+
+PG_N_FAMILIES = 12
+
+
+class pg_result(C.Structure):
+    _fields_ = [(n, C.POINTER(C.c_int64) if t == "i8" else C.POINTER(C.c_double))
+                for n, t, _ in _RESULT_FIELDS]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1705_03464_gb300.build_lib.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    sig = {
+        "pg_status_string": (C.c_char_p, [C.c_int]),
+        "pg_plan_create": (C.c_int, [C.POINTER(pg_params), C.POINTER(vp)]),
+        "pg_plan_destroy": (None, [vp]),
+        "pg_plan_reserve": (C.c_int, [vp, i64, i64]),
+        "pg_workspace_bytes": (C.c_size_t, [vp]),
+        "pg_forward": (C.c_int, [vp, i64, vp, vp, vp, C.POINTER(pg_result), vp]),
+        "pg_forward_host": (C.c_int, [vp, i64, vp, vp, vp, C.POINTER(pg_result), vp]),
+        "pg_correlate_points": (C.c_int, [vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]),
+        "pg_transform_positions": (C.c_int, [i64, dbl, dbl, vp, vp, vp, vp]),
+        "pg_find_pairs": (C.c_int, [vp, i64, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]),
+        "pg_deposit_dense": (C.c_int, [i64, vp, vp, dbl, i32, i32, vp, vp]),
+        "pg_fft_r2c_3d": (C.c_int, [vp, vp, vp, vp]),
+        "pg_fft_c2r_3d": (C.c_int, [vp, vp, vp, vp]),
+        "pg_plan_set_profiling": (C.c_int, [vp, i32]),
+        "pg_plan_last_stats": (C.c_int, [vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def exported_symbols():
+    return [n for n in dir(_lib) if n.startswith("pg_")]
+
+
+def status_string(s: int) -> str:
+    return _lib.pg_status_string(int(s)).decode()
+
+
+def _check(st, what):
+    if st != PG_OK:
+        raise PairgalError(st, what)
+
+
+def _ptr(t):
+    """Device/host address of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Plan:
+    """A pg_plan on the current CUDA device (pg_plan_create / pg_plan_destroy)."""
+
+    def __init__(self, box_L, mesh_n, assign, s_edges, n_mu, r_edges, n_mur,
+                 rsd_factor=0.0, r_perp_cut=0.0, precision=0, bins_per_batch=0):
+        self.s_edges = np.ascontiguousarray(s_edges, dtype=np.float64)
+        self.r_edges = np.ascontiguousarray(r_edges, dtype=np.float64)
+        self.n_s = len(self.s_edges) - 1
+        self.n_mu = int(n_mu)
+        self.n_r = len(self.r_edges) - 1
+        self.n_mur = int(n_mur)
+        self.params = pg_params(
+            float(box_L), int(mesh_n), int(assign), self.n_s,
+            self.s_edges.ctypes.data_as(C.POINTER(C.c_double)), self.n_mu, self.n_r,
+            self.r_edges.ctypes.data_as(C.POINTER(C.c_double)), self.n_mur,
+            float(rsd_factor), float(r_perp_cut), int(precision), int(bins_per_batch))
+        h = C.c_void_p()
+        _check(_lib.pg_plan_create(C.byref(self.params), C.byref(h)), "pg_plan_create")
+        self.handle = h
+        self.P = self.n_s * self.n_mu
+        self.Q = self.n_r * self.n_mur
+
+    @classmethod
+    def of(cls, wl, **kw):
+        args = dict(box_L=wl.box_L, mesh_n=wl.mesh_n, assign=wl.assign, s_edges=wl.s_edges,
+                    n_mu=wl.n_mu, r_edges=wl.r_edges, n_mur=wl.n_mur,
+                    rsd_factor=wl.rsd_factor, r_perp_cut=wl.r_perp_cut,
+                    precision=wl.precision, bins_per_batch=wl.bins_per_batch)
+        args.update(kw)
+        return cls(**args)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.pg_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self) -> int:
+        return int(_lib.pg_workspace_bytes(self.handle))
+
+    def set_profiling(self, on: bool):
+        _check(_lib.pg_plan_set_profiling(self.handle, 1 if on else 0), "pg_plan_set_profiling")
+
+    def last_stats(self):
+        """Per kernel family of the last forward call: launches, ms, bytes;
+        plus the total number of kernel launches of that call."""
+        arr = (pg_kernel_stat * PG_N_FAMILIES)()
+        tot = C.c_int64(0)
+        _check(_lib.pg_plan_last_stats(self.handle, arr, C.byref(tot)), "pg_plan_last_stats")
+        fams = {a.name.decode(): {"launches": int(a.launches), "ms": float(a.ms), "bytes": float(a.bytes)}
+                for a in arr}
+        return fams, int(tot.value)
+
+    def reserve(self, n_gal_max, n_pairs_max):
+        _check(_lib.pg_plan_reserve(self.handle, int(n_gal_max), int(n_pairs_max)), "pg_plan_reserve")
+
+    def new_result(self):
+        """Host arrays for every pg_result field and the struct pointing at them."""
+        P, Q = self.P, self.Q
+        sizes = {"P": P, "Q": Q, "PQ": P * Q, "1": 1, "2": 2}
+        arrs = {}
+        res = pg_result()
+        for name, t, sz in _RESULT_FIELDS:
+            a = np.full(sizes[sz], np.nan if t == "f8" else 0, dtype=np.float64 if t == "f8" else np.int64)
+            arrs[name] = a
+            ctype = C.c_int64 if t == "i8" else C.c_double
+            setattr(res, name, a.ctypes.data_as(C.POINTER(ctype)))
+        return res, arrs
+
+    def shape_result(self, arrs):
+        out = dict(arrs)
+        for k in ("xi_pg", "b_pg", "q_eff", "q_eff_sq", "sum_pg"):
+            out[k] = arrs[k].reshape(self.P, self.Q)
+        out["xi_dw_agg"] = float(arrs["xi_dw_agg"][0])
+        out["n_cells_agg"] = int(arrs["n_cells_agg"][0])
+        return out
+
+
+def pg_forward(plan: Plan, pos, vel=None, w=None, stream=None):
+    """Full forward path on device tensors: pos [n,3] float64, vel [n,3]
+    float32 or None, w [n] float32 or None. Returns host numpy outputs."""
+    n = 0 if pos is None else int(pos.shape[0])
+    res, arrs = plan.new_result()
+    st = _lib.pg_forward(plan.handle, n, _ptr(pos), _ptr(vel), _ptr(w), C.byref(res), _stream(stream))
+    _check(st, "pg_forward")
+    return plan.shape_result(arrs)
+
+
+def pg_forward_host(plan: Plan, pos: np.ndarray, vel=None, w=None, stream=None):
+    """Full forward path from host (preferably pinned) arrays."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64) if isinstance(pos, np.ndarray) else pos
+    n = int(pos.shape[0])
+    res, arrs = plan.new_result()
+    st = _lib.pg_forward_host(plan.handle, n, _ptr(pos), _ptr(vel), _ptr(w), C.byref(res), _stream(stream))
+    _check(st, "pg_forward_host")
+    return plan.shape_result(arrs)
+
+
+def pg_transform_positions(pos, box_L, rsd_factor=0.0, vel=None, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty_like(pos)
+    _check(_lib.pg_transform_positions(int(pos.shape[0]), float(box_L), float(rsd_factor),
+                                       _ptr(pos), _ptr(vel), _ptr(out), _stream(stream)),
+           "pg_transform_positions")
+    return out
+
+
+def pg_find_pairs(plan: Plan, pos, w=None, with_list=True, stream=None):
+    """Pairs of wrapped device positions: counts (and the bin-grouped list)."""
+    import torch
+    dev = pos.device
+    n = int(pos.shape[0])
+    dd = torch.zeros(plan.P, dtype=torch.int64, device=dev)
+    ddq = torch.zeros(plan.P, dtype=torch.int64, device=dev)
+    npairs = C.c_int64(0)
+    st = _lib.pg_find_pairs(plan.handle, n, _ptr(pos), _ptr(w), _ptr(dd), _ptr(ddq), 0,
+                            None, None, None, None, None, C.byref(npairs), _stream(stream))
+    _check(st, "pg_find_pairs")
+    out = {"dd": dd, "ddq": ddq, "n_pairs": int(npairs.value)}
+    if not with_list:
+        return out
+    cap = max(1, out["n_pairs"])
+    b = torch.empty(cap, dtype=torch.int32, device=dev)
+    i = torch.empty(cap, dtype=torch.int32, device=dev)
+    j = torch.empty(cap, dtype=torch.int32, device=dev)
+    mid = torch.empty((cap, 3), dtype=torch.float64, device=dev)
+    wp = torch.empty(cap, dtype=torch.float64, device=dev)
+    st = _lib.pg_find_pairs(plan.handle, n, _ptr(pos), _ptr(w), _ptr(dd), _ptr(ddq), cap,
+                            _ptr(b), _ptr(i), _ptr(j), _ptr(mid), _ptr(wp), C.byref(npairs),
+                            _stream(stream))
+    _check(st, "pg_find_pairs")
+    m = int(npairs.value)
+    out.update({"bin": b[:m], "i": i[:m], "j": j[:m], "mid": mid[:m], "weight": wp[:m]})
+    return out
+
+
+def pg_deposit_dense(pos, w, box_L, mesh_n, assign, mesh=None, stream=None):
+    import torch
+    if mesh is None:
+        mesh = torch.zeros((mesh_n, mesh_n, mesh_n), dtype=torch.int64, device=pos.device)
+    _check(_lib.pg_deposit_dense(int(pos.shape[0]), _ptr(pos), _ptr(w), float(box_L), int(mesh_n),
+                                 int(assign), _ptr(mesh), _stream(stream)), "pg_deposit_dense")
+    return mesh
+
+
+def pg_fft_r2c_3d(plan: Plan, f, out=None, stream=None):
+    import torch
+    N = f.shape[0]
+    cdt = torch.complex128 if f.dtype == torch.float64 else torch.complex64
+    if out is None:
+        out = torch.empty((N, N, N // 2 + 1), dtype=cdt, device=f.device)
+    _check(_lib.pg_fft_r2c_3d(plan.handle, _ptr(f), _ptr(out), _stream(stream)), "pg_fft_r2c_3d")
+    return out
+
+
+def pg_fft_c2r_3d(plan: Plan, F, out=None, stream=None):
+    import torch
+    N = F.shape[0]
+    rdt = torch.float64 if F.dtype == torch.complex128 else torch.float32
+    if out is None:
+        out = torch.empty((N, N, N), dtype=rdt, device=F.device)
+    _check(_lib.pg_fft_c2r_3d(plan.handle, _ptr(F), _ptr(out), _stream(stream)), "pg_fft_c2r_3d")
+    return out
+
+
+def pg_correlate_points(plan: Plan, pts_a, w_a, pts_b, w_b, stream=None):
+    Q = plan.Q
+    s1 = np.zeros(Q)
+    s2 = np.zeros(Q)
+    agg = np.zeros(2)
+    nc = np.zeros(Q, dtype=np.int64)
+    st = _lib.pg_correlate_points(plan.handle, int(pts_a.shape[0]), _ptr(pts_a), _ptr(w_a),
+                                  int(pts_b.shape[0]), _ptr(pts_b), _ptr(w_b), _ptr(s1), _ptr(s2),
+                                  _ptr(agg), _ptr(nc), _stream(stream))
+    _check(st, "pg_correlate_points")
+    return {"sum": s1, "sum2": s2, "agg": agg, "n_cells": nc}

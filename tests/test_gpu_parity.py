@@ -1,0 +1,318 @@
+"""GPU parity: every stage of the CUDA path, called through the C ABI,
+against the FP64 oracle on the same seeded inputs.
+
+Bars: integer work (pair lists, counts, Q32.32 meshes) bit-exact; xi_pg,
+xi_gg within 1e-5 relative or 1e-7 absolute, whichever is looser; b_pg and
+Q_eff within 1e-4 relative, with an absolute floor of 1e-4 * max|value| over
+the grid for bins whose denominator is near zero. The FP64 path is held to
+1e-9.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import correlate as oc, dft as odft, direct as od, mesh as om, pairs as op, pipeline  # noqa: E402
+from paper_1705_03464_gb300 import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pg():
+    from paper_1705_03464_gb300 import build_lib
+    build_lib.build(verbose=False)
+    from paper_1705_03464_gb300 import pairgal
+    assert torch.cuda.is_available()
+    return pairgal
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def xi_close(g, o, rel=1e-5, abs_=1e-7):
+    g = np.asarray(g, float)
+    o = np.asarray(o, float)
+    fin = np.isfinite(o)
+    assert np.array_equal(fin, np.isfinite(g)), "NaN pattern differs"
+    err = np.abs(g[fin] - o[fin])
+    tol = np.maximum(rel * np.abs(o[fin]), abs_)
+    assert np.all(err <= tol), f"max err {err.max():.3e}, worst ratio {(err / tol).max():.3g}"
+
+
+def ratio_close(g, o, rel=1e-4):
+    g = np.asarray(g, float)
+    o = np.asarray(o, float)
+    fin = np.isfinite(o) & np.isfinite(g)
+    assert np.count_nonzero(fin) >= 0.9 * np.count_nonzero(np.isfinite(o))
+    floor = rel * np.max(np.abs(o[fin])) if np.any(fin) else 0.0
+    err = np.abs(g[fin] - o[fin])
+    tol = np.maximum(rel * np.abs(o[fin]), floor)
+    assert np.all(err <= tol), f"max err {err.max():.3e}, worst ratio {(err / tol).max():.3g}"
+
+
+# ---------------------------------------------------------------- a1
+def test_transform_positions_bitexact(pg):
+    rng = np.random.default_rng(1)
+    L = 300.0
+    pos = rng.uniform(-2 * L, 3 * L, (5000, 3))
+    pos[0] = [0.0, L, -L]
+    pos[1] = [L - 1e-13, -1e-300, 2 * L]
+    vel = rng.normal(0, 600, (5000, 3)).astype(np.float32)
+    for rsd in (0.0, synth.RSD_FACTOR_Z05):
+        got = pg.pg_transform_positions(dev(pos), L, rsd, dev(vel)).cpu().numpy()
+        ref = op.transform_positions(pos, vel, L, rsd)
+        assert np.array_equal(got, ref)
+        assert np.all((got >= 0) & (got < L))
+
+
+# ---------------------------------------------------------------- a2, a3
+def _pairs_case(name):
+    if name == "halo_catalogue":
+        wl = synth.WORKLOADS["real_ngp_128"]
+        cat = synth.make_catalogue(wl, 0)
+        return wl.box_L, cat.pos, None, wl.s_edges, 1
+    if name == "weighted_mu3":
+        cat = synth.make_catalogue_box(100.0, 3000, seed=4)
+        return 100.0, cat.pos, synth.make_weights(cat.n, 4), (0.0, 1.0, 2.0, 4.0, 7.0), 3
+    if name == "rsd_subset":
+        wl = synth.WORKLOADS["rsd_cic_512"]
+        cat = synth.subsample(synth.make_catalogue(wl, 0), 12000)
+        x = op.transform_positions(cat.pos, cat.vel, wl.box_L, wl.rsd_factor)
+        return wl.box_L, x, None, wl.s_edges, wl.n_mu
+    if name == "single_cell":   # L / s_max < 3: one cell, all pairs tested
+        rng = np.random.default_rng(5)
+        return 20.0, rng.random((400, 3)) * 20.0, None, (0.0, 3.0, 9.0), 2
+    if name == "duplicates":   # coincident galaxies: s = 0 pairs, mu = 0
+        rng = np.random.default_rng(6)
+        p = rng.random((300, 3)) * 50.0
+        p[100:150] = p[:50]
+        return 50.0, p, None, (0.0, 0.5, 5.0), 2
+    if name == "tiny":
+        return 10.0, np.array([[1.0, 1.0, 1.0], [1.5, 1.0, 1.0]]), None, (0.0, 1.0), 1
+    if name == "empty":
+        return 10.0, np.zeros((0, 3)), None, (0.0, 1.0), 1
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("case", ["halo_catalogue", "weighted_mu3", "rsd_subset", "single_cell",
+                                  "duplicates", "tiny", "empty"])
+def test_find_pairs_bitexact(pg, case):
+    L, pos, w, s_edges, n_mu = _pairs_case(case)
+    x = op.transform_positions(pos, None, L, 0.0)
+    plan = pg.Plan(L, 32, 0, s_edges, n_mu, (0.0, L / 4), 1)
+    wt = None if w is None else dev(w)
+    out = pg.pg_find_pairs(plan, dev(x) if len(x) else torch.zeros((0, 3), dtype=torch.float64, device="cuda"), wt)
+    ref = op.find_pairs(x, w, L, s_edges, n_mu) if len(x) < 5000 else op.find_pairs_kdtree(x, w, L, s_edges, n_mu)
+    n_s = len(s_edges) - 1
+    dd, ddq = op.pair_counts(ref, n_s, n_mu)
+    assert out["dd"].cpu().numpy().tolist() == dd.tolist()
+    assert out["ddq"].cpu().numpy().tolist() == ddq.tolist()
+    assert out["n_pairs"] == len(ref["i"])
+    if out["n_pairs"] == 0:
+        return
+    gi = out["i"].cpu().numpy().astype(np.int64)
+    gj = out["j"].cpu().numpy().astype(np.int64)
+    gb = out["bin"].cpu().numpy()
+    # grouped by bin in ascending order
+    assert np.all(np.diff(gb) >= 0)
+    og = np.lexsort((gj, gi))
+    orf = np.lexsort((ref["j"], ref["i"]))
+    assert np.array_equal(gi[og], ref["i"][orf]) and np.array_equal(gj[og], ref["j"][orf])
+    assert np.array_equal(gb[og], (ref["sbin"] * n_mu + ref["mubin"])[orf])
+    assert np.array_equal(out["mid"].cpu().numpy()[og], ref["mid"][orf])
+    assert np.array_equal(out["weight"].cpu().numpy()[og], ref["weight"][orf])
+
+
+# ---------------------------------------------------------------- a4
+@pytest.mark.parametrize("assign", [0, 1])
+@pytest.mark.parametrize("N", [32, 64])
+def test_deposit_dense_bitexact(pg, assign, N):
+    rng = np.random.default_rng(N + assign)
+    L = 77.0
+    p = rng.random((20000, 3)) * L
+    dx = L / N
+    p[:3] = [[0.0, 0.0, 0.0], [L - 1e-12, dx * 5, dx * 7.5], [dx * (N - 0.5), dx * 0.5, L - dx / 2]]
+    w = rng.random(20000) * 2.0
+    for wt in (None, w):
+        got = pg.pg_deposit_dense(dev(p), None if wt is None else dev(wt), L, N, assign).cpu().numpy()
+        ref = om.deposit(p, wt, L, N, assign)
+        assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------- a6, a8
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("N", [32, 64, 128])
+def test_fft_r2c_c2r_against_oracle_dft(pg, precision, N):
+    rng = np.random.default_rng(N)
+    f = rng.standard_normal((N, N, N))
+    plan = pg.Plan(float(N), N, 1, (0.0, 1.0), 1, (1.0, 2.0), 1, precision=precision)
+    dt = torch.float64 if precision else torch.float32
+    F = pg.pg_fft_r2c_3d(plan, dev(f, dt)).cpu().numpy()
+    ref = odft.dft3(f.astype(np.float64) if precision else f.astype(np.float32).astype(np.float64))[:, :, : N // 2 + 1]
+    scale = math.sqrt(np.mean(np.abs(ref) ** 2))
+    err = np.max(np.abs(F - ref)) / scale
+    assert err < (1e-12 if precision else 2e-6), err
+    back = pg.pg_fft_c2r_3d(plan, dev(F)).cpu().numpy() / N ** 3
+    err2 = np.max(np.abs(back - f)) / np.sqrt(np.mean(f * f))
+    assert err2 < (1e-12 if precision else 2e-6), err2
+
+
+# ---------------------------------------------------------------- a4..a9 on point sets
+@pytest.mark.parametrize("precision", [0, 1])
+def test_correlate_points_matches_oracle_and_b_is_one(pg, precision):
+    L, N = 96.0, 64
+    cat = synth.make_catalogue_box(L, 4000, seed=21)
+    rng = np.random.default_rng(3)
+    a = rng.random((300, 3)) * L
+    wa = rng.random(300)
+    r_edges = (6.0, 10.0, 15.0, 22.0)
+    plan = pg.Plan(L, N, 1, (0.0, 1.0), 1, r_edges, 3, precision=precision)
+    w = oc.window_half(N, L, r_edges[-1])
+    bins, agg = oc.cell_bins(N, L, r_edges, 3, 0.0, w)
+    ga = pg.pg_correlate_points(plan, dev(a), dev(wa), dev(cat.pos), None)
+    Cm = oc.window_of(oc.correlate_mesh(om.deposit(a, wa, L, N, 1), om.deposit(cat.pos, None, L, N, 1)), w)
+    s1, s2, n, a1, a2, na = oc.bin_sums(Cm, bins, agg, 9)
+    assert ga["n_cells"].tolist() == n.tolist()
+    xi_close(ga["sum"] / n, s1 / n, rel=1e-9 if precision else 1e-5)
+    # the galaxy set against itself: b_pg = 1 exactly in the estimator
+    gg = pg.pg_correlate_points(plan, dev(cat.pos), None, dev(cat.pos), None)
+    Cg = oc.window_of(oc.correlate_mesh(om.deposit(cat.pos, None, L, N, 1), om.deposit(cat.pos, None, L, N, 1)), w)
+    g1, g2, _, _, _, _ = oc.bin_sums(Cg, bins, agg, 9)
+    xi_close(gg["sum"] / n, g1 / n, rel=1e-9 if precision else 1e-5)
+    xi_close(gg["sum2"], g2, rel=1e-9 if precision else 1e-5)
+
+
+# ---------------------------------------------------------------- full path
+def _compare_forward(got, ref, precision, nbins_checked=None):
+    assert got["dd"].tolist() == ref["dd"].tolist()
+    np.testing.assert_array_equal(got["dd_w"], ref["ddq"].astype(np.float64) / 2.0 ** 32)
+    assert got["n_cells"].tolist() == ref["n_cells"].tolist()
+    assert got["n_cells_agg"] == ref["n_cells_agg"]
+    xi_close(got["xi_ss"], ref["xi_ss"], rel=1e-12, abs_=1e-12)
+    rel = 1e-9 if precision else 1e-5
+    absx = 1e-12 if precision else 1e-7
+    xi_close(got["xi_gg"], ref["xi_gg"], rel, absx)
+    rows = slice(None) if nbins_checked is None else nbins_checked
+    xi_close(got["xi_pg"][rows], ref["xi_pg"][rows], rel, absx)
+    rr = 1e-9 if precision else 1e-4
+    ratio_close(got["b_pg"][rows], ref["b_pg"][rows], rr)
+    ratio_close(got["q_eff"][rows], ref["q_eff"][rows], rr)
+    ratio_close(got["q_eff_sq"][rows], ref["q_eff_sq"][rows], rr)
+    ratio_close(got["b_pg_agg"][rows], ref["b_pg_agg"][rows], rr)
+    ratio_close(got["q_eff_agg"][rows], ref["q_eff_agg"][rows], rr)
+    ratio_close(got["xi_dw"], ref["xi_dw"], rr)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_forward_real_ngp_128(pg, precision):
+    wl = synth.WORKLOADS["real_ngp_128"]
+    cat = synth.make_catalogue(wl, 0)
+    plan = pg.Plan.of(wl, precision=precision)
+    got = pg.pg_forward(plan, dev(cat.pos))
+    ref = pipeline.run(pipeline.Params.of(wl), cat.pos, form="direct")
+    _compare_forward(got, ref, precision)
+
+
+def _small_cic_rsd():
+    L = 128.0
+    cat = synth.make_catalogue_box(L, 3000, seed=8)
+    w = synth.make_weights(cat.n, 8)
+    p = pipeline.Params(L, 64, 1, (0.0, 2.0, 4.0, 6.0), 2, (8.0, 12.0, 17.0, 23.0, 30.0), 3,
+                        synth.RSD_FACTOR_Z05, 5.0)
+    return p, cat, w
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_forward_weighted_cic_rsd_perp_cut(pg, precision):
+    p, cat, w = _small_cic_rsd()
+    plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur,
+                   rsd_factor=p.rsd_factor, r_perp_cut=p.r_perp_cut, precision=precision,
+                   bins_per_batch=4)
+    got = pg.pg_forward(plan, dev(cat.pos), dev(cat.vel), dev(w))
+    ref = pipeline.run(p, cat.pos, cat.vel, w, form="mesh")
+    _compare_forward(got, ref, precision)
+
+
+def test_forward_host_equals_device_and_is_deterministic(pg):
+    p, cat, w = _small_cic_rsd()
+    plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur,
+                   rsd_factor=p.rsd_factor, r_perp_cut=p.r_perp_cut, precision=0)
+    a = pg.pg_forward(plan, dev(cat.pos), dev(cat.vel), dev(w))
+    b = pg.pg_forward(plan, dev(cat.pos), dev(cat.vel), dev(w))
+    pos_h = torch.from_numpy(cat.pos).pin_memory().numpy()
+    c = pg.pg_forward_host(plan, pos_h, np.ascontiguousarray(cat.vel), np.ascontiguousarray(w))
+    for k in ("dd", "sum_pg", "sum_gg", "sum2_gg", "xi_pg", "q_eff"):
+        np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(a[k], c[k])
+
+
+def test_forward_edge_cases(pg):
+    wl = synth.WORKLOADS["real_ngp_128"]
+    plan = pg.Plan.of(wl, precision=0)
+    empty = pg.pg_forward(plan, torch.zeros((0, 3), dtype=torch.float64, device="cuda"))
+    assert empty["dd"].tolist() == [0] * plan.P
+    assert np.all(np.isnan(empty["xi_pg"])) and np.all(np.isnan(empty["xi_gg"]))
+    one = pg.pg_forward(plan, dev(np.array([[1.0, 2.0, 3.0]])))
+    assert one["dd"].sum() == 0 and np.all(np.isnan(one["xi_pg"]))
+    assert np.all(np.isfinite(one["xi_gg"]))
+    bad = synth.make_catalogue(wl, 0).pos.copy()
+    bad[7, 1] = np.nan
+    with pytest.raises(pg.PairgalError) as e:
+        pg.pg_forward(plan, dev(bad))
+    assert e.value.status == pg.PG_ERR_INVALID_ARG
+    with pytest.raises(pg.PairgalError) as e:
+        pg.Plan(128.0, 48, 0, (0.0, 8.0), 1, (8.0, 40.0), 1)
+    assert e.value.status == pg.PG_ERR_UNSUPPORTED
+    with pytest.raises(pg.PairgalError) as e:
+        pg.Plan(128.0, 128, 0, (0.0, 8.0), 1, (8.0, 64.0), 1)   # r_max >= L/2
+    assert e.value.status == pg.PG_ERR_INVALID_ARG
+    with pytest.raises(pg.PairgalError) as e:
+        pg.Plan(128.0, 128, 0, (0.0, 8.0, 4.0), 1, (8.0, 40.0), 1)   # descending edges
+    assert e.value.status == pg.PG_ERR_INVALID_ARG
+    # RSD without velocities
+    plan_rsd = pg.Plan(128.0, 64, 1, (0.0, 8.0), 1, (8.0, 40.0), 1, rsd_factor=0.01)
+    with pytest.raises(pg.PairgalError):
+        pg.pg_forward(plan_rsd, dev(np.zeros((5, 3))))
+
+
+# ---------------------------------------------------------------- full sizes
+@pytest.mark.slow
+def test_forward_rsd_cic_512_full(pg):
+    """The 512^3 CIC redshift-space workload in the batched FP32 launch
+    configuration: counts bit-exact; xi_gg on every bin and xi_pg on three
+    sampled pair bins from the oracle's direct corner sums."""
+    wl = synth.WORKLOADS["rsd_cic_512"]
+    cat = synth.make_catalogue(wl, 0)
+    plan = pg.Plan.of(wl)
+    got = pg.pg_forward(plan, dev(cat.pos), dev(cat.vel))
+    x = op.transform_positions(cat.pos, cat.vel, wl.box_L, wl.rsd_factor)
+    pr = op.find_pairs_kdtree(x, None, wl.box_L, wl.s_edges, wl.n_mu)
+    dd, ddq = op.pair_counts(pr, len(wl.s_edges) - 1, wl.n_mu)
+    assert got["dd"].tolist() == dd.tolist()
+    N, L = wl.mesh_n, wl.box_L
+    w = oc.window_half(N, L, wl.r_edges[-1])
+    bins, agg = oc.cell_bins(N, L, wl.r_edges, wl.n_mur, 0.0, w)
+    nq = len(got["xi_gg"])
+    cg = od.window_C_parallel(x, None, x, None, L, N, 1, w, wl.r_edges[-1])
+    g1, g2, n, ga1, ga2, _ = oc.bin_sums(cg, bins, agg, nq)
+    assert got["n_cells"].tolist() == n.tolist()
+    xi_close(got["xi_gg"], g1 / n)
+    xi_close(got["sum2_gg"], g2, rel=1e-5, abs_=1e-3)
+    pb = pr["sbin"] * wl.n_mu + pr["mubin"]
+    xs, _ = op.xi_ss(ddq, None, x.shape[0], L, wl.s_edges, wl.n_mu)
+    for b in (3, 24, 49):
+        sel = pb == b
+        cp = od.window_C_parallel(pr["mid"][sel], pr["weight"][sel], x, None, L, N, 1, w, wl.r_edges[-1])
+        s1, _, _, a1, _, _ = oc.bin_sums(cp, bins, agg, nq)
+        xi_close(got["xi_pg"][b], s1 / n)
+        ref = oc.ratios({"s1": s1[None, :], "a1": np.array([a1])},
+                        {"s1": g1, "s2": g2, "n": n, "a1": ga1, "a2": ga2, "na": 0}, xs[b:b + 1])
+        ratio_close(got["b_pg"][b], ref["b_pg"][0])
+        ratio_close(got["q_eff"][b], ref["q_eff"][0])
