@@ -40,6 +40,8 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--bins-per-batch", type=int, default=0,
+                    help="pair meshes resident at once (0 = the plan's default)")
     return ap.parse_args()
 
 
@@ -224,7 +226,7 @@ def main():
     cat = synth.make_catalogue(wl, args.seed + rank)
     pos = torch.from_numpy(cat.pos).cuda()
     vel = torch.from_numpy(np.ascontiguousarray(cat.vel)).cuda() if wl.rsd else None
-    plan = pg.Plan.of(wl)
+    plan = pg.Plan.of(wl, **({"bins_per_batch": args.bins_per_batch} if args.bins_per_batch else {}))
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):

@@ -395,7 +395,8 @@ cudaError_t correlate_window(pg_plan* p, int nb, bool gg, double* sums, cudaStre
     ProfScope ps(p, PG_FAM_FFT_Z_CORR, s,
                  (gg ? 0.0 : nb * N * N * M1 * cs) + N * N * M1 * cs + nb * W * N * M1 * cs);
     PG_CUDA_TRY(FftPasses<R>::z_corr(p->N, nb, p->S.as<C>(), S_stride, p->Fg.as<C>(), gg, p->w,
-                                     p->Wz.as<C>(), Wz_stride, p->P, tw, s));
+                                     p->Wz.as<C>(), Wz_stride, p->P, tw,
+                                     p->flag.as<int32_t>() + 1, s));
   }
   {
     ProfScope ps(p, PG_FAM_FFT_Y_INV, s, nb * (W * N * M1 * cs + W * W * M1 * cs));
@@ -476,7 +477,7 @@ cudaError_t positions_and_pairs(pg_plan* p, int64_t n, const double* d_pos, cons
   PG_CUDA_TRY(ensure_gal(p, n));
   {
     ProfScope ps(p, PG_FAM_POSITIONS, s, 24.0 * n * 2 + (d_vel ? 12.0 * n : 0.0) + (d_w ? 4.0 * n : 0.0));
-    PG_CUDA_TRY(cudaMemsetAsync(p->flag.p, 0, 4, s));
+    PG_CUDA_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));   // [0] non-finite input, [1] device timeout
     PG_CUDA_TRY(launch_check_finite(n, d_pos, p->flag.as<int32_t>(), s));
     PG_CUDA_TRY(launch_transform(n, p->prm.box_L, p->prm.rsd_factor, d_pos, d_vel, nullptr,
                                  p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), s));
@@ -618,8 +619,11 @@ pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* 
     PG_TRY(copy_out(out->sum2_gg, o.sum2_gg, Qd, s));
     PG_TRY(copy_out(out->sum_gg_agg, o.sum_gg_agg, 16, s));
   }
+  int32_t herr = 0;
+  PG_TRY(cudaMemcpyAsync(&herr, p->flag.as<int32_t>() + 1, 4, cudaMemcpyDeviceToHost, s));
   PG_TRY(cudaStreamSynchronize(s));
   p->last_launches = launch_counter().load() - launches0;
+  if (herr) return PG_ERR_TIMEOUT;
   if (p->prof_on) prof_end(p);
   else
     for (int f = 0; f < PG_N_FAMILIES; ++f) p->stats[f].bytes = p->fam_bytes[f];
@@ -918,6 +922,7 @@ pg_status pg_correlate_points(pg_plan* p, int64_t n_a, const double* d_a, const 
   if (!p || n_a <= 0 || n_b <= 0 || !d_a || !d_b) return PG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t nmax = std::max(n_a, n_b);
+  PG_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));
   PG_TRY(ensure_gal(p, nmax));
   // set b -> Fg; set a -> one "pair" mesh in S[0]
   PG_TRY(launch_transform(n_b, p->prm.box_L, 0.0, d_b, nullptr, nullptr, p->x.as<double>(),
@@ -938,8 +943,11 @@ pg_status pg_correlate_points(pg_plan* p, int64_t n_a, const double* d_a, const 
   cudaError_t e = p->prm.precision ? run(double{}) : run(float{});
   if (e != cudaSuccess) { (void)cudaGetLastError(); return from_cuda(e); }
   std::vector<double> sums(2 * p->nL);
+  int32_t herr = 0;
   PG_TRY(cudaMemcpyAsync(sums.data(), p->sums_pg.p, 16 * p->nL, cudaMemcpyDeviceToHost, s));
+  PG_TRY(cudaMemcpyAsync(&herr, p->flag.as<int32_t>() + 1, 4, cudaMemcpyDeviceToHost, s));
   PG_TRY(cudaStreamSynchronize(s));
+  if (herr) return PG_ERR_TIMEOUT;
   for (int q = 0; q < p->nQ; ++q) {
     if (h_sum) h_sum[q] = sums[2 * q];
     if (h_sum2) h_sum2[q] = sums[2 * q + 1];

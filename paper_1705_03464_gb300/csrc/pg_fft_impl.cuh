@@ -8,8 +8,14 @@ namespace pg {
 
 namespace fft {
 template <typename R> struct Cols;
-template <> struct Cols<float> { static constexpr int B = 16; };
-template <> struct Cols<double> { static constexpr int B = 8; };
+// 64 KB column tiles, 256 threads: two or three CTAs share an SM, so one
+// CTA's loads overlap another's arithmetic
+template <> struct Cols<float> { static constexpr int B = 8; };
+template <> struct Cols<double> { static constexpr int B = 4; };
+// the fused z pass holds two mesh tiles and the galaxy tile: 64 KB each
+template <typename R> struct ZCols;
+template <> struct ZCols<float> { static constexpr int B = 8; };
+template <> struct ZCols<double> { static constexpr int B = 4; };
 }  // namespace fft
 
 #define PG_DISPATCH_N(N, ...)                               \
@@ -90,15 +96,32 @@ cudaError_t FftPasses<R>::z_fwd(int N, C* S, int P, const C* tw, cudaStream_t s)
 template <typename R>
 cudaError_t FftPasses<R>::z_corr(int N, int nb, const C* S, int64_t S_stride, const C* Fg,
                                  bool gg, int w, C* Wz, int64_t Wz_stride, int P, const C* tw,
-                                 cudaStream_t s) {
+                                 int* err, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  constexpr int B = fft::Cols<R>::B;
+  constexpr int B = fft::ZCols<R>::B;
+  constexpr int E = (int)(sizeof(C) / 8);
+  // tensor maps over 8-byte elements: [bin][z][ky][kx] with row pitch P
+  const uint64_t strides[3] = {(uint64_t)P * 8 * E, (uint64_t)N * P * 8 * E,
+                               (uint64_t)N * N * P * 8 * E};
+  const uint32_t zb = N < 256 ? (uint32_t)N : 256u;
+  const uint32_t box[4] = {(uint32_t)(B * E), 1u, zb, 1u};
+  const uint64_t dS[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)N, (uint64_t)nb};
+  const uint64_t dF[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)N, 1u};
+  CUtensorMap mF, mS;
+  if (!encode_map_4d(&mF, Fg, dF, strides, box)) return cudaErrorInvalidValue;
+  if (!encode_map_4d(&mS, gg ? (const void*)Fg : (const void*)S, gg ? dF : dS, strides, box))
+    return cudaErrorInvalidValue;
+  (void)S_stride;
+  int dev = 0, sms = 0;
+  PG_CUDA_TRY(cudaGetDevice(&dev));
+  PG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   PG_DISPATCH_N(N, {
-    using CP = fft::ColPass<C, NN, B>;
-    auto k = fft::k_z_corr<C, NN, B>;
-    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
-    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(nb, S, S_stride, Fg, gg ? 1 : 0, w, Wz, Wz_stride, P, tw);
+    using Z = fft::ZCorr<C, NN, B>;
+    auto k = fft::k_z_corr_tma<C, NN, B>;
+    PG_CUDA_TRY(set_smem(k, Z::smem_bytes()));
+    const int64_t items = cdiv(NN / 2 + 1, B) * (int64_t)NN;
+    const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
+    k<<<grid, Z::THREADS, Z::smem_bytes(), s>>>(mS, mF, nb, gg ? 1 : 0, w, Wz, Wz_stride, P, tw, err);
   });
   return launched();
 }

@@ -18,22 +18,37 @@
 #pragma once
 
 #include "pg_internal.cuh"
+#include "pg_tma.cuh"
 #include "pg_twiddle32.cuh"
 
 namespace pg {
 namespace fft {
 
-template <typename C> __device__ __forceinline__ C w32(int j);
-template <> __device__ __forceinline__ float2 w32<float2>(int j) { return c_w32f[j]; }
-template <> __device__ __forceinline__ double2 w32<double2>(int j) { return c_w32d[j]; }
+// W_32^j from constant memory on the device, from the same values on the host
+// (the host path exists only so that the register DFT can be checked on a CPU).
+template <typename C> __host__ __device__ __forceinline__ C w32(int j);
+template <> __host__ __device__ __forceinline__ float2 w32<float2>(int j) {
+#ifdef __CUDA_ARCH__
+  return c_w32f[j];
+#else
+  return h_w32f[j];
+#endif
+}
+template <> __host__ __device__ __forceinline__ double2 w32<double2>(int j) {
+#ifdef __CUDA_ARCH__
+  return c_w32d[j];
+#else
+  return h_w32d[j];
+#endif
+}
 
 template <typename C> struct Real;
 template <> struct Real<float2> { using T = float; };
 template <> struct Real<double2> { using T = double; };
 
-template <typename C> __device__ __forceinline__ C make_c(typename Real<C>::T x, typename Real<C>::T y);
-template <> __device__ __forceinline__ float2 make_c<float2>(float x, float y) { return make_float2(x, y); }
-template <> __device__ __forceinline__ double2 make_c<double2>(double x, double y) { return make_double2(x, y); }
+template <typename C> __host__ __device__ __forceinline__ C make_c(typename Real<C>::T x, typename Real<C>::T y);
+template <> __host__ __device__ __forceinline__ float2 make_c<float2>(float x, float y) { return make_float2(x, y); }
+template <> __host__ __device__ __forceinline__ double2 make_c<double2>(double x, double y) { return make_double2(x, y); }
 
 __host__ __device__ constexpr int cbitrev(int i, int bits) {
   int r = 0;
@@ -42,26 +57,52 @@ __host__ __device__ constexpr int cbitrev(int i, int bits) {
 }
 __host__ __device__ constexpr int clog2(int n) { return n <= 1 ? 0 : 1 + clog2(n >> 1); }
 
+template <int V> struct IC { static constexpr int value = V; };
+
+// Compile-time loop: f(IC<I>{}) for I in [B, E).
+template <int B, int E, typename F>
+__host__ __device__ __forceinline__ void sfor(F&& f) {
+  if constexpr (B < E) {
+    f(IC<B>{});
+    sfor<B + 1, E>(f);
+  }
+}
+
+// v * W_32^J (forward) or v * conj(W_32^J) (inverse) with J known at compile
+// time: multiples of 8 (1, -i, -1, i) cost no multiplication.
+template <int J, bool INV, typename C>
+__host__ __device__ __forceinline__ C tw32_mul(C v) {
+  constexpr int j = J & 31;
+  if constexpr (j == 0) {
+    return v;
+  } else if constexpr (j == 16) {
+    return make_c<C>(-v.x, -v.y);
+  } else if constexpr ((j == 8 && !INV) || (j == 24 && INV)) {   // times -i
+    return make_c<C>(v.y, -v.x);
+  } else if constexpr (j == 8 || j == 24) {  // times +i
+    return make_c<C>(-v.y, v.x);
+  } else {
+    C w = w32<C>(j);
+    if (INV) w.y = -w.y;
+    return cmul(v, w);
+  }
+}
+
 // One radix-2 stage (butterflies of span LEN) of the in-register DFT.
 template <typename C, int RL, bool INV, int LEN>
-__device__ __forceinline__ void dft_stage(C (&a)[RL]) {
+__host__ __device__ __forceinline__ void dft_stage(C (&a)[RL]) {
   if constexpr (LEN <= RL) {
     constexpr int half = LEN / 2;
-#pragma unroll
-    for (int i = 0; i < RL; i += LEN) {
-#pragma unroll
-      for (int k = 0; k < half; ++k) {
+    sfor<0, RL / LEN>([&](auto ii) {
+      constexpr int i = decltype(ii)::value * LEN;
+      sfor<0, half>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
         C u = a[i + k];
-        C v = a[i + k + half];
-        if (k != 0) {
-          C w = w32<C>(k * (32 / LEN));
-          if (INV) w.y = -w.y;
-          v = cmul(v, w);
-        }
+        C v = tw32_mul<k * (32 / LEN), INV>(a[i + k + half]);
         a[i + k] = cadd(u, v);
         a[i + k + half] = csub(u, v);
-      }
-    }
+      });
+    });
     dft_stage<C, RL, INV, LEN * 2>(a);
   }
 }
@@ -69,7 +110,7 @@ __device__ __forceinline__ void dft_stage(C (&a)[RL]) {
 // In-register DFT of length RL (1..32), forward (exp(-i...)) or inverse:
 // bit-reversal permutation, then radix-2 decimation-in-time stages.
 template <typename C, int RL, bool INV>
-__device__ __forceinline__ void reg_dft(C (&a)[RL]) {
+__host__ __device__ __forceinline__ void reg_dft(C (&a)[RL]) {
   if constexpr (RL > 1) {
     constexpr int bits = clog2(RL);
 #pragma unroll
@@ -81,16 +122,24 @@ __device__ __forceinline__ void reg_dft(C (&a)[RL]) {
   }
 }
 
+// Copies the twiddle table W_N^j (j < n) into shared memory; the caller's
+// next __syncthreads() publishes it.
+template <typename C>
+__device__ __forceinline__ const C* stage_tw(C* dst, const C* __restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  return dst;
+}
+
 template <typename C, bool INV>
-__device__ __forceinline__ C twid(const C* __restrict__ tw, int j) {
-  C w = __ldg(&tw[j]);
+__device__ __forceinline__ C twid(const C* tw, int j) {
+  C w = tw[j];
   if (INV) w.y = -w.y;
   return w;
 }
 
 // Step 1 of the split on B columns held as buf[n*LD + c]: tasks (c, j2).
 template <typename C, int N1, int N2, int B, bool INV>
-__device__ __forceinline__ void step1(C* buf, int LD, const C* __restrict__ tw, int tws) {
+__device__ __forceinline__ void step1(C* buf, int LD, const C* tw, int tws) {
   for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
     const int c = t % B, j2 = t / B;
     C a[N1];
@@ -118,7 +167,7 @@ __device__ __forceinline__ void step2(const C* buf, int LD, int c, int k1, C (&a
 // (c, k1) -> buf[(n2*N1 + k1)*LD + c] = W_N^(-+k1 n2) sum_k2 X W_N2^(-+k2 n2).
 template <typename C, int N1, int N2, bool INV>
 __device__ __forceinline__ void stepA(C* buf, int LD, int c, int k1, C (&a)[N2],
-                                      const C* __restrict__ tw, int tws) {
+                                      const C* tw, int tws) {
   reg_dft<C, N2, INV>(a);
   if (N2 > 1 && k1 > 0) {
 #pragma unroll
@@ -160,12 +209,12 @@ struct XPass {
   static constexpr int LB = (256 / N1) < 8 ? 8 : (256 / N1);   // lines per CTA
   static constexpr int LD = LB + 1;
   static constexpr int THREADS = LB * N1;
-  static constexpr size_t smem_bytes() { return sizeof(C) * (size_t)(M + 1) * LD; }
+  static constexpr size_t smem_bytes() { return sizeof(C) * ((size_t)(M + 1) * LD + N); }
 };
 
 template <typename C, int N, typename Loader>
 __device__ __forceinline__ void x_r2c_body(C* buf, int64_t l0, int64_t n_lines, C* __restrict__ spec,
-                                           int P, const C* __restrict__ tw, Loader load) {
+                                           int P, const C* tw, Loader load) {
   using X = XPass<C, N>;
   constexpr int M = X::M, LB = X::LB, LD = X::LD, N1 = X::N1, N2 = X::N2;
   for (int idx = threadIdx.x; idx < LB * M; idx += blockDim.x) {
@@ -196,7 +245,7 @@ __device__ __forceinline__ void x_r2c_body(C* buf, int64_t l0, int64_t n_lines, 
     C e = make_c<C>((zk.x + zm.x) * RT(0.5), (zk.y - zm.y) * RT(0.5));
     // (Z[k] - conj Z[M-k]) / (2i)
     C d = make_c<C>((zk.y + zm.y) * RT(0.5), -(zk.x - zm.x) * RT(0.5));
-    C w = __ldg(&tw[k]);
+    C w = tw[k];   // shared-memory twiddle table
     C o = cmul(d, w);
     spec[l * P + k] = cadd(e, o);
   }
@@ -209,10 +258,11 @@ k_x_r2c_lines(const int64_t* __restrict__ q, const int32_t* __restrict__ line_bi
               const double* __restrict__ scale, int64_t n_lines, C* __restrict__ spec, int P,
               const C* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using RT = typename Real<C>::T;
   const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
-  x_r2c_body<C, N>(buf, l0, n_lines, spec, P, tw, [&](int64_t l, int m) {
+  x_r2c_body<C, N>(buf, l0, n_lines, spec, P, tws, [&](int64_t l, int m) {
     const longlong2 qq = reinterpret_cast<const longlong2*>(q + l * N)[m];
     const double s = scale[line_bin[l]];
     return make_c<C>((RT)((double)qq.x * s), (RT)((double)qq.y * s));
@@ -224,9 +274,10 @@ __global__ void __launch_bounds__(XPass<C, N>::THREADS)
 k_x_r2c_dense(const typename Real<C>::T* __restrict__ f, int64_t n_lines, C* __restrict__ spec,
               int P, const C* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
-  x_r2c_body<C, N>(buf, l0, n_lines, spec, P, tw, [&](int64_t l, int m) {
+  x_r2c_body<C, N>(buf, l0, n_lines, spec, P, tws, [&](int64_t l, int m) {
     return reinterpret_cast<const C*>(f + l * N)[m];
   });
 }
@@ -238,7 +289,7 @@ template <typename C, int N, int B>
 struct ColPass {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   static constexpr int THREADS = B * N1;
-  static constexpr size_t smem_bytes() { return sizeof(C) * (size_t)N * B; }
+  static constexpr size_t smem_bytes() { return sizeof(C) * ((size_t)N * B + N); }
 };
 
 template <typename C, int B>
@@ -255,7 +306,8 @@ k_y_fwd(const C* __restrict__ spec, int P, const int32_t* __restrict__ idx,
         const int32_t* __restrict__ line_y, C* __restrict__ S, int64_t S_stride,
         const C* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using CP = ColPass<C, N, B>;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
   const int kx0 = blockIdx.x * B;
@@ -286,7 +338,7 @@ k_y_fwd(const C* __restrict__ spec, int P, const int32_t* __restrict__ idx,
     }
   }
   __syncthreads();
-  step1<C, N1, N2, B, false>(buf, B, tw, 1);
+  step1<C, N1, N2, B, false>(buf, B, tws, 1);
   __syncthreads();
   const int k1 = threadIdx.x / B;
   C a[N2];
@@ -315,7 +367,8 @@ template <typename C, int N, int B>
 __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
 k_z_fwd(C* __restrict__ S, int P, const C* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using CP = ColPass<C, N, B>;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
   const int kx0 = blockIdx.x * B, ky = blockIdx.y;
@@ -323,7 +376,7 @@ k_z_fwd(C* __restrict__ S, int P, const C* __restrict__ tw) {
   C* col = S + (int64_t)ky * P + kx0;
   load_zcol<C, N, B>(buf, col, P, ncol);
   __syncthreads();
-  step1<C, N1, N2, B, false>(buf, B, tw, 1);
+  step1<C, N1, N2, B, false>(buf, B, tws, 1);
   __syncthreads();
   const int c = threadIdx.x % B, k1 = threadIdx.x / B;
   C a[N2];
@@ -340,7 +393,8 @@ __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
 k_z_corr(int nb, const C* __restrict__ S, int64_t S_stride, const C* __restrict__ Fg, int gg,
          int w, C* __restrict__ Wz, int64_t Wz_stride, int P, const C* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using CP = ColPass<C, N, B>;
   using RT = typename Real<C>::T;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
@@ -355,7 +409,7 @@ k_z_corr(int nb, const C* __restrict__ S, int64_t S_stride, const C* __restrict_
     if (!gg) {
       load_zcol<C, N, B>(buf, S + (int64_t)b * S_stride + (int64_t)ky * P + kx0, P, ncol);
       __syncthreads();
-      step1<C, N1, N2, B, false>(buf, B, tw, 1);
+      step1<C, N1, N2, B, false>(buf, B, tws, 1);
       __syncthreads();
       step2<C, N1, N2, false>(buf, B, c, k1, a);
 #pragma unroll
@@ -377,7 +431,7 @@ k_z_corr(int nb, const C* __restrict__ S, int64_t S_stride, const C* __restrict_
     }
     if (dc_col && k1 == 0) { a[0].x = 0; a[0].y = 0; }   // k = 0 mode
     __syncthreads();
-    stepA<C, N1, N2, true>(buf, B, c, k1, a, tw, 1);
+    stepA<C, N1, N2, true>(buf, B, c, k1, a, tws, 1);
     __syncthreads();
     C* wout = Wz + (int64_t)b * Wz_stride + (int64_t)ky * P + kx0;
     for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
@@ -402,7 +456,8 @@ __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
 k_y_inv_win(const C* __restrict__ Wz, int64_t Wz_stride, int w, C* __restrict__ Wy,
             int64_t Wy_stride, int P, const C* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using CP = ColPass<C, N, B>;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
   const int kx0 = blockIdx.x * B, zw = blockIdx.y, b = blockIdx.z;
@@ -417,7 +472,7 @@ k_y_inv_win(const C* __restrict__ Wz, int64_t Wz_stride, int w, C* __restrict__ 
     buf[y * B + c] = v;
   }
   __syncthreads();
-  step1<C, N1, N2, B, true>(buf, B, tw, 1);
+  step1<C, N1, N2, B, true>(buf, B, tws, 1);
   __syncthreads();
   const int k1 = threadIdx.x / B;
   C a[N2];
@@ -439,7 +494,7 @@ k_y_inv_win(const C* __restrict__ Wz, int64_t Wz_stride, int w, C* __restrict__ 
 // ============================================================================
 template <typename C, int N, typename Store>
 __device__ __forceinline__ void x_c2r_body(C* buf, int64_t l0, int64_t n_lines, const C* __restrict__ src_of_line0,
-                                           int P, const C* __restrict__ tw, Store store) {
+                                           int P, const C* tw, Store store) {
   using X = XPass<C, N>;
   constexpr int M = X::M, LB = X::LB, LD = X::LD, N1 = X::N1, N2 = X::N2;
   for (int idx = threadIdx.x; idx < LB * (M + 1); idx += blockDim.x) {
@@ -494,7 +549,8 @@ __global__ void __launch_bounds__(XPass<C, N>::THREADS)
 k_x_c2r_win(const C* __restrict__ Wy, int64_t Wy_stride, int w, typename Real<C>::T* __restrict__ Cwin,
             int64_t Cwin_stride, int P, typename Real<C>::T scale, const C* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using RT = typename Real<C>::T;
   const int W = 2 * w + 1;
   const int64_t n_lines = (int64_t)W * W;
@@ -502,7 +558,7 @@ k_x_c2r_win(const C* __restrict__ Wy, int64_t Wy_stride, int w, typename Real<C>
   const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
   const C* src = Wy + (int64_t)b * Wy_stride + l0 * P;
   RT* out = Cwin + (int64_t)b * Cwin_stride;
-  x_c2r_body<C, N>(buf, l0, n_lines, src, P, tw, [&](int64_t l, int n, RT v) {
+  x_c2r_body<C, N>(buf, l0, n_lines, src, P, tws, [&](int64_t l, int n, RT v) {
     const int xw = win_index(n, N, w);
     if (xw >= 0) out[l * W + xw] = v * scale;
   });
@@ -514,11 +570,12 @@ __global__ void __launch_bounds__(XPass<C, N>::THREADS)
 k_x_c2r_full(const C* __restrict__ S, int P, typename Real<C>::T* __restrict__ out,
              const C* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using RT = typename Real<C>::T;
   const int64_t n_lines = (int64_t)N * N;
   const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
-  x_c2r_body<C, N>(buf, l0, n_lines, S + l0 * P, P, tw, [&](int64_t l, int n, RT v) {
+  x_c2r_body<C, N>(buf, l0, n_lines, S + l0 * P, P, tws, [&](int64_t l, int n, RT v) {
     out[l * N + n] = v;
   });
 }
@@ -528,7 +585,8 @@ template <typename C, int N, int B, bool ALONG_Z>
 __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
 k_col_inv_full(C* __restrict__ S, int P, const C* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using CP = ColPass<C, N, B>;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
   const int kx0 = blockIdx.x * B, other = blockIdx.y;
@@ -544,7 +602,7 @@ k_col_inv_full(C* __restrict__ S, int P, const C* __restrict__ tw) {
     buf[r * B + c] = v;
   }
   __syncthreads();
-  step1<C, N1, N2, B, true>(buf, B, tw, 1);
+  step1<C, N1, N2, B, true>(buf, B, tws, 1);
   __syncthreads();
   const int k1 = threadIdx.x / B;
   C a[N2];
@@ -552,6 +610,144 @@ k_col_inv_full(C* __restrict__ S, int P, const C* __restrict__ tw) {
   if (c < ncol) {
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) col[(int64_t)(k1 + N1 * k2) * rs + c] = a[k2];
+  }
+}
+
+// ============================================================================
+// Z pass fused, persistent and TMA fed. A work item is (ky, a tile of B kx
+// columns). For each item the CTA loads the galaxy spectrum tile once, then
+// runs every mesh of the batch through forward z -> * conj(F_g) / N^3 ->
+// k = 0 zeroed -> inverse z -> window rows. While one mesh is transformed the
+// next mesh's tile streams into the second shared buffer (TMA + mbarrier), so
+// HBM reads overlap the FFT arithmetic.
+// ============================================================================
+template <typename C, int N, int B>
+struct ZCorr {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int THREADS = B * N1;
+  static constexpr int TILE = N * B;
+  static constexpr int ZB = N < 256 ? N : 256;   // rows per TMA box
+  static constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
+  static constexpr int E = sizeof(C) / 8;        // 8-byte TMA elements per complex
+  static constexpr size_t smem_bytes() { return sizeof(C) * (3 * (size_t)TILE + N) + 64; }
+};
+
+template <typename C, int N, int B>
+__device__ __forceinline__ void zc_issue(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
+                                         int ky, int b) {
+  using Z = ZCorr<C, N, B>;
+  tma::mbar_arrive_expect_tx(bar, Z::TILE_BYTES);
+#pragma unroll
+  for (int z0 = 0; z0 < N; z0 += Z::ZB) tma::load_4d(dst + z0 * B, map, bar, kx0 * Z::E, ky, z0, b);
+}
+
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ZCorr<C, N, B>::THREADS, 1)
+k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mF,
+             int nb, int gg, int w, C* __restrict__ Wz, int64_t Wz_stride, int P,
+             const C* __restrict__ tw, int* __restrict__ err) {
+  using Z = ZCorr<C, N, B>;
+  using RT = typename Real<C>::T;
+  constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1;
+  constexpr uint64_t kLimitNs = 2000000000ull;   // 2 s per wait
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* const sbuf0 = reinterpret_cast<C*>(smem_raw);   // mesh buffers: sbuf0 + k * TILE
+  C* ftile = sbuf0 + 2 * TILE;
+  C* tws = ftile + TILE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);   // [0], [1]: mesh buffers, [2]: F_g
+  const int T = (M1 + B - 1) / B;
+  const int64_t n_items = (int64_t)T * N;
+  int64_t item = blockIdx.x;
+  if (item >= n_items) return;   // whole CTA
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::mbar_init(&bar[2], 1);
+    tma::fence_async_shared();
+    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
+    zc_issue<C, N, B>(ftile, &mF, &bar[2], kx0, ky, 0);
+    if (!gg) zc_issue<C, N, B>(sbuf0, &mS, &bar[0], kx0, ky, 0);
+  }
+  __syncthreads();
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  const RT inv_n3 = (RT)(1.0 / ((double)N * (double)N * (double)N));
+  uint32_t ph[3] = {0, 0, 0};
+  int64_t job = 0;
+  int failed = 0;
+  for (; item < n_items && !failed; item += gridDim.x) {
+    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
+    const int ncol = min(B, M1 - kx0);
+    if (__syncthreads_or(!tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
+    ph[2] ^= 1;
+    const bool dc_col = (kx0 + c == 0) && (ky == 0);
+    for (int b = 0; b < nb; ++b, ++job) {
+      const int cur = (int)(job & 1);
+      C* buf = sbuf0 + cur * TILE;
+      if (!gg && threadIdx.x == 0) {   // prefetch the next job's tile
+        int nbb = b + 1;
+        int64_t nitem = item;
+        if (nbb == nb) { nbb = 0; nitem = item + gridDim.x; }
+        if (nitem < n_items) {
+          tma::fence_async_shared();
+          zc_issue<C, N, B>(sbuf0 + (cur ^ 1) * TILE, &mS, &bar[cur ^ 1], (int)(nitem % T) * B,
+                            (int)(nitem / T), nbb);
+        }
+      }
+      C a[N2];
+      if (!gg) {
+        if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
+        ph[cur] ^= 1;
+        step1<C, N1, N2, B, false>(buf, B, tws, 1);
+        __syncthreads();
+        step2<C, N1, N2, false>(buf, B, c, k1, a);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+          const C g = ftile[(k1 + N1 * k2) * B + c];
+          a[k2] = cscale(cmulc(a[k2], g), inv_n3);
+        }
+      } else {
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+          const C g = ftile[(k1 + N1 * k2) * B + c];
+          a[k2].x = (g.x * g.x + g.y * g.y) * inv_n3;
+          a[k2].y = 0;
+        }
+      }
+      if (dc_col && k1 == 0) { a[0].x = 0; a[0].y = 0; }   // k = 0 mode
+      __syncthreads();
+      // after the last mesh of this item the galaxy tile is free: fetch the next
+      if (b == nb - 1 && threadIdx.x == 0 && item + gridDim.x < n_items) {
+        const int64_t nitem = item + gridDim.x;
+        tma::fence_async_shared();
+        zc_issue<C, N, B>(ftile, &mF, &bar[2], (int)(nitem % T) * B, (int)(nitem / T), 0);
+      }
+      C* wbuf = gg ? sbuf0 : buf;
+      stepA<C, N1, N2, true>(wbuf, B, c, k1, a, tws, 1);
+      __syncthreads();
+      C* wout = Wz + (int64_t)b * Wz_stride + (int64_t)ky * P + kx0;
+      for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+        const int cc = t % B, n2 = t / B;
+        C x[N1];
+        stepB<C, N1, N2, true>(wbuf, B, cc, n2, x);
+        if (cc < ncol) {
+#pragma unroll
+          for (int n1 = 0; n1 < N1; ++n1) {
+            const int zw = win_index(n2 + N2 * n1, N, w);
+            if (zw >= 0) wout[(int64_t)zw * N * P + cc] = x[n1];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, tma::kErrTmaTimeout);
+      // let copies still in flight land before the CTA exits (bounded)
+      for (int k = 0; k < 3; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
+    }
+    __syncthreads();
   }
 }
 
