@@ -401,7 +401,7 @@ cudaError_t correlate_window(pg_plan* p, int nb, bool gg, double* sums, cudaStre
   {
     ProfScope ps(p, PG_FAM_FFT_Y_INV, s, nb * (W * N * M1 * cs + W * W * M1 * cs));
     PG_CUDA_TRY(FftPasses<R>::y_inv_win(p->N, nb, p->Wz.as<C>(), Wz_stride, p->w, p->Wy.as<C>(),
-                                        Wy_stride, p->P, tw, s));
+                                        Wy_stride, p->P, tw, p->flag.as<int32_t>() + 1, s));
   }
   {
     ProfScope ps(p, PG_FAM_FFT_X_C2R, s, nb * (W * W * M1 * cs + W * W * W * (double)sizeof(R)));
@@ -677,7 +677,12 @@ pg_status pg_plan_create(const pg_params* prm, pg_plan** out) {
   cudaGetDevice(&p->device);
   p->N = q.mesh_n;
   p->M1 = p->N / 2 + 1;
-  p->P = p->N / 2 + 2;
+  // row pitch: a multiple of 64 bytes, so that every 64-byte tile row a TMA
+  // box reads is one aligned DRAM access
+  {
+    const int per64 = q.precision ? 4 : 8;   // complex elements per 64 bytes
+    p->P = (p->M1 + per64 - 1) / per64 * per64;
+  }
   p->dx = q.box_L / (double)q.mesh_n;
   const double r_max = q.r_edges[q.n_r];
   p->w = (int)ceil(r_max / p->dx);

@@ -128,15 +128,29 @@ cudaError_t FftPasses<R>::z_corr(int N, int nb, const C* S, int64_t S_stride, co
 
 template <typename R>
 cudaError_t FftPasses<R>::y_inv_win(int N, int nb, const C* Wz, int64_t Wz_stride, int w, C* Wy,
-                                    int64_t Wy_stride, int P, const C* tw, cudaStream_t s) {
+                                    int64_t Wy_stride, int P, const C* tw, int* err,
+                                    cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  constexpr int B = fft::Cols<R>::B;
+  constexpr int B = fft::ZCols<R>::B;
+  constexpr int E = (int)(sizeof(C) / 8);
+  const int W = 2 * w + 1;
+  // Wz as [bin][zw][ky][kx] over 8-byte elements
+  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)W, (uint64_t)nb};
+  const uint64_t strides[3] = {(uint64_t)P * 8 * E, (uint64_t)N * P * 8 * E,
+                               (uint64_t)Wz_stride * 8 * E};
+  const uint32_t box[4] = {(uint32_t)(B * E), N < 256 ? (uint32_t)N : 256u, 1u, 1u};
+  CUtensorMap mW;
+  if (!encode_map_4d(&mW, Wz, dims, strides, box)) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  PG_CUDA_TRY(cudaGetDevice(&dev));
+  PG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   PG_DISPATCH_N(N, {
-    using CP = fft::ColPass<C, NN, B>;
-    auto k = fft::k_y_inv_win<C, NN, B>;
-    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
-    dim3 g((unsigned)cdiv(NN / 2 + 1, B), 2 * w + 1, nb);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(Wz, Wz_stride, w, Wy, Wy_stride, P, tw);
+    using Y = fft::YInv<C, NN, B>;
+    auto k = fft::k_y_inv_tma<C, NN, B>;
+    PG_CUDA_TRY(set_smem(k, Y::smem_bytes()));
+    const int64_t items = cdiv(NN / 2 + 1, B) * (int64_t)W * nb;
+    const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
+    k<<<grid, Y::THREADS, Y::smem_bytes(), s>>>(mW, nb, w, Wy, Wy_stride, P, tw, err);
   });
   return launched();
 }

@@ -751,5 +751,104 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
   }
 }
 
+// ============================================================================
+// Inverse y on the window rows, persistent and TMA fed. A work item is
+// (mesh b, window row zw, tile of B kx columns); its column over ky is
+// Wz[b][zw][0..N)[kx0..kx0+B). Items alternate between two shared buffers so
+// the next column streams in while the current one is transformed; only the
+// |y| <= w outputs are stored, to Wy[b][zw][yw][kx].
+// ============================================================================
+template <typename C, int N, int B>
+struct YInv {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int THREADS = B * N1;
+  static constexpr int TILE = N * B;
+  static constexpr int YB = N < 256 ? N : 256;   // rows per TMA box
+  static constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
+  static constexpr int E = sizeof(C) / 8;
+  static constexpr size_t smem_bytes() { return sizeof(C) * (2 * (size_t)TILE + N) + 64; }
+};
+
+template <typename C, int N, int B>
+__device__ __forceinline__ void yi_issue(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
+                                         int zw, int b) {
+  using Y = YInv<C, N, B>;
+  tma::mbar_arrive_expect_tx(bar, Y::TILE_BYTES);
+#pragma unroll
+  for (int y0 = 0; y0 < N; y0 += Y::YB) tma::load_4d(dst + y0 * B, map, bar, kx0 * Y::E, y0, zw, b);
+}
+
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(YInv<C, N, B>::THREADS, 1)
+k_y_inv_tma(const __grid_constant__ CUtensorMap mW, int nb, int w, C* __restrict__ Wy,
+            int64_t Wy_stride, int P, const C* __restrict__ tw, int* __restrict__ err) {
+  using Y = YInv<C, N, B>;
+  constexpr int N1 = Y::N1, N2 = Y::N2, TILE = Y::TILE, M1 = N / 2 + 1;
+  constexpr uint64_t kLimitNs = 2000000000ull;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* const buf0 = reinterpret_cast<C*>(smem_raw);   // buffers: buf0 + k * TILE
+  C* tws = buf0 + 2 * TILE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);
+  const int W = 2 * w + 1;
+  const int T = (M1 + B - 1) / B;
+  const int64_t n_items = (int64_t)T * W * nb;
+  int64_t item = blockIdx.x;
+  if (item >= n_items) return;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
+  auto decode = [&](int64_t it, int& kx0, int& zw, int& b) {
+    kx0 = (int)(it % T) * B;
+    const int64_t r = it / T;
+    zw = (int)(r % W);
+    b = (int)(r / W);
+  };
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::fence_async_shared();
+    int kx0, zw, b;
+    decode(item, kx0, zw, b);
+    yi_issue<C, N, B>(buf0, &mW, &bar[0], kx0, zw, b);
+  }
+  __syncthreads();
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  uint32_t ph[2] = {0, 0};
+  int failed = 0;
+  for (int64_t job = 0; item < n_items; item += gridDim.x, ++job) {
+    const int cur = (int)(job & 1);
+    C* buf = buf0 + cur * TILE;
+    if (threadIdx.x == 0 && item + gridDim.x < n_items) {
+      int kx0n, zwn, bn;
+      decode(item + gridDim.x, kx0n, zwn, bn);
+      tma::fence_async_shared();
+      yi_issue<C, N, B>(buf0 + (cur ^ 1) * TILE, &mW, &bar[cur ^ 1], kx0n, zwn, bn);
+    }
+    if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
+    ph[cur] ^= 1;
+    int kx0, zw, b;
+    decode(item, kx0, zw, b);
+    const int ncol = min(B, M1 - kx0);
+    step1<C, N1, N2, B, true>(buf, B, tws, 1);
+    __syncthreads();
+    C a[N2];
+    step2<C, N1, N2, true>(buf, B, c, k1, a);
+    if (c < ncol) {
+      C* out = Wy + (int64_t)b * Wy_stride + (int64_t)zw * W * P + kx0 + c;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int yw = win_index(k1 + N1 * k2, N, w);
+        if (yw >= 0) out[(int64_t)yw * P] = a[k2];
+      }
+    }
+    __syncthreads();   // buffer free for the prefetch two items ahead
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, tma::kErrTmaTimeout);
+      for (int k = 0; k < 2; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace fft
 }  // namespace pg

@@ -168,7 +168,7 @@ struct FftPasses {
                             int* err, cudaStream_t s);
   // Inverse y on the window rows: Wz[b][zw][ky] -> Wy[b][zw][yw], |y| <= w.
   static cudaError_t y_inv_win(int N, int nb, const C* Wz, int64_t Wz_stride, int w, C* Wy,
-                               int64_t Wy_stride, int P, const C* tw, cudaStream_t s);
+                               int64_t Wy_stride, int P, const C* tw, int* err, cudaStream_t s);
   // Inverse x (C2R) on the window lines, x offsets |x| <= w, times `scale`:
   // Cwin[b] = [zw][yw][xw] real, (2w+1)^3 per mesh.
   static cudaError_t x_c2r_win(int N, int nb, const C* Wy, int64_t Wy_stride, int w,
