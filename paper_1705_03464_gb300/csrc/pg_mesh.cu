@@ -56,15 +56,15 @@ __device__ __forceinline__ unsigned long long node_q(const DepGeom& g, double w,
   return (unsigned long long)__double2ll_rn(__dmul_rn(v, 4294967296.0));
 }
 
-__constant__ DepGeom c_dep;
+// The mesh geometry travels by value as a kernel argument, so plans with
+// different meshes can run concurrently on separate streams.
 
 __global__ void __launch_bounds__(kThreads)
-k_mark_lines(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+k_mark_lines(DepGeom g, int64_t n, const double* __restrict__ x, const double* __restrict__ y,
              const double* __restrict__ z, const int32_t* __restrict__ pbin, int bin0,
              uint8_t* __restrict__ flags) {
   int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (p >= n) return;
-  const DepGeom& g = c_dep;
   Foot f;
   footprint(g, x[p], y[p], z[p], f);
   const int b = pbin ? pbin[p] - bin0 : 0;
@@ -97,7 +97,7 @@ __global__ void k_line_bases(int nb, const int64_t* __restrict__ seg_total,
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_deposit_lines(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+k_deposit_lines(DepGeom g, int64_t n, const double* __restrict__ x, const double* __restrict__ y,
                 const double* __restrict__ z, const double* __restrict__ w,
                 const int32_t* __restrict__ pbin, int bin0, const int32_t* __restrict__ idx,
                 const int64_t* __restrict__ line_base, unsigned long long* __restrict__ lines_q,
@@ -106,7 +106,6 @@ k_deposit_lines(int64_t n, const double* __restrict__ x, const double* __restric
   for (int t = threadIdx.x; t < kMaxBatch; t += kThreads) sh_q[t] = 0ull;
   __syncthreads();
   int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  const DepGeom& g = c_dep;
   if (p < n) {
     Foot f;
     footprint(g, x[p], y[p], z[p], f);
@@ -135,11 +134,10 @@ k_deposit_lines(int64_t n, const double* __restrict__ x, const double* __restric
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_deposit_dense(int64_t n, const double* __restrict__ aos, const double* __restrict__ w,
+k_deposit_dense(DepGeom g, int64_t n, const double* __restrict__ aos, const double* __restrict__ w,
                 unsigned long long* __restrict__ mesh) {
   int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (p >= n) return;
-  const DepGeom& g = c_dep;
   Foot f;
   footprint(g, aos[3 * p], aos[3 * p + 1], aos[3 * p + 2], f);
   const double wp = w ? w[p] : 1.0;
@@ -166,9 +164,8 @@ __global__ void k_field_scale(int nb, const unsigned long long* __restrict__ qsu
 cudaError_t launch_mark_lines(const DepGeom& g, int64_t n, const double* x, const double* y,
                               const double* z, const int32_t* pbin, int bin0, uint8_t* flags,
                               cudaStream_t s) {
-  PG_CUDA_TRY(cudaMemcpyToSymbolAsync(c_dep, &g, sizeof(DepGeom), 0, cudaMemcpyHostToDevice, s));
   if (n <= 0) return cudaSuccess;
-  k_mark_lines<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(n, x, y, z, pbin, bin0, flags);
+  k_mark_lines<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(g, n, x, y, z, pbin, bin0, flags);
   return launched();
 }
 
@@ -191,18 +188,16 @@ cudaError_t launch_deposit_lines(const DepGeom& g, int64_t n, const double* x, c
                                  const int32_t* idx, const int64_t* line_base,
                                  unsigned long long* lines_q, unsigned long long* qsum,
                                  cudaStream_t s) {
-  PG_CUDA_TRY(cudaMemcpyToSymbolAsync(c_dep, &g, sizeof(DepGeom), 0, cudaMemcpyHostToDevice, s));
   if (n <= 0) return cudaSuccess;
-  k_deposit_lines<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(n, x, y, z, w, pbin, bin0, idx,
+  k_deposit_lines<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(g, n, x, y, z, w, pbin, bin0, idx,
                                                                      line_base, lines_q, qsum);
   return launched();
 }
 
 cudaError_t launch_deposit_dense(const DepGeom& g, int64_t n, const double* aos, const double* w,
                                  unsigned long long* mesh, cudaStream_t s) {
-  PG_CUDA_TRY(cudaMemcpyToSymbolAsync(c_dep, &g, sizeof(DepGeom), 0, cudaMemcpyHostToDevice, s));
   if (n <= 0) return cudaSuccess;
-  k_deposit_dense<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(n, aos, w, mesh);
+  k_deposit_dense<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(g, n, aos, w, mesh);
   return launched();
 }
 

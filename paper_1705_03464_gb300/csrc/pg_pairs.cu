@@ -129,7 +129,8 @@ k_cell_gather(int64_t n, const int32_t* __restrict__ perm, const double* __restr
 
 // ---- pair enumeration ---------------------------------------------------------
 
-__constant__ PairGeom c_geom;
+// The pair geometry (box, cells, squared s edges) travels by value as a kernel
+// argument, so plans with different binning can run concurrently.
 
 __device__ __forceinline__ double min_image(double d, double L, double h) {
   if (d > h) d = __dsub_rn(d, L);
@@ -144,9 +145,8 @@ struct PairHit {
 };
 
 // Evaluates one unordered pair (orientation from input indices i < j).
-__device__ __forceinline__ bool eval_pair(const CellList& cl, bool use_w, int a, int b,
-                                          PairHit& h) {
-  const PairGeom& g = c_geom;
+__device__ __forceinline__ bool eval_pair(const PairGeom& g, const CellList& cl, bool use_w,
+                                          int a, int b, PairHit& h) {
   int oa = cl.perm[a], ob = cl.perm[b];
   int pi = a, pj = b;
   if (oa > ob) { pi = b; pj = a; int t = oa; oa = ob; ob = t; }
@@ -181,9 +181,9 @@ __device__ __forceinline__ unsigned long long q32(double w) {
 // with a ballot and appended with one atomic per warp and step.
 template <bool FILL>
 __global__ void __launch_bounds__(kThreads)
-k_pairs(int64_t n, CellList cl, bool use_w, PairOut po, int use_smem_hist) {
+k_pairs(const __grid_constant__ PairGeom g, int64_t n, CellList cl, bool use_w, PairOut po,
+        int use_smem_hist) {
   extern __shared__ unsigned long long hist[];   // [2 * P] when use_smem_hist
-  const PairGeom& g = c_geom;
   const int P = g.n_s * g.n_mu;
   if (!FILL && use_smem_hist) {
     for (int t = threadIdx.x; t < 2 * P; t += blockDim.x) hist[t] = 0ull;
@@ -221,7 +221,7 @@ k_pairs(int64_t n, CellList cl, bool use_w, PairOut po, int use_smem_hist) {
     for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
     for (int u = 0; u < maxlen; ++u) {
       PairHit h;
-      bool hit = (u < len) && eval_pair(cl, use_w, (int)a, b0 + u, h);
+      bool hit = (u < len) && eval_pair(g, cl, use_w, (int)a, b0 + u, h);
       if (!FILL) {
         if (hit) {
           unsigned long long q = q32(h.wp);
@@ -327,16 +327,15 @@ cudaError_t launch_cells(const PairGeom& g, int64_t n, const double* x, const do
 
 cudaError_t launch_pairs(const PairGeom& g, int64_t n, const CellList& cl, bool use_w, bool fill,
                          PairOut& po, cudaStream_t s) {
-  PG_CUDA_TRY(cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(PairGeom), 0, cudaMemcpyHostToDevice, s));
   if (n <= 1) return cudaSuccess;
   const int P = g.n_s * g.n_mu;
   unsigned grid = (unsigned)cdiv(n, kThreads);
   if (fill) {
-    k_pairs<true><<<grid, kThreads, 0, s>>>(n, cl, use_w, po, 0);
+    k_pairs<true><<<grid, kThreads, 0, s>>>(g, n, cl, use_w, po, 0);
   } else {
     size_t sm = sizeof(unsigned long long) * 2 * P;
     int use = sm <= 48 * 1024 ? 1 : 0;
-    k_pairs<false><<<grid, kThreads, use ? sm : 0, s>>>(n, cl, use_w, po, use);
+    k_pairs<false><<<grid, kThreads, use ? sm : 0, s>>>(g, n, cl, use_w, po, use);
   }
   return launched();
 }
