@@ -194,6 +194,28 @@ pg_status pg_fft_r2c_3d(pg_plan* plan, const void* d_in, void* d_out, void* stre
  * over the Hermitian-completed spectrum. d_in is not modified. */
 pg_status pg_fft_c2r_3d(pg_plan* plan, const void* d_in, void* d_out, void* stream);
 
+/* Pair counts DD(s, mu) of one catalogue, like the counts of pg_find_pairs,
+ * for callers that cannot allocate device memory: code running under a
+ * framework whose caching allocator owns the whole device budget, or a
+ * latency-critical host thread that must not take the device-wide
+ * synchronisation cudaMalloc / cudaFree can cause. This call allocates
+ * nothing and needs no plan: its cell-list scratch is a fixed array of about
+ * 8.4 MB compiled into the library, which every GPU that loads the library
+ * holds until the process exits. (The paper has no counterpart; this is a
+ * deployment variant of the pair enumeration.)
+ *   n <= 131072 galaxies, else PG_ERR_CAPACITY. d_pos [n][3] FP64 device,
+ *   already inside [0, L); d_w [n] FP32 device or NULL; s_edges [n_s+1] host,
+ *   ascending, s_edges[n_s] < box_L/2; d_dd, d_ddq [n_s*n_mu] int64 device
+ *   outputs (zeroed by the call): pair counts and sums of
+ *   llrint(w_i w_j 2^32). Asynchronous on `stream`.
+ * The first call on a device looks up the scratch array's device address for
+ * that device; make that first call before any stream capture. All calls
+ * share the one array, so calls that overlap on the GPU (different streams or
+ * host threads) race and must be serialised by the caller. */
+pg_status pg_pair_counts_static(int64_t n, const double* d_pos, const float* d_w,
+                                double box_L, int32_t n_s, const double* s_edges,
+                                int32_t n_mu, int64_t* d_dd, int64_t* d_ddq, void* stream);
+
 /* ---- measurement ---------------------------------------------------------- */
 
 /* Kernel families of the path, in the order of pg_plan_last_stats. */

@@ -79,6 +79,7 @@ def _load():
         "pg_deposit_dense": (C.c_int, [i64, vp, vp, dbl, i32, i32, vp, vp]),
         "pg_fft_r2c_3d": (C.c_int, [vp, vp, vp, vp]),
         "pg_fft_c2r_3d": (C.c_int, [vp, vp, vp, vp]),
+        "pg_pair_counts_static": (C.c_int, [i64, vp, vp, dbl, i32, vp, i32, vp, vp, vp]),
         "pg_plan_set_profiling": (C.c_int, [vp, i32]),
         "pg_plan_last_stats": (C.c_int, [vp, vp, vp]),
     }
@@ -303,3 +304,19 @@ def pg_correlate_points(plan: Plan, pts_a, w_a, pts_b, w_b, stream=None):
                                   _ptr(agg), _ptr(nc), _stream(stream))
     _check(st, "pg_correlate_points")
     return {"sum": s1, "sum2": s2, "agg": agg, "n_cells": nc}
+
+
+def pg_pair_counts_static(pos, w, box_L, s_edges, n_mu, stream=None):
+    """Pair counts (dd, ddq) from the allocation-free entry point; the call
+    itself allocates no device memory (the two output tensors are created
+    here, by torch, before the call)."""
+    import torch
+    edges = np.ascontiguousarray(s_edges, dtype=np.float64)
+    P = (len(edges) - 1) * int(n_mu)
+    dd = torch.empty(P, dtype=torch.int64, device=pos.device)
+    ddq = torch.empty(P, dtype=torch.int64, device=pos.device)
+    st = _lib.pg_pair_counts_static(int(pos.shape[0]), _ptr(pos), _ptr(w), float(box_L),
+                                    len(edges) - 1, _ptr(edges), int(n_mu), _ptr(dd), _ptr(ddq),
+                                    _stream(stream))
+    _check(st, "pg_pair_counts_static")
+    return dd, ddq
