@@ -54,20 +54,22 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_family, workload):
-    """DRAM bytes per launch of one kernel family from the committed ncu
-    summary (profiles/ncu_traffic.txt: 'family workload bytes_per_launch
-    source_hash'), or None."""
+def ncu_traffic(kernel_family, workload, algorithmic_bytes_per_launch):
+    """DRAM bytes per launch of one kernel family, from the committed ncu
+    summary (profiles/ncu_traffic.txt: 'family workload ratio:R source'): the
+    measured dram read+write bytes over the algorithmic bytes of the captured
+    launch, applied to this launch's algorithmic bytes. None if absent."""
     path = os.path.join(HERE, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel_family and parts[1] == workload:
-            try:
-                return float(parts[2])
-            except ValueError:
-                return None
+            if parts[2].startswith("ratio:"):
+                try:
+                    return float(parts[2][6:]) * algorithmic_bytes_per_launch
+                except ValueError:
+                    return None
     return None
 
 
@@ -299,7 +301,7 @@ def main():
     peak, peak_src = peaks()
     top = max(fam_ms, key=lambda k: fam_ms[k])
     achieved = fam_bytes[top] / (fam_ms[top] * 1e-3) / 1e9 if fam_ms[top] > 0 else None
-    traffic = ncu_traffic(top, wl.name)
+    traffic = ncu_traffic(top, wl.name, fam_bytes[top] / max(1, fam_launch[top]))
     roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": traffic, "peak_source": peak_src,
