@@ -134,6 +134,23 @@ pg_status pg_forward_host(pg_plan* plan, int64_t n_gal, const double* h_pos,
                           const float* h_vel, const float* h_w,
                           pg_result* host_out, void* stream);
 
+/* Adjoint of the last successful pg_forward / pg_forward_host call on this
+ * plan (same catalogue, still held in the plan's buffers): with the upstream
+ * gradients in *grad_out (HOST arrays in the pg_result layout; the fields
+ * xi_pg, xi_gg, b_pg, q_eff, q_eff_sq, xi_dw, b_pg_agg, q_eff_agg, xi_dw_agg,
+ * xi_ss, dd_w are read, NULL means zero, other fields are ignored), writes
+ * d_grad_w[n_gal] (device FP64) = dL/dw_i for L = sum over fields and bins of
+ * grad * output, outputs that are NaN contributing nothing. The reverse sweep
+ * follows the forward definitions (Sec. 2.1 eqs. bpg_initial /
+ * bpg_intermediate, Sec. 2.2 eqs. xi_dw, Qeff, Qeff_notsq, Sec. 3.4): ratio
+ * outputs -> bin sums -> window fields -> mesh adjoints by FFT correlation ->
+ * pair and galaxy weights -> w_i through w_p = w_i w_j. The galaxy and pair
+ * spectra are recomputed, not stored. Without weights in the forward call the
+ * gradient is taken at w = 1. Errors: PG_ERR_INVALID_ARG if no forward call
+ * preceded (or a stage entry point reused the plan since), PG_ERR_OOM,
+ * PG_ERR_CUDA, PG_ERR_TIMEOUT. Synchronises the stream. */
+pg_status pg_backward(pg_plan* plan, const pg_result* grad_out, double* d_grad_w, void* stream);
+
 /* Low-level form of the estimator for two arbitrary point sets (Sec. 2.1,
  * eq. bpg_initial): deposits set a and set b, correlates them, and bins
  * C_ab(r) = (1/N^3) sum_x delta_b(x) delta_a(x + r) by (r, mu_r).

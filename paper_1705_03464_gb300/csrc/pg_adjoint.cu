@@ -1,0 +1,360 @@
+// Adjoint of the forward path with respect to per-galaxy weights w_i.
+//
+// With w_p = w_i w_j for a pair, rho_b = sum_p w_p K(. - m_p), rho_g =
+// sum_j w_j K(. - x_j), f = rho N^3 / Q and C_b(r) = (1/N^3) sum_x f_g(x)
+// f_b(x + r) - 1 (Sec. 2.1, eqs. bpg_initial / bpg_intermediate), the
+// reverse sweep is: ratio outputs -> bin sums S[b][q], G[q], G2[q], DD, sum w,
+// sum w^2 (k_adjoint_ratios) -> a window field Cbar(r) per mesh
+// (k_window_field) -> mesh adjoints by FFT correlation (the FFT passes) ->
+// rho adjoints (normalisation) -> w_p and w_j by interpolating the mesh
+// adjoint at the points with the deposit's node weights (k_gather_*) ->
+// w_i = chain through w_p = w_i w_j (k_pair_chain). All scalars are FP64.
+#include <math.h>
+
+#include <algorithm>
+
+#include "pg_internal.cuh"
+
+namespace pg {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double gate(const double* g, const double* out, int64_t i) {
+  // upstream gradient of an output, zero where the forward output is not finite
+  if (!g) return 0.0;
+  const double v = out[i];
+  return isfinite(v) ? g[i] : 0.0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_adjoint_ratios(AdjRatioArgs a) {
+  const int P = a.P, Q = a.Q, L = Q + 1;
+  const double sw = a.wsum[0], sw2 = a.wsum[1];
+  const double npairs = 0.5 * (sw * sw - sw2);
+  const double L3 = a.L * a.L * a.L;
+  auto rr_of = [&](int p) {
+    const int ks = p / a.n_mu;
+    const double lo = a.s_edges[ks], hi = a.s_edges[ks + 1];
+    return npairs * ((4.0 * M_PI / 3.0) * (hi * hi * hi - lo * lo * lo) / (double)a.n_mu) / L3;
+  };
+  auto ddw_of = [&](int p) { return (double)(long long)a.ddq[p] * (1.0 / 4294967296.0); };
+  const double* S = a.sum_pg;   // [P][L][2]
+  const double* Gs = a.sum_gg;  // [L][2]
+  // per (pair bin, list): contributions
+  for (int t = threadIdx.x; t < P * L; t += kThreads) {
+    const int p = t / L, q = t % L;
+    double sb = 0.0, dg = 0.0, dg2 = 0.0, dx = 0.0;
+    const int64_t n = a.list_off[q + 1] - a.list_off[q];
+    const double G = Gs[2 * q], G2 = Gs[2 * q + 1];
+    if (a.pg_valid[p] && a.gg_valid && n > 0 && G != 0.0) {
+      const double s = S[((int64_t)p * L + q) * 2];
+      const double x = ddw_of(p) / rr_of(p) - 1.0;
+      const double bb = s / G, xw = G2 / G;
+      const double den = 2.0 * x + 1.5 * xw;
+      const double num = (1.0 + x) * bb - 2.0 - xw / (2.0 * x);
+      if (q < Q) {
+        const int64_t o = (int64_t)p * Q + q;
+        const double gq = gate(a.g.q_eff, a.o.q_eff, o), gs = gate(a.g.q_eff_sq, a.o.q_eff_sq, o);
+        // terms of an output whose gradient is zero are skipped (they may be 0 * inf)
+        double dbb = gate(a.g.b_pg, a.o.b_pg, o), dxw = 0.0;
+        if (gq != 0.0) {
+          dbb += gq * (1.0 + x) / den;
+          dx += gq * ((bb + xw / (2.0 * x * x)) / den - 2.0 * num / (den * den));
+          dxw += gq * (-1.0 / (2.0 * x) / den - 1.5 * num / (den * den));
+        }
+        if (gs != 0.0) {
+          dbb += gs * (1.0 + x) / (2.0 * x);
+          dx += gs * (bb / (2.0 * x) - ((1.0 + x) * bb - 2.0) / (2.0 * x * x));
+        }
+        sb = gate(a.g.xi_pg, a.o.xi_pg, o) / (double)n + dbb / G;
+        dg = -dbb * s / (G * G) - dxw * G2 / (G * G);
+        dg2 = dxw / G;
+      } else {
+        const double ga = gate(a.g.q_eff_agg, a.o.q_eff_agg, p);
+        double dba = gate(a.g.b_pg_agg, a.o.b_pg_agg, p), dxwa = 0.0;
+        if (ga != 0.0) {
+          dba += ga * (1.0 + x) / den;
+          dx = ga * ((bb + xw / (2.0 * x * x)) / den - 2.0 * num / (den * den));
+          dxwa = ga * (-1.0 / (2.0 * x) / den - 1.5 * num / (den * den));
+        }
+        sb = dba / G;
+        dg = -dba * s / (G * G) - dxwa * G2 / (G * G);
+        dg2 = dxwa / G;
+      }
+    }
+    a.Sbar[t] = sb;
+    a.tmp[3 * (int64_t)t] = dg;
+    a.tmp[3 * (int64_t)t + 1] = dg2;
+    a.tmp[3 * (int64_t)t + 2] = dx;
+  }
+  __syncthreads();
+  // galaxy sums: reduce over pair bins (fixed order)
+  for (int q = threadIdx.x; q < L; q += kThreads) {
+    const int64_t n = a.list_off[q + 1] - a.list_off[q];
+    const double G = Gs[2 * q], G2 = Gs[2 * q + 1];
+    double gb = 0.0, g2b = 0.0;
+    for (int p = 0; p < P; ++p) {
+      gb += a.tmp[3 * ((int64_t)p * L + q)];
+      g2b += a.tmp[3 * ((int64_t)p * L + q) + 1];
+    }
+    if (a.gg_valid && n > 0 && G != 0.0) {
+      if (q < Q) {
+        const double gx = gate(a.g.xi_dw, a.o.xi_dw, q);
+        gb += gate(a.g.xi_gg, a.o.xi_gg, q) / (double)n - gx * G2 / (G * G);
+        g2b += gx / G;
+      } else {
+        const double gx = gate(a.g.xi_dw_agg, a.o.xi_dw_agg, 0);
+        gb += -gx * G2 / (G * G);
+        g2b += gx / G;
+      }
+    }
+    a.Gbar[q] = gb;
+    a.G2bar[q] = g2b;
+  }
+  // pair counts and the RR normalisation
+  __shared__ double red[kThreads];
+  double npb = 0.0;
+  for (int p = threadIdx.x; p < P; p += kThreads) {
+    double xsb = gate(a.g.xi_ss, a.o.xi_ss, p);
+    for (int q = 0; q < L; ++q) xsb += a.tmp[3 * ((int64_t)p * L + q) + 2];
+    const double rr = rr_of(p), ddw = ddw_of(p);
+    const double ddb = gate(a.g.dd_w, a.o.dd_w, p) + (rr > 0.0 ? xsb / rr : 0.0);
+    a.DDbar[p] = ddb;
+    if (rr > 0.0) {
+      const int ks = p / a.n_mu;
+      const double lo = a.s_edges[ks], hi = a.s_edges[ks + 1];
+      const double vb = (4.0 * M_PI / 3.0) * (hi * hi * hi - lo * lo * lo) / (double)a.n_mu;
+      npb += (-xsb * ddw / (rr * rr)) * vb / L3;
+    }
+  }
+  red[threadIdx.x] = npb;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.wsbar[0] = red[0] * sw;     // d/d(sum w)
+    a.wsbar[1] = -0.5 * red[0];   // d/d(sum w^2)
+  }
+}
+
+// Window adjoint field laid out as the W^2 x-lines of the window, in mesh
+// order of (z, y); a line of N reals holds Cbar at x offsets |x| <= w (mesh
+// index x mod N) and zeros elsewhere.
+//   pair mode:  Cbar(r) = Sbar[q(r)] + agg(r) Sbar[Q]
+//   gg mode:    Cbar(r) = Gbar[q] + 2 C_gg(r) G2bar[q] + agg(r) (Gbar[Q] + 2 C_gg(r) G2bar[Q])
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_window_field(int N, int w, const int32_t* __restrict__ cell_bin, const uint8_t* __restrict__ cell_agg,
+               int Q, const double* __restrict__ sbar, const double* __restrict__ gbar,
+               const double* __restrict__ g2bar, const R* __restrict__ cgg, R* __restrict__ lines) {
+  const int W = 2 * w + 1;
+  const int64_t total = (int64_t)W * W * N;
+  for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * kThreads) {
+    const int64_t line = t / N;
+    const int x = (int)(t % N);
+    const int ox = x <= N / 2 ? x : x - N;
+    double v = 0.0;
+    if (ox >= -w && ox <= w) {
+      // lines are in mesh order (z, then y): rank r <= w is offset r, rank
+      // r > w is offset r - W; window coordinate = offset + w
+      const int rz = (int)(line / W), ry = (int)(line % W);
+      const int zw = rz <= w ? rz + w : rz - w - 1;
+      const int yw = ry <= w ? ry + w : ry - w - 1;
+      const int64_t cell = ((int64_t)zw * W + yw) * W + (ox + w);
+      const int q = cell_bin[cell];
+      const bool ag = cell_agg[cell] != 0;
+      if (!gbar) {
+        if (q >= 0) v += sbar[q];
+        if (ag) v += sbar[Q];
+      } else {
+        const double c = (double)cgg[cell];
+        if (q >= 0) v += gbar[q] + 2.0 * c * g2bar[q];
+        if (ag) v += gbar[Q] + 2.0 * c * g2bar[Q];
+      }
+    }
+    lines[t] = (R)v;
+  }
+}
+
+// A = 2 Re(X) F_g over the half spectrum (the galaxy auto-correlation term).
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+k_acc_gg(int64_t n, const C* __restrict__ X, const C* __restrict__ Fg, C* __restrict__ A) {
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    const C x = X[i], g = Fg[i];
+    C o;
+    o.x = 2 * x.x * g.x;
+    o.y = 2 * x.x * g.y;
+    A[i] = o;
+  }
+}
+
+// Interpolation of a mesh adjoint held as compact real lines at points, with
+// the deposit's node weights (unrounded): g[k] = sum_nodes K * field(node).
+// Also the partial sums of w[k] * g[k] per block.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_gather(DepGeom geo, int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+         const double* __restrict__ z, const double* __restrict__ wt,
+         const int32_t* __restrict__ idx, const R* __restrict__ lines, double* __restrict__ g,
+         double* __restrict__ partial) {
+  const int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  double v = 0.0, wv = 0.0;
+  if (k < n) {
+    const int N = geo.N;
+    const double u[3] = {x[k] / geo.dx, y[k] / geo.dx, z[k] / geo.dx};
+    int i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+      if (geo.assign == 0) {
+        i0[a] = ((int)floor(u[a] + 0.5)) % N;
+        f[a] = 0.0;
+      } else {
+        const double fl = floor(u[a]);
+        i0[a] = ((int)fl) % N;
+        f[a] = u[a] - fl;
+      }
+      if (i0[a] < 0) i0[a] += N;
+    }
+    const int nn = geo.assign == 0 ? 1 : 2;
+    for (int cz = 0; cz < nn; ++cz)
+      for (int cy = 0; cy < nn; ++cy) {
+        const int iz = (i0[2] + cz) % N, iy = (i0[1] + cy) % N;
+        const int64_t line = idx[(int64_t)iz * N + iy];
+        const double kz = geo.assign == 0 ? 1.0 : (cz ? f[2] : 1.0 - f[2]);
+        const double ky = geo.assign == 0 ? 1.0 : (cy ? f[1] : 1.0 - f[1]);
+        for (int cx = 0; cx < nn; ++cx) {
+          const int ix = (i0[0] + cx) % N;
+          const double kx = geo.assign == 0 ? 1.0 : (cx ? f[0] : 1.0 - f[0]);
+          v += kx * ky * kz * (double)lines[line * N + ix];
+        }
+      }
+    g[k] = v;
+    wv = (wt ? wt[k] : 1.0) * v;
+  }
+  __shared__ double red[kThreads];
+  red[threadIdx.x] = wv;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_partials(int nblk, const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double red[kThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += kThreads) s += partial[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// w_p adjoint of the pairs of one mesh and its chain to the two galaxies:
+// wbar_p = (N^3/Q)(g_p - T/Q) + DDbar; wbar[i] += wbar_p w_j, wbar[j] += wbar_p w_i.
+__global__ void __launch_bounds__(kThreads)
+k_pair_chain(int64_t np, const double* __restrict__ g, const double* __restrict__ T,
+             const unsigned long long* __restrict__ qsum, double n3, const double* __restrict__ ddbar,
+             const int32_t* __restrict__ pi, const int32_t* __restrict__ pj,
+             const double* __restrict__ wgal, double* __restrict__ wbar) {
+  const int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (k >= np) return;
+  const double Q = (double)(long long)qsum[0] * (1.0 / 4294967296.0);
+  const double wp = (n3 / Q) * (g[k] - *T / Q) + *ddbar;
+  const int i = pi[k], j = pj[k];
+  const double wi = wgal ? wgal[i] : 1.0, wj = wgal ? wgal[j] : 1.0;
+  atomicAdd(&wbar[i], wp * wj);
+  atomicAdd(&wbar[j], wp * wi);
+}
+
+// Galaxy mesh term and the sum-w terms: wbar[j] += (N^3/Q)(g_j - T/Q)
+// + d/d(sum w) + 2 w_j d/d(sum w^2).
+__global__ void __launch_bounds__(kThreads)
+k_gal_final(int64_t n, const double* __restrict__ g, const double* __restrict__ T,
+            const unsigned long long* __restrict__ qsum, double n3,
+            const double* __restrict__ wsbar, const double* __restrict__ wgal,
+            double* __restrict__ wbar) {
+  const int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (k >= n) return;
+  const double Q = (double)(long long)qsum[0] * (1.0 / 4294967296.0);
+  const double wk = wgal ? wgal[k] : 1.0;
+  wbar[k] += (n3 / Q) * (g[k] - *T / Q) + wsbar[0] + 2.0 * wk * wsbar[1];
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint_ratios(const AdjRatioArgs& a, cudaStream_t s) {
+  k_adjoint_ratios<<<1, kThreads, 0, s>>>(a);
+  return launched();
+}
+
+template <typename R>
+cudaError_t launch_window_field(int N, int w, const int32_t* cell_bin, const uint8_t* cell_agg, int Q,
+                                const double* sbar, const double* gbar, const double* g2bar,
+                                const R* cgg, R* lines, cudaStream_t s) {
+  const int64_t total = (int64_t)(2 * w + 1) * (2 * w + 1) * N;
+  const unsigned grid = (unsigned)std::min<int64_t>(cdiv(total, kThreads), 65536);
+  k_window_field<R><<<grid, kThreads, 0, s>>>(N, w, cell_bin, cell_agg, Q, sbar, gbar, g2bar, cgg, lines);
+  return launched();
+}
+template cudaError_t launch_window_field<float>(int, int, const int32_t*, const uint8_t*, int, const double*,
+                                                const double*, const double*, const float*, float*, cudaStream_t);
+template cudaError_t launch_window_field<double>(int, int, const int32_t*, const uint8_t*, int, const double*,
+                                                 const double*, const double*, const double*, double*,
+                                                 cudaStream_t);
+
+template <typename R>
+cudaError_t launch_acc_gg(int64_t n, const typename CT<R>::C* X, const typename CT<R>::C* Fg,
+                          typename CT<R>::C* A, cudaStream_t s) {
+  const unsigned grid = (unsigned)std::min<int64_t>(cdiv(n, kThreads), 1 << 20);
+  k_acc_gg<typename CT<R>::C><<<grid, kThreads, 0, s>>>(n, X, Fg, A);
+  return launched();
+}
+template cudaError_t launch_acc_gg<float>(int64_t, const float2*, const float2*, float2*, cudaStream_t);
+template cudaError_t launch_acc_gg<double>(int64_t, const double2*, const double2*, double2*, cudaStream_t);
+
+template <typename R>
+cudaError_t launch_gather(const DepGeom& geo, int64_t n, const double* x, const double* y,
+                          const double* z, const double* wt, const int32_t* idx, const R* lines,
+                          double* g, double* partial, double* T, cudaStream_t s) {
+  if (n <= 0) return cudaMemsetAsync(T, 0, sizeof(double), s);
+  const unsigned nblk = (unsigned)cdiv(n, kThreads);
+  k_gather<R><<<nblk, kThreads, 0, s>>>(geo, n, x, y, z, wt, idx, lines, g, partial);
+  PG_CUDA_TRY(launched());
+  k_sum_partials<<<1, kThreads, 0, s>>>((int)nblk, partial, T);
+  return launched();
+}
+template cudaError_t launch_gather<float>(const DepGeom&, int64_t, const double*, const double*,
+                                          const double*, const double*, const int32_t*, const float*,
+                                          double*, double*, double*, cudaStream_t);
+template cudaError_t launch_gather<double>(const DepGeom&, int64_t, const double*, const double*,
+                                           const double*, const double*, const int32_t*,
+                                           const double*, double*, double*, double*, cudaStream_t);
+
+cudaError_t launch_pair_chain(int64_t np, const double* g, const double* T,
+                              const unsigned long long* qsum, double n3, const double* ddbar,
+                              const int32_t* pi, const int32_t* pj, const double* wgal,
+                              double* wbar, cudaStream_t s) {
+  if (np <= 0) return cudaSuccess;
+  k_pair_chain<<<(unsigned)cdiv(np, kThreads), kThreads, 0, s>>>(np, g, T, qsum, n3, ddbar, pi, pj,
+                                                                  wgal, wbar);
+  return launched();
+}
+
+cudaError_t launch_gal_final(int64_t n, const double* g, const double* T,
+                             const unsigned long long* qsum, double n3, const double* wsbar,
+                             const double* wgal, double* wbar, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_gal_final<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(n, g, T, qsum, n3, wsbar, wgal, wbar);
+  return launched();
+}
+
+}  // namespace pg

@@ -87,6 +87,14 @@ struct pg_plan {
   // meshes
   DevBuf flags, lidx, seg_total, line_base, n_lines, stmp, line_y, line_bin, lines_q, qsum, scale;
   DevBuf spec, S, Fg, Wz, Wy, Cwin, sums_pg, sums_gg, pg_valid, tmpfft;
+  // adjoint: line z, pair galaxy indices, window geometry, spectra X and A,
+  // galaxy-window correlation, scalar adjoints, upstream gradients, gathers
+  DevBuf line_z, psi, psj, cell_bin, cell_agg, wl_idx, wl_tot, wl_base, wl_y, wlines;
+  DevBuf Xs, As, cggw, adjb, gout, gp, gj, part;
+  // state of the last successful forward call, which pg_backward differentiates
+  bool fwd_ok = false, last_has_w = false;
+  int64_t last_n = 0;
+  std::vector<unsigned long long> last_hdd;
   // outputs
   DevBuf out;
   int64_t cap_gal = -1, cap_pairs = -1, cap_lines = -1;
@@ -208,6 +216,8 @@ cudaError_t ensure_pairs(pg_plan* p, int64_t np) {
   PG_CUDA_TRY(p->py.ensure(8 * c, t));
   PG_CUDA_TRY(p->pz.ensure(8 * c, t));
   PG_CUDA_TRY(p->pw.ensure(8 * c, t));
+  PG_CUDA_TRY(p->psi.ensure(4 * c, t));
+  PG_CUDA_TRY(p->psj.ensure(4 * c, t));
   p->cap_pairs = c;
   return cudaSuccess;
 }
@@ -218,6 +228,7 @@ cudaError_t ensure_lines(pg_plan* p, int64_t nl) {
   size_t* t = &p->total;
   PG_CUDA_TRY(p->line_y.ensure(4 * c, t));
   PG_CUDA_TRY(p->line_bin.ensure(4 * c, t));
+  PG_CUDA_TRY(p->line_z.ensure(4 * c, t));
   PG_CUDA_TRY(p->lines_q.ensure(8 * (size_t)c * p->N, t));
   PG_CUDA_TRY(p->spec.ensure(csize(p) * (size_t)c * p->P, t));
   p->cap_lines = c;
@@ -346,7 +357,7 @@ cudaError_t deposit_batch(pg_plan* p, int64_t n, const double* x, const double* 
     ProfScope ps(p, PG_FAM_DEPOSIT, s, (double)nl * p->N * 8 + 40.0 * n * (p->prm.assign ? 8 : 1));
     PG_CUDA_TRY(launch_line_compact(p->N, nb, p->flags.as<uint8_t>(), p->lidx.as<int32_t>(),
                                     p->line_base.as<int64_t>(), p->line_y.as<int32_t>(),
-                                    p->line_bin.as<int32_t>(), s));
+                                    p->line_bin.as<int32_t>(), p->line_z.as<int32_t>(), s));
     PG_CUDA_TRY(cudaMemsetAsync(p->lines_q.p, 0, (size_t)nl * p->N * 8, s));
     PG_CUDA_TRY(cudaMemsetAsync(p->qsum.p, 0, 8 * (size_t)nb, s));
     PG_CUDA_TRY(launch_deposit_lines(g, n, x, y, z, w, pbin, bin0, p->lidx.as<int32_t>(),
@@ -435,9 +446,11 @@ struct OutPtrs {
   int64_t *dd, *n_cells, *n_cells_agg;
 };
 
-OutPtrs out_layout(pg_plan* p) {
+// Output arrays carved out of one device block (the forward outputs in
+// p->out; the same layout holds the upstream gradients of pg_backward).
+OutPtrs out_layout_of(pg_plan* p, double* base) {
   const size_t PQ = (size_t)p->nPB * p->nQ, P = p->nPB, Q = p->nQ;
-  double* d = p->out.as<double>();
+  double* d = base;
   OutPtrs o;
   o.xi_pg = d; d += PQ;
   o.b_pg = d; d += PQ;
@@ -463,6 +476,8 @@ OutPtrs out_layout(pg_plan* p) {
   o.n_cells_agg = i;
   return o;
 }
+
+OutPtrs out_layout(pg_plan* p) { return out_layout_of(p, p->out.as<double>()); }
 
 cudaError_t copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   if (!dst) return cudaSuccess;
@@ -523,7 +538,8 @@ cudaError_t positions_and_pairs(pg_plan* p, int64_t n, const double* d_pos, cons
   for (int b = 1; b < p->nPB; ++b) off[b] = off[b - 1] + hdd[b - 1];
   PG_CUDA_TRY(cudaMemcpyAsync(p->bcursor.p, off.data(), 8 * p->nPB, cudaMemcpyHostToDevice, s));
   PG_CUDA_TRY(launch_pair_scatter(np, po, p->bcursor.as<unsigned long long>(), p->pbin.as<int32_t>(),
-                                  nullptr, nullptr, nullptr, p->px.as<double>(), p->py.as<double>(),
+                                  p->psi.as<int32_t>(), p->psj.as<int32_t>(), nullptr,
+                                  p->px.as<double>(), p->py.as<double>(),
                                   p->pz.as<double>(), p->pw.as<double>(), s));
   // the scatter reads the host offsets before this function's vector dies
   return cudaStreamSynchronize(s);
@@ -535,6 +551,7 @@ pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* 
   std::vector<unsigned long long> hdd;
   int64_t np = 0;
   int nonfinite = 0;
+  p->fwd_ok = false;
   prof_begin(p);
   const long long launches0 = launch_counter().load();
   PG_TRY(positions_and_pairs(p, n, d_pos, d_vel, d_w, hdd, &np, &nonfinite, s));
@@ -624,10 +641,204 @@ pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* 
   PG_TRY(cudaStreamSynchronize(s));
   p->last_launches = launch_counter().load() - launches0;
   if (herr) return PG_ERR_TIMEOUT;
+  p->fwd_ok = true;
+  p->last_n = n;
+  p->last_has_w = d_w != nullptr;
+  p->last_hdd = hdd;
   if (p->prof_on) prof_end(p);
   else
     for (int f = 0; f < PG_N_FAMILIES; ++f) p->stats[f].bytes = p->fam_bytes[f];
   return PG_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Plan-time geometry of the adjoint: for every window cell its (r, mu_r) bin
+// (-1 if none) and aggregate flag, and the W^2 window x-lines as a compact
+// line set (mesh order of (z, y)) that the y pass can read.
+cudaError_t build_window_geometry(pg_plan* p, const std::vector<int32_t>& cells) {
+  const int N = p->N, w = p->w, W = p->W;
+  const int64_t W3 = (int64_t)W * W * W, NN = (int64_t)N * N;
+  std::vector<int32_t> cb(W3, -1);
+  std::vector<uint8_t> ca(W3, 0);
+  for (int q = 0; q <= p->nQ; ++q)
+    for (int64_t i = p->h_list_off[q]; i < p->h_list_off[q + 1]; ++i) {
+      if (q < p->nQ) cb[cells[i]] = q;
+      else ca[cells[i]] = 1;
+    }
+  auto mesh_of_rank = [&](int r) { return r <= w ? r : r - W + N; };
+  std::vector<uint8_t> flag(NN, 0);
+  for (int rz = 0; rz < W; ++rz)
+    for (int ry = 0; ry < W; ++ry) flag[(int64_t)mesh_of_rank(rz) * N + mesh_of_rank(ry)] = 1;
+  std::vector<int32_t> idx(NN);
+  int32_t run = 0;
+  for (int64_t i = 0; i < NN; ++i) { idx[i] = run; run += flag[i]; }
+  std::vector<int32_t> ly(W * W);
+  for (int rz = 0; rz < W; ++rz)
+    for (int ry = 0; ry < W; ++ry) ly[rz * W + ry] = mesh_of_rank(ry);
+  const int64_t tot = (int64_t)W * W, zero = 0;
+  size_t* t = &p->total;
+  PG_CUDA_TRY(p->cell_bin.ensure(4 * W3, t));
+  PG_CUDA_TRY(p->cell_agg.ensure(W3, t));
+  PG_CUDA_TRY(p->wl_idx.ensure(4 * NN, t));
+  PG_CUDA_TRY(p->wl_tot.ensure(8, t));
+  PG_CUDA_TRY(p->wl_base.ensure(8, t));
+  PG_CUDA_TRY(p->wl_y.ensure(4 * W * W, t));
+  PG_CUDA_TRY(cudaMemcpy(p->cell_bin.p, cb.data(), 4 * W3, cudaMemcpyHostToDevice));
+  PG_CUDA_TRY(cudaMemcpy(p->cell_agg.p, ca.data(), W3, cudaMemcpyHostToDevice));
+  PG_CUDA_TRY(cudaMemcpy(p->wl_idx.p, idx.data(), 4 * NN, cudaMemcpyHostToDevice));
+  PG_CUDA_TRY(cudaMemcpy(p->wl_tot.p, &tot, 8, cudaMemcpyHostToDevice));
+  PG_CUDA_TRY(cudaMemcpy(p->wl_base.p, &zero, 8, cudaMemcpyHostToDevice));
+  return cudaMemcpy(p->wl_y.p, ly.data(), 4 * W * W, cudaMemcpyHostToDevice);
+}
+
+// Spectrum X of one window adjoint field (pair mode: sbar of one mesh; gg
+// mode: gbar, g2bar and the galaxy correlation window).
+template <typename R>
+cudaError_t window_spectrum(pg_plan* p, const double* sbar, const double* gbar,
+                            const double* g2bar, cudaStream_t s) {
+  using C = typename CT<R>::C;
+  const C* tw = p->tw.as<C>();
+  const int64_t nl = (int64_t)p->W * p->W;
+  PG_CUDA_TRY(launch_window_field<R>(p->N, p->w, p->cell_bin.as<int32_t>(), p->cell_agg.as<uint8_t>(),
+                                     p->nQ, sbar, gbar, g2bar, p->cggw.as<R>(), p->wlines.as<R>(), s));
+  PG_CUDA_TRY(FftPasses<R>::x_r2c_real(p->N, p->wlines.as<R>(), nl, p->spec.as<C>(), p->P, tw, s));
+  PG_CUDA_TRY(FftPasses<R>::y_fwd(p->N, 1, p->spec.as<C>(), p->P, p->wl_idx.as<int32_t>(),
+                                  p->wl_tot.as<int64_t>(), p->wl_base.as<int64_t>(),
+                                  p->wl_y.as<int32_t>(), p->Xs.as<C>(), 0, tw, s));
+  return FftPasses<R>::z_fwd(p->N, p->Xs.as<C>(), p->P, tw, s);
+}
+
+// Reverse sweep of the last forward call (see pg_backward in pairgal.h).
+template <typename R>
+cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaStream_t s) {
+  using C = typename CT<R>::C;
+  const C* tw = p->tw.as<C>();
+  const int N = p->N, P = p->nPB, Lq = p->nL;
+  const int64_t n = p->last_n;
+  const int64_t NN = (int64_t)N * N;
+  const int64_t spec_elems = NN * p->P;
+  const int64_t W3 = (int64_t)p->W * p->W * p->W;
+  const double n3 = (double)N * N * N;
+  const double scale6 = 1.0 / (n3 * n3);
+  const DepGeom geo{N, p->dx, p->prm.assign};
+  size_t* t = &p->total;
+  // buffers of the reverse sweep
+  int64_t np_max = 0;
+  for (auto v : p->last_hdd) np_max = std::max<int64_t>(np_max, (int64_t)v);
+  PG_CUDA_TRY(ensure_lines(p, (int64_t)p->W * p->W));
+  PG_CUDA_TRY(p->Xs.ensure(sizeof(C) * spec_elems, t));
+  PG_CUDA_TRY(p->As.ensure(sizeof(C) * spec_elems, t));
+  PG_CUDA_TRY(p->cggw.ensure(sizeof(R) * W3, t));
+  PG_CUDA_TRY(p->wlines.ensure(sizeof(R) * p->W * p->W * N, t));
+  const size_t nadj = (size_t)P * Lq * 4 + 2 * Lq + P + 4;
+  PG_CUDA_TRY(p->adjb.ensure(sizeof(double) * nadj, t));
+  PG_CUDA_TRY(p->gp.ensure(sizeof(double) * std::max<int64_t>(np_max, 1), t));
+  PG_CUDA_TRY(p->gj.ensure(sizeof(double) * std::max<int64_t>(n, 1), t));
+  PG_CUDA_TRY(p->part.ensure(sizeof(double) * (cdiv(std::max<int64_t>(std::max(n, np_max), 1), 256) + 4), t));
+  double* Sbar = p->adjb.as<double>();
+  double* tmp = Sbar + (size_t)P * Lq;
+  double* Gbar = tmp + (size_t)P * Lq * 3;
+  double* G2bar = Gbar + Lq;
+  double* DDbar = G2bar + Lq;
+  double* wsbar = DDbar + P;
+  double* Tdev = wsbar + 2;
+  // upstream gradients to the device, in the forward output layout
+  PG_CUDA_TRY(p->gout.ensure(p->out.bytes, t));
+  OutPtrs go = out_layout_of(p, p->gout.as<double>());
+  OutPtrs fo = out_layout(p);
+  const size_t PQ = sizeof(double) * P * p->nQ, Pd = sizeof(double) * P, Qd = sizeof(double) * p->nQ;
+  OutSet g{}, o{};
+  auto up = [&](const double* h, double* d, size_t bytes, const double*& slot) -> cudaError_t {
+    if (!h) { slot = nullptr; return cudaSuccess; }
+    slot = d;
+    return cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s);
+  };
+  if (gin) {
+    PG_CUDA_TRY(up(gin->xi_pg, go.xi_pg, PQ, g.xi_pg));
+    PG_CUDA_TRY(up(gin->xi_gg, go.xi_gg, Qd, g.xi_gg));
+    PG_CUDA_TRY(up(gin->b_pg, go.b_pg, PQ, g.b_pg));
+    PG_CUDA_TRY(up(gin->q_eff, go.q_eff, PQ, g.q_eff));
+    PG_CUDA_TRY(up(gin->q_eff_sq, go.q_eff_sq, PQ, g.q_eff_sq));
+    PG_CUDA_TRY(up(gin->xi_dw, go.xi_dw, Qd, g.xi_dw));
+    PG_CUDA_TRY(up(gin->b_pg_agg, go.b_pg_agg, Pd, g.b_pg_agg));
+    PG_CUDA_TRY(up(gin->q_eff_agg, go.q_eff_agg, Pd, g.q_eff_agg));
+    PG_CUDA_TRY(up(gin->xi_dw_agg, go.xi_dw_agg, 8, g.xi_dw_agg));
+    PG_CUDA_TRY(up(gin->xi_ss, go.xi_ss, Pd, g.xi_ss));
+    PG_CUDA_TRY(up(gin->dd_w, go.dd_w, Pd, g.dd_w));
+  }
+  o = OutSet{fo.xi_pg, fo.xi_gg, fo.b_pg, fo.q_eff, fo.q_eff_sq, fo.xi_dw, fo.b_pg_agg, fo.q_eff_agg,
+             fo.xi_dw_agg, fo.xi_ss, fo.dd_w};
+  AdjRatioArgs ra{};
+  ra.P = P; ra.Q = p->nQ; ra.n_mu = p->prm.n_mu;
+  ra.s_edges = p->s_edges_d.as<double>();
+  ra.L = p->prm.box_L;
+  ra.ddq = p->ddq.as<unsigned long long>();
+  ra.wsum = p->wsum.as<double>();
+  ra.sum_pg = p->sums_pg.as<double>();
+  ra.pg_valid = p->pg_valid.as<unsigned char>();
+  ra.sum_gg = p->sums_gg.as<double>();
+  ra.gg_valid = n > 0 ? 1 : 0;
+  ra.list_off = p->list_off.as<int64_t>();
+  ra.o = o;
+  ra.g = g;
+  ra.tmp = tmp;
+  ra.Sbar = Sbar; ra.Gbar = Gbar; ra.G2bar = G2bar; ra.DDbar = DDbar; ra.wsbar = wsbar;
+  PG_CUDA_TRY(launch_adjoint_ratios(ra, s));
+  PG_CUDA_TRY(cudaMemsetAsync(wbar, 0, sizeof(double) * std::max<int64_t>(n, 1), s));
+  if (n == 0) return cudaSuccess;
+  const double* gw = p->last_has_w ? p->gw.as<double>() : nullptr;
+  // galaxy spectrum and galaxy correlation window, recomputed
+  PG_CUDA_TRY((galaxy_pass<R>(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, true, s)));
+  PG_CUDA_TRY(cudaMemcpyAsync(p->cggw.p, p->Cwin.p, sizeof(R) * W3, cudaMemcpyDeviceToDevice, s));
+  // A = 2 Re(F[Cbar_gg]) F_g
+  PG_CUDA_TRY(window_spectrum<R>(p, nullptr, Gbar, G2bar, s));
+  PG_CUDA_TRY(launch_acc_gg<R>(spec_elems, p->Xs.as<C>(), p->Fg.as<C>(), p->As.as<C>(), s));
+  // every pair mesh
+  std::vector<int64_t> off(P + 1, 0);
+  for (int b = 0; b < P; ++b) off[b + 1] = off[b] + (int64_t)p->last_hdd[b];
+  for (int b = 0; b < P; ++b) {
+    const int64_t npb = (int64_t)p->last_hdd[b];
+    if (npb == 0) continue;
+    PG_CUDA_TRY(window_spectrum<R>(p, Sbar + (size_t)b * Lq, nullptr, nullptr, s));
+    int64_t nl = 0;
+    const int64_t o0 = off[b];
+    PG_CUDA_TRY(deposit_batch(p, npb, p->px.as<double>() + o0, p->py.as<double>() + o0,
+                              p->pz.as<double>() + o0, p->pw.as<double>() + o0,
+                              p->pbin.as<int32_t>() + o0, b, 1, &nl, s));
+    PG_CUDA_TRY(lines_to_S<R>(p, 1, nl, p->S.as<C>(), 0, s));
+    // galaxy side: A += F_b conj(F[Cbar_b])
+    PG_CUDA_TRY(FftPasses<R>::z_fwd_acc(N, p->S.as<C>(), p->Xs.as<C>(), p->As.as<C>(), p->P, tw, s));
+    // pair side: h_b = N^-6 IDFT[F[Cbar_b] F_g] on the lines of this mesh
+    PG_CUDA_TRY(FftPasses<R>::z_mul_inv(N, p->Xs.as<C>(), p->Fg.as<C>(), p->P, tw, s));
+    PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, p->Xs.as<C>(), p->P, tw, s));
+    R* hl = reinterpret_cast<R*>(p->lines_q.p);   // the deposit's lines were consumed by the x pass
+    PG_CUDA_TRY(FftPasses<R>::x_c2r_lines(N, p->Xs.as<C>(), p->P, nl, p->line_y.as<int32_t>(),
+                                          p->line_z.as<int32_t>(), hl, scale6, tw, s));
+    PG_CUDA_TRY(launch_gather<R>(geo, npb, p->px.as<double>() + o0, p->py.as<double>() + o0,
+                                 p->pz.as<double>() + o0, p->pw.as<double>() + o0,
+                                 p->lidx.as<int32_t>(), hl, p->gp.as<double>(), p->part.as<double>(),
+                                 Tdev, s));
+    PG_CUDA_TRY(launch_pair_chain(npb, p->gp.as<double>(), Tdev, p->qsum.as<unsigned long long>(), n3,
+                                  DDbar + b, p->psi.as<int32_t>() + o0, p->psj.as<int32_t>() + o0, gw,
+                                  wbar, s));
+  }
+  // galaxy side: f_g adjoint = N^-6 IDFT[A] at the galaxy lines
+  PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, p->As.as<C>(), p->P, tw, s));
+  PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, p->As.as<C>(), p->P, tw, s));
+  int64_t nlg = 0;
+  PG_CUDA_TRY(deposit_batch(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, nullptr,
+                            0, 1, &nlg, s));
+  R* hl = reinterpret_cast<R*>(p->lines_q.p);
+  PG_CUDA_TRY(FftPasses<R>::x_c2r_lines(N, p->As.as<C>(), p->P, nlg, p->line_y.as<int32_t>(),
+                                        p->line_z.as<int32_t>(), hl, scale6, tw, s));
+  PG_CUDA_TRY(launch_gather<R>(geo, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw,
+                               p->lidx.as<int32_t>(), hl, p->gj.as<double>(), p->part.as<double>(),
+                               Tdev, s));
+  return launch_gal_final(n, p->gj.as<double>(), Tdev, p->qsum.as<unsigned long long>(), n3, wsbar,
+                          gw, wbar, s);
 }
 
 }  // namespace
@@ -714,6 +925,7 @@ pg_status pg_plan_create(const pg_params* prm, pg_plan** out) {
   std::vector<int32_t> cells;
   build_cell_lists(p, cells, p->h_list_off);
   p->n_cells_listed = (int64_t)cells.size();
+  if (e == cudaSuccess) e = build_window_geometry(p, cells);
   if (e == cudaSuccess) e = p->cells.ensure(4 * std::max<size_t>(cells.size(), 1), &p->total);
   if (e == cudaSuccess && !cells.empty())
     e = cudaMemcpy(p->cells.p, cells.data(), 4 * cells.size(), cudaMemcpyHostToDevice);
@@ -747,7 +959,10 @@ void pg_plan_destroy(pg_plan* p) {
                    &p->bcursor, &p->flags, &p->lidx, &p->seg_total, &p->line_base, &p->n_lines,
                    &p->stmp, &p->line_y, &p->line_bin, &p->lines_q, &p->qsum, &p->scale, &p->spec,
                    &p->S, &p->Fg, &p->Wz, &p->Wy, &p->Cwin, &p->sums_pg, &p->sums_gg,
-                   &p->pg_valid, &p->tmpfft, &p->out};
+                   &p->pg_valid, &p->tmpfft, &p->out, &p->line_z, &p->psi, &p->psj,
+                   &p->cell_bin, &p->cell_agg, &p->wl_idx, &p->wl_tot, &p->wl_base, &p->wl_y,
+                   &p->wlines, &p->Xs, &p->As, &p->cggw, &p->adjb, &p->gout, &p->gp, &p->gj,
+                   &p->part};
   for (DevBuf* b : all) b->release(&p->total);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   cudaSetDevice(cur);
@@ -765,6 +980,23 @@ pg_status pg_plan_reserve(pg_plan* p, int64_t n_gal_max, int64_t n_pairs_max) {
 }
 
 size_t pg_workspace_bytes(const pg_plan* p) { return p ? p->total : 0; }
+
+pg_status pg_backward(pg_plan* p, const pg_result* grad_out, double* d_grad_w, void* stream) {
+  if (!p || !d_grad_w) return PG_ERR_INVALID_ARG;
+  if (!p->fwd_ok) return PG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PG_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));
+  cudaError_t e = p->prm.precision ? backward_impl<double>(p, grad_out, d_grad_w, s)
+                                   : backward_impl<float>(p, grad_out, d_grad_w, s);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return from_cuda(e);
+  }
+  int32_t herr = 0;
+  PG_TRY(cudaMemcpyAsync(&herr, p->flag.as<int32_t>() + 1, 4, cudaMemcpyDeviceToHost, s));
+  PG_TRY(cudaStreamSynchronize(s));
+  return herr ? PG_ERR_TIMEOUT : PG_OK;
+}
 
 pg_status pg_plan_set_profiling(pg_plan* p, int32_t enable) {
   if (!p) return PG_ERR_INVALID_ARG;
@@ -828,6 +1060,7 @@ pg_status pg_find_pairs(pg_plan* p, int64_t n, const double* d_pos, const float*
   if (capacity > 0 && (!d_bin || !d_i || !d_j || !d_mid || !d_wp)) return PG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   PG_TRY(ensure_gal(p, n));
+  p->fwd_ok = false;   // the plan's pair and position buffers are reused
   // positions are taken as given (already wrapped); split them to SoA
   PG_TRY(launch_transform(n, p->prm.box_L, 0.0, d_pos, nullptr, nullptr, p->x.as<double>(),
                           p->y.as<double>(), p->z.as<double>(), s));
@@ -929,6 +1162,7 @@ pg_status pg_correlate_points(pg_plan* p, int64_t n_a, const double* d_a, const 
   const int64_t nmax = std::max(n_a, n_b);
   PG_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));
   PG_TRY(ensure_gal(p, nmax));
+  p->fwd_ok = false;   // the plan's spectra and sums are reused
   // set b -> Fg; set a -> one "pair" mesh in S[0]
   PG_TRY(launch_transform(n_b, p->prm.box_L, 0.0, d_b, nullptr, nullptr, p->x.as<double>(),
                           p->y.as<double>(), p->z.as<double>(), s));

@@ -212,4 +212,59 @@ cudaError_t FftPasses<R>::x_c2r_full(int N, const C* S, int P, R* out, const C* 
 template <typename R>
 cudaError_t FftPasses<R>::set_smem_limits() { return cudaSuccess; }
 
+template <typename R>
+cudaError_t FftPasses<R>::x_r2c_real(int N, const R* f, int64_t n_lines, C* spec, int P, const C* tw,
+                                     cudaStream_t s) {
+  if (n_lines <= 0) return cudaSuccess;
+  PG_DISPATCH_N(N, {
+    using X = fft::XPass<C, NN>;
+    auto k = fft::k_x_r2c_dense<C, NN>;
+    PG_CUDA_TRY(set_smem(k, X::smem_bytes()));
+    k<<<(unsigned)cdiv(n_lines, X::LB), X::THREADS, X::smem_bytes(), s>>>(f, n_lines, spec, P, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::z_fwd_acc(int N, const C* S, const C* X, C* A, int P, const C* tw,
+                                    cudaStream_t s) {
+  constexpr int B = fft::Cols<R>::B;
+  PG_DISPATCH_N(N, {
+    using CP = fft::ColPass<C, NN, B>;
+    auto k = fft::k_z_fwd_acc<C, NN, B>;
+    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
+    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, X, A, P, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::z_mul_inv(int N, C* X, const C* Fg, int P, const C* tw, cudaStream_t s) {
+  constexpr int B = fft::Cols<R>::B;
+  PG_DISPATCH_N(N, {
+    using CP = fft::ColPass<C, NN, B>;
+    auto k = fft::k_z_mul_inv<C, NN, B>;
+    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
+    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(X, Fg, P, tw);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::x_c2r_lines(int N, const C* S, int P, int64_t n_lines,
+                                      const int32_t* line_y, const int32_t* line_z, R* out,
+                                      double scale, const C* tw, cudaStream_t s) {
+  if (n_lines <= 0) return cudaSuccess;
+  PG_DISPATCH_N(N, {
+    using X = fft::XPass<C, NN>;
+    auto k = fft::k_x_c2r_lines<C, NN>;
+    PG_CUDA_TRY(set_smem(k, X::smem_bytes()));
+    k<<<(unsigned)cdiv(n_lines, X::LB), X::THREADS, X::smem_bytes(), s>>>(S, P, n_lines, line_y,
+                                                                        line_z, out, (R)scale, tw);
+  });
+  return launched();
+}
+
 }  // namespace pg

@@ -494,7 +494,12 @@ k_y_inv_win(const C* __restrict__ Wz, int64_t Wz_stride, int w, C* __restrict__ 
 // ============================================================================
 template <typename C, int N, typename Store>
 __device__ __forceinline__ void x_c2r_body(C* buf, int64_t l0, int64_t n_lines, const C* __restrict__ src_of_line0,
-                                           int P, const C* tw, Store store) {
+                                           int P, const C* tw, Store store);
+
+// C2R of LB lines whose half spectra come from load(line, k), k = 0..N/2.
+template <typename C, int N, typename Loader, typename Store>
+__device__ __forceinline__ void x_c2r_core(C* buf, int64_t l0, int64_t n_lines, Loader load,
+                                           const C* tw, Store store) {
   using X = XPass<C, N>;
   constexpr int M = X::M, LB = X::LB, LD = X::LD, N1 = X::N1, N2 = X::N2;
   for (int idx = threadIdx.x; idx < LB * (M + 1); idx += blockDim.x) {
@@ -502,7 +507,7 @@ __device__ __forceinline__ void x_c2r_body(C* buf, int64_t l0, int64_t n_lines, 
     const int64_t l = l0 + cc;
     C v;
     v.x = 0; v.y = 0;
-    if (l < n_lines) v = src_of_line0[(l - l0) * P + k];
+    if (l < n_lines) v = load(l, k);
     buf[k * LD + cc] = v;
   }
   __syncthreads();
@@ -539,6 +544,108 @@ __device__ __forceinline__ void x_c2r_body(C* buf, int64_t l0, int64_t n_lines, 
       const int m = k1 + N1 * k2;
       store(l, 2 * m, a[k2].x);
       store(l, 2 * m + 1, a[k2].y);
+    }
+  }
+}
+
+// Lines l0.. stored contiguously at src_of_line0 with pitch P.
+template <typename C, int N, typename Store>
+__device__ __forceinline__ void x_c2r_body(C* buf, int64_t l0, int64_t n_lines, const C* __restrict__ src_of_line0,
+                                           int P, const C* tw, Store store) {
+  x_c2r_core<C, N>(buf, l0, n_lines,
+                   [&](int64_t l, int k) { return src_of_line0[(l - l0) * P + k]; }, tw, store);
+}
+
+// C2R of scattered lines of a dense half spectrum S[z][y][P]: line l is
+// (line_z[l], line_y[l]); out[l][x] = scale * x-line value (the adjoint
+// fields at the lines that hold deposited points).
+template <typename C, int N>
+__global__ void __launch_bounds__(XPass<C, N>::THREADS)
+k_x_c2r_lines(const C* __restrict__ S, int P, int64_t n_lines, const int32_t* __restrict__ line_y,
+              const int32_t* __restrict__ line_z, typename Real<C>::T* __restrict__ out,
+              typename Real<C>::T scale, const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
+  using RT = typename Real<C>::T;
+  const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
+  x_c2r_core<C, N>(
+      buf, l0, n_lines,
+      [&](int64_t l, int k) { return S[((int64_t)line_z[l] * N + line_y[l]) * P + k]; }, tws,
+      [&](int64_t l, int n, RT v) { out[l * N + n] = v * scale; });
+}
+
+// Adjoint z pass, galaxy side: forward z of a mesh spectrum column (S after
+// the y pass), times conj(X) of the same column, added to A. CTA = (kx tile, ky).
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+k_z_fwd_acc(const C* __restrict__ S, const C* __restrict__ X, C* __restrict__ A, int P,
+            const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
+  using CP = ColPass<C, N, B>;
+  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  const int kx0 = blockIdx.x * B, ky = blockIdx.y;
+  const int ncol = min(B, M1 - kx0);
+  load_zcol<C, N, B>(buf, S + (int64_t)ky * P + kx0, P, ncol);
+  __syncthreads();
+  step1<C, N1, N2, B, false>(buf, B, tws, 1);
+  __syncthreads();
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  C a[N2];
+  step2<C, N1, N2, false>(buf, B, c, k1, a);
+  if (c < ncol) {
+    const int64_t base = (int64_t)ky * P + kx0 + c;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int64_t o = base + (int64_t)(k1 + N1 * k2) * N * P;
+      C acc = A[o];
+      const C t = cmulc(a[k2], X[o]);   // F_b conj(X)
+      acc.x += t.x;
+      acc.y += t.y;
+      A[o] = acc;
+    }
+  }
+}
+
+// Adjoint z pass, pair side: X * F_g (k = 0 zeroed), inverse z over the full
+// column, in place in X. CTA = (kx tile, ky).
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+k_z_mul_inv(C* __restrict__ X, const C* __restrict__ Fg, int P, const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
+  using CP = ColPass<C, N, B>;
+  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  const int kx0 = blockIdx.x * B, ky = blockIdx.y;
+  const int ncol = min(B, M1 - kx0);
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  const int64_t base = (int64_t)ky * P + kx0 + c;
+  C a[N2];
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    C v;
+    v.x = 0; v.y = 0;
+    if (c < ncol) {
+      const int64_t o = base + (int64_t)(k1 + N1 * k2) * N * P;
+      v = cmul(X[o], Fg[o]);
+    }
+    a[k2] = v;
+  }
+  if (kx0 + c == 0 && ky == 0 && k1 == 0) { a[0].x = 0; a[0].y = 0; }
+  __syncthreads();   // twiddles staged
+  stepA<C, N1, N2, true>(buf, B, c, k1, a, tws, 1);
+  __syncthreads();
+  for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+    const int cc = t % B, n2 = t / B;
+    C x[N1];
+    stepB<C, N1, N2, true>(buf, B, cc, n2, x);
+    if (cc < ncol) {
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1)
+        X[(int64_t)ky * P + kx0 + cc + (int64_t)(n2 + N2 * n1) * N * P] = x[n1];
     }
   }
 }

@@ -124,6 +124,7 @@ cudaError_t launch_mark_lines(const DepGeom& g, int64_t n, const double* x, cons
                               uint8_t* flags, cudaStream_t s);
 cudaError_t launch_line_compact(int N, int nb, const uint8_t* flags, const int32_t* idx,
                                 const int64_t* line_base, int32_t* line_y, int32_t* line_bin,
+                                int32_t* line_z,
                                 cudaStream_t s);
 cudaError_t launch_line_bases(int nb, const int64_t* seg_total, int64_t* line_base,
                               int64_t* n_lines_total, cudaStream_t s);
@@ -180,6 +181,18 @@ struct FftPasses {
   static cudaError_t x_c2r_full(int N, const C* S, int P, R* out, const C* tw,
                                 cudaStream_t s);
   static cudaError_t set_smem_limits();
+  // Adjoint passes. x R2C of n_lines real lines (line l at f + l*N).
+  static cudaError_t x_r2c_real(int N, const R* f, int64_t n_lines, C* spec, int P, const C* tw,
+                                cudaStream_t s);
+  // A[kz][ky][kx] += F(kz) conj(X[kz][ky][kx]) with F the z transform of S.
+  static cudaError_t z_fwd_acc(int N, const C* S, const C* X, C* A, int P, const C* tw,
+                               cudaStream_t s);
+  // X <- inverse z of X * Fg (k = 0 zeroed), full columns, in place.
+  static cudaError_t z_mul_inv(int N, C* X, const C* Fg, int P, const C* tw, cudaStream_t s);
+  // out[l][x] = scale * C2R of row (line_z[l], line_y[l]) of S.
+  static cudaError_t x_c2r_lines(int N, const C* S, int P, int64_t n_lines, const int32_t* line_y,
+                                 const int32_t* line_z, R* out, double scale, const C* tw,
+                                 cudaStream_t s);
 };
 
 // ---- binning and ratios (pg_bin.cu) -----------------------------------------
@@ -207,5 +220,46 @@ struct RatioArgs {
   int64_t *o_dd, *n_cells, *n_cells_agg;
 };
 cudaError_t launch_ratios(const RatioArgs& a, cudaStream_t s);
+
+// ---- adjoint (pg_adjoint.cu) ----------------------------------------------------
+struct OutSet {   // device arrays with the pg_result layout (any may be null)
+  const double *xi_pg, *xi_gg, *b_pg, *q_eff, *q_eff_sq, *xi_dw, *b_pg_agg, *q_eff_agg,
+      *xi_dw_agg, *xi_ss, *dd_w;
+};
+struct AdjRatioArgs {
+  int P, Q, n_mu;
+  const double* s_edges;
+  double L;
+  const unsigned long long* ddq;
+  const double* wsum;
+  const double* sum_pg;            // [P][Q+1][2]
+  const unsigned char* pg_valid;
+  const double* sum_gg;            // [Q+1][2]
+  int gg_valid;
+  const int64_t* list_off;
+  OutSet o;                        // forward outputs (for gating non-finite ones)
+  OutSet g;                        // upstream gradients
+  double* tmp;                     // [P][Q+1][3] scratch
+  double *Sbar, *Gbar, *G2bar, *DDbar, *wsbar;   // [P][Q+1], [Q+1], [Q+1], [P], [2]
+};
+cudaError_t launch_adjoint_ratios(const AdjRatioArgs& a, cudaStream_t s);
+template <typename R>
+cudaError_t launch_window_field(int N, int w, const int32_t* cell_bin, const uint8_t* cell_agg, int Q,
+                                const double* sbar, const double* gbar, const double* g2bar,
+                                const R* cgg, R* lines, cudaStream_t s);
+template <typename R>
+cudaError_t launch_acc_gg(int64_t n, const typename CT<R>::C* X, const typename CT<R>::C* Fg,
+                          typename CT<R>::C* A, cudaStream_t s);
+template <typename R>
+cudaError_t launch_gather(const DepGeom& geo, int64_t n, const double* x, const double* y,
+                          const double* z, const double* wt, const int32_t* idx, const R* lines,
+                          double* g, double* partial, double* T, cudaStream_t s);
+cudaError_t launch_pair_chain(int64_t np, const double* g, const double* T,
+                              const unsigned long long* qsum, double n3, const double* ddbar,
+                              const int32_t* pi, const int32_t* pj, const double* wgal,
+                              double* wbar, cudaStream_t s);
+cudaError_t launch_gal_final(int64_t n, const double* g, const double* T,
+                             const unsigned long long* qsum, double n3, const double* wsbar,
+                             const double* wgal, double* wbar, cudaStream_t s);
 
 }  // namespace pg

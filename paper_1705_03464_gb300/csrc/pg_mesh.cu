@@ -76,7 +76,7 @@ k_mark_lines(DepGeom g, int64_t n, const double* __restrict__ x, const double* _
 __global__ void __launch_bounds__(kThreads)
 k_line_compact(int N, int nb, const uint8_t* __restrict__ flags, const int32_t* __restrict__ idx,
                const int64_t* __restrict__ line_base, int32_t* __restrict__ line_y,
-               int32_t* __restrict__ line_bin) {
+               int32_t* __restrict__ line_bin, int32_t* __restrict__ line_z) {
   const int64_t NN = (int64_t)N * N;
   int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (t >= NN * nb) return;
@@ -86,6 +86,7 @@ k_line_compact(int N, int nb, const uint8_t* __restrict__ flags, const int32_t* 
   int64_t l = line_base[b] + idx[t];
   line_y[l] = (int32_t)(zy % N);
   line_bin[l] = b;
+  if (line_z) line_z[l] = (int32_t)(zy / N);
 }
 
 __global__ void k_line_bases(int nb, const int64_t* __restrict__ seg_total,
@@ -171,9 +172,11 @@ cudaError_t launch_mark_lines(const DepGeom& g, int64_t n, const double* x, cons
 
 cudaError_t launch_line_compact(int N, int nb, const uint8_t* flags, const int32_t* idx,
                                 const int64_t* line_base, int32_t* line_y, int32_t* line_bin,
+                                int32_t* line_z,
                                 cudaStream_t s) {
   int64_t tot = (int64_t)N * N * nb;
-  k_line_compact<<<(unsigned)cdiv(tot, kThreads), kThreads, 0, s>>>(N, nb, flags, idx, line_base, line_y, line_bin);
+  k_line_compact<<<(unsigned)cdiv(tot, kThreads), kThreads, 0, s>>>(N, nb, flags, idx, line_base, line_y, line_bin,
+                                                                       line_z);
   return launched();
 }
 

@@ -80,6 +80,7 @@ def _load():
         "pg_fft_r2c_3d": (C.c_int, [vp, vp, vp, vp]),
         "pg_fft_c2r_3d": (C.c_int, [vp, vp, vp, vp]),
         "pg_pair_counts_static": (C.c_int, [i64, vp, vp, dbl, i32, vp, i32, vp, vp, vp]),
+        "pg_backward": (C.c_int, [vp, C.POINTER(pg_result), vp, vp]),
         "pg_plan_set_profiling": (C.c_int, [vp, i32]),
         "pg_plan_last_stats": (C.c_int, [vp, vp, vp]),
     }
@@ -320,3 +321,63 @@ def pg_pair_counts_static(pos, w, box_L, s_edges, n_mu, stream=None):
                                     _stream(stream))
     _check(st, "pg_pair_counts_static")
     return dd, ddq
+
+
+GRAD_FIELDS = ("xi_pg", "xi_gg", "b_pg", "q_eff", "q_eff_sq", "xi_dw", "b_pg_agg", "q_eff_agg",
+               "xi_dw_agg", "xi_ss", "dd_w")
+
+
+def pg_backward(plan: Plan, grads: dict, n_gal: int, stream=None):
+    """dL/dw (device FP64 tensor [n_gal]) of the last pg_forward on `plan`,
+    for L = sum over the given fields of grads[field] * output[field]."""
+    import torch
+    res = pg_result()
+    keep = []
+    for name in GRAD_FIELDS:
+        if name in grads and grads[name] is not None:
+            a = np.ascontiguousarray(np.asarray(grads[name], dtype=np.float64).reshape(-1))
+            keep.append(a)
+            setattr(res, name, a.ctypes.data_as(C.POINTER(C.c_double)))
+    out = torch.empty(max(int(n_gal), 1), dtype=torch.float64, device="cuda")
+    st = _lib.pg_backward(plan.handle, C.byref(res), _ptr(out), _stream(stream))
+    _check(st, "pg_backward")
+    return out[: int(n_gal)]
+
+
+class PairGalFn:
+    """torch.autograd.Function over the library: forward = pg_forward with the
+    given per-galaxy weights, backward = pg_backward (spectra recomputed).
+
+        outs = PairGalFn.apply(w, plan, pos, vel)   # w: [n] float32 CUDA, requires_grad
+    returns (b_pg, q_eff, xi_pg, xi_gg, b_pg_agg, q_eff_agg) as FP64 tensors on w's device."""
+
+    NAMES = ("b_pg", "q_eff", "xi_pg", "xi_gg", "b_pg_agg", "q_eff_agg")
+
+    @staticmethod
+    def _fn():
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, w, plan, pos, vel):
+                out = pg_forward(plan, pos, vel, w)
+                ctx.plan = plan
+                ctx.n = int(pos.shape[0])
+                ctx.shapes = [out[k].shape for k in PairGalFn.NAMES]
+                return tuple(torch.as_tensor(np.ascontiguousarray(out[k]), dtype=torch.float64,
+                                             device=w.device) for k in PairGalFn.NAMES)
+
+            @staticmethod
+            def backward(ctx, *gouts):
+                grads = {k: (g.detach().cpu().numpy() if g is not None else None)
+                         for k, g in zip(PairGalFn.NAMES, gouts)}
+                gw = pg_backward(ctx.plan, grads, ctx.n)
+                return gw.to(torch.float32), None, None, None
+
+        return _F
+
+    @classmethod
+    def apply(cls, w, plan, pos, vel=None):
+        if not hasattr(cls, "_F"):
+            cls._F = cls._fn()
+        return cls._F.apply(w, plan, pos, vel)
