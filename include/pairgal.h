@@ -151,6 +151,25 @@ pg_status pg_forward_host(pg_plan* plan, int64_t n_gal, const double* h_pos,
  * PG_ERR_CUDA, PG_ERR_TIMEOUT. Synchronises the stream. */
 pg_status pg_backward(pg_plan* plan, const pg_result* grad_out, double* d_grad_w, void* stream);
 
+/* Soft occupation weights of candidate galaxies under the five-parameter HOD
+ * of Sec. 3.3 (eq. hod), theta = (log10 M_cut, log10 M_1, sigma, alpha,
+ * kappa) in h_theta[5] (host):
+ *   kind 0 (central at the halo centre):  w = erfc(ln(M_cut/M)/(sqrt(2) sigma)) / 2
+ *   kind 1 (one of K satellite candidates of the halo):
+ *            w = ((M - kappa M_cut)/M_1)^alpha / K  for M > kappa M_cut, else 0
+ * d_mass [n] FP64 halo mass (Msun/h), d_kind [n] int32, d_kh [n] FP32 K (any
+ * value for centrals); writes d_w [n] FP32 and, if d_dw_dtheta is not NULL,
+ * d_dw_dtheta [n][5] FP64 = dw/dtheta. All device. Errors: PG_ERR_INVALID_ARG
+ * (sigma <= 0, NULL arrays). */
+pg_status pg_hod_weights(int64_t n, const double* d_mass, const int32_t* d_kind, const float* d_kh,
+                         const double* h_theta, float* d_w, double* d_dw_dtheta, void* stream);
+
+/* h_grad_theta[5] (host) = sum_i d_wbar[i] * d_dw_dtheta[i][k]: the chain from
+ * weight gradients (pg_backward) to the HOD parameters. Uses the plan's
+ * workspace; synchronises the stream. */
+pg_status pg_hod_chain(pg_plan* plan, int64_t n, const double* d_wbar, const double* d_dw_dtheta,
+                       double* h_grad_theta, void* stream);
+
 /* Low-level form of the estimator for two arbitrary point sets (Sec. 2.1,
  * eq. bpg_initial): deposits set a and set b, correlates them, and bins
  * C_ab(r) = (1/N^3) sum_x delta_b(x) delta_a(x + r) by (r, mu_r).

@@ -349,6 +349,85 @@ cudaError_t launch_pair_chain(int64_t np, const double* g, const double* T,
   return launched();
 }
 
+// Soft HOD occupation weights (Sec. 3.3, eq. hod) of candidate galaxies and
+// their derivatives in theta = (log10 M_cut, log10 M_1, sigma, alpha, kappa):
+//   central:   w = erfc(u)/2, u = ln(M_cut/M) / (sqrt(2) sigma)
+//   satellite: w = ((M - kappa M_cut)/M_1)^alpha / K for M > kappa M_cut, else 0
+// (K: the number of satellite candidates of the halo).
+__global__ void __launch_bounds__(256)
+k_hod_weights(int64_t n, const double* __restrict__ mass, const int32_t* __restrict__ kind,
+              const float* __restrict__ kh, double t0, double t1, double sig, double alpha,
+              double kappa, float* __restrict__ w, double* __restrict__ dw) {
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i >= n) return;
+  const double ln10 = 2.302585092994045684;
+  const double M = mass[i];
+  const double mcut = exp(t0 * ln10), m1 = exp(t1 * ln10);
+  double v = 0.0, d[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (kind[i] == 0) {
+    const double u = (t0 * ln10 - log(M)) / (sqrt(2.0) * sig);
+    v = 0.5 * erfc(u);
+    const double dv_du = -exp(-u * u) / sqrt(M_PI);
+    d[0] = dv_du * ln10 / (sqrt(2.0) * sig);
+    d[2] = dv_du * (-u / sig);
+  } else {
+    const double x = (M - kappa * mcut) / m1;
+    const double K = (double)kh[i];
+    if (x > 0.0) {
+      const double xa = pow(x, alpha);
+      v = xa / K;
+      const double dv_dx = alpha * xa / x / K;
+      d[0] = dv_dx * (-kappa * mcut * ln10 / m1);
+      d[1] = dv_dx * (-x * ln10);
+      d[3] = xa * log(x) / K;
+      d[4] = dv_dx * (-mcut / m1);
+    }
+  }
+  w[i] = (float)v;
+  if (dw)
+    for (int k = 0; k < 5; ++k) dw[5 * i + k] = d[k];
+}
+
+// dL/dtheta_k = sum_i wbar_i dw_i/dtheta_k, per-block partials then a fixed-order sum.
+__global__ void __launch_bounds__(256)
+k_hod_chain_partial(int64_t n, const double* __restrict__ wbar, const double* __restrict__ dw,
+                    double* __restrict__ partial) {
+  __shared__ double red[5][256];
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  for (int k = 0; k < 5; ++k) red[k][threadIdx.x] = i < n ? wbar[i] * dw[5 * i + k] : 0.0;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 5; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partial[5 * (int64_t)blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_hod_chain_final(int nblk, const double* __restrict__ partial, double* __restrict__ out) {
+  if (threadIdx.x >= 5) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[5 * (int64_t)b + threadIdx.x];
+  out[threadIdx.x] = s;
+}
+
+cudaError_t launch_hod_weights(int64_t n, const double* mass, const int32_t* kind, const float* kh,
+                               const double theta[5], float* w, double* dw, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_hod_weights<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(n, mass, kind, kh, theta[0], theta[1], theta[2],
+                                                        theta[3], theta[4], w, dw);
+  return launched();
+}
+
+cudaError_t launch_hod_chain(int64_t n, const double* wbar, const double* dw, double* partial,
+                             double* out5, cudaStream_t s) {
+  const int nblk = (int)std::max<int64_t>(1, cdiv(n, 256));
+  k_hod_chain_partial<<<nblk, 256, 0, s>>>(n, wbar, dw, partial);
+  PG_CUDA_TRY(launched());
+  k_hod_chain_final<<<1, 32, 0, s>>>(nblk, partial, out5);
+  return launched();
+}
+
 cudaError_t launch_gal_final(int64_t n, const double* g, const double* T,
                              const unsigned long long* qsum, double n3, const double* wsbar,
                              const double* wgal, double* wbar, cudaStream_t s) {

@@ -998,6 +998,28 @@ pg_status pg_backward(pg_plan* p, const pg_result* grad_out, double* d_grad_w, v
   return herr ? PG_ERR_TIMEOUT : PG_OK;
 }
 
+pg_status pg_hod_weights(int64_t n, const double* d_mass, const int32_t* d_kind, const float* d_kh,
+                         const double* h_theta, float* d_w, double* d_dw_dtheta, void* stream) {
+  if (n < 0 || !h_theta || (n > 0 && (!d_mass || !d_kind || !d_kh || !d_w))) return PG_ERR_INVALID_ARG;
+  if (!(h_theta[2] > 0.0)) return PG_ERR_INVALID_ARG;
+  PG_TRY(launch_hod_weights(n, d_mass, d_kind, d_kh, h_theta, d_w, d_dw_dtheta,
+                            static_cast<cudaStream_t>(stream)));
+  return PG_OK;
+}
+
+pg_status pg_hod_chain(pg_plan* p, int64_t n, const double* d_wbar, const double* d_dw_dtheta,
+                       double* h_grad_theta, void* stream) {
+  if (!p || n < 0 || !h_grad_theta || (n > 0 && (!d_wbar || !d_dw_dtheta))) return PG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PG_TRY(p->part.ensure(sizeof(double) * (5 * (cdiv(std::max<int64_t>(n, 1), 256) + 2)), &p->total));
+  double* part = p->part.as<double>();
+  const int64_t nblk = std::max<int64_t>(1, cdiv(n, 256));
+  PG_TRY(launch_hod_chain(n, d_wbar, d_dw_dtheta, part, part + 5 * nblk, s));
+  PG_TRY(cudaMemcpyAsync(h_grad_theta, part + 5 * nblk, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  PG_TRY(cudaStreamSynchronize(s));
+  return PG_OK;
+}
+
 pg_status pg_plan_set_profiling(pg_plan* p, int32_t enable) {
   if (!p) return PG_ERR_INVALID_ARG;
   p->prof_on = enable != 0;

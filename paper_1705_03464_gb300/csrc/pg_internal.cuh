@@ -258,6 +258,10 @@ cudaError_t launch_pair_chain(int64_t np, const double* g, const double* T,
                               const unsigned long long* qsum, double n3, const double* ddbar,
                               const int32_t* pi, const int32_t* pj, const double* wgal,
                               double* wbar, cudaStream_t s);
+cudaError_t launch_hod_weights(int64_t n, const double* mass, const int32_t* kind, const float* kh,
+                               const double theta[5], float* w, double* dw, cudaStream_t s);
+cudaError_t launch_hod_chain(int64_t n, const double* wbar, const double* dw, double* partial,
+                             double* out5, cudaStream_t s);
 cudaError_t launch_gal_final(int64_t n, const double* g, const double* T,
                              const unsigned long long* qsum, double n3, const double* wsbar,
                              const double* wgal, double* wbar, cudaStream_t s);

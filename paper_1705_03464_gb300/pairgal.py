@@ -81,6 +81,8 @@ def _load():
         "pg_fft_c2r_3d": (C.c_int, [vp, vp, vp, vp]),
         "pg_pair_counts_static": (C.c_int, [i64, vp, vp, dbl, i32, vp, i32, vp, vp, vp]),
         "pg_backward": (C.c_int, [vp, C.POINTER(pg_result), vp, vp]),
+        "pg_hod_weights": (C.c_int, [i64, vp, vp, vp, vp, vp, vp, vp]),
+        "pg_hod_chain": (C.c_int, [vp, i64, vp, vp, vp, vp]),
         "pg_plan_set_profiling": (C.c_int, [vp, i32]),
         "pg_plan_last_stats": (C.c_int, [vp, vp, vp]),
     }
@@ -381,3 +383,31 @@ class PairGalFn:
         if not hasattr(cls, "_F"):
             cls._F = cls._fn()
         return cls._F.apply(w, plan, pos, vel)
+
+
+def pg_hod_weights(mass, kind, kh, theta, with_grad=True, stream=None):
+    """Soft HOD weights w [n] FP32 and dw/dtheta [n, 5] FP64 (device tensors)."""
+    import torch
+    n = int(mass.shape[0])
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    w = torch.empty(max(n, 1), dtype=torch.float32, device=mass.device)
+    dw = torch.empty((max(n, 1), 5), dtype=torch.float64, device=mass.device) if with_grad else None
+    _check(_lib.pg_hod_weights(n, _ptr(mass), _ptr(kind), _ptr(kh), _ptr(th), _ptr(w), _ptr(dw),
+                               _stream(stream)), "pg_hod_weights")
+    return w[:n], (dw[:n] if dw is not None else None)
+
+
+def pg_hod_chain(plan: Plan, wbar, dw, stream=None):
+    out = np.zeros(5)
+    _check(_lib.pg_hod_chain(plan.handle, int(wbar.shape[0]), _ptr(wbar), _ptr(dw), _ptr(out),
+                             _stream(stream)), "pg_hod_chain")
+    return out
+
+
+def hod_gradient(plan: Plan, pos, vel, mass, kind, kh, theta, grads, stream=None):
+    """Outputs at HOD parameters theta and dL/dtheta for L = sum grads * outputs:
+    soft weights -> pg_forward -> pg_backward -> chain, all on the device."""
+    w, dw = pg_hod_weights(mass, kind, kh, theta, True, stream)
+    out = pg_forward(plan, pos, vel, w, stream)
+    wbar = pg_backward(plan, grads, int(pos.shape[0]), stream)
+    return out, pg_hod_chain(plan, wbar, dw, stream)

@@ -219,3 +219,44 @@ def subsample(cat: Catalogue, n_max: Optional[int], seed: int = 0) -> Catalogue:
     idx = np.sort(rng.choice(cat.n, n_max, replace=False))
     return Catalogue(cat.pos[idx], cat.vel[idx], cat.halo_id[idx],
                      cat.is_central[idx], cat.box_L)
+
+
+@dataclasses.dataclass
+class Candidates:
+    """Candidate galaxies whose weights are soft HOD occupations: one central
+    candidate per halo and K satellite candidates per halo that can host
+    satellites, at positions drawn once from the seed (so that a change of
+    HOD parameters changes only the weights)."""
+    pos: np.ndarray      # [n, 3] float64
+    vel: np.ndarray      # [n, 3] float32
+    mass: np.ndarray     # [n] float64, host halo mass
+    kind: np.ndarray     # [n] int32, 0 central, 1 satellite
+    kh: np.ndarray       # [n] float32, satellite candidates of the halo (1 for centrals)
+    box_L: float
+
+    @property
+    def n(self) -> int:
+        return self.pos.shape[0]
+
+
+def make_candidates(box_L: float, n_gal: int, seed: int, hod=HOD_Z09,
+                    min_ncen: float = 1e-3) -> Candidates:
+    halos = make_halos(box_L, n_gal, seed, hod)
+    rng = np.random.default_rng([seed, 5])
+    ncen, nsat = hod_mean_occupation(halos.mass, hod)
+    log_mcut, _, _, _, kappa = hod
+    cen = np.nonzero(ncen > min_ncen)[0]
+    # halos above 10^-0.2 kappa M_cut may host satellites under nearby HODs
+    can_sat = halos.mass > 10.0 ** (log_mcut - 0.2) * kappa * 0.999
+    k = np.where(can_sat, np.maximum(1, np.ceil(2.0 * nsat)), 0).astype(np.int64)
+    sat = np.repeat(np.arange(halos.mass.size), k)
+    off = _uniform_in_sphere(rng, sat.size) * halos.radius[sat, None]
+    sigma_v = np.sqrt(G_NEWTON * halos.mass / (2.0 * halos.radius))
+    sat_vel = halos.vel[sat] + rng.standard_normal((sat.size, 3)) * sigma_v[sat, None]
+    pos = np.mod(np.concatenate([halos.pos[cen], halos.pos[sat] + off]), box_L)
+    pos[pos >= box_L] = 0.0
+    vel = np.concatenate([halos.vel[cen], sat_vel]).astype(np.float32)
+    mass = np.concatenate([halos.mass[cen], halos.mass[sat]])
+    kind = np.concatenate([np.zeros(cen.size, np.int32), np.ones(sat.size, np.int32)])
+    kh = np.concatenate([np.ones(cen.size), k[sat]]).astype(np.float32)
+    return Candidates(pos, vel, mass, kind, kh, box_L)

@@ -85,3 +85,95 @@ def test_autograd_function(pg):
     ref = oa.grad_weights(st, {"b_pg": np.ones_like(o["b_pg"]), "q_eff": 0.5 * np.ones_like(o["q_eff"])})
     got = wt.grad.double().cpu().numpy()
     assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+def _hod_grads(pg, plan, cand, th, keys, seed):
+    pos, mass = dev(cand.pos), dev(cand.mass)
+    kind, kh = dev(cand.kind), dev(cand.kh)
+    w, _ = pg.pg_hod_weights(mass, kind, kh, th, with_grad=False)
+    out = pg.pg_forward(plan, pos, None, w)
+    rng = np.random.default_rng(seed)
+    gbar = {k: rng.standard_normal(np.asarray(out[k]).shape) for k in keys}
+    out, g = pg.hod_gradient(plan, pos, None, mass, kind, kh, th, gbar)
+
+    def loss(t):
+        wt, _ = pg.pg_hod_weights(mass, kind, kh, t, with_grad=False)
+        o = pg.pg_forward(plan, pos, None, wt)
+        return sum(float(np.nansum(gbar[k] * np.asarray(o[k]))) for k in keys)
+
+    return gbar, g, loss
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_hod_gradient_matches_oracle(pg, precision):
+    from oracle import hod
+    th = np.array(synth.HOD_Z09)
+    th[3] = 1.1
+    L = 64.0
+    cand = synth.make_candidates(L, 300, seed=4)
+    p = pipeline.Params(L, 32, 1, (0.0, 2.0, 4.0), 2, (6.0, 9.0, 13.0), 2)
+    plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur, precision=precision)
+    keys = ("b_pg", "q_eff", "xi_pg", "xi_gg")
+    gbar, g, _ = _hod_grads(pg, plan, cand, th, keys, 1)
+    # the weights themselves: device kernel against the oracle's eq. hod
+    w, dw = pg.pg_hod_weights(dev(cand.mass), dev(cand.kind), dev(cand.kh), th)
+    wo = hod.weights(th, cand.mass, cand.kind, cand.kh)
+    assert np.allclose(w.cpu().numpy(), wo.astype(np.float32), rtol=2e-7, atol=1e-12)
+    assert np.allclose(dw.cpu().numpy(), hod.dweights(th, cand.mass, cand.kind, cand.kh), rtol=1e-9, atol=1e-12)
+    # dL/dtheta: oracle reverse mode at the FP32 weights the GPU used
+    st = oa.forward_state(p, cand.pos, None, w.cpu().numpy().astype(np.float64))
+    wbar = oa.grad_weights(st, gbar)
+    ref = hod.grad_theta(th, cand.mass, cand.kind, cand.kh, wbar)
+    # each component is a sum with cancellation: bound the error by the sum
+    # of the magnitudes of its terms, sum_i |wbar_i dw_i/dtheta_k|
+    cond = np.abs(hod.dweights(th, cand.mass, cand.kind, cand.kh)).T @ np.abs(wbar)
+    tol = 1e-9 if precision else 2e-4
+    assert np.all(np.abs(g - ref) <= tol * cond), (g, ref, cond)
+
+
+@pytest.mark.slow
+def test_hod_gradient_finite_differences_512(pg):
+    """The 512^3 CIC gradient workload (about 40k candidates, 10 x 5 pair bins,
+    10 x 5 correlation bins). log10 M_1, sigma and alpha leave the set of
+    occupied satellites unchanged, so the loss is smooth in them and central
+    differences in theta check dL/dtheta directly. log10 M_cut and kappa move
+    the satellite threshold kappa M_cut, where w ~ x^alpha has an unbounded
+    second derivative for alpha < 2, so there the check is a difference along
+    dw/dtheta_k in weight space at FP32-representable points."""
+    wl = synth.WORKLOADS["rsd_cic_512"]
+    th = np.array(synth.HOD_Z09)
+    th[3] = 1.1
+    cand = synth.make_candidates(wl.box_L, 18000, seed=0, min_ncen=0.2)
+    keys = ("b_pg_agg", "q_eff_agg", "xi_gg")
+    plan64 = pg.Plan(wl.box_L, wl.mesh_n, 1, wl.s_edges, wl.n_mu, wl.r_edges, wl.n_mur, precision=1)
+    gbar, g64, loss = _hod_grads(pg, plan64, cand, th, keys, 3)
+    # the weights reach the plan rounded to FP32, a relative error of about
+    # 2^-24 / h on each weight's difference: a step of 1e-3 keeps it small
+    for k in (1, 2, 3):
+        tp, tm = th.copy(), th.copy()
+        tp[k] += 1e-3
+        tm[k] -= 1e-3
+        fd = (loss(tp) - loss(tm)) / 2e-3
+        assert abs(fd - g64[k]) <= 1e-3 * abs(g64[k]) + 1e-6, (k, fd, g64[k])
+    pos, mass = dev(cand.pos), dev(cand.mass)
+    w, dw = pg.pg_hod_weights(mass, dev(cand.kind), dev(cand.kh), th)
+    w, dw = w.cpu().numpy().astype(np.float64), dw.cpu().numpy()
+
+    def loss_w(wv):
+        o = pg.pg_forward(plan64, pos, None, dev(wv.astype(np.float32)))
+        return sum(float(np.nansum(gbar[k] * np.asarray(o[k]))) for k in keys)
+
+    pg.pg_forward(plan64, pos, None, dev(w.astype(np.float32)))
+    wbar = pg.pg_backward(plan64, gbar, cand.n).cpu().numpy()
+    for k in (0, 4):
+        wp = (w + 1e-4 * dw[:, k]).astype(np.float32).astype(np.float64)
+        wm = (w - 1e-4 * dw[:, k]).astype(np.float32).astype(np.float64)
+        fd = (loss_w(wp) - loss_w(wm)) / 2.0
+        # against the step actually taken, (wp - wm) / 2
+        assert abs(fd - wbar @ ((wp - wm) / 2.0)) <= 1e-4 * abs(fd), (k, fd)
+        # and the device chain against the same sum taken on the host
+        assert abs(dw[:, k] @ wbar - g64[k]) <= 1e-10 * (np.abs(dw[:, k]) @ np.abs(wbar)), (k, g64[k])
+    plan32 = pg.Plan(wl.box_L, wl.mesh_n, 1, wl.s_edges, wl.n_mu, wl.r_edges, wl.n_mur, precision=0)
+    _, g32, _ = _hod_grads(pg, plan32, cand, th, keys, 3)
+    cond = np.abs(dw).T @ np.abs(wbar)
+    assert np.all(np.abs(g32 - g64) <= 2e-4 * cond), (g32, g64, cond)
