@@ -405,7 +405,7 @@ cudaError_t correlate_window(pg_plan* p, int nb, bool gg, double* sums, cudaStre
     // find F_g in L2); writes the z window of each mesh
     ProfScope ps(p, PG_FAM_FFT_Z_CORR, s,
                  (gg ? 0.0 : nb * N * N * M1 * cs) + N * N * M1 * cs + nb * W * N * M1 * cs);
-    PG_CUDA_TRY(FftPasses<R>::z_corr(p->N, nb, p->S.as<C>(), S_stride, p->Fg.as<C>(), gg, p->w,
+    PG_CUDA_TRY(FftPasses<R>::z_corr(p->N, nb, p->S.as<C>(), p->Fg.as<C>(), gg, p->w,
                                      p->Wz.as<C>(), Wz_stride, p->P, tw,
                                      p->flag.as<int32_t>() + 1, s));
   }

@@ -12,10 +12,22 @@ template <typename R> struct Cols;
 // CTA's loads overlap another's arithmetic
 template <> struct Cols<float> { static constexpr int B = 8; };
 template <> struct Cols<double> { static constexpr int B = 4; };
-// the fused z pass holds two mesh tiles and the galaxy tile: 64 KB each
+// Tile width of the persistent TMA passes (fused z pass, windowed y
+// inverse): 64 KB tiles.
 template <typename R> struct ZCols;
 template <> struct ZCols<float> { static constexpr int B = 8; };
 template <> struct ZCols<double> { static constexpr int B = 4; };
+
+// Resident CTAs per SM of a persistent kernel, at least one.
+template <typename K>
+static cudaError_t persistent_grid(K kern, int threads, size_t smem, int64_t items, unsigned* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  PG_CUDA_TRY(cudaGetDevice(&dev));
+  PG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+  *grid = (unsigned)std::min<int64_t>(items, (int64_t)sms * std::max(1, per_sm));
+  return cudaSuccess;
+}
 }  // namespace fft
 
 #define PG_DISPATCH_N(N, ...)                               \
@@ -94,9 +106,8 @@ cudaError_t FftPasses<R>::z_fwd(int N, C* S, int P, const C* tw, cudaStream_t s)
 }
 
 template <typename R>
-cudaError_t FftPasses<R>::z_corr(int N, int nb, const C* S, int64_t S_stride, const C* Fg,
-                                 bool gg, int w, C* Wz, int64_t Wz_stride, int P, const C* tw,
-                                 int* err, cudaStream_t s) {
+cudaError_t FftPasses<R>::z_corr(int N, int nb, const C* S, const C* Fg, bool gg, int w, C* Wz,
+                                 int64_t Wz_stride, int P, const C* tw, int* err, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   constexpr int B = fft::ZCols<R>::B;
   constexpr int E = (int)(sizeof(C) / 8);
@@ -111,16 +122,12 @@ cudaError_t FftPasses<R>::z_corr(int N, int nb, const C* S, int64_t S_stride, co
   if (!encode_map_4d(&mF, Fg, dF, strides, box)) return cudaErrorInvalidValue;
   if (!encode_map_4d(&mS, gg ? (const void*)Fg : (const void*)S, gg ? dF : dS, strides, box))
     return cudaErrorInvalidValue;
-  (void)S_stride;
-  int dev = 0, sms = 0;
-  PG_CUDA_TRY(cudaGetDevice(&dev));
-  PG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   PG_DISPATCH_N(N, {
     using Z = fft::ZCorr<C, NN, B>;
     auto k = fft::k_z_corr_tma<C, NN, B>;
     PG_CUDA_TRY(set_smem(k, Z::smem_bytes()));
-    const int64_t items = cdiv(NN / 2 + 1, B) * (int64_t)NN;
-    const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
+    unsigned grid = 0;
+    PG_CUDA_TRY(fft::persistent_grid(k, Z::THREADS, Z::smem_bytes(), cdiv(NN / 2 + 1, B) * (int64_t)NN, &grid));
     k<<<grid, Z::THREADS, Z::smem_bytes(), s>>>(mS, mF, nb, gg ? 1 : 0, w, Wz, Wz_stride, P, tw, err);
   });
   return launched();
@@ -141,15 +148,12 @@ cudaError_t FftPasses<R>::y_inv_win(int N, int nb, const C* Wz, int64_t Wz_strid
   const uint32_t box[4] = {(uint32_t)(B * E), N < 256 ? (uint32_t)N : 256u, 1u, 1u};
   CUtensorMap mW;
   if (!encode_map_4d(&mW, Wz, dims, strides, box)) return cudaErrorInvalidValue;
-  int dev = 0, sms = 0;
-  PG_CUDA_TRY(cudaGetDevice(&dev));
-  PG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   PG_DISPATCH_N(N, {
     using Y = fft::YInv<C, NN, B>;
     auto k = fft::k_y_inv_tma<C, NN, B>;
     PG_CUDA_TRY(set_smem(k, Y::smem_bytes()));
-    const int64_t items = cdiv(NN / 2 + 1, B) * (int64_t)W * nb;
-    const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
+    unsigned grid = 0;
+    PG_CUDA_TRY(fft::persistent_grid(k, Y::THREADS, Y::smem_bytes(), cdiv(NN / 2 + 1, B) * (int64_t)W * nb, &grid));
     k<<<grid, Y::THREADS, Y::smem_bytes(), s>>>(mW, nb, w, Wy, Wy_stride, P, tw, err);
   });
   return launched();

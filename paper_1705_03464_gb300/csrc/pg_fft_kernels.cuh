@@ -137,10 +137,24 @@ __device__ __forceinline__ C twid(const C* tw, int j) {
   return w;
 }
 
-// Step 1 of the split on B columns held as buf[n*LD + c]: tasks (c, j2).
-template <typename C, int N1, int N2, int B, bool INV>
-__device__ __forceinline__ void step1(C* buf, int LD, const C* tw, int tws) {
-  for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+// Rows of the split in shared memory. Tasks of one warp touch rows hi*span +
+// lo for consecutive hi; with rows of B complex values (fewer than 128 bytes)
+// those rows share banks. Storing row (hi, lo) at lo ^ (hi mod X), X = 128
+// bytes / row bytes, spreads them over all banks. X = 1 keeps the natural
+// order.
+template <int X>
+__device__ __forceinline__ int prow(int hi, int lo, int span) { return hi * span + (lo ^ (hi & (X - 1))); }
+
+// Step 1 of the split on B columns held as buf[n*LD + c]: tasks (c, j2). It
+// reads rows in natural order and writes row (k1, j2) at prow<X>(k1, j2, N2);
+// the tasks j2 ^ m it overwrites belong to the same warp (B * X <= 32), so a
+// warp barrier between its reads and writes makes it safe in place.
+// tid / nthr: this thread's index in, and the size of, the (warp-aligned)
+// group of threads sharing the tile.
+template <typename C, int N1, int N2, int B, bool INV, int X = 1>
+__device__ __forceinline__ void step1(C* buf, int LD, const C* tw, int tws, int tid, int nthr) {
+  static_assert(X == 1 || (B * X <= 32 && N2 % X == 0 && (B * N2) % 32 == 0), "row permutation");
+  for (int t = tid; t < B * N2; t += nthr) {
     const int c = t % B, j2 = t / B;
     C a[N1];
 #pragma unroll
@@ -150,22 +164,29 @@ __device__ __forceinline__ void step1(C* buf, int LD, const C* tw, int tws) {
 #pragma unroll
       for (int k1 = 1; k1 < N1; ++k1) a[k1] = cmul(a[k1], twid<C, INV>(tw, j2 * k1 * tws));
     }
+    if (X > 1) __syncwarp();
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) buf[(N2 * k1 + j2) * LD + c] = a[k1];
+    for (int k1 = 0; k1 < N1; ++k1) buf[prow<X>(k1, j2, N2) * LD + c] = a[k1];
   }
 }
 
+template <typename C, int N1, int N2, int B, bool INV, int X = 1>
+__device__ __forceinline__ void step1(C* buf, int LD, const C* tw, int tws) {
+  step1<C, N1, N2, B, INV, X>(buf, LD, tw, tws, (int)threadIdx.x, (int)blockDim.x);
+}
+
 // Step 2: task (c, k1) reads its N2 values and leaves X[k1 + N1*k2] in a[k2].
-template <typename C, int N1, int N2, bool INV>
+template <typename C, int N1, int N2, bool INV, int X = 1>
 __device__ __forceinline__ void step2(const C* buf, int LD, int c, int k1, C (&a)[N2]) {
 #pragma unroll
-  for (int j2 = 0; j2 < N2; ++j2) a[j2] = buf[(N2 * k1 + j2) * LD + c];
+  for (int j2 = 0; j2 < N2; ++j2) a[j2] = buf[prow<X>(k1, j2, N2) * LD + c];
   reg_dft<C, N2, INV>(a);
 }
 
 // Step A (inverse split from registers): a[k2] = X[k1 + N1*k2] of task
-// (c, k1) -> buf[(n2*N1 + k1)*LD + c] = W_N^(-+k1 n2) sum_k2 X W_N2^(-+k2 n2).
-template <typename C, int N1, int N2, bool INV>
+// (c, k1) -> row (n2, k1) = W_N^(-+k1 n2) sum_k2 X W_N2^(-+k2 n2), stored at
+// prow<X>(n2, k1, N1).
+template <typename C, int N1, int N2, bool INV, int X = 1>
 __device__ __forceinline__ void stepA(C* buf, int LD, int c, int k1, C (&a)[N2],
                                       const C* tw, int tws) {
   reg_dft<C, N2, INV>(a);
@@ -174,14 +195,14 @@ __device__ __forceinline__ void stepA(C* buf, int LD, int c, int k1, C (&a)[N2],
     for (int n2 = 1; n2 < N2; ++n2) a[n2] = cmul(a[n2], twid<C, INV>(tw, k1 * n2 * tws));
   }
 #pragma unroll
-  for (int n2 = 0; n2 < N2; ++n2) buf[(n2 * N1 + k1) * LD + c] = a[n2];
+  for (int n2 = 0; n2 < N2; ++n2) buf[prow<X>(n2, k1, N1) * LD + c] = a[n2];
 }
 
 // Step B: task (c, n2) -> out[n1] = x[n2 + N2*n1].
-template <typename C, int N1, int N2, bool INV>
+template <typename C, int N1, int N2, bool INV, int X = 1>
 __device__ __forceinline__ void stepB(const C* buf, int LD, int c, int n2, C (&a)[N1]) {
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) a[k1] = buf[(n2 * N1 + k1) * LD + c];
+  for (int k1 = 0; k1 < N1; ++k1) a[k1] = buf[prow<X>(n2, k1, N1) * LD + c];
   reg_dft<C, N1, INV>(a);
 }
 
@@ -189,6 +210,15 @@ template <int N> struct Split {
   static constexpr int N1 = N < 32 ? N : 32;
   static constexpr int N2 = N / N1;
 };
+
+// Row permutation span for column tiles of B complex values (see prow).
+template <typename C, int N, int B>
+__host__ __device__ constexpr int xperm() {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  constexpr int row = B * (int)sizeof(C);
+  constexpr int X = row >= 128 ? 1 : 128 / row;
+  return (N2 % X == 0 && N1 % X == 0 && (B * N2) % 32 == 0 && B * X <= 32) ? X : 1;
+}
 
 __device__ __forceinline__ int win_index(int n, int N, int w) {
   // signed offset of mesh index n in (-N/2, N/2]; returns offset + w, or -1
@@ -257,7 +287,7 @@ __global__ void __launch_bounds__(XPass<C, N>::THREADS)
 k_x_r2c_lines(const int64_t* __restrict__ q, const int32_t* __restrict__ line_bin,
               const double* __restrict__ scale, int64_t n_lines, C* __restrict__ spec, int P,
               const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using RT = typename Real<C>::T;
@@ -273,7 +303,7 @@ template <typename C, int N>
 __global__ void __launch_bounds__(XPass<C, N>::THREADS)
 k_x_r2c_dense(const typename Real<C>::T* __restrict__ f, int64_t n_lines, C* __restrict__ spec,
               int P, const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
@@ -305,11 +335,12 @@ k_y_fwd(const C* __restrict__ spec, int P, const int32_t* __restrict__ idx,
         const int64_t* __restrict__ seg_total, const int64_t* __restrict__ line_base,
         const int32_t* __restrict__ line_y, C* __restrict__ S, int64_t S_stride,
         const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using CP = ColPass<C, N, B>;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
   const int kx0 = blockIdx.x * B;
   const int z = blockIdx.y;
   const int b = blockIdx.z;
@@ -338,11 +369,11 @@ k_y_fwd(const C* __restrict__ spec, int P, const int32_t* __restrict__ idx,
     }
   }
   __syncthreads();
-  step1<C, N1, N2, B, false>(buf, B, tws, 1);
+  step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
   __syncthreads();
   const int k1 = threadIdx.x / B;
   C a[N2];
-  step2<C, N1, N2, false>(buf, B, c, k1, a);
+  step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
   if (c < ncol) {
     C* out = S + (int64_t)b * S_stride + (int64_t)z * N * P + kx0 + c;
 #pragma unroll
@@ -366,124 +397,25 @@ __device__ __forceinline__ void load_zcol(C* buf, const C* __restrict__ src, int
 template <typename C, int N, int B>
 __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
 k_z_fwd(C* __restrict__ S, int P, const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using CP = ColPass<C, N, B>;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
   const int kx0 = blockIdx.x * B, ky = blockIdx.y;
   const int ncol = min(B, M1 - kx0);
   C* col = S + (int64_t)ky * P + kx0;
   load_zcol<C, N, B>(buf, col, P, ncol);
   __syncthreads();
-  step1<C, N1, N2, B, false>(buf, B, tws, 1);
+  step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
   __syncthreads();
   const int c = threadIdx.x % B, k1 = threadIdx.x / B;
   C a[N2];
-  step2<C, N1, N2, false>(buf, B, c, k1, a);
+  step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
   if (c < ncol) {
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) col[(int64_t)(k1 + N1 * k2) * N * P + c] = a[k2];
-  }
-}
-
-// Z pass fused: forward z, multiply, inverse z, window rows. CTA = (kx tile, ky).
-template <typename C, int N, int B>
-__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
-k_z_corr(int nb, const C* __restrict__ S, int64_t S_stride, const C* __restrict__ Fg, int gg,
-         int w, C* __restrict__ Wz, int64_t Wz_stride, int P, const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
-  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
-  using CP = ColPass<C, N, B>;
-  using RT = typename Real<C>::T;
-  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
-  const int kx0 = blockIdx.x * B, ky = blockIdx.y;
-  const int ncol = min(B, M1 - kx0);
-  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
-  const RT inv_n3 = (RT)(1.0 / ((double)N * (double)N * (double)N));
-  const C* gcol = Fg + (int64_t)ky * P + kx0 + c;
-  const bool dc_col = (kx0 + c == 0) && (ky == 0);
-  for (int b = 0; b < nb; ++b) {
-    C a[N2];
-    if (!gg) {
-      load_zcol<C, N, B>(buf, S + (int64_t)b * S_stride + (int64_t)ky * P + kx0, P, ncol);
-      __syncthreads();
-      step1<C, N1, N2, B, false>(buf, B, tws, 1);
-      __syncthreads();
-      step2<C, N1, N2, false>(buf, B, c, k1, a);
-#pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) {
-        C g;
-        g.x = 0; g.y = 0;
-        if (c < ncol) g = gcol[(int64_t)(k1 + N1 * k2) * N * P];
-        a[k2] = cscale(cmulc(a[k2], g), inv_n3);
-      }
-    } else {
-#pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) {
-        C g;
-        g.x = 0; g.y = 0;
-        if (c < ncol) g = gcol[(int64_t)(k1 + N1 * k2) * N * P];
-        a[k2].x = (g.x * g.x + g.y * g.y) * inv_n3;
-        a[k2].y = 0;
-      }
-    }
-    if (dc_col && k1 == 0) { a[0].x = 0; a[0].y = 0; }   // k = 0 mode
-    __syncthreads();
-    stepA<C, N1, N2, true>(buf, B, c, k1, a, tws, 1);
-    __syncthreads();
-    C* wout = Wz + (int64_t)b * Wz_stride + (int64_t)ky * P + kx0;
-    for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
-      const int cc = t % B, n2 = t / B;
-      C x[N1];
-      stepB<C, N1, N2, true>(buf, B, cc, n2, x);
-      if (cc < ncol) {
-#pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) {
-          const int zw = win_index(n2 + N2 * n1, N, w);
-          if (zw >= 0) wout[(int64_t)zw * N * P + cc] = x[n1];
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Inverse y on the window rows. CTA = (kx tile, zw, mesh).
-template <typename C, int N, int B>
-__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
-k_y_inv_win(const C* __restrict__ Wz, int64_t Wz_stride, int w, C* __restrict__ Wy,
-            int64_t Wy_stride, int P, const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
-  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
-  using CP = ColPass<C, N, B>;
-  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
-  const int kx0 = blockIdx.x * B, zw = blockIdx.y, b = blockIdx.z;
-  const int W = 2 * w + 1;
-  const int ncol = min(B, M1 - kx0);
-  const int c = threadIdx.x % B;
-  const C* src = Wz + (int64_t)b * Wz_stride + (int64_t)zw * N * P + kx0;
-  for (int y = threadIdx.x / B; y < N; y += blockDim.x / B) {
-    C v;
-    v.x = 0; v.y = 0;
-    if (c < ncol) v = src[(int64_t)y * P + c];
-    buf[y * B + c] = v;
-  }
-  __syncthreads();
-  step1<C, N1, N2, B, true>(buf, B, tws, 1);
-  __syncthreads();
-  const int k1 = threadIdx.x / B;
-  C a[N2];
-  step2<C, N1, N2, true>(buf, B, c, k1, a);
-  if (c < ncol) {
-    C* out = Wy + (int64_t)b * Wy_stride + (int64_t)zw * W * P + kx0 + c;
-#pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) {
-      const int yw = win_index(k1 + N1 * k2, N, w);
-      if (yw >= 0) out[(int64_t)yw * P] = a[k2];
-    }
   }
 }
 
@@ -564,7 +496,7 @@ __global__ void __launch_bounds__(XPass<C, N>::THREADS)
 k_x_c2r_lines(const C* __restrict__ S, int P, int64_t n_lines, const int32_t* __restrict__ line_y,
               const int32_t* __restrict__ line_z, typename Real<C>::T* __restrict__ out,
               typename Real<C>::T scale, const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using RT = typename Real<C>::T;
@@ -581,20 +513,21 @@ template <typename C, int N, int B>
 __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
 k_z_fwd_acc(const C* __restrict__ S, const C* __restrict__ X, C* __restrict__ A, int P,
             const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using CP = ColPass<C, N, B>;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
   const int kx0 = blockIdx.x * B, ky = blockIdx.y;
   const int ncol = min(B, M1 - kx0);
   load_zcol<C, N, B>(buf, S + (int64_t)ky * P + kx0, P, ncol);
   __syncthreads();
-  step1<C, N1, N2, B, false>(buf, B, tws, 1);
+  step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
   __syncthreads();
   const int c = threadIdx.x % B, k1 = threadIdx.x / B;
   C a[N2];
-  step2<C, N1, N2, false>(buf, B, c, k1, a);
+  step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
   if (c < ncol) {
     const int64_t base = (int64_t)ky * P + kx0 + c;
 #pragma unroll
@@ -614,11 +547,12 @@ k_z_fwd_acc(const C* __restrict__ S, const C* __restrict__ X, C* __restrict__ A,
 template <typename C, int N, int B>
 __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
 k_z_mul_inv(C* __restrict__ X, const C* __restrict__ Fg, int P, const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using CP = ColPass<C, N, B>;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
   const int kx0 = blockIdx.x * B, ky = blockIdx.y;
   const int ncol = min(B, M1 - kx0);
   const int c = threadIdx.x % B, k1 = threadIdx.x / B;
@@ -636,12 +570,12 @@ k_z_mul_inv(C* __restrict__ X, const C* __restrict__ Fg, int P, const C* __restr
   }
   if (kx0 + c == 0 && ky == 0 && k1 == 0) { a[0].x = 0; a[0].y = 0; }
   __syncthreads();   // twiddles staged
-  stepA<C, N1, N2, true>(buf, B, c, k1, a, tws, 1);
+  stepA<C, N1, N2, true, XP>(buf, B, c, k1, a, tws, 1);
   __syncthreads();
   for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
     const int cc = t % B, n2 = t / B;
     C x[N1];
-    stepB<C, N1, N2, true>(buf, B, cc, n2, x);
+    stepB<C, N1, N2, true, XP>(buf, B, cc, n2, x);
     if (cc < ncol) {
 #pragma unroll
       for (int n1 = 0; n1 < N1; ++n1)
@@ -655,7 +589,7 @@ template <typename C, int N>
 __global__ void __launch_bounds__(XPass<C, N>::THREADS)
 k_x_c2r_win(const C* __restrict__ Wy, int64_t Wy_stride, int w, typename Real<C>::T* __restrict__ Cwin,
             int64_t Cwin_stride, int P, typename Real<C>::T scale, const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using RT = typename Real<C>::T;
@@ -676,7 +610,7 @@ template <typename C, int N>
 __global__ void __launch_bounds__(XPass<C, N>::THREADS)
 k_x_c2r_full(const C* __restrict__ S, int P, typename Real<C>::T* __restrict__ out,
              const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using RT = typename Real<C>::T;
@@ -691,11 +625,12 @@ k_x_c2r_full(const C* __restrict__ S, int P, typename Real<C>::T* __restrict__ o
 template <typename C, int N, int B, bool ALONG_Z>
 __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
 k_col_inv_full(C* __restrict__ S, int P, const C* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
   using CP = ColPass<C, N, B>;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
   const int kx0 = blockIdx.x * B, other = blockIdx.y;
   const int ncol = min(B, M1 - kx0);
   const int c = threadIdx.x % B;
@@ -709,11 +644,11 @@ k_col_inv_full(C* __restrict__ S, int P, const C* __restrict__ tw) {
     buf[r * B + c] = v;
   }
   __syncthreads();
-  step1<C, N1, N2, B, true>(buf, B, tws, 1);
+  step1<C, N1, N2, B, true, XP>(buf, B, tws, 1);
   __syncthreads();
   const int k1 = threadIdx.x / B;
   C a[N2];
-  step2<C, N1, N2, true>(buf, B, c, k1, a);
+  step2<C, N1, N2, true, XP>(buf, B, c, k1, a);
   if (c < ncol) {
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) col[(int64_t)(k1 + N1 * k2) * rs + c] = a[k2];
@@ -736,7 +671,9 @@ struct ZCorr {
   static constexpr int ZB = N < 256 ? N : 256;   // rows per TMA box
   static constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
   static constexpr int E = sizeof(C) / 8;        // 8-byte TMA elements per complex
-  static constexpr size_t smem_bytes() { return sizeof(C) * (3 * (size_t)TILE + N) + 64; }
+  static constexpr size_t SMEM = sizeof(C) * (3 * (size_t)TILE + N) + 64;
+  static constexpr int MINB = SMEM <= 110 * 1024 ? 2 : 1;   // resident CTAs per SM
+  static constexpr size_t smem_bytes() { return SMEM; }
 };
 
 template <typename C, int N, int B>
@@ -749,13 +686,14 @@ __device__ __forceinline__ void zc_issue(C* dst, const CUtensorMap* map, uint64_
 }
 
 template <typename C, int N, int B>
-__global__ void __launch_bounds__(ZCorr<C, N, B>::THREADS, 1)
+__global__ void __launch_bounds__(ZCorr<C, N, B>::THREADS, ZCorr<C, N, B>::MINB)
 k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mF,
              int nb, int gg, int w, C* __restrict__ Wz, int64_t Wz_stride, int P,
              const C* __restrict__ tw, int* __restrict__ err) {
   using Z = ZCorr<C, N, B>;
   using RT = typename Real<C>::T;
   constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
   constexpr uint64_t kLimitNs = 2000000000ull;   // 2 s per wait
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* const sbuf0 = reinterpret_cast<C*>(smem_raw);   // mesh buffers: sbuf0 + k * TILE
@@ -805,9 +743,9 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
       if (!gg) {
         if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
         ph[cur] ^= 1;
-        step1<C, N1, N2, B, false>(buf, B, tws, 1);
+        step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
         __syncthreads();
-        step2<C, N1, N2, false>(buf, B, c, k1, a);
+        step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
           const C g = ftile[(k1 + N1 * k2) * B + c];
@@ -830,13 +768,13 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
         zc_issue<C, N, B>(ftile, &mF, &bar[2], (int)(nitem % T) * B, (int)(nitem / T), 0);
       }
       C* wbuf = gg ? sbuf0 : buf;
-      stepA<C, N1, N2, true>(wbuf, B, c, k1, a, tws, 1);
+      stepA<C, N1, N2, true, XP>(wbuf, B, c, k1, a, tws, 1);
       __syncthreads();
       C* wout = Wz + (int64_t)b * Wz_stride + (int64_t)ky * P + kx0;
       for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
         const int cc = t % B, n2 = t / B;
         C x[N1];
-        stepB<C, N1, N2, true>(wbuf, B, cc, n2, x);
+        stepB<C, N1, N2, true, XP>(wbuf, B, cc, n2, x);
         if (cc < ncol) {
 #pragma unroll
           for (int n1 = 0; n1 < N1; ++n1) {
@@ -873,7 +811,9 @@ struct YInv {
   static constexpr int YB = N < 256 ? N : 256;   // rows per TMA box
   static constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
   static constexpr int E = sizeof(C) / 8;
-  static constexpr size_t smem_bytes() { return sizeof(C) * (2 * (size_t)TILE + N) + 64; }
+  static constexpr size_t SMEM = sizeof(C) * (2 * (size_t)TILE + N) + 64;
+  static constexpr int MINB = SMEM <= 74 * 1024 ? 3 : SMEM <= 110 * 1024 ? 2 : 1;
+  static constexpr size_t smem_bytes() { return SMEM; }
 };
 
 template <typename C, int N, int B>
@@ -886,11 +826,12 @@ __device__ __forceinline__ void yi_issue(C* dst, const CUtensorMap* map, uint64_
 }
 
 template <typename C, int N, int B>
-__global__ void __launch_bounds__(YInv<C, N, B>::THREADS, 1)
+__global__ void __launch_bounds__(YInv<C, N, B>::THREADS, YInv<C, N, B>::MINB)
 k_y_inv_tma(const __grid_constant__ CUtensorMap mW, int nb, int w, C* __restrict__ Wy,
             int64_t Wy_stride, int P, const C* __restrict__ tw, int* __restrict__ err) {
   using Y = YInv<C, N, B>;
   constexpr int N1 = Y::N1, N2 = Y::N2, TILE = Y::TILE, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
   constexpr uint64_t kLimitNs = 2000000000ull;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* const buf0 = reinterpret_cast<C*>(smem_raw);   // buffers: buf0 + k * TILE
@@ -934,10 +875,10 @@ k_y_inv_tma(const __grid_constant__ CUtensorMap mW, int nb, int w, C* __restrict
     int kx0, zw, b;
     decode(item, kx0, zw, b);
     const int ncol = min(B, M1 - kx0);
-    step1<C, N1, N2, B, true>(buf, B, tws, 1);
+    step1<C, N1, N2, B, true, XP>(buf, B, tws, 1);
     __syncthreads();
     C a[N2];
-    step2<C, N1, N2, true>(buf, B, c, k1, a);
+    step2<C, N1, N2, true, XP>(buf, B, c, k1, a);
     if (c < ncol) {
       C* out = Wy + (int64_t)b * Wy_stride + (int64_t)zw * W * P + kx0 + c;
 #pragma unroll

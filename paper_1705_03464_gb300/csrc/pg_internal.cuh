@@ -164,9 +164,8 @@ struct FftPasses {
   // only the |z| <= w rows written: Wz[b] = [2w+1][ky][P]. Persistent and
   // TMA fed; S must be [nb][N][N][P] contiguous (S_stride = N*N*P) and P*sizeof(C)
   // a multiple of 16. A bounded wait that gives up sets *err (device) nonzero.
-  static cudaError_t z_corr(int N, int nb, const C* S, int64_t S_stride, const C* Fg,
-                            bool gg, int w, C* Wz, int64_t Wz_stride, int P, const C* tw,
-                            int* err, cudaStream_t s);
+  static cudaError_t z_corr(int N, int nb, const C* S, const C* Fg, bool gg, int w, C* Wz,
+                            int64_t Wz_stride, int P, const C* tw, int* err, cudaStream_t s);
   // Inverse y on the window rows: Wz[b][zw][ky] -> Wy[b][zw][yw], |y| <= w.
   static cudaError_t y_inv_win(int N, int nb, const C* Wz, int64_t Wz_stride, int w, C* Wy,
                                int64_t Wy_stride, int P, const C* tw, int* err, cudaStream_t s);
