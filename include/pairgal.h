@@ -145,10 +145,13 @@ pg_status pg_forward_host(pg_plan* plan, int64_t n_gal, const double* h_pos,
  * bpg_intermediate, Sec. 2.2 eqs. xi_dw, Qeff, Qeff_notsq, Sec. 3.4): ratio
  * outputs -> bin sums -> window fields -> mesh adjoints by FFT correlation ->
  * pair and galaxy weights -> w_i through w_p = w_i w_j. The galaxy and pair
- * spectra are recomputed, not stored. Without weights in the forward call the
- * gradient is taken at w = 1. Errors: PG_ERR_INVALID_ARG if no forward call
- * preceded (or a stage entry point reused the plan since), PG_ERR_OOM,
- * PG_ERR_CUDA, PG_ERR_TIMEOUT. Synchronises the stream. */
+ * spectra are recomputed, not stored; pair meshes go in the forward's
+ * batches. Without weights in the forward call the gradient is taken at
+ * w = 1. Errors: PG_ERR_INVALID_ARG if no forward call preceded (or a stage
+ * entry point reused the plan since), PG_ERR_UNSUPPORTED if the window side
+ * 2w+1 (w = ceil(r_max / (L/N))) exceeds 256 or the batched adjoint's shared
+ * tiles do not fit (FP64 at N = 1024: 2w+1 <= 151), PG_ERR_OOM, PG_ERR_CUDA,
+ * PG_ERR_TIMEOUT. Synchronises the stream. */
 pg_status pg_backward(pg_plan* plan, const pg_result* grad_out, double* d_grad_w, void* stream);
 
 /* Soft occupation weights of candidate galaxies under the five-parameter HOD
@@ -268,6 +271,14 @@ enum {
   PG_FAM_FFT_X_C2R,       /* x pass complex to real on the window */
   PG_FAM_BIN,             /* (r, mu_r) sums */
   PG_FAM_RATIOS,          /* xi, b_pg, Q_eff */
+  PG_FAM_ADJ_RATIOS,      /* adjoint: ratios -> bin-sum adjoints */
+  PG_FAM_ADJ_WINDOW,      /* adjoint: window fields, their x and y passes */
+  PG_FAM_ADJ_Z_GAL,       /* adjoint: A += F_b conj(X_b) (z transforms of S_b, X_b) */
+  PG_FAM_ADJ_Z_PAIR,      /* adjoint: z inverse of X_b F_g */
+  PG_FAM_ADJ_Y_INV,       /* adjoint: y inverse at the pair lines */
+  PG_FAM_ADJ_X_C2R,       /* adjoint: x C2R of the pair lines */
+  PG_FAM_ADJ_GATHER,      /* adjoint: interpolation at the pairs, chain to w_i */
+  PG_FAM_ADJ_GALAXY,      /* adjoint: galaxy side (inverse of A, gather, final) */
   PG_N_FAMILIES
 };
 
@@ -279,10 +290,11 @@ typedef struct pg_kernel_stat {
 } pg_kernel_stat;
 
 /* Enables (1) or disables (0) per-family event timing on later calls of
- * pg_forward / pg_forward_host on this plan. */
+ * pg_forward / pg_forward_host / pg_backward on this plan. */
 pg_status pg_plan_set_profiling(pg_plan* plan, int32_t enable);
 
-/* Statistics of the last pg_forward / pg_forward_host call: out[PG_N_FAMILIES]
+/* Statistics of the last pg_forward / pg_forward_host / pg_backward call
+ * (pg_backward's include the recomputed forward passes): out[PG_N_FAMILIES]
  * (host; times are 0 unless profiling was enabled) and *total_launches, the
  * number of kernels that call launched (always counted). Either may be NULL. */
 pg_status pg_plan_last_stats(const pg_plan* plan, pg_kernel_stat* out, int64_t* total_launches);

@@ -90,7 +90,7 @@ struct pg_plan {
   // adjoint: line z, pair galaxy indices, window geometry, spectra X and A,
   // galaxy-window correlation, scalar adjoints, upstream gradients, gathers
   DevBuf line_z, psi, psj, cell_bin, cell_agg, wl_idx, wl_tot, wl_base, wl_y, wlines;
-  DevBuf Xs, As, cggw, adjb, gout, gp, gj, part;
+  DevBuf Xs, As, Xw, cggw, adjb, gout, gp, gj, part;
   // state of the last successful forward call, which pg_backward differentiates
   bool fwd_ok = false, last_has_w = false;
   int64_t last_n = 0;
@@ -122,7 +122,9 @@ size_t rsize(const pg_plan* p) { return p->prm.precision ? sizeof(double) : size
 
 const char* kFamNames[PG_N_FAMILIES] = {"positions", "cells", "pairs", "deposit", "fft_x_r2c",
                                         "fft_y_fwd", "fft_z_fwd", "fft_z_corr", "fft_y_inv",
-                                        "fft_x_c2r", "bin", "ratios"};
+                                        "fft_x_c2r", "bin", "ratios", "adj_ratios",
+                                        "adj_window", "adj_z_gal", "adj_z_pair", "adj_y_inv",
+                                        "adj_x_c2r", "adj_gather", "adj_galaxy"};
 
 // Times the launches issued inside its scope (one kernel family) with a pair
 // of CUDA events on the call's stream, and books the family's algorithmic
@@ -728,11 +730,15 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   // buffers of the reverse sweep
   int64_t np_max = 0;
   for (auto v : p->last_hdd) np_max = std::max<int64_t>(np_max, (int64_t)v);
-  PG_CUDA_TRY(ensure_lines(p, (int64_t)p->W * p->W));
+  const int W = p->W, nbmax = p->nbmax;
+  const int64_t W2 = (int64_t)W * W;
+  const int64_t Xw_stride = (int64_t)W * N * p->P;
+  PG_CUDA_TRY(ensure_lines(p, nbmax * W2));
   PG_CUDA_TRY(p->Xs.ensure(sizeof(C) * spec_elems, t));
   PG_CUDA_TRY(p->As.ensure(sizeof(C) * spec_elems, t));
+  PG_CUDA_TRY(p->Xw.ensure(sizeof(C) * Xw_stride * nbmax, t));
   PG_CUDA_TRY(p->cggw.ensure(sizeof(R) * W3, t));
-  PG_CUDA_TRY(p->wlines.ensure(sizeof(R) * p->W * p->W * N, t));
+  PG_CUDA_TRY(p->wlines.ensure(sizeof(R) * W2 * N * nbmax, t));
   const size_t nadj = (size_t)P * Lq * 4 + 2 * Lq + P + 4;
   PG_CUDA_TRY(p->adjb.ensure(sizeof(double) * nadj, t));
   PG_CUDA_TRY(p->gp.ensure(sizeof(double) * std::max<int64_t>(np_max, 1), t));
@@ -786,52 +792,106 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   ra.g = g;
   ra.tmp = tmp;
   ra.Sbar = Sbar; ra.Gbar = Gbar; ra.G2bar = G2bar; ra.DDbar = DDbar; ra.wsbar = wsbar;
-  PG_CUDA_TRY(launch_adjoint_ratios(ra, s));
+  {
+    ProfScope ps(p, PG_FAM_ADJ_RATIOS, s, 0.0);
+    PG_CUDA_TRY(launch_adjoint_ratios(ra, s));
+  }
   PG_CUDA_TRY(cudaMemsetAsync(wbar, 0, sizeof(double) * std::max<int64_t>(n, 1), s));
   if (n == 0) return cudaSuccess;
   const double* gw = p->last_has_w ? p->gw.as<double>() : nullptr;
   // galaxy spectrum and galaxy correlation window, recomputed
   PG_CUDA_TRY((galaxy_pass<R>(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, true, s)));
   PG_CUDA_TRY(cudaMemcpyAsync(p->cggw.p, p->Cwin.p, sizeof(R) * W3, cudaMemcpyDeviceToDevice, s));
-  // A = 2 Re(F[Cbar_gg]) F_g
-  PG_CUDA_TRY(window_spectrum<R>(p, nullptr, Gbar, G2bar, s));
-  PG_CUDA_TRY(launch_acc_gg<R>(spec_elems, p->Xs.as<C>(), p->Fg.as<C>(), p->As.as<C>(), s));
-  // every pair mesh
-  std::vector<int64_t> off(P + 1, 0);
+  const double cs = (double)sizeof(C), rs = (double)sizeof(R), M1 = p->M1, Nd = N;
+  {
+    // A = 2 Re(F[Cbar_gg]) F_g: dense y and z passes of the gg window field
+    ProfScope ps(p, PG_FAM_ADJ_GALAXY, s, 5.0 * NN * M1 * cs);
+    PG_CUDA_TRY(window_spectrum<R>(p, nullptr, Gbar, G2bar, s));
+    PG_CUDA_TRY(launch_acc_gg<R>(spec_elems, p->Xs.as<C>(), p->Fg.as<C>(), p->As.as<C>(), s));
+  }
+  // the pair meshes in the forward's batches: S_b recomputed, the compact
+  // window spectra X_b, A += F_b conj(X_b), Y_b = z-inverse of X_b F_g over
+  // S's memory, its y inverse at the lines of the batch, their x C2R, and the
+  // gather at the pairs
+  const int64_t S_stride = NN * p->P;
+  int* err = p->flag.as<int32_t>() + 1;
+  R* hl = reinterpret_cast<R*>(p->lines_q.p);   // the deposit's lines are consumed by the x pass
+  std::vector<int64_t> off(P + 1, 0), hbase(nbmax, 0);
   for (int b = 0; b < P; ++b) off[b + 1] = off[b] + (int64_t)p->last_hdd[b];
-  for (int b = 0; b < P; ++b) {
-    const int64_t npb = (int64_t)p->last_hdd[b];
-    if (npb == 0) continue;
-    PG_CUDA_TRY(window_spectrum<R>(p, Sbar + (size_t)b * Lq, nullptr, nullptr, s));
+  int b0 = 0;
+  while (b0 < P) {
+    while (b0 < P && p->last_hdd[b0] == 0) ++b0;
+    if (b0 >= P) break;
+    const int b1 = std::min(P, b0 + nbmax);
+    const int nb = b1 - b0;
     int64_t nl = 0;
-    const int64_t o0 = off[b];
-    PG_CUDA_TRY(deposit_batch(p, npb, p->px.as<double>() + o0, p->py.as<double>() + o0,
-                              p->pz.as<double>() + o0, p->pw.as<double>() + o0,
-                              p->pbin.as<int32_t>() + o0, b, 1, &nl, s));
-    PG_CUDA_TRY(lines_to_S<R>(p, 1, nl, p->S.as<C>(), 0, s));
-    // galaxy side: A += F_b conj(F[Cbar_b])
-    PG_CUDA_TRY(FftPasses<R>::z_fwd_acc(N, p->S.as<C>(), p->Xs.as<C>(), p->As.as<C>(), p->P, tw, s));
-    // pair side: h_b = N^-6 IDFT[F[Cbar_b] F_g] on the lines of this mesh
-    PG_CUDA_TRY(FftPasses<R>::z_mul_inv(N, p->Xs.as<C>(), p->Fg.as<C>(), p->P, tw, s));
-    PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, p->Xs.as<C>(), p->P, tw, s));
-    R* hl = reinterpret_cast<R*>(p->lines_q.p);   // the deposit's lines were consumed by the x pass
-    PG_CUDA_TRY(FftPasses<R>::x_c2r_lines(N, p->Xs.as<C>(), p->P, nl, p->line_y.as<int32_t>(),
-                                          p->line_z.as<int32_t>(), hl, scale6, tw, s));
-    PG_CUDA_TRY(launch_gather<R>(geo, npb, p->px.as<double>() + o0, p->py.as<double>() + o0,
-                                 p->pz.as<double>() + o0, p->pw.as<double>() + o0,
-                                 p->lidx.as<int32_t>(), hl, p->gp.as<double>(), p->part.as<double>(),
-                                 Tdev, s));
-    PG_CUDA_TRY(launch_pair_chain(npb, p->gp.as<double>(), Tdev, p->qsum.as<unsigned long long>(), n3,
-                                  DDbar + b, p->psi.as<int32_t>() + o0, p->psj.as<int32_t>() + o0, gw,
-                                  wbar, s));
+    PG_CUDA_TRY(deposit_batch(p, off[b1] - off[b0], p->px.as<double>() + off[b0],
+                              p->py.as<double>() + off[b0], p->pz.as<double>() + off[b0],
+                              p->pw.as<double>() + off[b0], p->pbin.as<int32_t>() + off[b0], b0, nb,
+                              &nl, s));
+    PG_CUDA_TRY(cudaMemcpyAsync(hbase.data(), p->line_base.p, sizeof(int64_t) * nb,
+                                cudaMemcpyDeviceToHost, s));
+    PG_CUDA_TRY(lines_to_S<R>(p, nb, nl, p->S.as<C>(), S_stride, s));
+    const double dnb = nb, Wd = W, spec1 = NN * M1 * cs, win1 = Wd * Nd * M1 * cs;
+    {
+      ProfScope ps(p, PG_FAM_ADJ_WINDOW, s,
+                   dnb * (2.0 * W2 * Nd * rs + 2.0 * W2 * M1 * cs + win1));
+      for (int j = 0; j < nb; ++j)
+        PG_CUDA_TRY(launch_window_field<R>(N, p->w, p->cell_bin.as<int32_t>(), p->cell_agg.as<uint8_t>(),
+                                           p->nQ, Sbar + (size_t)(b0 + j) * Lq, nullptr, nullptr,
+                                           p->cggw.as<R>(), p->wlines.as<R>() + j * W2 * N, s));
+      PG_CUDA_TRY(FftPasses<R>::x_r2c_real(N, p->wlines.as<R>(), nb * W2, p->spec.as<C>(), p->P, tw, s));
+      PG_CUDA_TRY(FftPasses<R>::y_fwd_win(N, nb, p->spec.as<C>(), p->P, p->w, p->Xw.as<C>(), Xw_stride,
+                                          tw, s));
+    }
+    {
+      // S and the compact window spectra of every mesh, A read and written once
+      ProfScope ps(p, PG_FAM_ADJ_Z_GAL, s, dnb * (spec1 + win1) + 2.0 * spec1);
+      PG_CUDA_TRY(FftPasses<R>::zadj_gal(N, nb, p->S.as<C>(), p->Xw.as<C>(), Xw_stride, p->As.as<C>(),
+                                         p->w, p->P, tw, err, s));
+    }
+    {
+      // the window spectra and F_g in, Y_b out
+      ProfScope ps(p, PG_FAM_ADJ_Z_PAIR, s, dnb * (win1 + spec1) + spec1);
+      PG_CUDA_TRY(FftPasses<R>::zadj_pair(N, nb, p->Xw.as<C>(), Xw_stride, p->Fg.as<C>(), p->S.as<C>(),
+                                          S_stride, p->w, p->P, tw, err, s));
+    }
+    {
+      // Y_b in (planes that hold lines; counted whole), the lines out
+      ProfScope ps(p, PG_FAM_ADJ_Y_INV, s, dnb * spec1 + (double)nl * M1 * cs);
+      PG_CUDA_TRY(FftPasses<R>::y_inv_lines(N, nb, p->S.as<C>(), S_stride, p->P, p->lidx.as<int32_t>(),
+                                            p->seg_total.as<int64_t>(), p->line_base.as<int64_t>(),
+                                            p->line_y.as<int32_t>(), p->spec.as<C>(), tw, s));
+    }
+    {
+      ProfScope ps(p, PG_FAM_ADJ_X_C2R, s, (double)nl * (M1 * cs + Nd * rs));
+      PG_CUDA_TRY(FftPasses<R>::x_c2r_lines(N, p->spec.as<C>(), p->P, nl, nullptr, nullptr, hl, scale6,
+                                            tw, s));
+    }
+    PG_CUDA_TRY(cudaStreamSynchronize(s));   // hbase
+    ProfScope ps(p, PG_FAM_ADJ_GATHER, s, 96.0 * (double)(off[b1] - off[b0]));
+    for (int j = 0; j < nb; ++j) {
+      const int b = b0 + j;
+      const int64_t npb = (int64_t)p->last_hdd[b], o0 = off[b];
+      if (npb == 0) continue;
+      PG_CUDA_TRY(launch_gather<R>(geo, npb, p->px.as<double>() + o0, p->py.as<double>() + o0,
+                                   p->pz.as<double>() + o0, p->pw.as<double>() + o0,
+                                   p->lidx.as<int32_t>() + (size_t)j * NN, hl + hbase[j] * N,
+                                   p->gp.as<double>(), p->part.as<double>(), Tdev, s));
+      PG_CUDA_TRY(launch_pair_chain(npb, p->gp.as<double>(), Tdev, p->qsum.as<unsigned long long>() + j,
+                                    n3, DDbar + b, p->psi.as<int32_t>() + o0, p->psj.as<int32_t>() + o0,
+                                    gw, wbar, s));
+    }
+    b0 = b1;
   }
   // galaxy side: f_g adjoint = N^-6 IDFT[A] at the galaxy lines
+  ProfScope ps(p, PG_FAM_ADJ_GALAXY, s, 4.0 * NN * M1 * cs + 96.0 * (double)n);
   PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, p->As.as<C>(), p->P, tw, s));
   PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, p->As.as<C>(), p->P, tw, s));
   int64_t nlg = 0;
   PG_CUDA_TRY(deposit_batch(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, nullptr,
                             0, 1, &nlg, s));
-  R* hl = reinterpret_cast<R*>(p->lines_q.p);
+  hl = reinterpret_cast<R*>(p->lines_q.p);   // ensure_lines may have moved it
   PG_CUDA_TRY(FftPasses<R>::x_c2r_lines(N, p->As.as<C>(), p->P, nlg, p->line_y.as<int32_t>(),
                                         p->line_z.as<int32_t>(), hl, scale6, tw, s));
   PG_CUDA_TRY(launch_gather<R>(geo, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw,
@@ -984,7 +1044,12 @@ size_t pg_workspace_bytes(const pg_plan* p) { return p ? p->total : 0; }
 pg_status pg_backward(pg_plan* p, const pg_result* grad_out, double* d_grad_w, void* stream) {
   if (!p || !d_grad_w) return PG_ERR_INVALID_ARG;
   if (!p->fwd_ok) return PG_ERR_INVALID_ARG;
+  const bool fits = p->prm.precision ? FftPasses<double>::adj_fits(p->N, p->w)
+                                     : FftPasses<float>::adj_fits(p->N, p->w);
+  if (!fits) return PG_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  prof_begin(p);
+  const long long launches0 = launch_counter().load();
   PG_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));
   cudaError_t e = p->prm.precision ? backward_impl<double>(p, grad_out, d_grad_w, s)
                                    : backward_impl<float>(p, grad_out, d_grad_w, s);
@@ -995,6 +1060,10 @@ pg_status pg_backward(pg_plan* p, const pg_result* grad_out, double* d_grad_w, v
   int32_t herr = 0;
   PG_TRY(cudaMemcpyAsync(&herr, p->flag.as<int32_t>() + 1, 4, cudaMemcpyDeviceToHost, s));
   PG_TRY(cudaStreamSynchronize(s));
+  p->last_launches = launch_counter().load() - launches0;
+  if (p->prof_on) prof_end(p);
+  else
+    for (int f = 0; f < PG_N_FAMILIES; ++f) p->stats[f].bytes = p->fam_bytes[f];
   return herr ? PG_ERR_TIMEOUT : PG_OK;
 }
 

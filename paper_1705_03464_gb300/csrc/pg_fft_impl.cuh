@@ -230,28 +230,117 @@ cudaError_t FftPasses<R>::x_r2c_real(int N, const R* f, int64_t n_lines, C* spec
 }
 
 template <typename R>
-cudaError_t FftPasses<R>::z_fwd_acc(int N, const C* S, const C* X, C* A, int P, const C* tw,
-                                    cudaStream_t s) {
-  constexpr int B = fft::Cols<R>::B;
+bool FftPasses<R>::adj_fits(int N, int w) {
+  constexpr int B = fft::ZCols<R>::B;
+  const int W = 2 * w + 1;
+  if (W > 256 || W > N) return false;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  size_t need = 0;
+  PG_DISPATCH_N(N, { need = fft::ZAdj<C, NN, B>::smem_gal(W); });
+  return need <= (size_t)optin;
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::y_fwd_win(int N, int nb, const C* spec, int P, int w, C* Xw,
+                                    int64_t Xw_stride, const C* tw, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  constexpr int B = fft::ZCols<R>::B;
   PG_DISPATCH_N(N, {
     using CP = fft::ColPass<C, NN, B>;
-    auto k = fft::k_z_fwd_acc<C, NN, B>;
+    auto k = fft::k_y_fwd_win<C, NN, B>;
     PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
-    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, X, A, P, tw);
+    dim3 g((unsigned)cdiv(NN / 2 + 1, B), (unsigned)(2 * w + 1), (unsigned)nb);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(spec, P, w, Xw, Xw_stride, tw);
+  });
+  return launched();
+}
+
+namespace fft {
+// Tensor maps of the adjoint passes, over 8-byte elements: full columns of a
+// [b][z][ky][kx] array (pitch P, nb meshes) and compact window columns of
+// Xw[b][zr][ky][kx].
+template <typename R>
+static bool adj_col_map(CUtensorMap* m, const void* base, int N, int P, int nb) {
+  using C = typename CT<R>::C;
+  constexpr int B = ZCols<R>::B, E = (int)(sizeof(C) / 8);
+  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)N, (uint64_t)nb};
+  const uint64_t strides[3] = {(uint64_t)P * 8 * E, (uint64_t)N * P * 8 * E,
+                               (uint64_t)N * N * P * 8 * E};
+  const uint32_t box[4] = {(uint32_t)(B * E), 1u, N < 256 ? (uint32_t)N : 256u, 1u};
+  return encode_map_4d(m, base, dims, strides, box);
+}
+template <typename R>
+static bool adj_win_map(CUtensorMap* m, const void* base, int N, int P, int W, int nb, int64_t stride) {
+  using C = typename CT<R>::C;
+  constexpr int B = ZCols<R>::B, E = (int)(sizeof(C) / 8);
+  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)W, (uint64_t)nb};
+  const uint64_t strides[3] = {(uint64_t)P * 8 * E, (uint64_t)N * P * 8 * E, (uint64_t)stride * 8 * E};
+  const uint32_t box[4] = {(uint32_t)(B * E), 1u, (uint32_t)W, 1u};
+  return encode_map_4d(m, base, dims, strides, box);
+}
+}  // namespace fft
+
+template <typename R>
+cudaError_t FftPasses<R>::zadj_gal(int N, int nb, const C* S, const C* Xw, int64_t Xw_stride, C* A,
+                                   int w, int P, const C* tw, int* err, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  if (!adj_fits(N, w)) return cudaErrorInvalidValue;
+  constexpr int B = fft::ZCols<R>::B;
+  const int W = 2 * w + 1;
+  CUtensorMap mS, mX, mA;
+  if (!fft::adj_col_map<R>(&mS, S, N, P, nb) || !fft::adj_win_map<R>(&mX, Xw, N, P, W, nb, Xw_stride) ||
+      !fft::adj_col_map<R>(&mA, A, N, P, 1))
+    return cudaErrorInvalidValue;
+  PG_DISPATCH_N(N, {
+    using Z = fft::ZAdj<C, NN, B>;
+    auto k = fft::k_zadj_gal<C, NN, B>;
+    const size_t sm = Z::smem_gal(W);
+    PG_CUDA_TRY(set_smem(k, sm));
+    unsigned grid = 0;
+    PG_CUDA_TRY(fft::persistent_grid(k, Z::THREADS, sm, cdiv(NN / 2 + 1, B) * (int64_t)NN, &grid));
+    k<<<grid, Z::THREADS, sm, s>>>(mS, mX, mA, nb, w, A, P, tw, err);
   });
   return launched();
 }
 
 template <typename R>
-cudaError_t FftPasses<R>::z_mul_inv(int N, C* X, const C* Fg, int P, const C* tw, cudaStream_t s) {
-  constexpr int B = fft::Cols<R>::B;
+cudaError_t FftPasses<R>::zadj_pair(int N, int nb, const C* Xw, int64_t Xw_stride, const C* Fg, C* Y,
+                                    int64_t Y_stride, int w, int P, const C* tw, int* err,
+                                    cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  if (!adj_fits(N, w)) return cudaErrorInvalidValue;
+  constexpr int B = fft::ZCols<R>::B;
+  const int W = 2 * w + 1;
+  CUtensorMap mX, mF;
+  if (!fft::adj_win_map<R>(&mX, Xw, N, P, W, nb, Xw_stride) || !fft::adj_col_map<R>(&mF, Fg, N, P, 1))
+    return cudaErrorInvalidValue;
+  PG_DISPATCH_N(N, {
+    using Z = fft::ZAdj<C, NN, B>;
+    auto k = fft::k_zadj_pair<C, NN, B>;
+    const size_t sm = Z::smem_pair(W);
+    PG_CUDA_TRY(set_smem(k, sm));
+    unsigned grid = 0;
+    PG_CUDA_TRY(fft::persistent_grid(k, Z::THREADS, sm, cdiv(NN / 2 + 1, B) * (int64_t)NN, &grid));
+    k<<<grid, Z::THREADS, sm, s>>>(mX, mF, nb, w, Y, Y_stride, P, tw, err);
+  });
+  return launched();
+}
+
+template <typename R>
+cudaError_t FftPasses<R>::y_inv_lines(int N, int nb, const C* Y, int64_t Y_stride, int P,
+                                      const int32_t* idx, const int64_t* seg_total,
+                                      const int64_t* line_base, const int32_t* line_y, C* hspec,
+                                      const C* tw, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  constexpr int B = fft::ZCols<R>::B;
   PG_DISPATCH_N(N, {
     using CP = fft::ColPass<C, NN, B>;
-    auto k = fft::k_z_mul_inv<C, NN, B>;
+    auto k = fft::k_y_inv_lines<C, NN, B>;
     PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
-    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(X, Fg, P, tw);
+    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN, (unsigned)nb);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(Y, Y_stride, P, idx, seg_total, line_base, line_y, hspec, tw);
   });
   return launched();
 }

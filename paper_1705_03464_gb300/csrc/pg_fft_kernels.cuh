@@ -490,7 +490,8 @@ __device__ __forceinline__ void x_c2r_body(C* buf, int64_t l0, int64_t n_lines, 
 
 // C2R of scattered lines of a dense half spectrum S[z][y][P]: line l is
 // (line_z[l], line_y[l]); out[l][x] = scale * x-line value (the adjoint
-// fields at the lines that hold deposited points).
+// fields at the lines that hold deposited points). line_y == null: the
+// lines are compact, line l at S + l * P.
 template <typename C, int N>
 __global__ void __launch_bounds__(XPass<C, N>::THREADS)
 k_x_c2r_lines(const C* __restrict__ S, int P, int64_t n_lines, const int32_t* __restrict__ line_y,
@@ -503,85 +504,11 @@ k_x_c2r_lines(const C* __restrict__ S, int P, int64_t n_lines, const int32_t* __
   const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
   x_c2r_core<C, N>(
       buf, l0, n_lines,
-      [&](int64_t l, int k) { return S[((int64_t)line_z[l] * N + line_y[l]) * P + k]; }, tws,
+      [&](int64_t l, int k) {
+        return line_y ? S[((int64_t)line_z[l] * N + line_y[l]) * P + k] : S[l * P + k];
+      },
+      tws,
       [&](int64_t l, int n, RT v) { out[l * N + n] = v * scale; });
-}
-
-// Adjoint z pass, galaxy side: forward z of a mesh spectrum column (S after
-// the y pass), times conj(X) of the same column, added to A. CTA = (kx tile, ky).
-template <typename C, int N, int B>
-__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
-k_z_fwd_acc(const C* __restrict__ S, const C* __restrict__ X, C* __restrict__ A, int P,
-            const C* __restrict__ tw) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw) + N;
-  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
-  using CP = ColPass<C, N, B>;
-  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
-  constexpr int XP = xperm<C, N, B>();
-  const int kx0 = blockIdx.x * B, ky = blockIdx.y;
-  const int ncol = min(B, M1 - kx0);
-  load_zcol<C, N, B>(buf, S + (int64_t)ky * P + kx0, P, ncol);
-  __syncthreads();
-  step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
-  __syncthreads();
-  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
-  C a[N2];
-  step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
-  if (c < ncol) {
-    const int64_t base = (int64_t)ky * P + kx0 + c;
-#pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) {
-      const int64_t o = base + (int64_t)(k1 + N1 * k2) * N * P;
-      C acc = A[o];
-      const C t = cmulc(a[k2], X[o]);   // F_b conj(X)
-      acc.x += t.x;
-      acc.y += t.y;
-      A[o] = acc;
-    }
-  }
-}
-
-// Adjoint z pass, pair side: X * F_g (k = 0 zeroed), inverse z over the full
-// column, in place in X. CTA = (kx tile, ky).
-template <typename C, int N, int B>
-__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
-k_z_mul_inv(C* __restrict__ X, const C* __restrict__ Fg, int P, const C* __restrict__ tw) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw) + N;
-  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
-  using CP = ColPass<C, N, B>;
-  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
-  constexpr int XP = xperm<C, N, B>();
-  const int kx0 = blockIdx.x * B, ky = blockIdx.y;
-  const int ncol = min(B, M1 - kx0);
-  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
-  const int64_t base = (int64_t)ky * P + kx0 + c;
-  C a[N2];
-#pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) {
-    C v;
-    v.x = 0; v.y = 0;
-    if (c < ncol) {
-      const int64_t o = base + (int64_t)(k1 + N1 * k2) * N * P;
-      v = cmul(X[o], Fg[o]);
-    }
-    a[k2] = v;
-  }
-  if (kx0 + c == 0 && ky == 0 && k1 == 0) { a[0].x = 0; a[0].y = 0; }
-  __syncthreads();   // twiddles staged
-  stepA<C, N1, N2, true, XP>(buf, B, c, k1, a, tws, 1);
-  __syncthreads();
-  for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
-    const int cc = t % B, n2 = t / B;
-    C x[N1];
-    stepB<C, N1, N2, true, XP>(buf, B, cc, n2, x);
-    if (cc < ncol) {
-#pragma unroll
-      for (int n1 = 0; n1 < N1; ++n1)
-        X[(int64_t)ky * P + kx0 + cc + (int64_t)(n2 + N2 * n1) * N * P] = x[n1];
-    }
-  }
 }
 
 // Window lines of one mesh: line = zw*W + yw, output x offsets |x| <= w.
@@ -895,6 +822,359 @@ k_y_inv_tma(const __grid_constant__ CUtensorMap mW, int nb, int w, C* __restrict
       for (int k = 0; k < 2; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
     }
     __syncthreads();
+  }
+}
+
+
+// ============================================================================
+// Adjoint passes, batched like the forward (reverse sweep of Sec. 2.1's
+// correlation through FFTs). A window adjoint field is supported on the
+// |r| <= w window, so after its x and y passes only the W = 2w+1 window z
+// planes are nonzero; they are held compactly as Xw[b][zr][ky][kx], zr the
+// window rank of z (mesh_of_rank). Its z transform zero-pads those rows.
+// ============================================================================
+__device__ __forceinline__ int mesh_of_rank(int r, int N, int w) { return r <= w ? r : r - (2 * w + 1) + N; }
+
+// Y pass forward of the window lines of nb meshes into their W window
+// planes. Window line (b, zr, ry) is spec[((b * W + zr) * W + ry) * P] with
+// y = mesh_of_rank(ry). CTA = (kx tile, zr, mesh b).
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_t Xw_stride,
+            const C* __restrict__ tw) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
+  using CP = ColPass<C, N, B>;
+  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
+  const int W = 2 * w + 1;
+  const int kx0 = blockIdx.x * B, zr = blockIdx.y, b = blockIdx.z;
+  const int ncol = min(B, M1 - kx0);
+  const int c = threadIdx.x % B;
+  zero_tile<C, B>(buf, N);
+  __syncthreads();
+  const int64_t l0 = ((int64_t)b * W + zr) * W;
+  for (int r = threadIdx.x / B; r < W; r += blockDim.x / B)
+    if (c < ncol) buf[mesh_of_rank(r, N, w) * B + c] = spec[(l0 + r) * P + kx0 + c];
+  __syncthreads();
+  step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
+  __syncthreads();
+  const int k1 = threadIdx.x / B;
+  C a[N2];
+  step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
+  if (c < ncol) {
+    C* out = Xw + (int64_t)b * Xw_stride + (int64_t)zr * N * P + kx0 + c;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) out[(int64_t)(k1 + N1 * k2) * P] = a[k2];
+  }
+}
+
+template <typename C, int N, int B>
+struct ZAdj {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int THREADS = B * N1;
+  static constexpr int TILE = N * B;
+  static constexpr int ZB = N < 256 ? N : 256;   // rows per TMA box of a full column
+  static constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
+  static constexpr int E = sizeof(C) / 8;
+  // compact window slot in complex elements: W rows of B, rounded up to 128
+  // bytes (a TMA destination in shared memory must be 128-byte aligned)
+  static __host__ __device__ int win_slot(int W) {
+    constexpr int e = 128 / (int)sizeof(C);
+    return (W * B + e - 1) / e * e;
+  }
+  // galaxy side: two mesh tiles, the A tile, two compact window slots
+  static size_t smem_gal(int W) { return sizeof(C) * (3 * (size_t)TILE + 2 * (size_t)win_slot(W) + N) + 64; }
+  // pair side: the F_g tile, one work tile, two compact window slots
+  static size_t smem_pair(int W) { return sizeof(C) * (2 * (size_t)TILE + 2 * (size_t)win_slot(W) + N) + 64; }
+};
+
+// Full column (N rows) of a [b][z][ky][kx] array into dst.
+template <typename C, int N, int B>
+__device__ __forceinline__ void za_issue_col(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
+                                             int ky, int b) {
+  using Z = ZAdj<C, N, B>;
+#pragma unroll
+  for (int z0 = 0; z0 < N; z0 += Z::ZB) tma::load_4d(dst + z0 * B, map, bar, kx0 * Z::E, ky, z0, b);
+}
+
+// Compact window column (W rows) of Xw[b][zr][ky][kx] into dst.
+template <typename C, int N, int B>
+__device__ __forceinline__ void za_issue_win(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
+                                             int ky, int b) {
+  tma::load_4d(dst, map, bar, kx0 * ZAdj<C, N, B>::E, ky, 0, b);
+}
+
+// Zero-padded full column in natural row order from a compact window column.
+template <typename C, int N, int B>
+__device__ __forceinline__ void za_expand(C* buf, const C* xc, int w) {
+  const int W = 2 * w + 1;
+  for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
+    const int z = t / B, cc = t % B;
+    const int r = z <= w ? z : (z >= N - w ? z - N + W : -1);
+    C v;
+    v.x = 0; v.y = 0;
+    if (r >= 0) v = xc[r * B + cc];
+    buf[t] = v;
+  }
+}
+
+// Galaxy side: for every mesh b of the batch, A += F_b conj(X_b) with F_b
+// the z transform of S_b and X_b that of the window column; A accumulates in
+// shared memory over the batch and is read and written once per work item
+// (ky, kx tile). Persistent and TMA fed; mesh b's S and window tiles share
+// one of two slots so the next mesh streams in during the transforms.
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ZAdj<C, N, B>::THREADS, 1)
+k_zadj_gal(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mX,
+           const __grid_constant__ CUtensorMap mA, int nb, int w, C* __restrict__ A, int P,
+           const C* __restrict__ tw, int* __restrict__ err) {
+  using Z = ZAdj<C, N, B>;
+  constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
+  constexpr uint64_t kLimitNs = 2000000000ull;
+  const int W = 2 * w + 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* const sb0 = reinterpret_cast<C*>(smem_raw);   // slots: sb0 + k * TILE
+  C* const at = sb0 + 2 * TILE;                     // A tile
+  const int WS = Z::win_slot(W);
+  C* const xb0 = at + TILE;                         // compact window slots: xb0 + k * WS
+  C* const tws = xb0 + 2 * WS;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);   // [0], [1]: slots, [2]: A tile
+  const uint32_t slot_bytes = Z::TILE_BYTES + (uint32_t)(W * B * sizeof(C));
+  const int T = (M1 + B - 1) / B;
+  const int64_t n_items = (int64_t)T * N;
+  int64_t item = blockIdx.x;
+  if (item >= n_items) return;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
+  auto issue_slot = [&](int k, int64_t it, int b) {
+    const int ky = (int)(it / T), kx0 = (int)(it % T) * B;
+    tma::mbar_arrive_expect_tx(&bar[k], slot_bytes);
+    za_issue_col<C, N, B>(sb0 + k * TILE, &mS, &bar[k], kx0, ky, b);
+    za_issue_win<C, N, B>(xb0 + k * WS, &mX, &bar[k], kx0, ky, b);
+  };
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) tma::mbar_init(&bar[k], 1);
+    tma::fence_async_shared();
+    tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
+    za_issue_col<C, N, B>(at, &mA, &bar[2], (int)(item % T) * B, (int)(item / T), 0);
+    issue_slot(0, item, 0);
+  }
+  __syncthreads();
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  uint32_t ph[3] = {0, 0, 0};
+  int64_t job = 0;
+  int failed = 0;
+  for (; item < n_items && !failed; item += gridDim.x) {
+    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
+    if (__syncthreads_or(!tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
+    ph[2] ^= 1;
+    for (int b = 0; b < nb; ++b, ++job) {
+      const int cur = (int)(job & 1);
+      C* buf = sb0 + cur * TILE;
+      if (threadIdx.x == 0) {   // the next job's tiles into the other slot
+        int nbb = b + 1;
+        int64_t nitem = item;
+        if (nbb == nb) { nbb = 0; nitem = item + gridDim.x; }
+        if (nitem < n_items) {
+          tma::fence_async_shared();
+          issue_slot(cur ^ 1, nitem, nbb);
+        }
+      }
+      if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
+      ph[cur] ^= 1;
+      step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
+      __syncthreads();
+      C a[N2];
+      step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
+      __syncthreads();
+      za_expand<C, N, B>(buf, xb0 + cur * WS, w);
+      __syncthreads();
+      step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
+      __syncthreads();
+      C x[N2];
+      step2<C, N1, N2, false, XP>(buf, B, c, k1, x);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        C* o = &at[(k1 + N1 * k2) * B + c];
+        const C t = cmulc(a[k2], x[k2]);   // F_b conj(X_b)
+        C v = *o;
+        v.x += t.x;
+        v.y += t.y;
+        *o = v;
+      }
+      __syncthreads();   // slot free for the job after next
+    }
+    if (failed) break;
+    // the item's A column back to global memory, then the next item's A tile
+    C* ag = A + (int64_t)ky * P + kx0;
+    for (int t = threadIdx.x; t < TILE; t += blockDim.x) {
+      const int z = t / B, cc = t % B;
+      ag[(int64_t)z * N * P + cc] = at[t];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && item + gridDim.x < n_items) {
+      const int64_t nitem = item + gridDim.x;
+      tma::fence_async_shared();
+      tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
+      za_issue_col<C, N, B>(at, &mA, &bar[2], (int)(nitem % T) * B, (int)(nitem / T), 0);
+    }
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, tma::kErrTmaTimeout);
+      for (int k = 0; k < 3; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
+    }
+    __syncthreads();
+  }
+}
+
+// Pair side: for every mesh b of the batch, Y_b = inverse z of X_b F_g
+// (k = 0 set to zero) over the full column, written to Y[b][z][ky][kx] (the
+// next pass inverts y at the lines that hold pairs). Persistent and TMA fed:
+// the F_g tile once per work item, the window tiles in two slots.
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ZAdj<C, N, B>::THREADS, 1)
+k_zadj_pair(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mF, int nb,
+            int w, C* __restrict__ Y, int64_t Y_stride, int P, const C* __restrict__ tw,
+            int* __restrict__ err) {
+  using Z = ZAdj<C, N, B>;
+  constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
+  constexpr uint64_t kLimitNs = 2000000000ull;
+  const int W = 2 * w + 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* const ft = reinterpret_cast<C*>(smem_raw);   // F_g tile
+  C* const wb = ft + TILE;                         // work tile
+  const int WS = Z::win_slot(W);
+  C* const xb0 = wb + TILE;                        // compact window slots: xb0 + k * WS
+  C* const tws = xb0 + 2 * WS;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);   // [0], [1]: slots, [2]: F_g
+  const uint32_t win_bytes = (uint32_t)(W * B * sizeof(C));
+  const int T = (M1 + B - 1) / B;
+  const int64_t n_items = (int64_t)T * N;
+  int64_t item = blockIdx.x;
+  if (item >= n_items) return;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
+  auto issue_slot = [&](int k, int64_t it, int b) {
+    tma::mbar_arrive_expect_tx(&bar[k], win_bytes);
+    za_issue_win<C, N, B>(xb0 + k * WS, &mX, &bar[k], (int)(it % T) * B, (int)(it / T), b);
+  };
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) tma::mbar_init(&bar[k], 1);
+    tma::fence_async_shared();
+    tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
+    za_issue_col<C, N, B>(ft, &mF, &bar[2], (int)(item % T) * B, (int)(item / T), 0);
+    issue_slot(0, item, 0);
+  }
+  __syncthreads();
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  uint32_t ph[3] = {0, 0, 0};
+  int64_t job = 0;
+  int failed = 0;
+  for (; item < n_items && !failed; item += gridDim.x) {
+    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
+    const int ncol = min(B, M1 - kx0);
+    if (__syncthreads_or(!tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
+    ph[2] ^= 1;
+    const bool dc_col = (kx0 + c == 0) && (ky == 0);
+    for (int b = 0; b < nb; ++b, ++job) {
+      const int cur = (int)(job & 1);
+      if (threadIdx.x == 0) {
+        int nbb = b + 1;
+        int64_t nitem = item;
+        if (nbb == nb) { nbb = 0; nitem = item + gridDim.x; }
+        if (nitem < n_items) {
+          tma::fence_async_shared();
+          issue_slot(cur ^ 1, nitem, nbb);
+        }
+      }
+      if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
+      ph[cur] ^= 1;
+      za_expand<C, N, B>(wb, xb0 + cur * WS, w);
+      __syncthreads();
+      step1<C, N1, N2, B, false, XP>(wb, B, tws, 1);
+      __syncthreads();
+      C x[N2];
+      step2<C, N1, N2, false, XP>(wb, B, c, k1, x);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) x[k2] = cmul(x[k2], ft[(k1 + N1 * k2) * B + c]);
+      if (dc_col && k1 == 0) { x[0].x = 0; x[0].y = 0; }   // k = 0 mode
+      __syncthreads();
+      stepA<C, N1, N2, true, XP>(wb, B, c, k1, x, tws, 1);
+      __syncthreads();
+      C* yout = Y + (int64_t)b * Y_stride + (int64_t)ky * P + kx0;
+      for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+        const int cc = t % B, n2 = t / B;
+        C v[N1];
+        stepB<C, N1, N2, true, XP>(wb, B, cc, n2, v);
+        if (cc < ncol) {
+#pragma unroll
+          for (int n1 = 0; n1 < N1; ++n1) yout[(int64_t)(n2 + N2 * n1) * N * P + cc] = v[n1];
+        }
+      }
+      __syncthreads();   // work tile and slot free
+    }
+    if (failed) break;
+    if (threadIdx.x == 0 && item + gridDim.x < n_items) {   // F_g tile free after the barrier above
+      const int64_t nitem = item + gridDim.x;
+      tma::fence_async_shared();
+      tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
+      za_issue_col<C, N, B>(ft, &mF, &bar[2], (int)(nitem % T) * B, (int)(nitem / T), 0);
+    }
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, tma::kErrTmaTimeout);
+      for (int k = 0; k < 3; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
+    }
+    __syncthreads();
+  }
+}
+
+// Inverse y of Y_b on the z planes that hold lines of mesh b, stored only at
+// those lines: hspec[line][kx] for the compact lines of the batch (the
+// forward deposit's numbering). CTA = (kx tile, z plane, mesh b).
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+k_y_inv_lines(const C* __restrict__ Y, int64_t Y_stride, int P, const int32_t* __restrict__ idx,
+              const int64_t* __restrict__ seg_total, const int64_t* __restrict__ line_base,
+              const int32_t* __restrict__ line_y, C* __restrict__ hspec, const C* __restrict__ tw) {
+  using CP = ColPass<C, N, B>;
+  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
+  const int kx0 = blockIdx.x * B, z = blockIdx.y, b = blockIdx.z;
+  const int64_t NN = (int64_t)N * N;
+  const int32_t* ib = idx + (int64_t)b * NN;
+  const int64_t lo = ib[(int64_t)z * N];
+  const int64_t hi = (z + 1 < N) ? ib[(int64_t)(z + 1) * N] : seg_total[b];
+  if (lo >= hi) return;   // no lines of this mesh in plane z (whole CTA)
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
+  const int ncol = min(B, M1 - kx0);
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  const C* col = Y + (int64_t)b * Y_stride + (int64_t)z * N * P + kx0;
+  for (int ky = threadIdx.x / B; ky < N; ky += blockDim.x / B) {
+    C v;
+    v.x = 0; v.y = 0;
+    if (c < ncol) v = col[(int64_t)ky * P + c];
+    buf[ky * B + c] = v;
+  }
+  __syncthreads();
+  step1<C, N1, N2, B, true, XP>(buf, B, tws, 1);
+  __syncthreads();
+  C a[N2];
+  step2<C, N1, N2, true, XP>(buf, B, c, k1, a);
+  __syncthreads();
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) buf[(k1 + N1 * k2) * B + c] = a[k2];   // natural row y
+  __syncthreads();
+  const int64_t base = line_base[b];
+  for (int64_t r = lo + threadIdx.x / B; r < hi; r += blockDim.x / B) {
+    const int64_t l = base + r;
+    if (c < ncol) hspec[l * P + kx0 + c] = buf[line_y[l] * B + c];
   }
 }
 

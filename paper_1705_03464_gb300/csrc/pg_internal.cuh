@@ -183,12 +183,28 @@ struct FftPasses {
   // Adjoint passes. x R2C of n_lines real lines (line l at f + l*N).
   static cudaError_t x_r2c_real(int N, const R* f, int64_t n_lines, C* spec, int P, const C* tw,
                                 cudaStream_t s);
-  // A[kz][ky][kx] += F(kz) conj(X[kz][ky][kx]) with F the z transform of S.
-  static cudaError_t z_fwd_acc(int N, const C* S, const C* X, C* A, int P, const C* tw,
-                               cudaStream_t s);
-  // X <- inverse z of X * Fg (k = 0 zeroed), full columns, in place.
-  static cudaError_t z_mul_inv(int N, C* X, const C* Fg, int P, const C* tw, cudaStream_t s);
-  // out[l][x] = scale * C2R of row (line_z[l], line_y[l]) of S.
+  // Batched adjoint passes over nb pair meshes; window spectra are compact,
+  // Xw[b] = [W][N][P] over the window z planes (window rank zr), W = 2w+1.
+  // True when the fused passes fit this N and w (shared memory, TMA box).
+  static bool adj_fits(int N, int w);
+  // Y pass of the window lines (spec line (b*W + zr)*W + ry) into Xw.
+  static cudaError_t y_fwd_win(int N, int nb, const C* spec, int P, int w, C* Xw,
+                               int64_t Xw_stride, const C* tw, cudaStream_t s);
+  // A[kz][ky][kx] += sum_b F_b conj(X_b): F_b the z transform of S[b]
+  // ([nb][N][N][P] contiguous), X_b that of Xw[b] zero-padded.
+  static cudaError_t zadj_gal(int N, int nb, const C* S, const C* Xw, int64_t Xw_stride, C* A, int w,
+                              int P, const C* tw, int* err, cudaStream_t s);
+  // Y[b] = inverse z of X_b Fg (k = 0 zeroed), full columns.
+  static cudaError_t zadj_pair(int N, int nb, const C* Xw, int64_t Xw_stride, const C* Fg, C* Y,
+                               int64_t Y_stride, int w, int P, const C* tw, int* err, cudaStream_t s);
+  // Inverse y of Y[b] at the compact lines of the batch (numbering of the
+  // forward deposit: idx, seg_total, line_base, line_y) into hspec[line][P].
+  static cudaError_t y_inv_lines(int N, int nb, const C* Y, int64_t Y_stride, int P,
+                                 const int32_t* idx, const int64_t* seg_total,
+                                 const int64_t* line_base, const int32_t* line_y, C* hspec,
+                                 const C* tw, cudaStream_t s);
+  // out[l][x] = scale * C2R of row (line_z[l], line_y[l]) of S; line_y ==
+  // null: of the compact line S + l*P.
   static cudaError_t x_c2r_lines(int N, const C* S, int P, int64_t n_lines, const int32_t* line_y,
                                  const int32_t* line_z, R* out, double scale, const C* tw,
                                  cudaStream_t s);

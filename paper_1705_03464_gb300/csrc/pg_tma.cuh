@@ -62,9 +62,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   }
 }
 
-// 4D tiled load global -> shared, completion counted on `bar`.
+// 4D tiled load global -> shared, completion counted on `bar`. The shared
+// destination must be 128-byte aligned; a misaligned one is not issued, so
+// the waiting side runs into its bounded wait and reports an error.
 __device__ __forceinline__ void load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
                                         int c1, int c2, int c3) {
+  if (smem_addr(dst) & 127u) return;
   asm volatile(
       "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),

@@ -52,7 +52,7 @@ class pg_kernel_stat(C.Structure):
                 ("bytes", C.c_double)]
 
 
-PG_N_FAMILIES = 12
+PG_N_FAMILIES = 20
 
 
 class pg_result(C.Structure):
@@ -174,7 +174,7 @@ class Plan:
         _check(_lib.pg_plan_set_profiling(self.handle, 1 if on else 0), "pg_plan_set_profiling")
 
     def last_stats(self):
-        """Per kernel family of the last forward call: launches, ms, bytes;
+        """Per kernel family of the last forward or backward call: launches, ms, bytes;
         plus the total number of kernel launches of that call."""
         arr = (pg_kernel_stat * PG_N_FAMILIES)()
         tot = C.c_int64(0)

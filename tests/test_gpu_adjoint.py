@@ -49,6 +49,30 @@ def test_backward_matches_oracle_gradient(pg, precision, assign, rsd, cut):
     assert np.max(np.abs(got - ref)) <= tol * scale, np.max(np.abs(got - ref)) / scale
 
 
+@pytest.mark.parametrize("precision", [1, 0])
+def test_backward_across_batches(pg, precision):
+    """Pair meshes split over batches (4 meshes in one batch, in 3 + 1 and in
+    2 + 2): the batched passes run the same transforms per column and A
+    accumulates in the same order, so the gradients agree up to the order of
+    the FP64 atomic adds of the pair chain. (The one-batch gradient is held
+    to the oracle by the test above.)"""
+    p, cat, w = _case(1, 0.011, 3.0, seed=9)
+    rng = np.random.default_rng(12)
+    gbar = None
+    got = []
+    for per_batch in (4, 3, 2):
+        plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur,
+                       rsd_factor=p.rsd_factor, r_perp_cut=p.r_perp_cut, precision=precision,
+                       bins_per_batch=per_batch)
+        out = pg.pg_forward(plan, dev(cat.pos), dev(cat.vel), dev(w))
+        if gbar is None:
+            gbar = {k: rng.standard_normal(np.asarray(out[k]).shape) for k in oa.OUTPUT_KEYS}
+        got.append(pg.pg_backward(plan, gbar, cat.n).cpu().numpy())
+    scale = np.max(np.abs(got[0]))
+    for g in got[1:]:
+        assert np.max(np.abs(g - got[0])) <= 1e-12 * scale
+
+
 def test_backward_directional_finite_difference(pg):
     p, cat, w = _case(1, 0.011, 0.0, seed=5)
     plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur,
