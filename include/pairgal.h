@@ -273,8 +273,7 @@ enum {
   PG_FAM_RATIOS,          /* xi, b_pg, Q_eff */
   PG_FAM_ADJ_RATIOS,      /* adjoint: ratios -> bin-sum adjoints */
   PG_FAM_ADJ_WINDOW,      /* adjoint: window fields, their x and y passes */
-  PG_FAM_ADJ_Z_GAL,       /* adjoint: A += F_b conj(X_b) (z transforms of S_b, X_b) */
-  PG_FAM_ADJ_Z_PAIR,      /* adjoint: z inverse of X_b F_g */
+  PG_FAM_ADJ_Z,           /* adjoint z pass: A += F_b conj(X_b), z inverse of X_b F_g */
   PG_FAM_ADJ_Y_INV,       /* adjoint: y inverse at the pair lines */
   PG_FAM_ADJ_X_C2R,       /* adjoint: x C2R of the pair lines */
   PG_FAM_ADJ_GATHER,      /* adjoint: interpolation at the pairs, chain to w_i */

@@ -123,7 +123,7 @@ size_t rsize(const pg_plan* p) { return p->prm.precision ? sizeof(double) : size
 const char* kFamNames[PG_N_FAMILIES] = {"positions", "cells", "pairs", "deposit", "fft_x_r2c",
                                         "fft_y_fwd", "fft_z_fwd", "fft_z_corr", "fft_y_inv",
                                         "fft_x_c2r", "bin", "ratios", "adj_ratios",
-                                        "adj_window", "adj_z_gal", "adj_z_pair", "adj_y_inv",
+                                        "adj_window", "adj_z", "adj_y_inv",
                                         "adj_x_c2r", "adj_gather", "adj_galaxy"};
 
 // Times the launches issued inside its scope (one kernel family) with a pair
@@ -845,23 +845,18 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
                                           tw, s));
     }
     {
-      // S and the compact window spectra of every mesh, A read and written once
-      ProfScope ps(p, PG_FAM_ADJ_Z_GAL, s, dnb * (spec1 + win1) + 2.0 * spec1);
-      PG_CUDA_TRY(FftPasses<R>::zadj_gal(N, nb, p->S.as<C>(), p->Xw.as<C>(), Xw_stride, p->As.as<C>(),
-                                         p->w, p->P, tw, err, s));
-    }
-    {
-      // the window spectra and F_g in, Y_b out
-      ProfScope ps(p, PG_FAM_ADJ_Z_PAIR, s, dnb * (win1 + spec1) + spec1);
-      PG_CUDA_TRY(FftPasses<R>::zadj_pair(N, nb, p->Xw.as<C>(), Xw_stride, p->Fg.as<C>(), p->S.as<C>(),
-                                          S_stride, p->w, p->P, tw, err, s));
+      // S and the compact window spectra of every mesh in, Y_b out; A read
+      // and written once (F_g from L2, counted once)
+      ProfScope ps(p, PG_FAM_ADJ_Z, s, dnb * (2.0 * spec1 + win1) + 3.0 * spec1);
+      PG_CUDA_TRY(FftPasses<R>::zadj(N, nb, p->S.as<C>(), S_stride, p->Xw.as<C>(), Xw_stride,
+                                     p->Fg.as<C>(), p->As.as<C>(), p->w, p->P, tw, err, s));
     }
     {
       // Y_b in (planes that hold lines; counted whole), the lines out
       ProfScope ps(p, PG_FAM_ADJ_Y_INV, s, dnb * spec1 + (double)nl * M1 * cs);
       PG_CUDA_TRY(FftPasses<R>::y_inv_lines(N, nb, p->S.as<C>(), S_stride, p->P, p->lidx.as<int32_t>(),
                                             p->seg_total.as<int64_t>(), p->line_base.as<int64_t>(),
-                                            p->line_y.as<int32_t>(), p->spec.as<C>(), tw, s));
+                                            p->line_y.as<int32_t>(), p->spec.as<C>(), tw, err, s));
     }
     {
       ProfScope ps(p, PG_FAM_ADJ_X_C2R, s, (double)nl * (M1 * cs + Nd * rs));

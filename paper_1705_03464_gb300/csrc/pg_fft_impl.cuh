@@ -238,7 +238,7 @@ bool FftPasses<R>::adj_fits(int N, int w) {
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
   size_t need = 0;
-  PG_DISPATCH_N(N, { need = fft::ZAdj<C, NN, B>::smem_gal(W); });
+  PG_DISPATCH_N(N, { need = fft::ZAdj<C, NN, B>::smem(W); });
   return need <= (size_t)optin;
 }
 
@@ -283,8 +283,8 @@ static bool adj_win_map(CUtensorMap* m, const void* base, int N, int P, int W, i
 }  // namespace fft
 
 template <typename R>
-cudaError_t FftPasses<R>::zadj_gal(int N, int nb, const C* S, const C* Xw, int64_t Xw_stride, C* A,
-                                   int w, int P, const C* tw, int* err, cudaStream_t s) {
+cudaError_t FftPasses<R>::zadj(int N, int nb, C* S, int64_t S_stride, const C* Xw, int64_t Xw_stride,
+                               const C* Fg, C* A, int w, int P, const C* tw, int* err, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   if (!adj_fits(N, w)) return cudaErrorInvalidValue;
   constexpr int B = fft::ZCols<R>::B;
@@ -295,35 +295,12 @@ cudaError_t FftPasses<R>::zadj_gal(int N, int nb, const C* S, const C* Xw, int64
     return cudaErrorInvalidValue;
   PG_DISPATCH_N(N, {
     using Z = fft::ZAdj<C, NN, B>;
-    auto k = fft::k_zadj_gal<C, NN, B>;
-    const size_t sm = Z::smem_gal(W);
+    auto k = fft::k_zadj<C, NN, B>;
+    const size_t sm = Z::smem(W);
     PG_CUDA_TRY(set_smem(k, sm));
     unsigned grid = 0;
     PG_CUDA_TRY(fft::persistent_grid(k, Z::THREADS, sm, cdiv(NN / 2 + 1, B) * (int64_t)NN, &grid));
-    k<<<grid, Z::THREADS, sm, s>>>(mS, mX, mA, nb, w, A, P, tw, err);
-  });
-  return launched();
-}
-
-template <typename R>
-cudaError_t FftPasses<R>::zadj_pair(int N, int nb, const C* Xw, int64_t Xw_stride, const C* Fg, C* Y,
-                                    int64_t Y_stride, int w, int P, const C* tw, int* err,
-                                    cudaStream_t s) {
-  if (nb <= 0) return cudaSuccess;
-  if (!adj_fits(N, w)) return cudaErrorInvalidValue;
-  constexpr int B = fft::ZCols<R>::B;
-  const int W = 2 * w + 1;
-  CUtensorMap mX, mF;
-  if (!fft::adj_win_map<R>(&mX, Xw, N, P, W, nb, Xw_stride) || !fft::adj_col_map<R>(&mF, Fg, N, P, 1))
-    return cudaErrorInvalidValue;
-  PG_DISPATCH_N(N, {
-    using Z = fft::ZAdj<C, NN, B>;
-    auto k = fft::k_zadj_pair<C, NN, B>;
-    const size_t sm = Z::smem_pair(W);
-    PG_CUDA_TRY(set_smem(k, sm));
-    unsigned grid = 0;
-    PG_CUDA_TRY(fft::persistent_grid(k, Z::THREADS, sm, cdiv(NN / 2 + 1, B) * (int64_t)NN, &grid));
-    k<<<grid, Z::THREADS, sm, s>>>(mX, mF, nb, w, Y, Y_stride, P, tw, err);
+    k<<<grid, Z::THREADS, sm, s>>>(mS, mX, mA, nb, w, S, S_stride, Fg, A, P, tw, err);
   });
   return launched();
 }
@@ -332,15 +309,25 @@ template <typename R>
 cudaError_t FftPasses<R>::y_inv_lines(int N, int nb, const C* Y, int64_t Y_stride, int P,
                                       const int32_t* idx, const int64_t* seg_total,
                                       const int64_t* line_base, const int32_t* line_y, C* hspec,
-                                      const C* tw, cudaStream_t s) {
+                                      const C* tw, int* err, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   constexpr int B = fft::ZCols<R>::B;
+  constexpr int E = (int)(sizeof(C) / 8);
+  // Y as [b][z][ky][kx] over 8-byte elements; a box is one kx tile of up to
+  // 256 ky rows of one plane
+  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)N, (uint64_t)nb};
+  const uint64_t strides[3] = {(uint64_t)P * 8 * E, (uint64_t)N * P * 8 * E, (uint64_t)Y_stride * 8 * E};
+  const uint32_t box[4] = {(uint32_t)(B * E), N < 256 ? (uint32_t)N : 256u, 1u, 1u};
+  CUtensorMap mY;
+  if (!encode_map_4d(&mY, Y, dims, strides, box)) return cudaErrorInvalidValue;
   PG_DISPATCH_N(N, {
-    using CP = fft::ColPass<C, NN, B>;
+    using YL = fft::YLines<C, NN, B>;
     auto k = fft::k_y_inv_lines<C, NN, B>;
-    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
-    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN, (unsigned)nb);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(Y, Y_stride, P, idx, seg_total, line_base, line_y, hspec, tw);
+    PG_CUDA_TRY(set_smem(k, YL::smem_bytes()));
+    unsigned grid = 0;
+    PG_CUDA_TRY(fft::persistent_grid(k, YL::THREADS, YL::smem_bytes(),
+                                     cdiv(NN / 2 + 1, B) * (int64_t)NN * nb, &grid));
+    k<<<grid, YL::THREADS, YL::smem_bytes(), s>>>(mY, nb, P, idx, seg_total, line_base, line_y, hspec, tw, err);
   });
   return launched();
 }

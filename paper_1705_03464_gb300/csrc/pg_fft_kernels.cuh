@@ -884,52 +884,70 @@ struct ZAdj {
     constexpr int e = 128 / (int)sizeof(C);
     return (W * B + e - 1) / e * e;
   }
-  // galaxy side: two mesh tiles, the A tile, two compact window slots
-  static size_t smem_gal(int W) { return sizeof(C) * (3 * (size_t)TILE + 2 * (size_t)win_slot(W) + N) + 64; }
-  // pair side: the F_g tile, one work tile, two compact window slots
-  static size_t smem_pair(int W) { return sizeof(C) * (2 * (size_t)TILE + 2 * (size_t)win_slot(W) + N) + 64; }
+  // two mesh tiles, the A tile, two compact window slots
+  static size_t smem(int W) { return sizeof(C) * (3 * (size_t)TILE + 2 * (size_t)win_slot(W) + N) + 64; }
 };
 
 // Full column (N rows) of a [b][z][ky][kx] array into dst.
 template <typename C, int N, int B>
 __device__ __forceinline__ void za_issue_col(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
-                                             int ky, int b) {
+                                             int ky, int b, uint64_t policy) {
   using Z = ZAdj<C, N, B>;
 #pragma unroll
-  for (int z0 = 0; z0 < N; z0 += Z::ZB) tma::load_4d(dst + z0 * B, map, bar, kx0 * Z::E, ky, z0, b);
+  for (int z0 = 0; z0 < N; z0 += Z::ZB)
+    tma::load_4d_hint(dst + z0 * B, map, bar, kx0 * Z::E, ky, z0, b, policy);
 }
 
 // Compact window column (W rows) of Xw[b][zr][ky][kx] into dst.
 template <typename C, int N, int B>
 __device__ __forceinline__ void za_issue_win(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
-                                             int ky, int b) {
-  tma::load_4d(dst, map, bar, kx0 * ZAdj<C, N, B>::E, ky, 0, b);
+                                             int ky, int b, uint64_t policy) {
+  tma::load_4d_hint(dst, map, bar, kx0 * ZAdj<C, N, B>::E, ky, 0, b, policy);
 }
 
-// Zero-padded full column in natural row order from a compact window column.
-template <typename C, int N, int B>
-__device__ __forceinline__ void za_expand(C* buf, const C* xc, int w) {
+// Step 1 of the split (see step1) on the zero-padded window column whose
+// nonzero rows z <= w and z >= N - w come from the compact slot
+// xc[rank * B + c]: reads the slot directly, writes buf like step1.
+template <typename C, int N, int B, int X>
+__device__ __forceinline__ void step1_win(C* buf, const C* xc, int w, const C* tw) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   const int W = 2 * w + 1;
-  for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
-    const int z = t / B, cc = t % B;
-    const int r = z <= w ? z : (z >= N - w ? z - N + W : -1);
-    C v;
-    v.x = 0; v.y = 0;
-    if (r >= 0) v = xc[r * B + cc];
-    buf[t] = v;
+  for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+    const int c = t % B, j2 = t / B;
+    C a[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) {
+      const int z = N2 * j1 + j2;
+      const int r = z <= w ? z : (z >= N - w ? z - N + W : -1);
+      C v;
+      v.x = 0; v.y = 0;
+      if (r >= 0) v = xc[r * B + c];
+      a[j1] = v;
+    }
+    reg_dft<C, N1, false>(a);
+    if (N2 > 1 && j2 > 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) a[k1] = cmul(a[k1], twid<C, false>(tw, j2 * k1));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) buf[prow<X>(k1, j2, N2) * B + c] = a[k1];
   }
 }
 
-// Galaxy side: for every mesh b of the batch, A += F_b conj(X_b) with F_b
-// the z transform of S_b and X_b that of the window column; A accumulates in
-// shared memory over the batch and is read and written once per work item
-// (ky, kx tile). Persistent and TMA fed; mesh b's S and window tiles share
-// one of two slots so the next mesh streams in during the transforms.
+// Both sides of the adjoint z pass for every mesh b of the batch, per work
+// item (ky, kx tile): F_b = z transform of S_b, X_b = z transform of the
+// zero-padded window column; A += F_b conj(X_b) accumulates in shared memory
+// over the batch (A read and written once per item); then Y_b = inverse z of
+// X_b F_g (k = 0 set to zero), written over S_b's column, which this CTA has
+// already read. Persistent and TMA fed; mesh b's S and window tiles share one
+// of two slots so the next mesh streams in during the transforms. F_g is read
+// from global memory (L2: its tile is reused by every mesh of the item).
 template <typename C, int N, int B>
 __global__ void __launch_bounds__(ZAdj<C, N, B>::THREADS, 1)
-k_zadj_gal(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mX,
-           const __grid_constant__ CUtensorMap mA, int nb, int w, C* __restrict__ A, int P,
-           const C* __restrict__ tw, int* __restrict__ err) {
+k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mX,
+       const __grid_constant__ CUtensorMap mA, int nb, int w, C* __restrict__ S, int64_t S_stride,
+       const C* __restrict__ Fg, C* __restrict__ A, int P, const C* __restrict__ tw,
+       int* __restrict__ err) {
   using Z = ZAdj<C, N, B>;
   constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1;
   constexpr int XP = xperm<C, N, B>();
@@ -948,17 +966,20 @@ k_zadj_gal(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUten
   int64_t item = blockIdx.x;
   if (item >= n_items) return;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
+  // S, A and Y pass through once: evict first; the item's F_g column is
+  // re-read for every mesh of the batch: evict last
+  const uint64_t pol_stream = tma::policy_evict_first(), pol_keep = tma::policy_evict_last();
   auto issue_slot = [&](int k, int64_t it, int b) {
     const int ky = (int)(it / T), kx0 = (int)(it % T) * B;
     tma::mbar_arrive_expect_tx(&bar[k], slot_bytes);
-    za_issue_col<C, N, B>(sb0 + k * TILE, &mS, &bar[k], kx0, ky, b);
-    za_issue_win<C, N, B>(xb0 + k * WS, &mX, &bar[k], kx0, ky, b);
+    za_issue_col<C, N, B>(sb0 + k * TILE, &mS, &bar[k], kx0, ky, b, pol_stream);
+    za_issue_win<C, N, B>(xb0 + k * WS, &mX, &bar[k], kx0, ky, b, pol_stream);
   };
   if (threadIdx.x == 0) {
     for (int k = 0; k < 3; ++k) tma::mbar_init(&bar[k], 1);
     tma::fence_async_shared();
     tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
-    za_issue_col<C, N, B>(at, &mA, &bar[2], (int)(item % T) * B, (int)(item / T), 0);
+    za_issue_col<C, N, B>(at, &mA, &bar[2], (int)(item % T) * B, (int)(item / T), 0, pol_stream);
     issue_slot(0, item, 0);
   }
   __syncthreads();
@@ -968,6 +989,9 @@ k_zadj_gal(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUten
   int failed = 0;
   for (; item < n_items && !failed; item += gridDim.x) {
     const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
+    const int ncol = min(B, M1 - kx0);
+    const bool dc_col = (kx0 + c == 0) && (ky == 0);
+    const C* fcol = Fg + (int64_t)ky * P + kx0 + c;
     if (__syncthreads_or(!tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
     ph[2] ^= 1;
     for (int b = 0; b < nb; ++b, ++job) {
@@ -989,9 +1013,7 @@ k_zadj_gal(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUten
       C a[N2];
       step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
       __syncthreads();
-      za_expand<C, N, B>(buf, xb0 + cur * WS, w);
-      __syncthreads();
-      step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
+      step1_win<C, N, B, XP>(buf, xb0 + cur * WS, w, tws);
       __syncthreads();
       C x[N2];
       step2<C, N1, N2, false, XP>(buf, B, c, k1, x);
@@ -1004,6 +1026,28 @@ k_zadj_gal(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUten
         v.y += t.y;
         *o = v;
       }
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        C f;
+        f.x = 0; f.y = 0;
+        if (c < ncol) f = tma::ld_hint(fcol + (int64_t)(k1 + N1 * k2) * N * P, pol_keep);
+        x[k2] = cmul(x[k2], f);
+      }
+      if (dc_col && k1 == 0) { x[0].x = 0; x[0].y = 0; }   // k = 0 mode
+      __syncthreads();
+      stepA<C, N1, N2, true, XP>(buf, B, c, k1, x, tws, 1);
+      __syncthreads();
+      C* yout = S + (int64_t)b * S_stride + (int64_t)ky * P + kx0;
+      for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+        const int cc = t % B, n2 = t / B;
+        C v[N1];
+        stepB<C, N1, N2, true, XP>(buf, B, cc, n2, v);
+        if (cc < ncol) {
+#pragma unroll
+          for (int n1 = 0; n1 < N1; ++n1)
+            tma::st_hint(yout + (int64_t)(n2 + N2 * n1) * N * P + cc, v[n1], pol_stream);
+        }
+      }
       __syncthreads();   // slot free for the job after next
     }
     if (failed) break;
@@ -1011,117 +1055,14 @@ k_zadj_gal(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUten
     C* ag = A + (int64_t)ky * P + kx0;
     for (int t = threadIdx.x; t < TILE; t += blockDim.x) {
       const int z = t / B, cc = t % B;
-      ag[(int64_t)z * N * P + cc] = at[t];
+      tma::st_hint(ag + (int64_t)z * N * P + cc, at[t], pol_stream);
     }
     __syncthreads();
     if (threadIdx.x == 0 && item + gridDim.x < n_items) {
       const int64_t nitem = item + gridDim.x;
       tma::fence_async_shared();
       tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
-      za_issue_col<C, N, B>(at, &mA, &bar[2], (int)(nitem % T) * B, (int)(nitem / T), 0);
-    }
-  }
-  if (failed) {
-    if (threadIdx.x == 0) {
-      atomicExch(err, tma::kErrTmaTimeout);
-      for (int k = 0; k < 3; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
-    }
-    __syncthreads();
-  }
-}
-
-// Pair side: for every mesh b of the batch, Y_b = inverse z of X_b F_g
-// (k = 0 set to zero) over the full column, written to Y[b][z][ky][kx] (the
-// next pass inverts y at the lines that hold pairs). Persistent and TMA fed:
-// the F_g tile once per work item, the window tiles in two slots.
-template <typename C, int N, int B>
-__global__ void __launch_bounds__(ZAdj<C, N, B>::THREADS, 1)
-k_zadj_pair(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mF, int nb,
-            int w, C* __restrict__ Y, int64_t Y_stride, int P, const C* __restrict__ tw,
-            int* __restrict__ err) {
-  using Z = ZAdj<C, N, B>;
-  constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1;
-  constexpr int XP = xperm<C, N, B>();
-  constexpr uint64_t kLimitNs = 2000000000ull;
-  const int W = 2 * w + 1;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  C* const ft = reinterpret_cast<C*>(smem_raw);   // F_g tile
-  C* const wb = ft + TILE;                         // work tile
-  const int WS = Z::win_slot(W);
-  C* const xb0 = wb + TILE;                        // compact window slots: xb0 + k * WS
-  C* const tws = xb0 + 2 * WS;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);   // [0], [1]: slots, [2]: F_g
-  const uint32_t win_bytes = (uint32_t)(W * B * sizeof(C));
-  const int T = (M1 + B - 1) / B;
-  const int64_t n_items = (int64_t)T * N;
-  int64_t item = blockIdx.x;
-  if (item >= n_items) return;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
-  auto issue_slot = [&](int k, int64_t it, int b) {
-    tma::mbar_arrive_expect_tx(&bar[k], win_bytes);
-    za_issue_win<C, N, B>(xb0 + k * WS, &mX, &bar[k], (int)(it % T) * B, (int)(it / T), b);
-  };
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < 3; ++k) tma::mbar_init(&bar[k], 1);
-    tma::fence_async_shared();
-    tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
-    za_issue_col<C, N, B>(ft, &mF, &bar[2], (int)(item % T) * B, (int)(item / T), 0);
-    issue_slot(0, item, 0);
-  }
-  __syncthreads();
-  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
-  uint32_t ph[3] = {0, 0, 0};
-  int64_t job = 0;
-  int failed = 0;
-  for (; item < n_items && !failed; item += gridDim.x) {
-    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
-    const int ncol = min(B, M1 - kx0);
-    if (__syncthreads_or(!tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
-    ph[2] ^= 1;
-    const bool dc_col = (kx0 + c == 0) && (ky == 0);
-    for (int b = 0; b < nb; ++b, ++job) {
-      const int cur = (int)(job & 1);
-      if (threadIdx.x == 0) {
-        int nbb = b + 1;
-        int64_t nitem = item;
-        if (nbb == nb) { nbb = 0; nitem = item + gridDim.x; }
-        if (nitem < n_items) {
-          tma::fence_async_shared();
-          issue_slot(cur ^ 1, nitem, nbb);
-        }
-      }
-      if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
-      ph[cur] ^= 1;
-      za_expand<C, N, B>(wb, xb0 + cur * WS, w);
-      __syncthreads();
-      step1<C, N1, N2, B, false, XP>(wb, B, tws, 1);
-      __syncthreads();
-      C x[N2];
-      step2<C, N1, N2, false, XP>(wb, B, c, k1, x);
-#pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) x[k2] = cmul(x[k2], ft[(k1 + N1 * k2) * B + c]);
-      if (dc_col && k1 == 0) { x[0].x = 0; x[0].y = 0; }   // k = 0 mode
-      __syncthreads();
-      stepA<C, N1, N2, true, XP>(wb, B, c, k1, x, tws, 1);
-      __syncthreads();
-      C* yout = Y + (int64_t)b * Y_stride + (int64_t)ky * P + kx0;
-      for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
-        const int cc = t % B, n2 = t / B;
-        C v[N1];
-        stepB<C, N1, N2, true, XP>(wb, B, cc, n2, v);
-        if (cc < ncol) {
-#pragma unroll
-          for (int n1 = 0; n1 < N1; ++n1) yout[(int64_t)(n2 + N2 * n1) * N * P + cc] = v[n1];
-        }
-      }
-      __syncthreads();   // work tile and slot free
-    }
-    if (failed) break;
-    if (threadIdx.x == 0 && item + gridDim.x < n_items) {   // F_g tile free after the barrier above
-      const int64_t nitem = item + gridDim.x;
-      tma::fence_async_shared();
-      tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
-      za_issue_col<C, N, B>(ft, &mF, &bar[2], (int)(nitem % T) * B, (int)(nitem / T), 0);
+      za_issue_col<C, N, B>(at, &mA, &bar[2], (int)(nitem % T) * B, (int)(nitem / T), 0, pol_stream);
     }
   }
   if (failed) {
@@ -1135,46 +1076,123 @@ k_zadj_pair(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUte
 
 // Inverse y of Y_b on the z planes that hold lines of mesh b, stored only at
 // those lines: hspec[line][kx] for the compact lines of the batch (the
-// forward deposit's numbering). CTA = (kx tile, z plane, mesh b).
+// forward deposit's numbering: idx, seg_total, line_base, line_y). Work item
+// = (kx tile, z, mesh b); items whose plane holds no lines are skipped by the
+// leader thread, which streams the next item's column into the other buffer.
 template <typename C, int N, int B>
-__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
-k_y_inv_lines(const C* __restrict__ Y, int64_t Y_stride, int P, const int32_t* __restrict__ idx,
+struct YLines {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int THREADS = B * N1;
+  static constexpr int TILE = N * B;
+  static constexpr int YB = N < 256 ? N : 256;   // rows per TMA box
+  static constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
+  static constexpr int E = sizeof(C) / 8;
+  static constexpr size_t SMEM = sizeof(C) * (2 * (size_t)TILE + N) + 128;
+  static constexpr int MINB = SMEM <= 74 * 1024 ? 3 : SMEM <= 110 * 1024 ? 2 : 1;
+  static constexpr size_t smem_bytes() { return SMEM; }
+};
+
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(YLines<C, N, B>::THREADS, YLines<C, N, B>::MINB)
+k_y_inv_lines(const __grid_constant__ CUtensorMap mY, int nb, int P, const int32_t* __restrict__ idx,
               const int64_t* __restrict__ seg_total, const int64_t* __restrict__ line_base,
-              const int32_t* __restrict__ line_y, C* __restrict__ hspec, const C* __restrict__ tw) {
-  using CP = ColPass<C, N, B>;
-  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+              const int32_t* __restrict__ line_y, C* __restrict__ hspec, const C* __restrict__ tw,
+              int* __restrict__ err) {
+  using Y = YLines<C, N, B>;
+  constexpr int N1 = Y::N1, N2 = Y::N2, TILE = Y::TILE, M1 = N / 2 + 1;
   constexpr int XP = xperm<C, N, B>();
-  const int kx0 = blockIdx.x * B, z = blockIdx.y, b = blockIdx.z;
-  const int64_t NN = (int64_t)N * N;
-  const int32_t* ib = idx + (int64_t)b * NN;
-  const int64_t lo = ib[(int64_t)z * N];
-  const int64_t hi = (z + 1 < N) ? ib[(int64_t)(z + 1) * N] : seg_total[b];
-  if (lo >= hi) return;   // no lines of this mesh in plane z (whole CTA)
+  constexpr uint64_t kLimitNs = 2000000000ull;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw) + N;
-  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
-  const int ncol = min(B, M1 - kx0);
-  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
-  const C* col = Y + (int64_t)b * Y_stride + (int64_t)z * N * P + kx0;
-  for (int ky = threadIdx.x / B; ky < N; ky += blockDim.x / B) {
-    C v;
-    v.x = 0; v.y = 0;
-    if (c < ncol) v = col[(int64_t)ky * P + c];
-    buf[ky * B + c] = v;
+  C* const buf0 = reinterpret_cast<C*>(smem_raw);   // buffers: buf0 + k * TILE
+  C* const tws = buf0 + 2 * TILE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);
+  int64_t* s_item = reinterpret_cast<int64_t*>(bar + 2);   // [2] item per buffer
+  int64_t* s_lo = s_item + 2;                              // [2] line range
+  int64_t* s_hi = s_lo + 2;
+  const int T = (M1 + B - 1) / B;
+  const int64_t NN = (int64_t)N * N;
+  const int64_t n_items = (int64_t)T * N * nb;
+  // first item at or after `it` (stride gridDim.x) whose plane holds lines
+  auto find = [&](int64_t it, int64_t& lo, int64_t& hi) {
+    for (; it < n_items; it += gridDim.x) {
+      const int64_t r = it / T;
+      const int z = (int)(r % N), b = (int)(r / N);
+      const int32_t* ib = idx + (int64_t)b * NN;
+      lo = ib[(int64_t)z * N];
+      hi = (z + 1 < N) ? ib[(int64_t)(z + 1) * N] : seg_total[b];
+      if (lo < hi) return it;
+    }
+    return n_items;
+  };
+  auto issue = [&](int k, int64_t it) {
+    const int64_t r = it / T;
+    tma::mbar_arrive_expect_tx(&bar[k], Y::TILE_BYTES);
+#pragma unroll
+    for (int y0 = 0; y0 < N; y0 += Y::YB)
+      tma::load_4d(buf0 + k * TILE + y0 * B, &mY, &bar[k], (int)(it % T) * B * Y::E, y0, (int)(r % N),
+                   (int)(r / N));
+  };
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::fence_async_shared();
+    for (int k = 0; k < 2; ++k) {
+      const int64_t it = find(k == 0 ? (int64_t)blockIdx.x : s_item[0] + gridDim.x, s_lo[k], s_hi[k]);
+      s_item[k] = it;
+      if (it < n_items) issue(k, it);
+      else break;
+    }
+    if (s_item[0] >= n_items) s_item[1] = n_items;
   }
   __syncthreads();
-  step1<C, N1, N2, B, true, XP>(buf, B, tws, 1);
-  __syncthreads();
-  C a[N2];
-  step2<C, N1, N2, true, XP>(buf, B, c, k1, a);
-  __syncthreads();
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  uint32_t ph[2] = {0, 0};
+  int failed = 0;
+  for (int64_t job = 0;; ++job) {
+    const int cur = (int)(job & 1);
+    const int64_t it = s_item[cur];
+    if (it >= n_items) break;
+    C* buf = buf0 + cur * TILE;
+    if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
+    ph[cur] ^= 1;
+    const int64_t r = it / T;
+    const int b = (int)(r / N);
+    const int kx0 = (int)(it % T) * B;
+    const int ncol = min(B, M1 - kx0);
+    const int64_t lo = s_lo[cur], hi = s_hi[cur];
+    step1<C, N1, N2, B, true, XP>(buf, B, tws, 1);
+    __syncthreads();
+    C a[N2];
+    step2<C, N1, N2, true, XP>(buf, B, c, k1, a);
+    __syncthreads();
 #pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) buf[(k1 + N1 * k2) * B + c] = a[k2];   // natural row y
-  __syncthreads();
-  const int64_t base = line_base[b];
-  for (int64_t r = lo + threadIdx.x / B; r < hi; r += blockDim.x / B) {
-    const int64_t l = base + r;
-    if (c < ncol) hspec[l * P + kx0 + c] = buf[line_y[l] * B + c];
+    for (int k2 = 0; k2 < N2; ++k2) buf[(k1 + N1 * k2) * B + c] = a[k2];   // natural row y
+    __syncthreads();
+    const int64_t base = line_base[b];
+    for (int64_t q = lo + threadIdx.x / B; q < hi; q += blockDim.x / B) {
+      const int64_t l = base + q;
+      if (c < ncol) hspec[l * P + kx0 + c] = buf[line_y[l] * B + c];
+    }
+    __syncthreads();   // buffer free: stream in the item after the next
+    if (threadIdx.x == 0) {
+      const int64_t nx = s_item[cur ^ 1];
+      int64_t it2 = n_items;
+      if (nx < n_items) it2 = find(nx + gridDim.x, s_lo[cur], s_hi[cur]);
+      s_item[cur] = it2;
+      if (it2 < n_items) {
+        tma::fence_async_shared();
+        issue(cur, it2);
+      }
+    }
+    __syncthreads();
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, tma::kErrTmaTimeout);
+      for (int k = 0; k < 2; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
+    }
+    __syncthreads();
   }
 }
 

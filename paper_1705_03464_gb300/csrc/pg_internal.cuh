@@ -190,19 +190,18 @@ struct FftPasses {
   // Y pass of the window lines (spec line (b*W + zr)*W + ry) into Xw.
   static cudaError_t y_fwd_win(int N, int nb, const C* spec, int P, int w, C* Xw,
                                int64_t Xw_stride, const C* tw, cudaStream_t s);
-  // A[kz][ky][kx] += sum_b F_b conj(X_b): F_b the z transform of S[b]
-  // ([nb][N][N][P] contiguous), X_b that of Xw[b] zero-padded.
-  static cudaError_t zadj_gal(int N, int nb, const C* S, const C* Xw, int64_t Xw_stride, C* A, int w,
-                              int P, const C* tw, int* err, cudaStream_t s);
-  // Y[b] = inverse z of X_b Fg (k = 0 zeroed), full columns.
-  static cudaError_t zadj_pair(int N, int nb, const C* Xw, int64_t Xw_stride, const C* Fg, C* Y,
-                               int64_t Y_stride, int w, int P, const C* tw, int* err, cudaStream_t s);
+  // Both sides of the adjoint z pass: A[kz][ky][kx] += sum_b F_b conj(X_b)
+  // (F_b the z transform of S[b], [nb][N][N][P] contiguous; X_b that of
+  // Xw[b] zero-padded), and Y_b = inverse z of X_b Fg (k = 0 zeroed) written
+  // over S[b].
+  static cudaError_t zadj(int N, int nb, C* S, int64_t S_stride, const C* Xw, int64_t Xw_stride,
+                          const C* Fg, C* A, int w, int P, const C* tw, int* err, cudaStream_t s);
   // Inverse y of Y[b] at the compact lines of the batch (numbering of the
   // forward deposit: idx, seg_total, line_base, line_y) into hspec[line][P].
   static cudaError_t y_inv_lines(int N, int nb, const C* Y, int64_t Y_stride, int P,
                                  const int32_t* idx, const int64_t* seg_total,
                                  const int64_t* line_base, const int32_t* line_y, C* hspec,
-                                 const C* tw, cudaStream_t s);
+                                 const C* tw, int* err, cudaStream_t s);
   // out[l][x] = scale * C2R of row (line_z[l], line_y[l]) of S; line_y ==
   // null: of the compact line S + l*P.
   static cudaError_t x_c2r_lines(int N, const C* S, int P, int64_t n_lines, const int32_t* line_y,

@@ -52,7 +52,7 @@ class pg_kernel_stat(C.Structure):
                 ("bytes", C.c_double)]
 
 
-PG_N_FAMILIES = 20
+PG_N_FAMILIES = 19
 
 
 class pg_result(C.Structure):
