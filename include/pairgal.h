@@ -105,14 +105,26 @@ typedef struct pg_result {
  * Errors: PG_ERR_INVALID_ARG, PG_ERR_UNSUPPORTED, PG_ERR_OOM, PG_ERR_CUDA. */
 pg_status pg_plan_create(const pg_params* params, pg_plan** out);
 
-/* Frees the plan and its device workspace (synchronises the device first). */
+/* pg_plan_create whose mesh-sized scratch (line buffers, spectra, windows,
+ * adjoint spectra: the bulk of the device memory at large N) is shared with
+ * `share_with`, a plan of the same mesh_n and precision on the same device;
+ * its other parameters (box, bins, batch size) may differ. Shared scratch
+ * grows to the largest need. Plans that share scratch must not run
+ * concurrently (one stream, or one call at a time). Errors as
+ * pg_plan_create, plus PG_ERR_INVALID_ARG if share_with is NULL or differs
+ * in mesh_n, precision or device. */
+pg_status pg_plan_create_shared(const pg_params* params, const pg_plan* share_with, pg_plan** out);
+
+/* Frees the plan and its device workspace (synchronises the device first);
+ * shared scratch is freed with the last plan that uses it. */
 void pg_plan_destroy(pg_plan* plan);
 
 /* Allocates workspace for catalogues up to n_gal_max galaxies and
  * n_pairs_max pairs so that later calls allocate nothing. */
 pg_status pg_plan_reserve(pg_plan* plan, int64_t n_gal_max, int64_t n_pairs_max);
 
-/* Device bytes currently held by the plan. */
+/* Device bytes currently held by the plan, including the scratch it may
+ * share with other plans. */
 size_t pg_workspace_bytes(const pg_plan* plan);
 
 /* The full forward path (Sec. 2.1-2.2, 3.2-3.6) for one catalogue:
@@ -287,6 +299,51 @@ typedef struct pg_kernel_stat {
   double ms;              /* their summed duration: CUDA events on the call's stream */
   double bytes;           /* algorithmic bytes they must move (reads + writes) */
 } pg_kernel_stat;
+
+/* One mock of a many-mock batch: its own problem and HOST catalogue (as in
+ * pg_forward_host) and host outputs laid out for its params. */
+typedef struct pg_mock {
+  pg_params params;     /* edge arrays must stay valid during the call */
+  int64_t n_gal;
+  const double* h_pos;  /* [n_gal][3] */
+  const float* h_vel;   /* [n_gal][3] or NULL */
+  const float* h_w;     /* [n_gal] or NULL */
+  pg_result* out;
+} pg_mock;
+
+typedef struct pg_batch_stats {
+  double wall_ms;       /* the whole call, host clock */
+  double mocks_per_s;   /* completed mocks / wall */
+  double p50_ms;        /* per-mock latency, median: from the mock's turn (waiting */
+  double p99_ms;        /*   for its plan included) to its results on the host */
+  int32_t n_plans;      /* plans built (one per distinct problem) */
+  int32_t n_workspaces; /* shared mesh scratch built (one per mesh_n x precision) */
+  int64_t gpu_launches; /* kernels launched by the mocks' forward calls */
+} pg_batch_stats;
+
+/* Many mocks of uneven size (box, mesh, catalogue; the batching pattern of a
+ * survey-scale HOD study, Sec. 3.3) through the forward path, in order, on
+ * `stream`. Plans are built per distinct problem by a host thread that runs
+ * up to two mocks ahead of the GPU, and share mesh scratch per (mesh_n,
+ * precision), so the device holds one scratch per mesh size; the plans are
+ * freed before return. A non-blocking stream lets plan building overlap the
+ * GPU work. latency_ms [n_mocks] (host, may be NULL) receives each mock's
+ * latency (NaN if it failed); *stats (may be NULL) the batch statistics.
+ * Returns the first failing mock's status (the others still run). Errors:
+ * PG_ERR_INVALID_ARG for a NULL mock array, a NULL output or positions. */
+pg_status pg_run_batch(const pg_mock* mocks, int32_t n_mocks, double* latency_ms,
+                       pg_batch_stats* stats, void* stream);
+
+/* Batch-size autotuner: times one forward (after one warm-up) of the given
+ * problem and HOST catalogue for each candidate bins_per_batch and writes the
+ * fastest to *best (ms_out [n_cand], host, may be NULL: each candidate's
+ * time, CUDA events on `stream`). Candidate plans share scratch, which grows
+ * to the largest candidate. Errors: PG_ERR_INVALID_ARG (NULL params,
+ * candidates or best, n_cand <= 0, a candidate <= 0), those of
+ * pg_plan_create and pg_forward_host. */
+pg_status pg_autotune(const pg_params* params, int64_t n_gal, const double* h_pos,
+                      const float* h_vel, const float* h_w, const int32_t* candidates,
+                      int32_t n_cand, int32_t* best, double* ms_out, void* stream);
 
 /* Enables (1) or disables (0) per-family event timing on later calls of
  * pg_forward / pg_forward_host / pg_backward on this plan. */

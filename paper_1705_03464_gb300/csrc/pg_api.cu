@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -25,7 +26,9 @@ namespace {
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  size_t* acct = nullptr;   // if set, growth is booked here instead of the caller's counter
   cudaError_t ensure(size_t want, size_t* total) {
+    if (acct) total = acct;
     if (want <= bytes) return cudaSuccess;
     if (p) { cudaFree(p); *total -= bytes; p = nullptr; bytes = 0; }
     if (want == 0) return cudaSuccess;
@@ -36,6 +39,7 @@ struct DevBuf {
     return cudaSuccess;
   }
   void release(size_t* total) {
+    if (acct) total = acct;
     if (p) { cudaFree(p); *total -= bytes; }
     p = nullptr;
     bytes = 0;
@@ -62,7 +66,41 @@ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 }  // namespace
 
+// Mesh-sized scratch of the forward and backward passes: line buffers,
+// spectra, windows, adjoint spectra. Plans of one mesh size and precision on
+// one device may share it (pg_plan_create_shared); every call uses it as
+// scratch only, so plans that share it must not run concurrently.
+struct Workspace {
+  int device = 0, N = 0, precision = 0;
+  size_t total = 0;
+  int64_t cap_lines = -1;
+  DevBuf flags, lidx, seg_total, line_base, n_lines, stmp, line_y, line_bin, line_z, lines_q, qsum,
+      scale, spec, S, Fg, Wz, Wy, Cwin, tmpfft, Xs, As, Xw, wlines, cggw;
+  DevBuf* all_bufs[24] = {&flags, &lidx, &seg_total, &line_base, &n_lines, &stmp, &line_y, &line_bin,
+                          &line_z, &lines_q, &qsum, &scale, &spec, &S, &Fg, &Wz, &Wy, &Cwin,
+                          &tmpfft, &Xs, &As, &Xw, &wlines, &cggw};
+  Workspace() {
+    for (DevBuf* b : all_bufs) b->acct = &total;
+  }
+  ~Workspace() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(device);
+    cudaDeviceSynchronize();
+    for (DevBuf* b : all_bufs) b->release(&total);
+    cudaSetDevice(cur);
+  }
+};
+
 struct pg_plan {
+  explicit pg_plan(std::shared_ptr<Workspace> w)
+      : wsp(std::move(w)), flags(wsp->flags), lidx(wsp->lidx), seg_total(wsp->seg_total),
+        line_base(wsp->line_base), n_lines(wsp->n_lines), stmp(wsp->stmp), line_y(wsp->line_y),
+        line_bin(wsp->line_bin), lines_q(wsp->lines_q), qsum(wsp->qsum), scale(wsp->scale),
+        spec(wsp->spec), S(wsp->S), Fg(wsp->Fg), Wz(wsp->Wz), Wy(wsp->Wy), Cwin(wsp->Cwin),
+        tmpfft(wsp->tmpfft), line_z(wsp->line_z), wlines(wsp->wlines), Xs(wsp->Xs), As(wsp->As),
+        Xw(wsp->Xw), cggw(wsp->cggw), cap_lines(wsp->cap_lines) {}
+  std::shared_ptr<Workspace> wsp;
   pg_params prm;
   std::vector<double> s_edges, r_edges;
   int device = 0;
@@ -84,20 +122,24 @@ struct pg_plan {
   // pairs
   DevBuf dd, ddq, pcursor, ubin, ui, uj, umx, umy, umz, uwp;
   DevBuf pbin, px, py, pz, pw, bcursor;
-  // meshes
-  DevBuf flags, lidx, seg_total, line_base, n_lines, stmp, line_y, line_bin, lines_q, qsum, scale;
-  DevBuf spec, S, Fg, Wz, Wy, Cwin, sums_pg, sums_gg, pg_valid, tmpfft;
+  // meshes (the workspace's)
+  DevBuf &flags, &lidx, &seg_total, &line_base, &n_lines, &stmp, &line_y, &line_bin, &lines_q,
+      &qsum, &scale;
+  DevBuf &spec, &S, &Fg, &Wz, &Wy, &Cwin, &tmpfft;
+  DevBuf sums_pg, sums_gg, pg_valid;
   // adjoint: line z, pair galaxy indices, window geometry, spectra X and A,
   // galaxy-window correlation, scalar adjoints, upstream gradients, gathers
-  DevBuf line_z, psi, psj, cell_bin, cell_agg, wl_idx, wl_tot, wl_base, wl_y, wlines;
-  DevBuf Xs, As, Xw, cggw, adjb, gout, gp, gj, part;
+  DevBuf &line_z, &wlines, &Xs, &As, &Xw, &cggw;
+  DevBuf psi, psj, cell_bin, cell_agg, wl_idx, wl_tot, wl_base, wl_y;
+  DevBuf adjb, gout, gp, gj, part;
   // state of the last successful forward call, which pg_backward differentiates
   bool fwd_ok = false, last_has_w = false;
   int64_t last_n = 0;
   std::vector<unsigned long long> last_hdd;
   // outputs
   DevBuf out;
-  int64_t cap_gal = -1, cap_pairs = -1, cap_lines = -1;
+  int64_t cap_gal = -1, cap_pairs = -1;
+  int64_t& cap_lines;
 
   // measurement: event pairs around each launch site of a profiled call
   bool prof_on = false;
@@ -237,6 +279,30 @@ cudaError_t ensure_lines(pg_plan* p, int64_t nl) {
   return cudaSuccess;
 }
 
+// Shared scratch at the sizes this plan needs. Called by the entry points,
+// on the calling thread, never at plan creation: growing a buffer frees the
+// old one, which another plan's calls may still be using.
+cudaError_t ensure_shared(pg_plan* p) {
+  size_t* t = &p->total;
+  const int64_t NN = (int64_t)p->N * p->N;
+  const int nb = p->nbmax;
+  PG_CUDA_TRY(p->flags.ensure((size_t)nb * NN, t));
+  PG_CUDA_TRY(p->lidx.ensure(4 * (size_t)nb * NN, t));
+  PG_CUDA_TRY(p->seg_total.ensure(8 * nb, t));
+  PG_CUDA_TRY(p->line_base.ensure(8 * nb, t));
+  PG_CUDA_TRY(p->n_lines.ensure(8, t));
+  PG_CUDA_TRY(p->stmp.ensure(8 * scan_tmp_elems(NN, nb), t));
+  PG_CUDA_TRY(p->qsum.ensure(8 * nb, t));
+  PG_CUDA_TRY(p->scale.ensure(8 * nb, t));
+  const size_t plane = csize(p) * (size_t)NN * p->P;
+  PG_CUDA_TRY(p->S.ensure(plane * nb, t));
+  PG_CUDA_TRY(p->Fg.ensure(plane, t));
+  PG_CUDA_TRY(p->Wz.ensure(csize(p) * (size_t)p->W * p->N * p->P * nb, t));
+  PG_CUDA_TRY(p->Wy.ensure(csize(p) * (size_t)p->W * p->W * p->P * nb, t));
+  PG_CUDA_TRY(p->Cwin.ensure(rsize(p) * (size_t)p->W * p->W * p->W * nb, t));
+  return cudaSuccess;
+}
+
 // Buffers whose size depends only on the plan.
 cudaError_t ensure_fixed(pg_plan* p) {
   size_t* t = &p->total;
@@ -255,20 +321,6 @@ cudaError_t ensure_fixed(pg_plan* p) {
   PG_CUDA_TRY(p->ddq.ensure(8 * p->nPB, t));
   PG_CUDA_TRY(p->pcursor.ensure(8, t));
   PG_CUDA_TRY(p->bcursor.ensure(8 * p->nPB, t));
-  PG_CUDA_TRY(p->flags.ensure((size_t)nb * NN, t));
-  PG_CUDA_TRY(p->lidx.ensure(4 * (size_t)nb * NN, t));
-  PG_CUDA_TRY(p->seg_total.ensure(8 * nb, t));
-  PG_CUDA_TRY(p->line_base.ensure(8 * nb, t));
-  PG_CUDA_TRY(p->n_lines.ensure(8, t));
-  PG_CUDA_TRY(p->stmp.ensure(8 * scan_tmp_elems(NN, nb), t));
-  PG_CUDA_TRY(p->qsum.ensure(8 * nb, t));
-  PG_CUDA_TRY(p->scale.ensure(8 * nb, t));
-  const size_t plane = csize(p) * (size_t)NN * p->P;
-  PG_CUDA_TRY(p->S.ensure(plane * nb, t));
-  PG_CUDA_TRY(p->Fg.ensure(plane, t));
-  PG_CUDA_TRY(p->Wz.ensure(csize(p) * (size_t)p->W * p->N * p->P * nb, t));
-  PG_CUDA_TRY(p->Wy.ensure(csize(p) * (size_t)p->W * p->W * p->P * nb, t));
-  PG_CUDA_TRY(p->Cwin.ensure(rsize(p) * (size_t)p->W * p->W * p->W * nb, t));
   PG_CUDA_TRY(p->sums_pg.ensure(sizeof(double) * 2 * (size_t)p->nPB * p->nL, t));
   PG_CUDA_TRY(p->sums_gg.ensure(sizeof(double) * 2 * (size_t)p->nL, t));
   PG_CUDA_TRY(p->pg_valid.ensure(p->nPB, t));
@@ -915,7 +967,10 @@ const char* pg_status_string(pg_status s) {
   return "unknown status";
 }
 
-pg_status pg_plan_create(const pg_params* prm, pg_plan** out) {
+}  // extern "C"
+
+namespace {
+pg_status plan_create(const pg_params* prm, const pg_plan* share, pg_plan** out) {
   if (!prm || !out) return PG_ERR_INVALID_ARG;
   *out = nullptr;
   const pg_params& q = *prm;
@@ -933,7 +988,20 @@ pg_status pg_plan_create(const pg_params* prm, pg_plan** out) {
   if (!(q.s_edges[q.n_s] < 0.5 * q.box_L) || !(q.r_edges[q.n_r] < 0.5 * q.box_L))
     return PG_ERR_INVALID_ARG;
   if (!isfinite(q.rsd_factor) || !(q.r_perp_cut >= 0.0)) return PG_ERR_INVALID_ARG;
-  pg_plan* p = new (std::nothrow) pg_plan();
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::shared_ptr<Workspace> ws;
+  if (share) {
+    ws = share->wsp;
+    if (ws->device != dev || ws->N != q.mesh_n || ws->precision != q.precision) return PG_ERR_INVALID_ARG;
+  } else {
+    ws = std::shared_ptr<Workspace>(new (std::nothrow) Workspace());
+    if (!ws) return PG_ERR_OOM;
+    ws->device = dev;
+    ws->N = q.mesh_n;
+    ws->precision = q.precision;
+  }
+  pg_plan* p = new (std::nothrow) pg_plan(ws);
   if (!p) return PG_ERR_OOM;
   p->prm = q;
   p->s_edges.assign(q.s_edges, q.s_edges + q.n_s + 1);
@@ -999,6 +1067,16 @@ pg_status pg_plan_create(const pg_params* prm, pg_plan** out) {
   *out = p;
   return PG_OK;
 }
+}  // namespace
+
+extern "C" {
+
+pg_status pg_plan_create(const pg_params* prm, pg_plan** out) { return plan_create(prm, nullptr, out); }
+
+pg_status pg_plan_create_shared(const pg_params* prm, const pg_plan* share_with, pg_plan** out) {
+  if (!share_with) return PG_ERR_INVALID_ARG;
+  return plan_create(prm, share_with, out);
+}
 
 void pg_plan_destroy(pg_plan* p) {
   if (!p) return;
@@ -1011,13 +1089,9 @@ void pg_plan_destroy(pg_plan* p) {
                    &p->cstart, &p->ccursor, &p->perm, &p->xs, &p->ys, &p->zs, &p->ws, &p->ctmp,
                    &p->ctot, &p->dd, &p->ddq, &p->pcursor, &p->ubin, &p->ui, &p->uj, &p->umx,
                    &p->umy, &p->umz, &p->uwp, &p->pbin, &p->px, &p->py, &p->pz, &p->pw,
-                   &p->bcursor, &p->flags, &p->lidx, &p->seg_total, &p->line_base, &p->n_lines,
-                   &p->stmp, &p->line_y, &p->line_bin, &p->lines_q, &p->qsum, &p->scale, &p->spec,
-                   &p->S, &p->Fg, &p->Wz, &p->Wy, &p->Cwin, &p->sums_pg, &p->sums_gg,
-                   &p->pg_valid, &p->tmpfft, &p->out, &p->line_z, &p->psi, &p->psj,
-                   &p->cell_bin, &p->cell_agg, &p->wl_idx, &p->wl_tot, &p->wl_base, &p->wl_y,
-                   &p->wlines, &p->Xs, &p->As, &p->cggw, &p->adjb, &p->gout, &p->gp, &p->gj,
-                   &p->part};
+                   &p->bcursor, &p->sums_pg, &p->sums_gg, &p->pg_valid, &p->out, &p->psi,
+                   &p->psj, &p->cell_bin, &p->cell_agg, &p->wl_idx, &p->wl_tot, &p->wl_base,
+                   &p->wl_y, &p->adjb, &p->gout, &p->gp, &p->gj, &p->part};
   for (DevBuf* b : all) b->release(&p->total);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   cudaSetDevice(cur);
@@ -1026,6 +1100,7 @@ void pg_plan_destroy(pg_plan* p) {
 
 pg_status pg_plan_reserve(pg_plan* p, int64_t n_gal_max, int64_t n_pairs_max) {
   if (!p || n_gal_max < 0 || n_pairs_max < 0) return PG_ERR_INVALID_ARG;
+  PG_TRY(ensure_shared(p));
   PG_TRY(ensure_gal(p, n_gal_max));
   PG_TRY(ensure_pairs(p, n_pairs_max));
   const int64_t NN = (int64_t)p->N * p->N;
@@ -1034,7 +1109,7 @@ pg_status pg_plan_reserve(pg_plan* p, int64_t n_gal_max, int64_t n_pairs_max) {
   return PG_OK;
 }
 
-size_t pg_workspace_bytes(const pg_plan* p) { return p ? p->total : 0; }
+size_t pg_workspace_bytes(const pg_plan* p) { return p ? p->total + p->wsp->total : 0; }
 
 pg_status pg_backward(pg_plan* p, const pg_result* grad_out, double* d_grad_w, void* stream) {
   if (!p || !d_grad_w) return PG_ERR_INVALID_ARG;
@@ -1043,6 +1118,7 @@ pg_status pg_backward(pg_plan* p, const pg_result* grad_out, double* d_grad_w, v
                                      : FftPasses<float>::adj_fits(p->N, p->w);
   if (!fits) return PG_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PG_TRY(ensure_shared(p));
   prof_begin(p);
   const long long launches0 = launch_counter().load();
   PG_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));
@@ -1103,6 +1179,7 @@ pg_status pg_forward(pg_plan* p, int64_t n, const double* d_pos, const float* d_
   if (p->prm.rsd_factor != 0.0 && n > 0 && !d_vel) return PG_ERR_INVALID_ARG;
   if (n > INT32_MAX / 2) return PG_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PG_TRY(ensure_shared(p));
   return p->prm.precision ? forward_impl<double>(p, n, d_pos, d_vel, d_w, out, s)
                           : forward_impl<float>(p, n, d_pos, d_vel, d_w, out, s);
 }
@@ -1246,6 +1323,7 @@ pg_status pg_correlate_points(pg_plan* p, int64_t n_a, const double* d_a, const 
   if (!p || n_a <= 0 || n_b <= 0 || !d_a || !d_b) return PG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t nmax = std::max(n_a, n_b);
+  PG_TRY(ensure_shared(p));
   PG_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));
   PG_TRY(ensure_gal(p, nmax));
   p->fwd_ok = false;   // the plan's spectra and sums are reused

@@ -47,6 +47,17 @@ _RESULT_FIELDS = [
 ]
 
 
+class pg_mock(C.Structure):
+    _fields_ = [("params", pg_params), ("n_gal", C.c_int64), ("h_pos", C.c_void_p),
+                ("h_vel", C.c_void_p), ("h_w", C.c_void_p), ("out", C.c_void_p)]
+
+
+class pg_batch_stats(C.Structure):
+    _fields_ = [("wall_ms", C.c_double), ("mocks_per_s", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("n_plans", C.c_int32), ("n_workspaces", C.c_int32),
+                ("gpu_launches", C.c_int64)]
+
+
 class pg_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double),
                 ("bytes", C.c_double)]
@@ -68,6 +79,9 @@ def _load():
     sig = {
         "pg_status_string": (C.c_char_p, [C.c_int]),
         "pg_plan_create": (C.c_int, [C.POINTER(pg_params), C.POINTER(vp)]),
+        "pg_plan_create_shared": (C.c_int, [C.POINTER(pg_params), vp, C.POINTER(vp)]),
+        "pg_run_batch": (C.c_int, [vp, i32, vp, vp, vp]),
+        "pg_autotune": (C.c_int, [C.POINTER(pg_params), i64, vp, vp, vp, vp, i32, vp, vp, vp]),
         "pg_plan_destroy": (None, [vp]),
         "pg_plan_reserve": (C.c_int, [vp, i64, i64]),
         "pg_workspace_bytes": (C.c_size_t, [vp]),
@@ -125,8 +139,9 @@ def _stream(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
-class Plan:
-    """A pg_plan on the current CUDA device (pg_plan_create / pg_plan_destroy)."""
+class Problem:
+    """A pg_params with its edge arrays (kept alive here), and host output
+    arrays laid out for it; no device state."""
 
     def __init__(self, box_L, mesh_n, assign, s_edges, n_mu, r_edges, n_mur,
                  rsd_factor=0.0, r_perp_cut=0.0, precision=0, bins_per_batch=0):
@@ -141,11 +156,57 @@ class Plan:
             self.s_edges.ctypes.data_as(C.POINTER(C.c_double)), self.n_mu, self.n_r,
             self.r_edges.ctypes.data_as(C.POINTER(C.c_double)), self.n_mur,
             float(rsd_factor), float(r_perp_cut), int(precision), int(bins_per_batch))
-        h = C.c_void_p()
-        _check(_lib.pg_plan_create(C.byref(self.params), C.byref(h)), "pg_plan_create")
-        self.handle = h
         self.P = self.n_s * self.n_mu
         self.Q = self.n_r * self.n_mur
+
+    @classmethod
+    def of(cls, wl, **kw):
+        args = dict(box_L=wl.box_L, mesh_n=wl.mesh_n, assign=wl.assign, s_edges=wl.s_edges,
+                    n_mu=wl.n_mu, r_edges=wl.r_edges, n_mur=wl.n_mur,
+                    rsd_factor=wl.rsd_factor, r_perp_cut=wl.r_perp_cut,
+                    precision=wl.precision, bins_per_batch=wl.bins_per_batch)
+        args.update(kw)
+        return cls(**args)
+
+    def new_result(self):
+        """Host arrays for every pg_result field and the struct pointing at them."""
+        P, Q = self.P, self.Q
+        sizes = {"P": P, "Q": Q, "PQ": P * Q, "1": 1, "2": 2}
+        arrs = {}
+        res = pg_result()
+        for name, t, sz in _RESULT_FIELDS:
+            a = np.full(sizes[sz], np.nan if t == "f8" else 0, dtype=np.float64 if t == "f8" else np.int64)
+            arrs[name] = a
+            ctype = C.c_int64 if t == "i8" else C.c_double
+            setattr(res, name, a.ctypes.data_as(C.POINTER(ctype)))
+        return res, arrs
+
+    def shape_result(self, arrs):
+        out = dict(arrs)
+        for k in ("xi_pg", "b_pg", "q_eff", "q_eff_sq", "sum_pg"):
+            out[k] = arrs[k].reshape(self.P, self.Q)
+        out["xi_dw_agg"] = float(arrs["xi_dw_agg"][0])
+        out["n_cells_agg"] = int(arrs["n_cells_agg"][0])
+        return out
+
+
+class Plan(Problem):
+    """A pg_plan on the current CUDA device (pg_plan_create / pg_plan_destroy);
+    with share_with, a plan that shares that plan's mesh scratch
+    (pg_plan_create_shared)."""
+
+    def __init__(self, box_L, mesh_n, assign, s_edges, n_mu, r_edges, n_mur,
+                 rsd_factor=0.0, r_perp_cut=0.0, precision=0, bins_per_batch=0, share_with=None):
+        super().__init__(box_L, mesh_n, assign, s_edges, n_mu, r_edges, n_mur, rsd_factor,
+                         r_perp_cut, precision, bins_per_batch)
+        h = C.c_void_p()
+        if share_with is None:
+            _check(_lib.pg_plan_create(C.byref(self.params), C.byref(h)), "pg_plan_create")
+        else:
+            _check(_lib.pg_plan_create_shared(C.byref(self.params), share_with.handle, C.byref(h)),
+                   "pg_plan_create_shared")
+            self._donor = share_with   # keeps the donor's Python object alive
+        self.handle = h
 
     @classmethod
     def of(cls, wl, **kw):
@@ -186,26 +247,6 @@ class Plan:
     def reserve(self, n_gal_max, n_pairs_max):
         _check(_lib.pg_plan_reserve(self.handle, int(n_gal_max), int(n_pairs_max)), "pg_plan_reserve")
 
-    def new_result(self):
-        """Host arrays for every pg_result field and the struct pointing at them."""
-        P, Q = self.P, self.Q
-        sizes = {"P": P, "Q": Q, "PQ": P * Q, "1": 1, "2": 2}
-        arrs = {}
-        res = pg_result()
-        for name, t, sz in _RESULT_FIELDS:
-            a = np.full(sizes[sz], np.nan if t == "f8" else 0, dtype=np.float64 if t == "f8" else np.int64)
-            arrs[name] = a
-            ctype = C.c_int64 if t == "i8" else C.c_double
-            setattr(res, name, a.ctypes.data_as(C.POINTER(ctype)))
-        return res, arrs
-
-    def shape_result(self, arrs):
-        out = dict(arrs)
-        for k in ("xi_pg", "b_pg", "q_eff", "q_eff_sq", "sum_pg"):
-            out[k] = arrs[k].reshape(self.P, self.Q)
-        out["xi_dw_agg"] = float(arrs["xi_dw_agg"][0])
-        out["n_cells_agg"] = int(arrs["n_cells_agg"][0])
-        return out
 
 
 def pg_forward(plan: Plan, pos, vel=None, w=None, stream=None):
@@ -411,3 +452,80 @@ def hod_gradient(plan: Plan, pos, vel, mass, kind, kh, theta, grads, stream=None
     out = pg_forward(plan, pos, vel, w, stream)
     wbar = pg_backward(plan, grads, int(pos.shape[0]), stream)
     return out, pg_hod_chain(plan, wbar, dw, stream)
+
+
+def _host(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def pg_run_batch(problems, catalogues, stream=None):
+    """Many mocks through the forward path (pg_run_batch): problems[i] a
+    Problem (or Plan), catalogues[i] = (pos [n,3] float64, vel [n,3] float32
+    or None, w [n] float32 or None), host arrays. Returns (outputs per mock,
+    latency_ms per mock, stats dict)."""
+    n = len(problems)
+    if len(catalogues) != n:
+        raise ValueError("one catalogue per problem")
+    mocks = (pg_mock * max(n, 1))()
+    keep, results = [], []
+    for i, (pr, cat) in enumerate(zip(problems, catalogues)):
+        pos, vel, w = (tuple(cat) + (None, None))[:3]
+        pos, vel, w = _host(pos, np.float64), _host(vel, np.float32), _host(w, np.float32)
+        res, arrs = pr.new_result()
+        keep += [pos, vel, w, res]
+        results.append(arrs)
+        m = mocks[i]
+        m.params = pr.params
+        m.n_gal = int(pos.shape[0])
+        m.h_pos = pos.ctypes.data
+        m.h_vel = None if vel is None else vel.ctypes.data
+        m.h_w = None if w is None else w.ctypes.data
+        m.out = C.addressof(res)
+    lat = np.full(max(n, 1), np.nan)
+    st = pg_batch_stats()
+    _check(_lib.pg_run_batch(C.addressof(mocks), n, lat.ctypes.data, C.byref(st), _stream(stream)),
+           "pg_run_batch")
+    stats = {k: getattr(st, k) for k, _ in pg_batch_stats._fields_}
+    return [pr.shape_result(a) for pr, a in zip(problems, results)], lat[:n], stats
+
+
+def pg_autotune(problem, pos, vel=None, w=None, candidates=(4, 8, 16, 32), stream=None):
+    """Batch-size autotuner (pg_autotune) on host arrays: returns (best
+    bins_per_batch, {candidate: ms})."""
+    pos, vel, w = _host(pos, np.float64), _host(vel, np.float32), _host(w, np.float32)
+    cand = np.ascontiguousarray(candidates, dtype=np.int32)
+    ms = np.zeros(len(cand))
+    best = C.c_int32(0)
+    _check(_lib.pg_autotune(C.byref(problem.params), int(pos.shape[0]), pos.ctypes.data,
+                            None if vel is None else vel.ctypes.data,
+                            None if w is None else w.ctypes.data, cand.ctypes.data, len(cand),
+                            C.byref(best), ms.ctypes.data, _stream(stream)), "pg_autotune")
+    return int(best.value), {int(c): float(t) for c, t in zip(cand, ms)}
+
+
+def autotune_cached(problem, pos, vel=None, w=None, cache_path=None, candidates=(4, 8, 16, 32),
+                    stream=None):
+    """pg_autotune with its result cached in a JSON file keyed by mesh size,
+    precision and device name (cache_path, or the PG_TUNE_CACHE environment
+    variable; no caching if neither is set)."""
+    import json
+    path = cache_path or os.environ.get("PG_TUNE_CACHE")
+    key = None
+    try:
+        import torch
+        dev = torch.cuda.get_device_name() if torch.cuda.is_available() else "none"
+    except Exception:
+        dev = "unknown"
+    key = f"N{problem.params.mesh_n}-p{problem.params.precision}-{dev}"
+    table = {}
+    if path and os.path.exists(path):
+        with open(path) as f:
+            table = json.load(f)
+    if key in table:
+        return int(table[key]["bins_per_batch"]), table[key].get("ms", {})
+    best, ms = pg_autotune(problem, pos, vel, w, candidates, stream)
+    if path:
+        table[key] = {"bins_per_batch": best, "ms": ms}
+        with open(path, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+    return best, ms

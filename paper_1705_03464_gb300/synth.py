@@ -260,3 +260,27 @@ def make_candidates(box_L: float, n_gal: int, seed: int, hod=HOD_Z09,
     kind = np.concatenate([np.zeros(cen.size, np.int32), np.ones(sat.size, np.int32)])
     kh = np.concatenate([np.ones(cen.size), k[sat]]).astype(np.float32)
     return Candidates(pos, vel, mass, kind, kh, box_L)
+
+
+def many_mocks(n_mocks: int = 64, seed0: int = 0):
+    """The uneven many-mock batch: for mock s, box L ~ U[256, 1100] Mpc/h, mesh
+    N = the power of two nearest L (cells of about 1 Mpc/h) clipped to
+    [256, 1024], target galaxy count log-uniform on [2e4, 4e5], HOD
+    parameters within +-0.2 dex of HOD_Z09 (added to the two log-masses,
+    a factor 10^U(-0.2, 0.2) on sigma, alpha and kappa); the paper-scale
+    binning (20 x 5 pair bins on s < 10, 10 x 5 correlation bins on
+    10 < r < 60), CIC, real space. Returns [(Workload, hod)], one per mock
+    (draw its catalogue with make_catalogue(w, seed, hod))."""
+    out = []
+    for s in range(seed0, seed0 + n_mocks):
+        rng = np.random.default_rng([s, 55])
+        L = float(rng.uniform(256.0, 1100.0))
+        N = int(2 ** int(np.clip(np.round(np.log2(L)), 8, 10)))
+        n_gal = int(round(math.exp(rng.uniform(math.log(2e4), math.log(4e5)))))
+        d = rng.uniform(-0.2, 0.2, 5)
+        t = HOD_Z09
+        hod = (t[0] + d[0], t[1] + d[1], t[2] * 10 ** d[2], t[3] * 10 ** d[3], t[4] * 10 ** d[4])
+        w = Workload(f"mock_{s}", L, N, 1, n_gal, _edges(0, 10, 20), 5, _edges(10, 60, 10), 5,
+                     False, 0)
+        out.append((w, hod))
+    return out

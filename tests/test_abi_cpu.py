@@ -41,6 +41,7 @@ def test_binding_has_c_names():
     from paper_1705_03464_gb300 import pairgal
     for n in _declared():
         if n in ("pg_plan_create", "pg_plan_destroy", "pg_plan_reserve", "pg_workspace_bytes",
-                 "pg_status_string", "pg_plan_set_profiling", "pg_plan_last_stats"):
+                 "pg_status_string", "pg_plan_set_profiling", "pg_plan_last_stats",
+                 "pg_plan_create_shared"):
             continue   # wrapped by pairgal.Plan / status_string
         assert hasattr(pairgal, n), n
