@@ -439,7 +439,7 @@ cudaError_t lines_to_S(pg_plan* p, int nb, int64_t nl, typename CT<R>::C* S, int
   ProfScope ps(p, PG_FAM_FFT_Y_FWD, s, (double)nl * M1 * cs + (double)nb * N * N * M1 * cs);
   return FftPasses<R>::y_fwd(p->N, nb, p->spec.as<C>(), p->P, p->lidx.as<int32_t>(),
                              p->seg_total.as<int64_t>(), p->line_base.as<int64_t>(),
-                             p->line_y.as<int32_t>(), S, S_stride, tw, s);
+                             p->line_y.as<int32_t>(), S, S_stride, lay_yz(p->N, p->P), tw, s);
 }
 
 // Correlation window of nb meshes against Fg (or Fg with itself) and its bin
@@ -460,7 +460,7 @@ cudaError_t correlate_window(pg_plan* p, int nb, bool gg, double* sums, cudaStre
     ProfScope ps(p, PG_FAM_FFT_Z_CORR, s,
                  (gg ? 0.0 : nb * N * N * M1 * cs) + N * N * M1 * cs + nb * W * N * M1 * cs);
     PG_CUDA_TRY(FftPasses<R>::z_corr(p->N, nb, p->S.as<C>(), p->Fg.as<C>(), gg, p->w,
-                                     p->Wz.as<C>(), Wz_stride, p->P, tw,
+                                     p->Wz.as<C>(), Wz_stride, p->P, lay_yz(p->N, p->P), tw,
                                      p->flag.as<int32_t>() + 1, s));
   }
   {
@@ -488,7 +488,7 @@ cudaError_t galaxy_pass(pg_plan* p, int64_t n, const double* x, const double* y,
   PG_CUDA_TRY(lines_to_S<R>(p, 1, nl, p->Fg.as<C>(), 0, s));
   {
     ProfScope ps(p, PG_FAM_FFT_Z_FWD, s, 2.0 * p->N * p->N * p->M1 * (double)sizeof(C));
-    PG_CUDA_TRY(FftPasses<R>::z_fwd(p->N, p->Fg.as<C>(), p->P, p->tw.as<C>(), s));
+    PG_CUDA_TRY(FftPasses<R>::z_fwd(p->N, p->Fg.as<C>(), lay_yz(p->N, p->P), p->tw.as<C>(), s));
   }
   if (do_gg) PG_CUDA_TRY(correlate_window<R>(p, 1, true, p->sums_gg.as<double>(), s));
   return cudaSuccess;
@@ -761,8 +761,8 @@ cudaError_t window_spectrum(pg_plan* p, const double* sbar, const double* gbar,
   PG_CUDA_TRY(FftPasses<R>::x_r2c_real(p->N, p->wlines.as<R>(), nl, p->spec.as<C>(), p->P, tw, s));
   PG_CUDA_TRY(FftPasses<R>::y_fwd(p->N, 1, p->spec.as<C>(), p->P, p->wl_idx.as<int32_t>(),
                                   p->wl_tot.as<int64_t>(), p->wl_base.as<int64_t>(),
-                                  p->wl_y.as<int32_t>(), p->Xs.as<C>(), 0, tw, s));
-  return FftPasses<R>::z_fwd(p->N, p->Xs.as<C>(), p->P, tw, s);
+                                  p->wl_y.as<int32_t>(), p->Xs.as<C>(), 0, lay_yz(p->N, p->P), tw, s));
+  return FftPasses<R>::z_fwd(p->N, p->Xs.as<C>(), lay_yz(p->N, p->P), tw, s);
 }
 
 // Reverse sweep of the last forward call (see pg_backward in pairgal.h).
@@ -785,6 +785,8 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   const int W = p->W, nbmax = p->nbmax;
   const int64_t W2 = (int64_t)W * W;
   const int64_t Xw_stride = (int64_t)W * N * p->P;
+  const Lay L = lay_yz(N, p->P);
+  const Lay XL{(int64_t)p->P, (int64_t)W * p->P};   // compact windows [ky][zr][kx]
   PG_CUDA_TRY(ensure_lines(p, nbmax * W2));
   PG_CUDA_TRY(p->Xs.ensure(sizeof(C) * spec_elems, t));
   PG_CUDA_TRY(p->As.ensure(sizeof(C) * spec_elems, t));
@@ -894,25 +896,25 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
                                            p->cggw.as<R>(), p->wlines.as<R>() + j * W2 * N, s));
       PG_CUDA_TRY(FftPasses<R>::x_r2c_real(N, p->wlines.as<R>(), nb * W2, p->spec.as<C>(), p->P, tw, s));
       PG_CUDA_TRY(FftPasses<R>::y_fwd_win(N, nb, p->spec.as<C>(), p->P, p->w, p->Xw.as<C>(), Xw_stride,
-                                          tw, s));
+                                          XL, tw, s));
     }
     {
       // S and the compact window spectra of every mesh in, Y_b out; A read
       // and written once (F_g from L2, counted once)
       ProfScope ps(p, PG_FAM_ADJ_Z, s, dnb * (2.0 * spec1 + win1) + 3.0 * spec1);
-      PG_CUDA_TRY(FftPasses<R>::zadj(N, nb, p->S.as<C>(), S_stride, p->Xw.as<C>(), Xw_stride,
+      PG_CUDA_TRY(FftPasses<R>::zadj(N, nb, p->S.as<C>(), S_stride, L, p->Xw.as<C>(), Xw_stride, XL,
                                      p->Fg.as<C>(), p->As.as<C>(), p->w, p->P, tw, err, s));
     }
     {
       // Y_b in (planes that hold lines; counted whole), the lines out
       ProfScope ps(p, PG_FAM_ADJ_Y_INV, s, dnb * spec1 + (double)nl * M1 * cs);
-      PG_CUDA_TRY(FftPasses<R>::y_inv_lines(N, nb, p->S.as<C>(), S_stride, p->P, p->lidx.as<int32_t>(),
+      PG_CUDA_TRY(FftPasses<R>::y_inv_lines(N, nb, p->S.as<C>(), S_stride, L, p->P, p->lidx.as<int32_t>(),
                                             p->seg_total.as<int64_t>(), p->line_base.as<int64_t>(),
                                             p->line_y.as<int32_t>(), p->spec.as<C>(), tw, err, s));
     }
     {
       ProfScope ps(p, PG_FAM_ADJ_X_C2R, s, (double)nl * (M1 * cs + Nd * rs));
-      PG_CUDA_TRY(FftPasses<R>::x_c2r_lines(N, p->spec.as<C>(), p->P, nl, nullptr, nullptr, hl, scale6,
+      PG_CUDA_TRY(FftPasses<R>::x_c2r_lines(N, p->spec.as<C>(), p->P, L, nl, nullptr, nullptr, hl, scale6,
                                             tw, s));
     }
     PG_CUDA_TRY(cudaStreamSynchronize(s));   // hbase
@@ -933,13 +935,13 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   }
   // galaxy side: f_g adjoint = N^-6 IDFT[A] at the galaxy lines
   ProfScope ps(p, PG_FAM_ADJ_GALAXY, s, 4.0 * NN * M1 * cs + 96.0 * (double)n);
-  PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, p->As.as<C>(), p->P, tw, s));
-  PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, p->As.as<C>(), p->P, tw, s));
+  PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, p->As.as<C>(), L, tw, s));
+  PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, p->As.as<C>(), L, tw, s));
   int64_t nlg = 0;
   PG_CUDA_TRY(deposit_batch(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, nullptr,
                             0, 1, &nlg, s));
   hl = reinterpret_cast<R*>(p->lines_q.p);   // ensure_lines may have moved it
-  PG_CUDA_TRY(FftPasses<R>::x_c2r_lines(N, p->As.as<C>(), p->P, nlg, p->line_y.as<int32_t>(),
+  PG_CUDA_TRY(FftPasses<R>::x_c2r_lines(N, p->As.as<C>(), p->P, L, nlg, p->line_y.as<int32_t>(),
                                         p->line_z.as<int32_t>(), hl, scale6, tw, s));
   PG_CUDA_TRY(launch_gather<R>(geo, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw,
                                p->lidx.as<int32_t>(), hl, p->gj.as<double>(), p->part.as<double>(),
@@ -1283,13 +1285,15 @@ pg_status pg_fft_r2c_3d(pg_plan* p, const void* d_in, void* d_out, void* stream)
   if (p->prm.precision) {
     using C = double2;
     PG_TRY(FftPasses<double>::x_r2c_dense(N, (const double*)d_in, (C*)d_out, P, p->tw.as<C>(), s));
-    PG_TRY(FftPasses<double>::y_fwd(N, 1, (C*)d_out, P, nullptr, nullptr, nullptr, nullptr, (C*)d_out, 0, p->tw.as<C>(), s));
-    PG_TRY(FftPasses<double>::z_fwd(N, (C*)d_out, P, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<double>::y_fwd(N, 1, (C*)d_out, P, nullptr, nullptr, nullptr, nullptr, (C*)d_out, 0,
+                                    lay_zy(N, P), p->tw.as<C>(), s));
+    PG_TRY(FftPasses<double>::z_fwd(N, (C*)d_out, lay_zy(N, P), p->tw.as<C>(), s));
   } else {
     using C = float2;
     PG_TRY(FftPasses<float>::x_r2c_dense(N, (const float*)d_in, (C*)d_out, P, p->tw.as<C>(), s));
-    PG_TRY(FftPasses<float>::y_fwd(N, 1, (C*)d_out, P, nullptr, nullptr, nullptr, nullptr, (C*)d_out, 0, p->tw.as<C>(), s));
-    PG_TRY(FftPasses<float>::z_fwd(N, (C*)d_out, P, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<float>::y_fwd(N, 1, (C*)d_out, P, nullptr, nullptr, nullptr, nullptr, (C*)d_out, 0,
+                                   lay_zy(N, P), p->tw.as<C>(), s));
+    PG_TRY(FftPasses<float>::z_fwd(N, (C*)d_out, lay_zy(N, P), p->tw.as<C>(), s));
   }
   return PG_OK;
 }
@@ -1304,14 +1308,14 @@ pg_status pg_fft_c2r_3d(pg_plan* p, const void* d_in, void* d_out, void* stream)
   if (p->prm.precision) {
     using C = double2;
     C* t = p->tmpfft.as<C>();
-    PG_TRY(FftPasses<double>::z_inv_full(N, t, P, p->tw.as<C>(), s));
-    PG_TRY(FftPasses<double>::y_inv_full(N, t, P, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<double>::z_inv_full(N, t, lay_zy(N, P), p->tw.as<C>(), s));
+    PG_TRY(FftPasses<double>::y_inv_full(N, t, lay_zy(N, P), p->tw.as<C>(), s));
     PG_TRY(FftPasses<double>::x_c2r_full(N, t, P, (double*)d_out, p->tw.as<C>(), s));
   } else {
     using C = float2;
     C* t = p->tmpfft.as<C>();
-    PG_TRY(FftPasses<float>::z_inv_full(N, t, P, p->tw.as<C>(), s));
-    PG_TRY(FftPasses<float>::y_inv_full(N, t, P, p->tw.as<C>(), s));
+    PG_TRY(FftPasses<float>::z_inv_full(N, t, lay_zy(N, P), p->tw.as<C>(), s));
+    PG_TRY(FftPasses<float>::y_inv_full(N, t, lay_zy(N, P), p->tw.as<C>(), s));
     PG_TRY(FftPasses<float>::x_c2r_full(N, t, P, (float*)d_out, p->tw.as<C>(), s));
   }
   return PG_OK;

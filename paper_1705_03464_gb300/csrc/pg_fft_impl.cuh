@@ -28,6 +28,21 @@ static cudaError_t persistent_grid(K kern, int threads, size_t smem, int64_t ite
   *grid = (unsigned)std::min<int64_t>(items, (int64_t)sms * std::max(1, per_sm));
   return cudaSuccess;
 }
+
+// Tensor map over 8-byte elements of nb spectra of layout L (each N*N*P
+// complex), dimensions (kx, z, ky, mesh), box (one kx tile, bz z rows, by ky
+// rows, one mesh).
+template <typename R>
+static bool spec_map(CUtensorMap* m, const void* base, int N, int P, Lay L, int nb, uint32_t bz,
+                     uint32_t by) {
+  using C = typename CT<R>::C;
+  constexpr int B = ZCols<R>::B, E = (int)(sizeof(C) / 8);
+  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)N, (uint64_t)nb};
+  const uint64_t strides[3] = {(uint64_t)L.zs * 8 * E, (uint64_t)L.ys * 8 * E,
+                               (uint64_t)N * N * P * 8 * E};
+  const uint32_t box[4] = {(uint32_t)(B * E), bz, by, 1u};
+  return encode_map_4d(m, base, dims, strides, box);
+}
 }  // namespace fft
 
 #define PG_DISPATCH_N(N, ...)                               \
@@ -78,8 +93,8 @@ cudaError_t FftPasses<R>::x_r2c_dense(int N, const R* f, C* spec, int P, const C
 template <typename R>
 cudaError_t FftPasses<R>::y_fwd(int N, int nb, const C* spec, int P, const int32_t* idx,
                                 const int64_t* seg_total, const int64_t* line_base,
-                                const int32_t* line_y, C* S, int64_t S_stride, const C* tw,
-                                cudaStream_t s) {
+                                const int32_t* line_y, C* S, int64_t S_stride, Lay L,
+                                const C* tw, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   constexpr int B = fft::Cols<R>::B;
   PG_DISPATCH_N(N, {
@@ -87,40 +102,33 @@ cudaError_t FftPasses<R>::y_fwd(int N, int nb, const C* spec, int P, const int32
     auto k = fft::k_y_fwd<C, NN, B>;
     PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
     dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN, nb);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(spec, P, idx, seg_total, line_base, line_y, S, S_stride, tw);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(spec, P, idx, seg_total, line_base, line_y, S, S_stride, L, tw);
   });
   return launched();
 }
 
 template <typename R>
-cudaError_t FftPasses<R>::z_fwd(int N, C* S, int P, const C* tw, cudaStream_t s) {
+cudaError_t FftPasses<R>::z_fwd(int N, C* S, Lay L, const C* tw, cudaStream_t s) {
   constexpr int B = fft::Cols<R>::B;
   PG_DISPATCH_N(N, {
     using CP = fft::ColPass<C, NN, B>;
     auto k = fft::k_z_fwd<C, NN, B>;
     PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
     dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, P, tw);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, L, tw);
   });
   return launched();
 }
 
 template <typename R>
 cudaError_t FftPasses<R>::z_corr(int N, int nb, const C* S, const C* Fg, bool gg, int w, C* Wz,
-                                 int64_t Wz_stride, int P, const C* tw, int* err, cudaStream_t s) {
+                                 int64_t Wz_stride, int P, Lay L, const C* tw, int* err, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   constexpr int B = fft::ZCols<R>::B;
-  constexpr int E = (int)(sizeof(C) / 8);
-  // tensor maps over 8-byte elements: [bin][z][ky][kx] with row pitch P
-  const uint64_t strides[3] = {(uint64_t)P * 8 * E, (uint64_t)N * P * 8 * E,
-                               (uint64_t)N * N * P * 8 * E};
   const uint32_t zb = N < 256 ? (uint32_t)N : 256u;
-  const uint32_t box[4] = {(uint32_t)(B * E), 1u, zb, 1u};
-  const uint64_t dS[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)N, (uint64_t)nb};
-  const uint64_t dF[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)N, 1u};
   CUtensorMap mF, mS;
-  if (!encode_map_4d(&mF, Fg, dF, strides, box)) return cudaErrorInvalidValue;
-  if (!encode_map_4d(&mS, gg ? (const void*)Fg : (const void*)S, gg ? dF : dS, strides, box))
+  if (!fft::spec_map<R>(&mF, Fg, N, P, L, 1, zb, 1) ||
+      !fft::spec_map<R>(&mS, gg ? (const void*)Fg : (const void*)S, N, P, L, gg ? 1 : nb, zb, 1))
     return cudaErrorInvalidValue;
   PG_DISPATCH_N(N, {
     using Z = fft::ZCorr<C, NN, B>;
@@ -176,27 +184,27 @@ cudaError_t FftPasses<R>::x_c2r_win(int N, int nb, const C* Wy, int64_t Wy_strid
 }
 
 template <typename R>
-cudaError_t FftPasses<R>::z_inv_full(int N, C* S, int P, const C* tw, cudaStream_t s) {
+cudaError_t FftPasses<R>::z_inv_full(int N, C* S, Lay L, const C* tw, cudaStream_t s) {
   constexpr int B = fft::Cols<R>::B;
   PG_DISPATCH_N(N, {
     using CP = fft::ColPass<C, NN, B>;
     auto k = fft::k_col_inv_full<C, NN, B, true>;
     PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
     dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, P, tw);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, L, tw);
   });
   return launched();
 }
 
 template <typename R>
-cudaError_t FftPasses<R>::y_inv_full(int N, C* S, int P, const C* tw, cudaStream_t s) {
+cudaError_t FftPasses<R>::y_inv_full(int N, C* S, Lay L, const C* tw, cudaStream_t s) {
   constexpr int B = fft::Cols<R>::B;
   PG_DISPATCH_N(N, {
     using CP = fft::ColPass<C, NN, B>;
     auto k = fft::k_col_inv_full<C, NN, B, false>;
     PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
     dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, P, tw);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, L, tw);
   });
   return launched();
 }
@@ -244,7 +252,7 @@ bool FftPasses<R>::adj_fits(int N, int w) {
 
 template <typename R>
 cudaError_t FftPasses<R>::y_fwd_win(int N, int nb, const C* spec, int P, int w, C* Xw,
-                                    int64_t Xw_stride, const C* tw, cudaStream_t s) {
+                                    int64_t Xw_stride, Lay XL, const C* tw, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   constexpr int B = fft::ZCols<R>::B;
   PG_DISPATCH_N(N, {
@@ -252,46 +260,38 @@ cudaError_t FftPasses<R>::y_fwd_win(int N, int nb, const C* spec, int P, int w, 
     auto k = fft::k_y_fwd_win<C, NN, B>;
     PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
     dim3 g((unsigned)cdiv(NN / 2 + 1, B), (unsigned)(2 * w + 1), (unsigned)nb);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(spec, P, w, Xw, Xw_stride, tw);
+    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(spec, P, w, Xw, Xw_stride, XL, tw);
   });
   return launched();
 }
 
 namespace fft {
-// Tensor maps of the adjoint passes, over 8-byte elements: full columns of a
-// [b][z][ky][kx] array (pitch P, nb meshes) and compact window columns of
-// Xw[b][zr][ky][kx].
+// Tensor map of compact window spectra Xw (layout XL: strides of zr and ky),
+// dimensions (kx, zr, ky, mesh), box (one kx tile, all W rows, one ky, one mesh).
 template <typename R>
-static bool adj_col_map(CUtensorMap* m, const void* base, int N, int P, int nb) {
+static bool adj_win_map(CUtensorMap* m, const void* base, int N, int P, int W, int nb, int64_t stride,
+                        Lay XL) {
   using C = typename CT<R>::C;
   constexpr int B = ZCols<R>::B, E = (int)(sizeof(C) / 8);
-  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)N, (uint64_t)nb};
-  const uint64_t strides[3] = {(uint64_t)P * 8 * E, (uint64_t)N * P * 8 * E,
-                               (uint64_t)N * N * P * 8 * E};
-  const uint32_t box[4] = {(uint32_t)(B * E), 1u, N < 256 ? (uint32_t)N : 256u, 1u};
-  return encode_map_4d(m, base, dims, strides, box);
-}
-template <typename R>
-static bool adj_win_map(CUtensorMap* m, const void* base, int N, int P, int W, int nb, int64_t stride) {
-  using C = typename CT<R>::C;
-  constexpr int B = ZCols<R>::B, E = (int)(sizeof(C) / 8);
-  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)W, (uint64_t)nb};
-  const uint64_t strides[3] = {(uint64_t)P * 8 * E, (uint64_t)N * P * 8 * E, (uint64_t)stride * 8 * E};
-  const uint32_t box[4] = {(uint32_t)(B * E), 1u, (uint32_t)W, 1u};
+  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)W, (uint64_t)N, (uint64_t)nb};
+  const uint64_t strides[3] = {(uint64_t)XL.zs * 8 * E, (uint64_t)XL.ys * 8 * E, (uint64_t)stride * 8 * E};
+  const uint32_t box[4] = {(uint32_t)(B * E), (uint32_t)W, 1u, 1u};
   return encode_map_4d(m, base, dims, strides, box);
 }
 }  // namespace fft
 
 template <typename R>
-cudaError_t FftPasses<R>::zadj(int N, int nb, C* S, int64_t S_stride, const C* Xw, int64_t Xw_stride,
-                               const C* Fg, C* A, int w, int P, const C* tw, int* err, cudaStream_t s) {
+cudaError_t FftPasses<R>::zadj(int N, int nb, C* S, int64_t S_stride, Lay L, const C* Xw,
+                               int64_t Xw_stride, Lay XL, const C* Fg, C* A, int w, int P, const C* tw,
+                               int* err, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   if (!adj_fits(N, w)) return cudaErrorInvalidValue;
   constexpr int B = fft::ZCols<R>::B;
   const int W = 2 * w + 1;
+  const uint32_t zb = N < 256 ? (uint32_t)N : 256u;
   CUtensorMap mS, mX, mA;
-  if (!fft::adj_col_map<R>(&mS, S, N, P, nb) || !fft::adj_win_map<R>(&mX, Xw, N, P, W, nb, Xw_stride) ||
-      !fft::adj_col_map<R>(&mA, A, N, P, 1))
+  if (!fft::spec_map<R>(&mS, S, N, P, L, nb, zb, 1) ||
+      !fft::adj_win_map<R>(&mX, Xw, N, P, W, nb, Xw_stride, XL) || !fft::spec_map<R>(&mA, A, N, P, L, 1, zb, 1))
     return cudaErrorInvalidValue;
   PG_DISPATCH_N(N, {
     using Z = fft::ZAdj<C, NN, B>;
@@ -300,26 +300,22 @@ cudaError_t FftPasses<R>::zadj(int N, int nb, C* S, int64_t S_stride, const C* X
     PG_CUDA_TRY(set_smem(k, sm));
     unsigned grid = 0;
     PG_CUDA_TRY(fft::persistent_grid(k, Z::THREADS, sm, cdiv(NN / 2 + 1, B) * (int64_t)NN, &grid));
-    k<<<grid, Z::THREADS, sm, s>>>(mS, mX, mA, nb, w, S, S_stride, Fg, A, P, tw, err);
+    k<<<grid, Z::THREADS, sm, s>>>(mS, mX, mA, nb, w, S, S_stride, L, Fg, A, tw, err);
   });
   return launched();
 }
 
 template <typename R>
-cudaError_t FftPasses<R>::y_inv_lines(int N, int nb, const C* Y, int64_t Y_stride, int P,
+cudaError_t FftPasses<R>::y_inv_lines(int N, int nb, const C* Y, int64_t Y_stride, Lay L, int P,
                                       const int32_t* idx, const int64_t* seg_total,
                                       const int64_t* line_base, const int32_t* line_y, C* hspec,
                                       const C* tw, int* err, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   constexpr int B = fft::ZCols<R>::B;
-  constexpr int E = (int)(sizeof(C) / 8);
-  // Y as [b][z][ky][kx] over 8-byte elements; a box is one kx tile of up to
-  // 256 ky rows of one plane
-  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)N, (uint64_t)nb};
-  const uint64_t strides[3] = {(uint64_t)P * 8 * E, (uint64_t)N * P * 8 * E, (uint64_t)Y_stride * 8 * E};
-  const uint32_t box[4] = {(uint32_t)(B * E), N < 256 ? (uint32_t)N : 256u, 1u, 1u};
+  // a box is one kx tile of up to 256 ky rows of one z plane
+  if (Y_stride != (int64_t)N * N * P) return cudaErrorInvalidValue;
   CUtensorMap mY;
-  if (!encode_map_4d(&mY, Y, dims, strides, box)) return cudaErrorInvalidValue;
+  if (!fft::spec_map<R>(&mY, Y, N, P, L, nb, 1, N < 256 ? (uint32_t)N : 256u)) return cudaErrorInvalidValue;
   PG_DISPATCH_N(N, {
     using YL = fft::YLines<C, NN, B>;
     auto k = fft::k_y_inv_lines<C, NN, B>;
@@ -333,7 +329,7 @@ cudaError_t FftPasses<R>::y_inv_lines(int N, int nb, const C* Y, int64_t Y_strid
 }
 
 template <typename R>
-cudaError_t FftPasses<R>::x_c2r_lines(int N, const C* S, int P, int64_t n_lines,
+cudaError_t FftPasses<R>::x_c2r_lines(int N, const C* S, int P, Lay L, int64_t n_lines,
                                       const int32_t* line_y, const int32_t* line_z, R* out,
                                       double scale, const C* tw, cudaStream_t s) {
   if (n_lines <= 0) return cudaSuccess;
@@ -341,7 +337,7 @@ cudaError_t FftPasses<R>::x_c2r_lines(int N, const C* S, int P, int64_t n_lines,
     using X = fft::XPass<C, NN>;
     auto k = fft::k_x_c2r_lines<C, NN>;
     PG_CUDA_TRY(set_smem(k, X::smem_bytes()));
-    k<<<(unsigned)cdiv(n_lines, X::LB), X::THREADS, X::smem_bytes(), s>>>(S, P, n_lines, line_y,
+    k<<<(unsigned)cdiv(n_lines, X::LB), X::THREADS, X::smem_bytes(), s>>>(S, P, L, n_lines, line_y,
                                                                         line_z, out, (R)scale, tw);
   });
   return launched();

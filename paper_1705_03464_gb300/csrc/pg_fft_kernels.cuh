@@ -333,7 +333,7 @@ template <typename C, int N, int B>
 __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
 k_y_fwd(const C* __restrict__ spec, int P, const int32_t* __restrict__ idx,
         const int64_t* __restrict__ seg_total, const int64_t* __restrict__ line_base,
-        const int32_t* __restrict__ line_y, C* __restrict__ S, int64_t S_stride,
+        const int32_t* __restrict__ line_y, C* __restrict__ S, int64_t S_stride, Lay L,
         const C* __restrict__ tw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
@@ -375,20 +375,20 @@ k_y_fwd(const C* __restrict__ spec, int P, const int32_t* __restrict__ idx,
   C a[N2];
   step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
   if (c < ncol) {
-    C* out = S + (int64_t)b * S_stride + (int64_t)z * N * P + kx0 + c;
+    C* out = S + (int64_t)b * S_stride + (int64_t)z * L.zs + kx0 + c;
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) out[(int64_t)(k1 + N1 * k2) * P] = a[k2];
+    for (int k2 = 0; k2 < N2; ++k2) out[(int64_t)(k1 + N1 * k2) * L.ys] = a[k2];
   }
 }
 
-// Column tile load of one (ky, kx tile) z-column: rows z at stride N*P.
+// Column tile load of one (ky, kx tile) z-column: rows z at stride zs.
 template <typename C, int N, int B>
-__device__ __forceinline__ void load_zcol(C* buf, const C* __restrict__ src, int P, int ncol) {
+__device__ __forceinline__ void load_zcol(C* buf, const C* __restrict__ src, int64_t zs, int ncol) {
   const int c = threadIdx.x % B;
   for (int z = threadIdx.x / B; z < N; z += blockDim.x / B) {
     C v;
     v.x = 0; v.y = 0;
-    if (c < ncol) v = src[(int64_t)z * N * P + c];
+    if (c < ncol) v = src[(int64_t)z * zs + c];
     buf[z * B + c] = v;
   }
 }
@@ -396,7 +396,7 @@ __device__ __forceinline__ void load_zcol(C* buf, const C* __restrict__ src, int
 // Z pass forward in place (galaxy spectrum). CTA = (kx tile, ky).
 template <typename C, int N, int B>
 __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
-k_z_fwd(C* __restrict__ S, int P, const C* __restrict__ tw) {
+k_z_fwd(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
@@ -405,8 +405,8 @@ k_z_fwd(C* __restrict__ S, int P, const C* __restrict__ tw) {
   constexpr int XP = xperm<C, N, B>();
   const int kx0 = blockIdx.x * B, ky = blockIdx.y;
   const int ncol = min(B, M1 - kx0);
-  C* col = S + (int64_t)ky * P + kx0;
-  load_zcol<C, N, B>(buf, col, P, ncol);
+  C* col = S + (int64_t)ky * L.ys + kx0;
+  load_zcol<C, N, B>(buf, col, L.zs, ncol);
   __syncthreads();
   step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
   __syncthreads();
@@ -415,7 +415,7 @@ k_z_fwd(C* __restrict__ S, int P, const C* __restrict__ tw) {
   step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
   if (c < ncol) {
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) col[(int64_t)(k1 + N1 * k2) * N * P + c] = a[k2];
+    for (int k2 = 0; k2 < N2; ++k2) col[(int64_t)(k1 + N1 * k2) * L.zs + c] = a[k2];
   }
 }
 
@@ -494,7 +494,7 @@ __device__ __forceinline__ void x_c2r_body(C* buf, int64_t l0, int64_t n_lines, 
 // lines are compact, line l at S + l * P.
 template <typename C, int N>
 __global__ void __launch_bounds__(XPass<C, N>::THREADS)
-k_x_c2r_lines(const C* __restrict__ S, int P, int64_t n_lines, const int32_t* __restrict__ line_y,
+k_x_c2r_lines(const C* __restrict__ S, int P, Lay L, int64_t n_lines, const int32_t* __restrict__ line_y,
               const int32_t* __restrict__ line_z, typename Real<C>::T* __restrict__ out,
               typename Real<C>::T scale, const C* __restrict__ tw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -505,7 +505,7 @@ k_x_c2r_lines(const C* __restrict__ S, int P, int64_t n_lines, const int32_t* __
   x_c2r_core<C, N>(
       buf, l0, n_lines,
       [&](int64_t l, int k) {
-        return line_y ? S[((int64_t)line_z[l] * N + line_y[l]) * P + k] : S[l * P + k];
+        return line_y ? S[(int64_t)line_z[l] * L.zs + (int64_t)line_y[l] * L.ys + k] : S[l * P + k];
       },
       tws,
       [&](int64_t l, int n, RT v) { out[l * N + n] = v * scale; });
@@ -551,7 +551,7 @@ k_x_c2r_full(const C* __restrict__ S, int P, typename Real<C>::T* __restrict__ o
 // Full inverse along z or y in place on a dense half spectrum (stage entry).
 template <typename C, int N, int B, bool ALONG_Z>
 __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
-k_col_inv_full(C* __restrict__ S, int P, const C* __restrict__ tw) {
+k_col_inv_full(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
   const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
@@ -562,8 +562,8 @@ k_col_inv_full(C* __restrict__ S, int P, const C* __restrict__ tw) {
   const int ncol = min(B, M1 - kx0);
   const int c = threadIdx.x % B;
   // ALONG_Z: column over z at fixed y = other; else over y at fixed z = other
-  const int64_t rs = ALONG_Z ? (int64_t)N * P : (int64_t)P;
-  C* col = S + (ALONG_Z ? (int64_t)other * P : (int64_t)other * N * P) + kx0;
+  const int64_t rs = ALONG_Z ? L.zs : L.ys;
+  C* col = S + (int64_t)other * (ALONG_Z ? L.ys : L.zs) + kx0;
   for (int r = threadIdx.x / B; r < N; r += blockDim.x / B) {
     C v;
     v.x = 0; v.y = 0;
@@ -609,7 +609,7 @@ __device__ __forceinline__ void zc_issue(C* dst, const CUtensorMap* map, uint64_
   using Z = ZCorr<C, N, B>;
   tma::mbar_arrive_expect_tx(bar, Z::TILE_BYTES);
 #pragma unroll
-  for (int z0 = 0; z0 < N; z0 += Z::ZB) tma::load_4d(dst + z0 * B, map, bar, kx0 * Z::E, ky, z0, b);
+  for (int z0 = 0; z0 < N; z0 += Z::ZB) tma::load_4d(dst + z0 * B, map, bar, kx0 * Z::E, z0, ky, b);
 }
 
 template <typename C, int N, int B>
@@ -840,7 +840,7 @@ __device__ __forceinline__ int mesh_of_rank(int r, int N, int w) { return r <= w
 // y = mesh_of_rank(ry). CTA = (kx tile, zr, mesh b).
 template <typename C, int N, int B>
 __global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
-k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_t Xw_stride,
+k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_t Xw_stride, Lay XL,
             const C* __restrict__ tw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;
@@ -864,9 +864,9 @@ k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_
   C a[N2];
   step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
   if (c < ncol) {
-    C* out = Xw + (int64_t)b * Xw_stride + (int64_t)zr * N * P + kx0 + c;
+    C* out = Xw + (int64_t)b * Xw_stride + (int64_t)zr * XL.zs + kx0 + c;
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) out[(int64_t)(k1 + N1 * k2) * P] = a[k2];
+    for (int k2 = 0; k2 < N2; ++k2) out[(int64_t)(k1 + N1 * k2) * XL.ys] = a[k2];
   }
 }
 
@@ -888,21 +888,23 @@ struct ZAdj {
   static size_t smem(int W) { return sizeof(C) * (3 * (size_t)TILE + 2 * (size_t)win_slot(W) + N) + 64; }
 };
 
-// Full column (N rows) of a [b][z][ky][kx] array into dst.
+// Full z column (N rows) of a spectrum array into dst; the tensor map's
+// dimensions are (kx, z, ky, mesh).
 template <typename C, int N, int B>
 __device__ __forceinline__ void za_issue_col(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
                                              int ky, int b, uint64_t policy) {
   using Z = ZAdj<C, N, B>;
 #pragma unroll
   for (int z0 = 0; z0 < N; z0 += Z::ZB)
-    tma::load_4d_hint(dst + z0 * B, map, bar, kx0 * Z::E, ky, z0, b, policy);
+    tma::load_4d_hint(dst + z0 * B, map, bar, kx0 * Z::E, z0, ky, b, policy);
 }
 
-// Compact window column (W rows) of Xw[b][zr][ky][kx] into dst.
+// Compact window column (W rows) of Xw into dst; the tensor map's
+// dimensions are (kx, zr, ky, mesh).
 template <typename C, int N, int B>
 __device__ __forceinline__ void za_issue_win(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
                                              int ky, int b, uint64_t policy) {
-  tma::load_4d_hint(dst, map, bar, kx0 * ZAdj<C, N, B>::E, ky, 0, b, policy);
+  tma::load_4d_hint(dst, map, bar, kx0 * ZAdj<C, N, B>::E, 0, ky, b, policy);
 }
 
 // Step 1 of the split (see step1) on the zero-padded window column whose
@@ -946,7 +948,7 @@ template <typename C, int N, int B>
 __global__ void __launch_bounds__(ZAdj<C, N, B>::THREADS, 1)
 k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mX,
        const __grid_constant__ CUtensorMap mA, int nb, int w, C* __restrict__ S, int64_t S_stride,
-       const C* __restrict__ Fg, C* __restrict__ A, int P, const C* __restrict__ tw,
+       Lay L, const C* __restrict__ Fg, C* __restrict__ A, const C* __restrict__ tw,
        int* __restrict__ err) {
   using Z = ZAdj<C, N, B>;
   constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1;
@@ -991,7 +993,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
     const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
     const int ncol = min(B, M1 - kx0);
     const bool dc_col = (kx0 + c == 0) && (ky == 0);
-    const C* fcol = Fg + (int64_t)ky * P + kx0 + c;
+    const C* fcol = Fg + (int64_t)ky * L.ys + kx0 + c;
     if (__syncthreads_or(!tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
     ph[2] ^= 1;
     for (int b = 0; b < nb; ++b, ++job) {
@@ -1030,14 +1032,14 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
       for (int k2 = 0; k2 < N2; ++k2) {
         C f;
         f.x = 0; f.y = 0;
-        if (c < ncol) f = tma::ld_hint(fcol + (int64_t)(k1 + N1 * k2) * N * P, pol_keep);
+        if (c < ncol) f = tma::ld_hint(fcol + (int64_t)(k1 + N1 * k2) * L.zs, pol_keep);
         x[k2] = cmul(x[k2], f);
       }
       if (dc_col && k1 == 0) { x[0].x = 0; x[0].y = 0; }   // k = 0 mode
       __syncthreads();
       stepA<C, N1, N2, true, XP>(buf, B, c, k1, x, tws, 1);
       __syncthreads();
-      C* yout = S + (int64_t)b * S_stride + (int64_t)ky * P + kx0;
+      C* yout = S + (int64_t)b * S_stride + (int64_t)ky * L.ys + kx0;
       for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
         const int cc = t % B, n2 = t / B;
         C v[N1];
@@ -1045,17 +1047,17 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
         if (cc < ncol) {
 #pragma unroll
           for (int n1 = 0; n1 < N1; ++n1)
-            tma::st_hint(yout + (int64_t)(n2 + N2 * n1) * N * P + cc, v[n1], pol_stream);
+            tma::st_hint(yout + (int64_t)(n2 + N2 * n1) * L.zs + cc, v[n1], pol_stream);
         }
       }
       __syncthreads();   // slot free for the job after next
     }
     if (failed) break;
     // the item's A column back to global memory, then the next item's A tile
-    C* ag = A + (int64_t)ky * P + kx0;
+    C* ag = A + (int64_t)ky * L.ys + kx0;
     for (int t = threadIdx.x; t < TILE; t += blockDim.x) {
       const int z = t / B, cc = t % B;
-      tma::st_hint(ag + (int64_t)z * N * P + cc, at[t], pol_stream);
+      tma::st_hint(ag + (int64_t)z * L.zs + cc, at[t], pol_stream);
     }
     __syncthreads();
     if (threadIdx.x == 0 && item + gridDim.x < n_items) {
@@ -1129,7 +1131,7 @@ k_y_inv_lines(const __grid_constant__ CUtensorMap mY, int nb, int P, const int32
     tma::mbar_arrive_expect_tx(&bar[k], Y::TILE_BYTES);
 #pragma unroll
     for (int y0 = 0; y0 < N; y0 += Y::YB)
-      tma::load_4d(buf0 + k * TILE + y0 * B, &mY, &bar[k], (int)(it % T) * B * Y::E, y0, (int)(r % N),
+      tma::load_4d(buf0 + k * TILE + y0 * B, &mY, &bar[k], (int)(it % T) * B * Y::E, (int)(r % N), y0,
                    (int)(r / N));
   };
   for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];

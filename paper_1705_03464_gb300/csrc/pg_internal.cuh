@@ -139,6 +139,16 @@ cudaError_t launch_field_scale(int nb, const unsigned long long* qsum, int N, do
                                cudaStream_t s);
 
 // ---- FFT passes (pg_fft_f32.cu / pg_fft_f64.cu) -----------------------------
+// Strides, in complex elements, of z and y in a half-spectrum array (kx has
+// stride 1). The plan's own spectra are [y][z][kx]: a z column of one (ky,
+// kx tile) then lies in a few memory pages, where [z][y][kx] puts each of
+// its N rows in its own page. The stage entry points keep [z][y][kx].
+struct Lay {
+  int64_t zs, ys;
+};
+inline Lay lay_zy(int N, int P) { return {(int64_t)N * P, (int64_t)P}; }
+inline Lay lay_yz(int N, int P) { return {(int64_t)P, (int64_t)N * P}; }
+
 // Spectra are complex R pairs; P = row pitch in complex elements (>= N/2+1).
 template <typename R>
 struct FftPasses {
@@ -155,17 +165,17 @@ struct FftPasses {
   // l = z*N + y of one mesh). S[b] = [z][ky][P].
   static cudaError_t y_fwd(int N, int nb, const C* spec, int P, const int32_t* idx,
                            const int64_t* seg_total, const int64_t* line_base,
-                           const int32_t* line_y, C* S, int64_t S_stride, const C* tw,
+                           const int32_t* line_y, C* S, int64_t S_stride, Lay L, const C* tw,
                            cudaStream_t s);
   // Z pass forward in place: S[z][ky][kx] -> F[kz][ky][kx].
-  static cudaError_t z_fwd(int N, C* S, int P, const C* tw, cudaStream_t s);
+  static cudaError_t z_fwd(int N, C* S, Lay L, const C* tw, cudaStream_t s);
   // Z pass fused: for each of nb meshes, forward z, times conj(Fg) / N^3
   // (gg: P = |Fg|^2 / N^3 from Fg itself), k = 0 set to zero, inverse z, and
   // only the |z| <= w rows written: Wz[b] = [2w+1][ky][P]. Persistent and
   // TMA fed; S must be [nb][N][N][P] contiguous (S_stride = N*N*P) and P*sizeof(C)
   // a multiple of 16. A bounded wait that gives up sets *err (device) nonzero.
   static cudaError_t z_corr(int N, int nb, const C* S, const C* Fg, bool gg, int w, C* Wz,
-                            int64_t Wz_stride, int P, const C* tw, int* err, cudaStream_t s);
+                            int64_t Wz_stride, int P, Lay L, const C* tw, int* err, cudaStream_t s);
   // Inverse y on the window rows: Wz[b][zw][ky] -> Wy[b][zw][yw], |y| <= w.
   static cudaError_t y_inv_win(int N, int nb, const C* Wz, int64_t Wz_stride, int w, C* Wy,
                                int64_t Wy_stride, int P, const C* tw, int* err, cudaStream_t s);
@@ -175,8 +185,8 @@ struct FftPasses {
                                R* Cwin, int64_t Cwin_stride, int P, double scale,
                                const C* tw, cudaStream_t s);
   // Dense inverse passes for the stage entry point: full y, full x.
-  static cudaError_t z_inv_full(int N, C* S, int P, const C* tw, cudaStream_t s);
-  static cudaError_t y_inv_full(int N, C* S, int P, const C* tw, cudaStream_t s);
+  static cudaError_t z_inv_full(int N, C* S, Lay L, const C* tw, cudaStream_t s);
+  static cudaError_t y_inv_full(int N, C* S, Lay L, const C* tw, cudaStream_t s);
   static cudaError_t x_c2r_full(int N, const C* S, int P, R* out, const C* tw,
                                 cudaStream_t s);
   static cudaError_t set_smem_limits();
@@ -189,22 +199,23 @@ struct FftPasses {
   static bool adj_fits(int N, int w);
   // Y pass of the window lines (spec line (b*W + zr)*W + ry) into Xw.
   static cudaError_t y_fwd_win(int N, int nb, const C* spec, int P, int w, C* Xw,
-                               int64_t Xw_stride, const C* tw, cudaStream_t s);
+                               int64_t Xw_stride, Lay XL, const C* tw, cudaStream_t s);
   // Both sides of the adjoint z pass: A[kz][ky][kx] += sum_b F_b conj(X_b)
   // (F_b the z transform of S[b], [nb][N][N][P] contiguous; X_b that of
   // Xw[b] zero-padded), and Y_b = inverse z of X_b Fg (k = 0 zeroed) written
   // over S[b].
-  static cudaError_t zadj(int N, int nb, C* S, int64_t S_stride, const C* Xw, int64_t Xw_stride,
-                          const C* Fg, C* A, int w, int P, const C* tw, int* err, cudaStream_t s);
+  static cudaError_t zadj(int N, int nb, C* S, int64_t S_stride, Lay L, const C* Xw,
+                          int64_t Xw_stride, Lay XL, const C* Fg, C* A, int w, int P, const C* tw,
+                          int* err, cudaStream_t s);
   // Inverse y of Y[b] at the compact lines of the batch (numbering of the
   // forward deposit: idx, seg_total, line_base, line_y) into hspec[line][P].
-  static cudaError_t y_inv_lines(int N, int nb, const C* Y, int64_t Y_stride, int P,
+  static cudaError_t y_inv_lines(int N, int nb, const C* Y, int64_t Y_stride, Lay L, int P,
                                  const int32_t* idx, const int64_t* seg_total,
                                  const int64_t* line_base, const int32_t* line_y, C* hspec,
                                  const C* tw, int* err, cudaStream_t s);
   // out[l][x] = scale * C2R of row (line_z[l], line_y[l]) of S; line_y ==
   // null: of the compact line S + l*P.
-  static cudaError_t x_c2r_lines(int N, const C* S, int P, int64_t n_lines, const int32_t* line_y,
+  static cudaError_t x_c2r_lines(int N, const C* S, int P, Lay L, int64_t n_lines, const int32_t* line_y,
                                  const int32_t* line_z, R* out, double scale, const C* tw,
                                  cudaStream_t s);
 };
