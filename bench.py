@@ -209,6 +209,26 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ---------------------------------------------------------- ranks
+def mock_seed(seed, rank):
+    """Each rank draws its own mock: the path shards by mock (weak scaling)."""
+    return seed + rank
+
+
+def max_over_ranks(x, dist, torch, device):
+    """The slowest rank's value (the job's step time); x itself without ranks."""
+    if not dist:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_mock(ms_per_step, world):
+    """Whole-job ms per mock: every rank finishes one mock per step."""
+    return ms_per_step / world
+
+
 # ---------------------------------------------------------- many mocks
 def _draw_mock(k):
     from paper_1705_03464_gb300 import synth
@@ -308,7 +328,7 @@ def main():
     from paper_1705_03464_gb300 import pairgal as pg, synth
 
     wl = synth.WORKLOADS[args.workload]
-    cat = synth.make_catalogue(wl, args.seed + rank)
+    cat = synth.make_catalogue(wl, mock_seed(args.seed, rank))
     pos = torch.from_numpy(cat.pos).cuda()
     vel = torch.from_numpy(np.ascontiguousarray(cat.vel)).cuda() if wl.rsd else None
     plan = pg.Plan.of(wl, **({"bins_per_batch": args.bins_per_batch} if args.bins_per_batch else {}))
@@ -342,14 +362,10 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    t_ms = e0.elapsed_time(e1)
-    if dist:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(e0.elapsed_time(e1), dist, torch, "cuda")
     plan.set_profiling(False)
     ms_per_step = t_ms / args.steps
-    value = ms_per_step / world
+    value = per_mock(ms_per_step, world)
 
     # end to end through the host-buffer entry point: pinned inputs in,
     # result arrays out, both copies inside the timed region
@@ -372,12 +388,8 @@ def main():
             pg.pg_forward_host(plan, ph, vh, None, stream=stream)
         a1.record(stream)
         torch.cuda.synchronize()
-        te = a0.elapsed_time(a1)
-        if dist:
-            tt = torch.tensor([te], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": te / args.steps / world, "unit": UNIT,
+        te = max_over_ranks(a0.elapsed_time(a1), dist, torch, "cuda")
+        e2e = {"value": per_mock(te / args.steps, world), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "wall_s": time.perf_counter() - t0}
 
@@ -399,18 +411,14 @@ def main():
             wbar = pg.pg_backward(plan, grads, int(cat.n), stream=stream)
         b1.record(stream)
         torch.cuda.synchronize()
-        tb = b0.elapsed_time(b1)
-        if dist:
-            tt = torch.tensor([tb], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            tb = float(tt.item())
+        tb = max_over_ranks(b0.elapsed_time(b1), dist, torch, "cuda")
         # one more backward with per-family event timing (outside the timed steps)
         plan.set_profiling(True)
         pg.pg_backward(plan, grads, int(cat.n), stream=stream)
         bfams, bl = plan.last_stats()
         plan.set_profiling(False)
-        fwd_adj = {"ms_per_mock": tb / args.adjoint_steps / world, "steps": args.adjoint_steps,
-                   "ratio_to_fwd": (tb / args.adjoint_steps / world) / value,
+        fwd_adj = {"ms_per_mock": per_mock(tb / args.adjoint_steps, world), "steps": args.adjoint_steps,
+                   "ratio_to_fwd": per_mock(tb / args.adjoint_steps, world) / value,
                    "loss": "sum(b_pg) + sum(q_eff)",
                    "grad_finite": bool(torch.isfinite(wbar).all().item()),
                    "backward_launches": bl,
@@ -435,11 +443,7 @@ def main():
             ref64 = pg.pg_forward(plan64, pos, vel, stream=stream)
         c1.record(stream)
         torch.cuda.synchronize()
-        tp = c0.elapsed_time(c1)
-        if dist:
-            tt = torch.tensor([tp], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            tp = float(tt.item())
+        tp = max_over_ranks(c0.elapsed_time(c1), dist, torch, "cuda")
         del plan64
         torch.cuda.empty_cache()
 
@@ -448,7 +452,7 @@ def main():
             ok = np.isfinite(a) & np.isfinite(b)
             return float(np.max(np.abs(a[ok] - b[ok]) / np.maximum(np.abs(b[ok]), 1e-300))) if ok.any() else None
 
-        plain_ms = tp / args.plain_steps / world
+        plain_ms = per_mock(tp / args.plain_steps, world)
         plain = {"ms_per_mock": plain_ms, "steps": args.plain_steps,
                  "form": "FP64 FFT passes, one pair mesh per batch",
                  "speedup_of_fp32_batched": plain_ms / value,

@@ -345,6 +345,13 @@ pg_status pg_autotune(const pg_params* params, int64_t n_gal, const double* h_po
                       const float* h_vel, const float* h_w, const int32_t* candidates,
                       int32_t n_cand, int32_t* best, double* ms_out, void* stream);
 
+/* Failure-detection test of the device waits: one CTA waits on an mbarrier
+ * that nothing completes, with the same bounded wait the TMA-fed kernels use
+ * (there 2 s), here limit_ms (0 < limit_ms <= 5000). Returns PG_ERR_TIMEOUT
+ * when the wait gives up, which is the expected outcome; the context stays
+ * usable. PG_ERR_INVALID_ARG for a NULL plan or a limit out of range. */
+pg_status pg_selftest_wait(pg_plan* plan, double limit_ms, void* stream);
+
 /* Enables (1) or disables (0) per-family event timing on later calls of
  * pg_forward / pg_forward_host / pg_backward on this plan. */
 pg_status pg_plan_set_profiling(pg_plan* plan, int32_t enable);

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "pg_internal.cuh"
+#include "pg_tma.cuh"
 
 using namespace pg;
 
@@ -1160,6 +1161,17 @@ pg_status pg_hod_chain(pg_plan* p, int64_t n, const double* d_wbar, const double
   PG_TRY(cudaMemcpyAsync(h_grad_theta, part + 5 * nblk, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
   PG_TRY(cudaStreamSynchronize(s));
   return PG_OK;
+}
+
+pg_status pg_selftest_wait(pg_plan* p, double limit_ms, void* stream) {
+  if (!p || !(limit_ms > 0.0) || limit_ms > 5000.0) return PG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PG_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));
+  PG_TRY(pg::launch_wait_selftest((uint64_t)(limit_ms * 1e6), p->flag.as<int32_t>() + 1, s));
+  int32_t herr = 0;
+  PG_TRY(cudaMemcpyAsync(&herr, p->flag.as<int32_t>() + 1, 4, cudaMemcpyDeviceToHost, s));
+  PG_TRY(cudaStreamSynchronize(s));
+  return herr ? PG_ERR_TIMEOUT : PG_OK;
 }
 
 pg_status pg_plan_set_profiling(pg_plan* p, int32_t enable) {

@@ -42,4 +42,24 @@ bool encode_map_4d(CUtensorMap* map, const void* base, const uint64_t dims[4],
   return r == CUDA_SUCCESS;
 }
 
+namespace {
+// One CTA waits on an mbarrier that nothing completes, with the bounded wait
+// of the TMA kernels, and records that it gave up.
+__global__ void k_wait_selftest(uint64_t limit_ns, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&bar, 1);
+    tma::fence_async_shared();
+  }
+  __syncthreads();
+  const bool done = tma::mbar_wait(&bar, 0, limit_ns);
+  if (__syncthreads_or(!done) && threadIdx.x == 0) atomicExch(err, tma::kErrTmaTimeout);
+}
+}  // namespace
+
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int* err, cudaStream_t s) {
+  k_wait_selftest<<<1, 128, 0, s>>>(limit_ns, err);
+  return cudaGetLastError();
+}
+
 }  // namespace pg

@@ -136,4 +136,8 @@ __device__ __forceinline__ void st_hint(double2* p, double2 v, uint64_t policy) 
 bool encode_map_4d(CUtensorMap* map, const void* base, const uint64_t dims[4],
                    const uint64_t strides_bytes[3], const uint32_t box[4]);
 
+// Test of the bounded waits: one CTA waits on an mbarrier nothing completes
+// for limit_ns and sets *err (device) to kErrTmaTimeout when it gives up.
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int* err, cudaStream_t s);
+
 }  // namespace pg

@@ -81,6 +81,7 @@ def _load():
         "pg_plan_create": (C.c_int, [C.POINTER(pg_params), C.POINTER(vp)]),
         "pg_plan_create_shared": (C.c_int, [C.POINTER(pg_params), vp, C.POINTER(vp)]),
         "pg_run_batch": (C.c_int, [vp, i32, vp, vp, vp]),
+        "pg_selftest_wait": (C.c_int, [vp, C.c_double, vp]),
         "pg_autotune": (C.c_int, [C.POINTER(pg_params), i64, vp, vp, vp, vp, i32, vp, vp, vp]),
         "pg_plan_destroy": (None, [vp]),
         "pg_plan_reserve": (C.c_int, [vp, i64, i64]),
@@ -529,3 +530,9 @@ def autotune_cached(problem, pos, vel=None, w=None, cache_path=None, candidates=
         with open(path, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
     return best, ms
+
+
+def pg_selftest_wait(plan: Plan, limit_ms: float, stream=None) -> int:
+    """Failure-detection test of the bounded device waits: returns the status
+    (PG_ERR_TIMEOUT when the wait gave up, the expected outcome)."""
+    return int(_lib.pg_selftest_wait(plan.handle, float(limit_ms), _stream(stream)))

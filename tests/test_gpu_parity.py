@@ -321,3 +321,20 @@ def test_forward_rsd_cic_512_full(pg):
                         {"s1": g1, "s2": g2, "n": n, "a1": ga1, "a2": ga2, "na": 0}, xs[b:b + 1])
         ratio_close(got["b_pg"][b], ref["b_pg"][0])
         ratio_close(got["q_eff"][b], ref["q_eff"][0])
+
+
+def test_bounded_wait_gives_up_and_context_survives(pg):
+    """Failure detection without a fault: a device wait that nothing
+    completes gives up after its limit and reports PG_ERR_TIMEOUT; the
+    context keeps working."""
+    import time
+    p, cat, w = _small_cic_rsd()
+    plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur,
+                   rsd_factor=p.rsd_factor, r_perp_cut=p.r_perp_cut, precision=0)
+    t0 = time.perf_counter()
+    assert pg.pg_selftest_wait(plan, 50.0) == pg.PG_ERR_TIMEOUT
+    assert time.perf_counter() - t0 >= 0.045
+    assert pg.pg_selftest_wait(plan, 0.0) == pg.PG_ERR_INVALID_ARG
+    a = pg.pg_forward(plan, dev(cat.pos), dev(cat.vel), dev(w))
+    b = pg.pg_forward(plan, dev(cat.pos), dev(cat.vel), dev(w))
+    np.testing.assert_array_equal(a["xi_pg"], b["xi_pg"])
