@@ -440,7 +440,7 @@ cudaError_t lines_to_S(pg_plan* p, int nb, int64_t nl, typename CT<R>::C* S, int
   ProfScope ps(p, PG_FAM_FFT_Y_FWD, s, (double)nl * M1 * cs + (double)nb * N * N * M1 * cs);
   return FftPasses<R>::y_fwd(p->N, nb, p->spec.as<C>(), p->P, p->lidx.as<int32_t>(),
                              p->seg_total.as<int64_t>(), p->line_base.as<int64_t>(),
-                             p->line_y.as<int32_t>(), S, S_stride, lay_yz(p->N, p->P), tw, s);
+                             p->line_y.as<int32_t>(), S, S_stride, lay_plan(p->N, p->P), tw, s);
 }
 
 // Correlation window of nb meshes against Fg (or Fg with itself) and its bin
@@ -461,7 +461,7 @@ cudaError_t correlate_window(pg_plan* p, int nb, bool gg, double* sums, cudaStre
     ProfScope ps(p, PG_FAM_FFT_Z_CORR, s,
                  (gg ? 0.0 : nb * N * N * M1 * cs) + N * N * M1 * cs + nb * W * N * M1 * cs);
     PG_CUDA_TRY(FftPasses<R>::z_corr(p->N, nb, p->S.as<C>(), p->Fg.as<C>(), gg, p->w,
-                                     p->Wz.as<C>(), Wz_stride, p->P, lay_yz(p->N, p->P), tw,
+                                     p->Wz.as<C>(), Wz_stride, p->P, lay_plan(p->N, p->P), tw,
                                      p->flag.as<int32_t>() + 1, s));
   }
   {
@@ -489,7 +489,7 @@ cudaError_t galaxy_pass(pg_plan* p, int64_t n, const double* x, const double* y,
   PG_CUDA_TRY(lines_to_S<R>(p, 1, nl, p->Fg.as<C>(), 0, s));
   {
     ProfScope ps(p, PG_FAM_FFT_Z_FWD, s, 2.0 * p->N * p->N * p->M1 * (double)sizeof(C));
-    PG_CUDA_TRY(FftPasses<R>::z_fwd(p->N, p->Fg.as<C>(), lay_yz(p->N, p->P), p->tw.as<C>(), s));
+    PG_CUDA_TRY(FftPasses<R>::z_fwd(p->N, p->Fg.as<C>(), lay_plan(p->N, p->P), p->tw.as<C>(), s));
   }
   if (do_gg) PG_CUDA_TRY(correlate_window<R>(p, 1, true, p->sums_gg.as<double>(), s));
   return cudaSuccess;
@@ -762,8 +762,8 @@ cudaError_t window_spectrum(pg_plan* p, const double* sbar, const double* gbar,
   PG_CUDA_TRY(FftPasses<R>::x_r2c_real(p->N, p->wlines.as<R>(), nl, p->spec.as<C>(), p->P, tw, s));
   PG_CUDA_TRY(FftPasses<R>::y_fwd(p->N, 1, p->spec.as<C>(), p->P, p->wl_idx.as<int32_t>(),
                                   p->wl_tot.as<int64_t>(), p->wl_base.as<int64_t>(),
-                                  p->wl_y.as<int32_t>(), p->Xs.as<C>(), 0, lay_yz(p->N, p->P), tw, s));
-  return FftPasses<R>::z_fwd(p->N, p->Xs.as<C>(), lay_yz(p->N, p->P), tw, s);
+                                  p->wl_y.as<int32_t>(), p->Xs.as<C>(), 0, lay_plan(p->N, p->P), tw, s));
+  return FftPasses<R>::z_fwd(p->N, p->Xs.as<C>(), lay_plan(p->N, p->P), tw, s);
 }
 
 // Reverse sweep of the last forward call (see pg_backward in pairgal.h).
@@ -786,8 +786,8 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   const int W = p->W, nbmax = p->nbmax;
   const int64_t W2 = (int64_t)W * W;
   const int64_t Xw_stride = (int64_t)W * N * p->P;
-  const Lay L = lay_yz(N, p->P);
-  const Lay XL{(int64_t)p->P, (int64_t)W * p->P};   // compact windows [ky][zr][kx]
+  const Lay L = lay_plan(N, p->P);
+  const Lay XL{(int64_t)p->P, 0, (int64_t)W * p->P, 0};   // compact windows [ky][zr][kx]
   PG_CUDA_TRY(ensure_lines(p, nbmax * W2));
   PG_CUDA_TRY(p->Xs.ensure(sizeof(C) * spec_elems, t));
   PG_CUDA_TRY(p->As.ensure(sizeof(C) * spec_elems, t));

@@ -29,19 +29,23 @@ static cudaError_t persistent_grid(K kern, int threads, size_t smem, int64_t ite
   return cudaSuccess;
 }
 
-// Tensor map over 8-byte elements of nb spectra of layout L (each N*N*P
-// complex), dimensions (kx, z, ky, mesh), box (one kx tile, bz z rows, by ky
-// rows, one mesh).
+// Tensor map over 8-byte elements of nb spectra of the plan layout L (each
+// N*N*P complex), dimensions (kx, y mod K, z, y / K, mesh) with K = 2^L.ks,
+// box (one kx tile, then either bz z rows of one y (by = 1) or by y rows of
+// one z (bz = 1)).
 template <typename R>
 static bool spec_map(CUtensorMap* m, const void* base, int N, int P, Lay L, int nb, uint32_t bz,
                      uint32_t by) {
   using C = typename CT<R>::C;
   constexpr int B = ZCols<R>::B, E = (int)(sizeof(C) / 8);
-  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)N, (uint64_t)nb};
-  const uint64_t strides[3] = {(uint64_t)L.zs * 8 * E, (uint64_t)L.ys * 8 * E,
+  const int K = 1 << L.ks;
+  if (K > N || N % K != 0 || (by > 1 && by % K != 0)) return false;
+  const uint64_t dims[5] = {(uint64_t)P * E, (uint64_t)K, (uint64_t)N, (uint64_t)(N / K), (uint64_t)nb};
+  const uint64_t strides[4] = {(uint64_t)L.ys * 8 * E, (uint64_t)L.zs * 8 * E, (uint64_t)L.hs * 8 * E,
                                (uint64_t)N * N * P * 8 * E};
-  const uint32_t box[4] = {(uint32_t)(B * E), bz, by, 1u};
-  return encode_map_4d(m, base, dims, strides, box);
+  const uint32_t box[5] = {(uint32_t)(B * E), by > 1 ? (uint32_t)K : 1u, bz, by > 1 ? by / (uint32_t)K : 1u,
+                           1u};
+  return encode_map_5d(m, base, dims, strides, box);
 }
 }  // namespace fft
 
@@ -273,8 +277,9 @@ static bool adj_win_map(CUtensorMap* m, const void* base, int N, int P, int W, i
                         Lay XL) {
   using C = typename CT<R>::C;
   constexpr int B = ZCols<R>::B, E = (int)(sizeof(C) / 8);
+  if (XL.ks != 0) return false;   // one ky row per block: ky stride hs
   const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)W, (uint64_t)N, (uint64_t)nb};
-  const uint64_t strides[3] = {(uint64_t)XL.zs * 8 * E, (uint64_t)XL.ys * 8 * E, (uint64_t)stride * 8 * E};
+  const uint64_t strides[3] = {(uint64_t)XL.zs * 8 * E, (uint64_t)XL.hs * 8 * E, (uint64_t)stride * 8 * E};
   const uint32_t box[4] = {(uint32_t)(B * E), (uint32_t)W, 1u, 1u};
   return encode_map_4d(m, base, dims, strides, box);
 }

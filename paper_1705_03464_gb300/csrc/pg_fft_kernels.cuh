@@ -377,7 +377,7 @@ k_y_fwd(const C* __restrict__ spec, int P, const int32_t* __restrict__ idx,
   if (c < ncol) {
     C* out = S + (int64_t)b * S_stride + (int64_t)z * L.zs + kx0 + c;
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) out[(int64_t)(k1 + N1 * k2) * L.ys] = a[k2];
+    for (int k2 = 0; k2 < N2; ++k2) out[yoff(L, k1 + N1 * k2)] = a[k2];
   }
 }
 
@@ -405,7 +405,7 @@ k_z_fwd(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
   constexpr int XP = xperm<C, N, B>();
   const int kx0 = blockIdx.x * B, ky = blockIdx.y;
   const int ncol = min(B, M1 - kx0);
-  C* col = S + (int64_t)ky * L.ys + kx0;
+  C* col = S + yoff(L, ky) + kx0;
   load_zcol<C, N, B>(buf, col, L.zs, ncol);
   __syncthreads();
   step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
@@ -505,7 +505,7 @@ k_x_c2r_lines(const C* __restrict__ S, int P, Lay L, int64_t n_lines, const int3
   x_c2r_core<C, N>(
       buf, l0, n_lines,
       [&](int64_t l, int k) {
-        return line_y ? S[(int64_t)line_z[l] * L.zs + (int64_t)line_y[l] * L.ys + k] : S[l * P + k];
+        return line_y ? S[(int64_t)line_z[l] * L.zs + yoff(L, line_y[l]) + k] : S[l * P + k];
       },
       tws,
       [&](int64_t l, int n, RT v) { out[l * N + n] = v * scale; });
@@ -562,12 +562,13 @@ k_col_inv_full(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
   const int ncol = min(B, M1 - kx0);
   const int c = threadIdx.x % B;
   // ALONG_Z: column over z at fixed y = other; else over y at fixed z = other
-  const int64_t rs = ALONG_Z ? L.zs : L.ys;
-  C* col = S + (int64_t)other * (ALONG_Z ? L.ys : L.zs) + kx0;
+  // row r of the column: z = r (ALONG_Z) or y = r
+  auto row = [&](int r) { return ALONG_Z ? (int64_t)r * L.zs : yoff(L, r); };
+  C* col = S + (ALONG_Z ? yoff(L, other) : (int64_t)other * L.zs) + kx0;
   for (int r = threadIdx.x / B; r < N; r += blockDim.x / B) {
     C v;
     v.x = 0; v.y = 0;
-    if (c < ncol) v = col[(int64_t)r * rs + c];
+    if (c < ncol) v = col[row(r) + c];
     buf[r * B + c] = v;
   }
   __syncthreads();
@@ -578,7 +579,7 @@ k_col_inv_full(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
   step2<C, N1, N2, true, XP>(buf, B, c, k1, a);
   if (c < ncol) {
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) col[(int64_t)(k1 + N1 * k2) * rs + c] = a[k2];
+    for (int k2 = 0; k2 < N2; ++k2) col[row(k1 + N1 * k2) + c] = a[k2];
   }
 }
 
@@ -608,8 +609,12 @@ __device__ __forceinline__ void zc_issue(C* dst, const CUtensorMap* map, uint64_
                                          int ky, int b) {
   using Z = ZCorr<C, N, B>;
   tma::mbar_arrive_expect_tx(bar, Z::TILE_BYTES);
+  // spectra maps are (kx, y mod 8, z, y / 8, mesh)
+  const uint64_t pol = tma::policy_evict_first();
+  constexpr int KM = (1 << kYBlockShift) - 1;
 #pragma unroll
-  for (int z0 = 0; z0 < N; z0 += Z::ZB) tma::load_4d(dst + z0 * B, map, bar, kx0 * Z::E, z0, ky, b);
+  for (int z0 = 0; z0 < N; z0 += Z::ZB)
+    tma::load_5d_hint(dst + z0 * B, map, bar, kx0 * Z::E, ky & KM, z0, ky >> kYBlockShift, b, pol);
 }
 
 template <typename C, int N, int B>
@@ -866,7 +871,7 @@ k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_
   if (c < ncol) {
     C* out = Xw + (int64_t)b * Xw_stride + (int64_t)zr * XL.zs + kx0 + c;
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) out[(int64_t)(k1 + N1 * k2) * XL.ys] = a[k2];
+    for (int k2 = 0; k2 < N2; ++k2) out[yoff(XL, k1 + N1 * k2)] = a[k2];
   }
 }
 
@@ -896,7 +901,8 @@ __device__ __forceinline__ void za_issue_col(C* dst, const CUtensorMap* map, uin
   using Z = ZAdj<C, N, B>;
 #pragma unroll
   for (int z0 = 0; z0 < N; z0 += Z::ZB)
-    tma::load_4d_hint(dst + z0 * B, map, bar, kx0 * Z::E, z0, ky, b, policy);
+    tma::load_5d_hint(dst + z0 * B, map, bar, kx0 * Z::E, ky & ((1 << kYBlockShift) - 1), z0,
+                      ky >> kYBlockShift, b, policy);
 }
 
 // Compact window column (W rows) of Xw into dst; the tensor map's
@@ -993,7 +999,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
     const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
     const int ncol = min(B, M1 - kx0);
     const bool dc_col = (kx0 + c == 0) && (ky == 0);
-    const C* fcol = Fg + (int64_t)ky * L.ys + kx0 + c;
+    const C* fcol = Fg + yoff(L, ky) + kx0 + c;
     if (__syncthreads_or(!tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
     ph[2] ^= 1;
     for (int b = 0; b < nb; ++b, ++job) {
@@ -1039,7 +1045,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
       __syncthreads();
       stepA<C, N1, N2, true, XP>(buf, B, c, k1, x, tws, 1);
       __syncthreads();
-      C* yout = S + (int64_t)b * S_stride + (int64_t)ky * L.ys + kx0;
+      C* yout = S + (int64_t)b * S_stride + yoff(L, ky) + kx0;
       for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
         const int cc = t % B, n2 = t / B;
         C v[N1];
@@ -1054,7 +1060,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
     }
     if (failed) break;
     // the item's A column back to global memory, then the next item's A tile
-    C* ag = A + (int64_t)ky * L.ys + kx0;
+    C* ag = A + yoff(L, ky) + kx0;
     for (int t = threadIdx.x; t < TILE; t += blockDim.x) {
       const int z = t / B, cc = t % B;
       tma::st_hint(ag + (int64_t)z * L.zs + cc, at[t], pol_stream);
@@ -1126,13 +1132,14 @@ k_y_inv_lines(const __grid_constant__ CUtensorMap mY, int nb, int P, const int32
     }
     return n_items;
   };
+  const uint64_t pol_stream = tma::policy_evict_first();
   auto issue = [&](int k, int64_t it) {
     const int64_t r = it / T;
     tma::mbar_arrive_expect_tx(&bar[k], Y::TILE_BYTES);
 #pragma unroll
     for (int y0 = 0; y0 < N; y0 += Y::YB)
-      tma::load_4d(buf0 + k * TILE + y0 * B, &mY, &bar[k], (int)(it % T) * B * Y::E, (int)(r % N), y0,
-                   (int)(r / N));
+      tma::load_5d_hint(buf0 + k * TILE + y0 * B, &mY, &bar[k], (int)(it % T) * B * Y::E, 0, (int)(r % N),
+                        y0 >> kYBlockShift, (int)(r / N), pol_stream);
   };
   for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
   if (threadIdx.x == 0) {

@@ -139,15 +139,26 @@ cudaError_t launch_field_scale(int nb, const unsigned long long* qsum, int N, do
                                cudaStream_t s);
 
 // ---- FFT passes (pg_fft_f32.cu / pg_fft_f64.cu) -----------------------------
-// Strides, in complex elements, of z and y in a half-spectrum array (kx has
-// stride 1). The plan's own spectra are [y][z][kx]: a z column of one (ky,
-// kx tile) then lies in a few memory pages, where [z][y][kx] puts each of
-// its N rows in its own page. The stage entry points keep [z][y][kx].
+// Layout of a half-spectrum array, offsets in complex elements (kx has
+// stride 1): element (z, y) at z*zs + (y >> ks)*hs + (y & (2^ks - 1))*ys,
+// i.e. y split into blocks of 2^ks rows. The plan's own spectra are
+// [y / 8][z][y % 8][kx]: a z column of one (ky, kx tile) lies in about 17
+// memory pages and the ky rows one y pass writes fall in 128 blocks, where
+// [z][y][kx] puts each of a z column's N rows in its own page. The stage
+// entry points keep [z][y][kx] (ks large: one block).
 struct Lay {
-  int64_t zs, ys;
+  int64_t zs, ys, hs;
+  int ks;
 };
-inline Lay lay_zy(int N, int P) { return {(int64_t)N * P, (int64_t)P}; }
-inline Lay lay_yz(int N, int P) { return {(int64_t)P, (int64_t)N * P}; }
+__host__ __device__ __forceinline__ int64_t yoff(const Lay& L, int y) {
+  return (int64_t)(y >> L.ks) * L.hs + (int64_t)(y & ((1 << L.ks) - 1)) * L.ys;
+}
+inline Lay lay_zy(int N, int P) { return {(int64_t)N * P, (int64_t)P, 0, 30}; }
+constexpr int kYBlockShift = 3;   // 8 ky rows per block
+inline Lay lay_plan(int N, int P) {
+  const int K = 1 << kYBlockShift;
+  return {(int64_t)K * P, (int64_t)P, (int64_t)N * K * P, kYBlockShift};
+}
 
 // Spectra are complex R pairs; P = row pitch in complex elements (>= N/2+1).
 template <typename R>

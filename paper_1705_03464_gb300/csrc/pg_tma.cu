@@ -42,6 +42,20 @@ bool encode_map_4d(CUtensorMap* map, const void* base, const uint64_t dims[4],
   return r == CUDA_SUCCESS;
 }
 
+bool encode_map_5d(CUtensorMap* map, const void* base, const uint64_t dims[5],
+                   const uint64_t strides_bytes[4], const uint32_t box[5]) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t gd[5] = {dims[0], dims[1], dims[2], dims[3], dims[4]};
+  cuuint64_t gs[4] = {strides_bytes[0], strides_bytes[1], strides_bytes[2], strides_bytes[3]};
+  cuuint32_t bx[5] = {box[0], box[1], box[2], box[3], box[4]};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 5, const_cast<void*>(base), gd, gs, bx, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 namespace {
 // One CTA waits on an mbarrier that nothing completes, with the bounded wait
 // of the TMA kernels, and records that it gave up.

@@ -76,6 +76,18 @@ __device__ __forceinline__ void load_4d(void* dst, const CUtensorMap* map, uint6
       : "memory");
 }
 
+// 5D tiled load (same rules as load_4d), with an L2 cache policy.
+__device__ __forceinline__ void load_5d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                             int c1, int c2, int c3, int c4, uint64_t policy) {
+  if (smem_addr(dst) & 127u) return;
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+      "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+
 // L2 eviction policies for cache-hinted accesses (createpolicy): streamed
 // data that is read or written once is marked evict-first, data that the
 // same CTA re-reads soon is marked evict-last.
@@ -135,6 +147,10 @@ __device__ __forceinline__ void st_hint(double2* p, double2 v, uint64_t policy) 
 // driver rejects it.
 bool encode_map_4d(CUtensorMap* map, const void* base, const uint64_t dims[4],
                    const uint64_t strides_bytes[3], const uint32_t box[4]);
+
+// As encode_map_4d with five dimensions (strides for dims 1..4).
+bool encode_map_5d(CUtensorMap* map, const void* base, const uint64_t dims[5],
+                   const uint64_t strides_bytes[4], const uint32_t box[5]);
 
 // Test of the bounded waits: one CTA waits on an mbarrier nothing completes
 // for limit_ns and sets *err (device) to kErrTmaTimeout when it gives up.
