@@ -59,7 +59,7 @@ const char* pg_status_string(pg_status s);
 typedef struct pg_params {
   double box_L;             /* periodic box side, Mpc/h, > 0 */
   int32_t mesh_n;           /* N: power of two, 32..1024 (Sec. 3.5 mesh) */
-  int32_t assign;           /* 0 = NGP, 1 = CIC mass assignment (Sec. 3.5) */
+  int32_t assign;           /* 0 = NGP, 1 = CIC, 2 = TSC (the paper's) mass assignment (Sec. 3.5) */
   int32_t n_s;              /* pair separation bins, 1..64 */
   const double* s_edges;    /* [n_s+1] ascending, s_edges[0] >= 0, s_edges[n_s] < L/2 */
   int32_t n_mu;             /* equal bins of mu = |dz|/s on [0, 1], 1..64 */
@@ -224,7 +224,7 @@ pg_status pg_find_pairs(pg_plan* plan, int64_t n, const double* d_pos,
                         int32_t* d_j, double* d_mid, double* d_wp,
                         int64_t* h_n_pairs, void* stream);
 
-/* Sec. 3.5: NGP/CIC mass assignment of n points (device [n][3] FP64 in
+/* Sec. 3.5: NGP/CIC/TSC mass assignment of n points (device [n][3] FP64 in
  * [0, L)) with weights (device FP64 or NULL = 1) into a dense device mesh
  * d_mesh[N][N][N] int64 of Q32.32 node weights llrint(((w wx) wy) wz 2^32),
  * ADDED to its current contents (zero it first for a fresh mesh). Exact and

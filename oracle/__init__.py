@@ -12,7 +12,7 @@ Modules, each following the paper passage named in its docstring:
                 pair enumeration binned by (s, mu) with pair midpoints
                 (Sec. 2.1, eq. delta_pi_x), pair counts and xi(s, mu) = DD/RR - 1
                 (Sec. 3.4, eq. 2PCF_d_collapsed).
-* ``mesh``      NGP / CIC mass assignment in Q32.32 fixed point (Sec. 3.5).
+* ``mesh``      NGP / CIC / TSC mass assignment in Q32.32 fixed point (Sec. 3.5).
 * ``dft``       its own FP64 discrete Fourier transform (textbook
                 Cooley-Tukey split over direct matrix DFTs).
 * ``correlate`` the mesh cross-correlation C(r) (Sec. 2.1, eqs. bpg_initial,

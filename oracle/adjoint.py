@@ -35,27 +35,7 @@ OUTPUT_KEYS = ("xi_pg", "xi_gg", "b_pg", "q_eff", "q_eff_sq", "xi_dw", "b_pg_agg
 
 def _node_weights(points, L, N, assign):
     """Nodes (iz, iy, ix) and unrounded weights K of each point: [n, k] arrays."""
-    p = np.asarray(points, dtype=np.float64).reshape(-1, 3)
-    dx = L / N
-    u = p / dx
-    if assign == 0:
-        i = np.floor(u + 0.5).astype(np.int64) % N
-        return i[:, 2:3], i[:, 1:2], i[:, 0:1], np.ones((p.shape[0], 1))
-    i0 = np.floor(u)
-    f = u - i0
-    i0 = i0.astype(np.int64)
-    zs, ys, xs, ks = [], [], [], []
-    for cz in (0, 1):
-        for cy in (0, 1):
-            for cx in (0, 1):
-                wz = f[:, 2] if cz else 1.0 - f[:, 2]
-                wy = f[:, 1] if cy else 1.0 - f[:, 1]
-                wx = f[:, 0] if cx else 1.0 - f[:, 0]
-                zs.append((i0[:, 2] + cz) % N)
-                ys.append((i0[:, 1] + cy) % N)
-                xs.append((i0[:, 0] + cx) % N)
-                ks.append(wx * wy * wz)
-    return (np.stack(zs, 1), np.stack(ys, 1), np.stack(xs, 1), np.stack(ks, 1))
+    return om.node_weights(points, L, N, assign)
 
 
 def _gather(field, nodes):

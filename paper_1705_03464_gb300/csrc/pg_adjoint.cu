@@ -205,32 +205,15 @@ k_gather(DepGeom geo, int64_t n, const double* __restrict__ x, const double* __r
   double v = 0.0, wv = 0.0;
   if (k < n) {
     const int N = geo.N;
-    const double u[3] = {x[k] / geo.dx, y[k] / geo.dx, z[k] / geo.dx};
-    int i0[3];
-    double f[3];
-    for (int a = 0; a < 3; ++a) {
-      if (geo.assign == 0) {
-        i0[a] = ((int)floor(u[a] + 0.5)) % N;
-        f[a] = 0.0;
-      } else {
-        const double fl = floor(u[a]);
-        i0[a] = ((int)fl) % N;
-        f[a] = u[a] - fl;
-      }
-      if (i0[a] < 0) i0[a] += N;
-    }
-    const int nn = geo.assign == 0 ? 1 : 2;
+    int ix[3], iy[3], iz[3];
+    double kx[3], ky[3], kz[3];
+    const int nn = axis_nodes(geo, __ddiv_rn(x[k], geo.dx), ix, kx);
+    axis_nodes(geo, __ddiv_rn(y[k], geo.dx), iy, ky);
+    axis_nodes(geo, __ddiv_rn(z[k], geo.dx), iz, kz);
     for (int cz = 0; cz < nn; ++cz)
       for (int cy = 0; cy < nn; ++cy) {
-        const int iz = (i0[2] + cz) % N, iy = (i0[1] + cy) % N;
-        const int64_t line = idx[(int64_t)iz * N + iy];
-        const double kz = geo.assign == 0 ? 1.0 : (cz ? f[2] : 1.0 - f[2]);
-        const double ky = geo.assign == 0 ? 1.0 : (cy ? f[1] : 1.0 - f[1]);
-        for (int cx = 0; cx < nn; ++cx) {
-          const int ix = (i0[0] + cx) % N;
-          const double kx = geo.assign == 0 ? 1.0 : (cx ? f[0] : 1.0 - f[0]);
-          v += kx * ky * kz * (double)lines[line * N + ix];
-        }
+        const int64_t line = idx[(int64_t)iz[cz] * N + iy[cy]];
+        for (int cx = 0; cx < nn; ++cx) v += kx[cx] * ky[cy] * kz[cz] * (double)lines[line * N + ix[cx]];
       }
     g[k] = v;
     wv = (wt ? wt[k] : 1.0) * v;

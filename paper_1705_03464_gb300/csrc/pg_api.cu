@@ -409,7 +409,7 @@ cudaError_t deposit_batch(pg_plan* p, int64_t n, const double* x, const double* 
   PG_CUDA_TRY(cudaStreamSynchronize(s));
   PG_CUDA_TRY(ensure_lines(p, nl));
   {
-    ProfScope ps(p, PG_FAM_DEPOSIT, s, (double)nl * p->N * 8 + 40.0 * n * (p->prm.assign ? 8 : 1));
+    ProfScope ps(p, PG_FAM_DEPOSIT, s, (double)nl * p->N * 8 + 40.0 * n * (p->prm.assign == 2 ? 27 : p->prm.assign ? 8 : 1));
     PG_CUDA_TRY(launch_line_compact(p->N, nb, p->flags.as<uint8_t>(), p->lidx.as<int32_t>(),
                                     p->line_base.as<int64_t>(), p->line_y.as<int32_t>(),
                                     p->line_bin.as<int32_t>(), p->line_z.as<int32_t>(), s));
@@ -981,7 +981,7 @@ pg_status plan_create(const pg_params* prm, const pg_plan* share, pg_plan** out)
   if (q.n_s < 1 || q.n_s > 64 || q.n_mu < 1 || q.n_mu > 64 || q.n_r < 1 || q.n_r > 64 ||
       q.n_mur < 1 || q.n_mur > 64 || !q.s_edges || !q.r_edges)
     return PG_ERR_INVALID_ARG;
-  if (q.assign != 0 && q.assign != 1) return PG_ERR_INVALID_ARG;
+  if (q.assign < 0 || q.assign > 2) return PG_ERR_INVALID_ARG;
   if (q.precision != 0 && q.precision != 1) return PG_ERR_INVALID_ARG;
   if (!is_pow2(q.mesh_n) || q.mesh_n < 32 || q.mesh_n > 1024) return PG_ERR_UNSUPPORTED;
   for (int i = 0; i < q.n_s; ++i)
@@ -1107,7 +1107,7 @@ pg_status pg_plan_reserve(pg_plan* p, int64_t n_gal_max, int64_t n_pairs_max) {
   PG_TRY(ensure_gal(p, n_gal_max));
   PG_TRY(ensure_pairs(p, n_pairs_max));
   const int64_t NN = (int64_t)p->N * p->N;
-  const int64_t per = p->prm.assign ? 4 : 1;
+  const int64_t per = p->prm.assign == 2 ? 9 : p->prm.assign ? 4 : 1;
   PG_TRY(ensure_lines(p, std::min<int64_t>(NN * p->nbmax, std::max(per * n_gal_max, per * n_pairs_max))));
   return PG_OK;
 }
@@ -1281,7 +1281,7 @@ pg_status pg_find_pairs(pg_plan* p, int64_t n, const double* d_pos, const float*
 
 pg_status pg_deposit_dense(int64_t n, const double* d_pts, const double* d_w, double L,
                            int32_t N, int32_t assign, int64_t* d_mesh, void* stream) {
-  if (n < 0 || !(L > 0.0) || N < 1 || N > 4096 || (assign != 0 && assign != 1) || !d_mesh ||
+  if (n < 0 || !(L > 0.0) || N < 1 || N > 4096 || assign < 0 || assign > 2 || !d_mesh ||
       (n > 0 && !d_pts))
     return PG_ERR_INVALID_ARG;
   DepGeom g{N, L / (double)N, assign};

@@ -115,8 +115,48 @@ cudaError_t launch_pair_scatter(int64_t np, const PairOut& po, unsigned long lon
 struct DepGeom {
   int N;
   double dx;              // L / N
-  int assign;             // 0 NGP, 1 CIC
+  int assign;             // 0 NGP, 1 CIC, 2 TSC
 };
+
+// Nodes and weights of one axis of a point's assignment footprint (Sec. 3.5),
+// u = x / dx; returns the node count (1 NGP, 2 CIC, 3 TSC). NGP: node
+// floor(u + 1/2). CIC: floor(u) and the next node, weights 1 - f and f.
+// TSC: the nearest node c = floor(u + 1/2) and its neighbours, weights
+// (1/2)(1/2 - d)^2, 3/4 - d^2, (1/2)(1/2 + d)^2, d = u - c. Every operation
+// rounds once (no contraction), so the weights are bit-reproducible.
+__device__ __forceinline__ int axis_nodes(const DepGeom& g, double u, int* idx, double* wt) {
+  const int N = g.N;
+  if (g.assign == 0) {
+    int i = (int)floor(__dadd_rn(u, 0.5)) % N;
+    if (i < 0) i += N;
+    idx[0] = i;
+    wt[0] = 1.0;
+    return 1;
+  }
+  if (g.assign == 1) {
+    const double i0 = floor(u);
+    const double fr = __dsub_rn(u, i0);
+    int i = (int)i0 % N;
+    if (i < 0) i += N;
+    idx[0] = i;
+    idx[1] = (i + 1 == N) ? 0 : i + 1;
+    wt[0] = __dsub_rn(1.0, fr);
+    wt[1] = fr;
+    return 2;
+  }
+  const double c = floor(__dadd_rn(u, 0.5));
+  const double d = __dsub_rn(u, c);
+  int i = (int)c % N;
+  if (i < 0) i += N;
+  idx[0] = (i == 0) ? N - 1 : i - 1;
+  idx[1] = i;
+  idx[2] = (i + 1 == N) ? 0 : i + 1;
+  const double t0 = __dsub_rn(0.5, d), t2 = __dadd_rn(0.5, d);
+  wt[0] = __dmul_rn(0.5, __dmul_rn(t0, t0));
+  wt[1] = __dsub_rn(0.75, __dmul_rn(d, d));
+  wt[2] = __dmul_rn(0.5, __dmul_rn(t2, t2));
+  return 3;
+}
 // Points: SoA x,y,z (FP64, in [0,L)), weight FP64 or null; pbin: per point
 // bin index relative to the batch (null = all in bin 0).
 cudaError_t launch_mark_lines(const DepGeom& g, int64_t n, const double* x, const double* y,

@@ -1,4 +1,5 @@
-// Mass assignment (Sec. 3.5) into compact x-lines of Q32.32 int64 nodes.
+// Mass assignment (Sec. 3.5: NGP, CIC or the paper's TSC) into compact
+// x-lines of Q32.32 int64 nodes.
 //
 // A pair bin touches few mesh lines (Sec. 2.1: a pair field is a sum of
 // deltas at the pair midpoints), so each bin's mesh is stored as the list of
@@ -15,39 +16,15 @@ constexpr int kThreads = 256;
 constexpr int kMaxBatch = 64;   // bins whose totals are summed in shared memory
 
 struct Foot {
-  int ix[2], iy[2], iz[2];
-  double wx[2], wy[2], wz[2];
-  int n;  // 1 (NGP) or 2 (CIC) nodes per axis
+  int ix[3], iy[3], iz[3];
+  double wx[3], wy[3], wz[3];
+  int n;  // nodes per axis: 1 (NGP), 2 (CIC), 3 (TSC)
 };
 
 __device__ __forceinline__ void footprint(const DepGeom& g, double x, double y, double z, Foot& f) {
-  double u[3] = {__ddiv_rn(x, g.dx), __ddiv_rn(y, g.dx), __ddiv_rn(z, g.dx)};
-  int* idx[3] = {f.ix, f.iy, f.iz};
-  double* wt[3] = {f.wx, f.wy, f.wz};
-  if (g.assign == 0) {
-    f.n = 1;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      int i = (int)floor(__dadd_rn(u[a], 0.5));
-      i %= g.N;
-      if (i < 0) i += g.N;
-      idx[a][0] = i;
-      wt[a][0] = 1.0;
-    }
-  } else {
-    f.n = 2;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      double i0 = floor(u[a]);
-      double fr = __dsub_rn(u[a], i0);
-      int i = (int)i0 % g.N;
-      if (i < 0) i += g.N;
-      idx[a][0] = i;
-      idx[a][1] = (i + 1 == g.N) ? 0 : i + 1;
-      wt[a][0] = __dsub_rn(1.0, fr);
-      wt[a][1] = fr;
-    }
-  }
+  f.n = axis_nodes(g, __ddiv_rn(x, g.dx), f.ix, f.wx);
+  axis_nodes(g, __ddiv_rn(y, g.dx), f.iy, f.wy);
+  axis_nodes(g, __ddiv_rn(z, g.dx), f.iz, f.wz);
 }
 
 __device__ __forceinline__ unsigned long long node_q(const DepGeom& g, double w, double wx,

@@ -32,7 +32,7 @@ def _case(assign, rsd, cut, seed=3):
 
 
 @pytest.mark.parametrize("precision", [1, 0])
-@pytest.mark.parametrize("assign,rsd,cut", [(0, 0.0, 0.0), (1, 0.011, 3.0)])
+@pytest.mark.parametrize("assign,rsd,cut", [(0, 0.0, 0.0), (1, 0.011, 3.0), (2, 0.011, 0.0)])
 def test_backward_matches_oracle_gradient(pg, precision, assign, rsd, cut):
     p, cat, w = _case(assign, rsd, cut)
     plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur,

@@ -9,6 +9,8 @@ the grid for bins whose denominator is near zero. The FP64 path is held to
 """
 import math
 
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -131,7 +133,7 @@ def test_find_pairs_bitexact(pg, case):
 
 
 # ---------------------------------------------------------------- a4
-@pytest.mark.parametrize("assign", [0, 1])
+@pytest.mark.parametrize("assign", [0, 1, 2])
 @pytest.mark.parametrize("N", [32, 64])
 def test_deposit_dense_bitexact(pg, assign, N):
     rng = np.random.default_rng(N + assign)
@@ -237,6 +239,19 @@ def _small_cic_rsd():
 @pytest.mark.parametrize("precision", [1, 0])
 def test_forward_weighted_cic_rsd_perp_cut(pg, precision):
     p, cat, w = _small_cic_rsd()
+    plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur,
+                   rsd_factor=p.rsd_factor, r_perp_cut=p.r_perp_cut, precision=precision,
+                   bins_per_batch=4)
+    got = pg.pg_forward(plan, dev(cat.pos), dev(cat.vel), dev(w))
+    ref = pipeline.run(p, cat.pos, cat.vel, w, form="mesh")
+    _compare_forward(got, ref, precision)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_forward_tsc_weighted_rsd(pg, precision):
+    """The paper's TSC assignment (Sec. 3.5) through the whole forward path."""
+    p, cat, w = _small_cic_rsd()
+    p = dataclasses.replace(p, assign=2)
     plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur,
                    rsd_factor=p.rsd_factor, r_perp_cut=p.r_perp_cut, precision=precision,
                    bins_per_batch=4)
