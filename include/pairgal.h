@@ -146,6 +146,51 @@ pg_status pg_forward_host(pg_plan* plan, int64_t n_gal, const double* h_pos,
                           const float* h_vel, const float* h_w,
                           pg_result* host_out, void* stream);
 
+/* The Gauss-sigmoid weighting function of Sec. 3.6 (eq. weighting):
+ * W(r_perp, r_par) = 1 / (1 + exp(-s0 (r_perp - r_s))) *
+ * exp(-(r_perp^2 + r_par^2) / (2 sigma^2)) for r_perp >= r_cut and 0 inside
+ * that cylinder around the line of sight (z); r_perp, r_par are the offsets
+ * perpendicular and parallel to z. The paper's normalisation cancels and is
+ * taken as 1. Table tab:weightings: (30, 20, 0.8, 10) for d_p,max = 10 Mpc/h,
+ * (50, 35, 0.5, 20) for 30 Mpc/h. */
+typedef struct pg_smooth_params {
+  double sigma;   /* Mpc/h, > 0 */
+  double r_s;     /* Mpc/h */
+  double s0;      /* h/Mpc */
+  double r_cut;   /* Mpc/h, >= 0 */
+} pg_smooth_params;
+
+/* Host outputs of pg_forward_smooth, P = n_s * n_mu pair bins. */
+typedef struct pg_smooth_result {
+  int64_t* dd;     /* [P] pairs per (s, mu) bin */
+  double* xi_ss;   /* [P] xi(s, mu) = DD/RR - 1 */
+  double* num;     /* [P] weighted mean of (W * delta_g) over the bin's pair midpoints (weights w_i w_j) */
+  double* b_pg;    /* [P] num / den (eq. bpg_final); NaN for an empty bin */
+  double* q_eff;   /* [P] eq. Qeff_notsq with xi(d_p) = xi_ss and xi(d_w) below */
+  double* den;     /* [1] weighted mean of (W * delta_g) over the galaxies (weights w_j) */
+  double* xi_dw;   /* [1] eq. xi_dw: sum_r W C_gg^2 / sum_r W C_gg over the mesh offsets */
+} pg_smooth_result;
+
+/* The paper's own estimator (Sec. 2.1 eq. bpg_final) with the smooth W of
+ * Sec. 3.6: the galaxy overdensity is assigned to the plan's mesh (its NGP /
+ * CIC / TSC choice), convolved once with W by FFT (G = W * delta_g, k = 0
+ * removed), and G is interpolated with the same assignment weights at every
+ * pair midpoint and every galaxy. For each (s, mu) pair bin of the plan,
+ * b_pg is the ratio of the weighted means of G over the bin's pairs and over
+ * the galaxies (the mean times the volume is the sum divided by the number
+ * density), so all pair bins cost O(1) FFTs. xi(d_w) is eq. xi_dw with the
+ * measured galaxy auto-correlation C_gg; Q_eff is eq. Qeff_notsq. The plan's
+ * correlation bins are not used. Inputs as pg_forward (device positions,
+ * optional velocities and weights); W's spectrum is computed on the first
+ * call and kept in the plan while *w stays the same. Errors:
+ * PG_ERR_INVALID_ARG (NULL plan, parameters, outputs or positions, sigma
+ * <= 0, r_cut < 0, non-finite values, RSD without velocities),
+ * PG_ERR_UNSUPPORTED, PG_ERR_OOM, PG_ERR_CUDA, PG_ERR_TIMEOUT. Synchronises
+ * the stream. A pg_backward after this call returns PG_ERR_INVALID_ARG. */
+pg_status pg_forward_smooth(pg_plan* plan, const pg_smooth_params* w, int64_t n_gal, const double* d_pos,
+                            const float* d_vel, const float* d_w, pg_smooth_result* host_out,
+                            void* stream);
+
 /* Adjoint of the last successful pg_forward / pg_forward_host call on this
  * plan (same catalogue, still held in the plan's buffers): with the upstream
  * gradients in *grad_out (HOST arrays in the pg_result layout; the fields
@@ -290,6 +335,7 @@ enum {
   PG_FAM_ADJ_X_C2R,       /* adjoint: x C2R of the pair lines */
   PG_FAM_ADJ_GATHER,      /* adjoint: interpolation at the pairs, chain to w_i */
   PG_FAM_ADJ_GALAXY,      /* adjoint: galaxy side (inverse of A, gather, final) */
+  PG_FAM_SMOOTH,          /* smooth-W estimator: W spectrum, convolutions, interpolation, sums */
   PG_N_FAMILIES
 };
 

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <limits>
 #include <memory>
 #include <new>
 #include <vector>
@@ -133,6 +134,11 @@ struct pg_plan {
   DevBuf &line_z, &wlines, &Xs, &As, &Xw, &cggw;
   DevBuf psi, psj, cell_bin, cell_agg, wl_idx, wl_tot, wl_base, wl_y;
   DevBuf adjb, gout, gp, gj, part;
+  // smooth-W estimator: W's spectrum (cached for wk_key), a spectrum of
+  // scratch, bin offsets, sums, partial sums and outputs
+  DevBuf Wk, Gs, sm_off, sm_sums, sm_part, sm_out;
+  SmoothW wk_key{};
+  bool wk_valid = false;
   // state of the last successful forward call, which pg_backward differentiates
   bool fwd_ok = false, last_has_w = false;
   int64_t last_n = 0;
@@ -167,7 +173,7 @@ const char* kFamNames[PG_N_FAMILIES] = {"positions", "cells", "pairs", "deposit"
                                         "fft_y_fwd", "fft_z_fwd", "fft_z_corr", "fft_y_inv",
                                         "fft_x_c2r", "bin", "ratios", "adj_ratios",
                                         "adj_window", "adj_z", "adj_y_inv",
-                                        "adj_x_c2r", "adj_gather", "adj_galaxy"};
+                                        "adj_x_c2r", "adj_gather", "adj_galaxy", "smooth"};
 
 // Times the launches issued inside its scope (one kernel family) with a pair
 // of CUDA events on the call's stream, and books the family's algorithmic
@@ -951,6 +957,132 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
                           gw, wbar, s);
 }
 
+// The smooth-W estimator (Sec. 2.1 eq. bpg_final with eq. weighting): one
+// convolution G = W * delta_g on the mesh, G at every pair midpoint and
+// galaxy, weighted means per pair bin and over the galaxies, xi(d_w) from
+// the measured C_gg (eq. xi_dw), and the ratios (eq. Qeff_notsq).
+template <typename R>
+pg_status smooth_impl(pg_plan* p, const SmoothW& wp, int64_t n, const double* d_pos, const float* d_vel,
+                      const float* d_w, pg_smooth_result* out, cudaStream_t s) {
+  using C = typename CT<R>::C;
+  std::vector<unsigned long long> hdd;
+  int64_t np = 0;
+  int nonfinite = 0;
+  p->fwd_ok = false;
+  prof_begin(p);
+  const long long launches0 = launch_counter().load();
+  PG_TRY(positions_and_pairs(p, n, d_pos, d_vel, d_w, hdd, &np, &nonfinite, s));
+  if (nonfinite) return PG_ERR_INVALID_ARG;
+  const int N = p->N, P = p->nPB;
+  const int64_t NN = (int64_t)N * N;
+  size_t* t = &p->total;
+  const double cs = (double)sizeof(C), rs = (double)sizeof(R), spec = (double)NN * p->M1 * cs,
+               real_b = (double)NN * N * rs;
+  PG_TRY(p->Gs.ensure(sizeof(C) * NN * p->P, t));
+  PG_TRY(p->Wk.ensure(sizeof(C) * NN * p->P, t));
+  PG_TRY(p->sm_off.ensure(sizeof(int64_t) * (P + 3), t));
+  PG_TRY(p->sm_sums.ensure(sizeof(double) * (2 * P + 4), t));
+  PG_TRY(p->sm_part.ensure(sizeof(double) * 2 * wc_partials(), t));
+  PG_TRY(p->sm_out.ensure(sizeof(double) * (4 * P + 2), t));
+  PG_TRY(p->gp.ensure(sizeof(double) * std::max<int64_t>(np, 1), t));
+  PG_TRY(p->gj.ensure(sizeof(double) * std::max<int64_t>(n, 1), t));
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  for (int b = 0; b < P; ++b) out->dd[b] = (int64_t)hdd[b];
+  if (n == 0) {
+    for (int b = 0; b < P; ++b) out->xi_ss[b] = out->num[b] = out->b_pg[b] = out->q_eff[b] = nan;
+    out->den[0] = out->xi_dw[0] = nan;
+    p->last_launches = launch_counter().load() - launches0;
+    if (p->prof_on) prof_end(p);
+    return PG_OK;
+  }
+  const double* gw = nullptr;
+  if (d_w) {
+    PG_TRY(launch_widen_f32(n, d_w, p->gw.as<double>(), s));
+    gw = p->gw.as<double>();
+  }
+  const Lay L = lay_plan(N, p->P), Z = lay_zy(N, p->P);
+  const C* tw = p->tw.as<C>();
+  R* real = reinterpret_cast<R*>(p->S.p);   // shared scratch: at least one spectrum, so N^3 reals
+  C* Gs = p->Gs.as<C>();
+  C* Wk = p->Wk.as<C>();
+  PG_TRY((galaxy_pass<R>(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, false, s)));
+  {
+    ProfScope ps(p, PG_FAM_SMOOTH, s, 9.0 * spec + 2.0 * real_b);
+    if (!p->wk_valid || memcmp(&p->wk_key, &wp, sizeof(SmoothW)) != 0) {
+      // W's spectrum: W on the mesh offsets, then the dense R2C passes
+      PG_TRY(launch_w_mesh<R>(N, p->dx, wp, real, s));
+      PG_TRY(FftPasses<R>::x_r2c_dense(N, real, Gs, p->P, tw, s));
+      PG_TRY(FftPasses<R>::y_fwd(N, 1, Gs, p->P, nullptr, nullptr, nullptr, nullptr, Wk, 0, L, tw, s));
+      PG_TRY(FftPasses<R>::z_fwd(N, Wk, L, tw, s));
+      p->wk_key = wp;
+      p->wk_valid = true;
+    }
+    // G = W * delta_g = N^-3 IDFT[W~ F_g] (k = 0 zeroed), dense [z][y][x]
+    PG_TRY(launch_spec_mul<R>(N, p->P, L, Wk, p->Fg.as<C>(), 0, 1.0 / ((double)NN * N), Gs, s));
+    PG_TRY(FftPasses<R>::z_inv_full(N, Gs, Z, tw, s));
+    PG_TRY(FftPasses<R>::y_inv_full(N, Gs, Z, tw, s));
+    PG_TRY(FftPasses<R>::x_c2r_full(N, Gs, p->P, real, tw, s));
+    // G at the galaxies and at the pair midpoints (grouped by bin)
+    const DepGeom geo{N, p->dx, p->prm.assign};
+    PG_TRY(launch_interp<R>(geo, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), real,
+                            p->gj.as<double>(), s));
+    PG_TRY(launch_interp<R>(geo, np, p->px.as<double>(), p->py.as<double>(), p->pz.as<double>(), real,
+                            p->gp.as<double>(), s));
+    std::vector<int64_t> off(P + 3, 0);
+    for (int b = 0; b < P; ++b) off[b + 1] = off[b] + (int64_t)hdd[b];
+    off[P + 1] = 0;
+    off[P + 2] = n;
+    int64_t* doff = p->sm_off.as<int64_t>();
+    PG_TRY(cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (P + 3), cudaMemcpyHostToDevice, s));
+    double* sums = p->sm_sums.as<double>();
+    PG_TRY(launch_seg_sums(P, doff, p->gp.as<double>(), p->pw.as<double>(), sums, s));
+    PG_TRY(launch_seg_sums(1, doff + P + 1, p->gj.as<double>(), gw, sums + 2 * P, s));
+    // C_gg = N^-6 IDFT[|F_g|^2] (k = 0 zeroed), then sum W C^2 and sum W C
+    PG_TRY(launch_spec_mul<R>(N, p->P, L, nullptr, p->Fg.as<C>(), 1, 1.0 / ((double)NN * NN * NN), Gs, s));
+    PG_TRY(FftPasses<R>::z_inv_full(N, Gs, Z, tw, s));
+    PG_TRY(FftPasses<R>::y_inv_full(N, Gs, Z, tw, s));
+    PG_TRY(FftPasses<R>::x_c2r_full(N, Gs, p->P, real, tw, s));
+    PG_TRY(launch_wc_sums<R>(N, p->dx, wp, real, p->sm_part.as<double>(), sums + 2 * P + 2, s));
+    double* o = p->sm_out.as<double>();
+    SmoothArgs a{};
+    a.P = P;
+    a.n_mu = p->prm.n_mu;
+    a.s_edges = p->s_edges_d.as<double>();
+    a.L = p->prm.box_L;
+    a.ddq = p->ddq.as<unsigned long long>();
+    a.wsum = p->wsum.as<double>();
+    a.pairs = sums;
+    a.gal = sums + 2 * P;
+    a.wc = sums + 2 * P + 2;
+    a.xi_ss = o;
+    a.num = o + P;
+    a.b_pg = o + 2 * P;
+    a.q_eff = o + 3 * P;
+    a.den = o + 4 * P;
+    a.xi_dw = o + 4 * P + 1;
+    PG_TRY(launch_smooth_final(a, s));
+  }
+  std::vector<double> h(4 * P + 2);
+  PG_TRY(cudaMemcpyAsync(h.data(), p->sm_out.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  int32_t herr = 0;
+  PG_TRY(cudaMemcpyAsync(&herr, p->flag.as<int32_t>() + 1, 4, cudaMemcpyDeviceToHost, s));
+  PG_TRY(cudaStreamSynchronize(s));
+  if (herr) return PG_ERR_TIMEOUT;
+  for (int b = 0; b < P; ++b) {
+    out->xi_ss[b] = h[b];
+    out->num[b] = h[P + b];
+    out->b_pg[b] = h[2 * P + b];
+    out->q_eff[b] = h[3 * P + b];
+  }
+  out->den[0] = h[4 * P];
+  out->xi_dw[0] = h[4 * P + 1];
+  p->last_launches = launch_counter().load() - launches0;
+  if (p->prof_on) prof_end(p);
+  else
+    for (int f = 0; f < PG_N_FAMILIES; ++f) p->stats[f].bytes = p->fam_bytes[f];
+  return PG_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1094,7 +1226,8 @@ void pg_plan_destroy(pg_plan* p) {
                    &p->umy, &p->umz, &p->uwp, &p->pbin, &p->px, &p->py, &p->pz, &p->pw,
                    &p->bcursor, &p->sums_pg, &p->sums_gg, &p->pg_valid, &p->out, &p->psi,
                    &p->psj, &p->cell_bin, &p->cell_agg, &p->wl_idx, &p->wl_tot, &p->wl_base,
-                   &p->wl_y, &p->adjb, &p->gout, &p->gp, &p->gj, &p->part};
+                   &p->wl_y, &p->adjb, &p->gout, &p->gp, &p->gj, &p->part, &p->Wk, &p->Gs,
+                   &p->sm_off, &p->sm_sums, &p->sm_part, &p->sm_out};
   for (DevBuf* b : all) b->release(&p->total);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   cudaSetDevice(cur);
@@ -1196,6 +1329,23 @@ pg_status pg_forward(pg_plan* p, int64_t n, const double* d_pos, const float* d_
   PG_TRY(ensure_shared(p));
   return p->prm.precision ? forward_impl<double>(p, n, d_pos, d_vel, d_w, out, s)
                           : forward_impl<float>(p, n, d_pos, d_vel, d_w, out, s);
+}
+
+pg_status pg_forward_smooth(pg_plan* p, const pg_smooth_params* w, int64_t n, const double* d_pos,
+                            const float* d_vel, const float* d_w, pg_smooth_result* out, void* stream) {
+  if (!p || !w || !out || n < 0 || (n > 0 && !d_pos)) return PG_ERR_INVALID_ARG;
+  if (!out->dd || !out->xi_ss || !out->num || !out->b_pg || !out->q_eff || !out->den || !out->xi_dw)
+    return PG_ERR_INVALID_ARG;
+  if (!(w->sigma > 0.0) || !isfinite(w->sigma) || !isfinite(w->r_s) || !isfinite(w->s0) ||
+      !(w->r_cut >= 0.0) || !isfinite(w->r_cut))
+    return PG_ERR_INVALID_ARG;
+  if (p->prm.rsd_factor != 0.0 && n > 0 && !d_vel) return PG_ERR_INVALID_ARG;
+  if (n > INT32_MAX / 2) return PG_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PG_TRY(ensure_shared(p));
+  const SmoothW wp{w->sigma, w->r_s, w->s0, w->r_cut};
+  return p->prm.precision ? smooth_impl<double>(p, wp, n, d_pos, d_vel, d_w, out, s)
+                          : smooth_impl<float>(p, wp, n, d_pos, d_vel, d_w, out, s);
 }
 
 pg_status pg_forward_host(pg_plan* p, int64_t n, const double* h_pos, const float* h_vel,

@@ -271,6 +271,46 @@ struct FftPasses {
                                  cudaStream_t s);
 };
 
+// ---- smooth-W estimator (pg_smooth.cu) ----------------------------------------
+// Parameters of the Gauss-sigmoid W of eq. weighting (Mpc/h, h/Mpc).
+struct SmoothW {
+  double sigma, r_s, s0, r_cut;
+};
+// Inputs and outputs of the final ratios (all device pointers).
+struct SmoothArgs {
+  int P, n_mu;
+  const double* s_edges;
+  double L;
+  const unsigned long long* ddq;   // [P] Q32.32 weighted pair counts
+  const double* wsum;              // [2] sum w, sum w^2
+  const double* pairs;             // [P][2] sum w g, sum w over the bin's pairs
+  const double* gal;               // [2] the same over the galaxies
+  const double* wc;                // [2] sum W C^2, sum W C over the mesh offsets
+  double *xi_ss, *num, *b_pg, *q_eff, *den, *xi_dw;
+};
+// W on every mesh offset (minimum image), real [z][y][x], line of sight z.
+template <typename R>
+cudaError_t launch_w_mesh(int N, double dx, const SmoothW& p, R* out, cudaStream_t s);
+// out[kz][ky][kx] (pitch P) = scale * A * B (mode 0) or scale * |B|^2 (mode
+// 1), k = 0 zeroed; A, B in layout L.
+template <typename R>
+cudaError_t launch_spec_mul(int N, int P, Lay L, const typename CT<R>::C* A, const typename CT<R>::C* B,
+                            int mode, double scale, typename CT<R>::C* out, cudaStream_t s);
+// g[k] = dense real field G [z][y][x] at the points, assignment weights.
+template <typename R>
+cudaError_t launch_interp(const DepGeom& geo, int64_t n, const double* x, const double* y, const double* z,
+                          const R* G, double* g, cudaStream_t s);
+// Per-segment sums of w g and w (w null: 1), one CTA per segment.
+cudaError_t launch_seg_sums(int nseg, const int64_t* off, const double* g, const double* w, double* sums,
+                            cudaStream_t s);
+// out[0] = sum W C^2, out[1] = sum W C over the mesh offsets; part holds
+// 2 * wc_partials() doubles.
+int wc_partials();
+template <typename R>
+cudaError_t launch_wc_sums(int N, double dx, const SmoothW& p, const R* Cm, double* part, double* out,
+                           cudaStream_t s);
+cudaError_t launch_smooth_final(const SmoothArgs& a, cudaStream_t s);
+
 // ---- binning and ratios (pg_bin.cu) -----------------------------------------
 template <typename R>
 cudaError_t launch_bin_sums(int nb, int n_lists, const R* Cwin, int64_t Cwin_stride,

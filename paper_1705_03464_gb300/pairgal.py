@@ -47,6 +47,17 @@ _RESULT_FIELDS = [
 ]
 
 
+class pg_smooth_params(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("r_s", C.c_double), ("s0", C.c_double), ("r_cut", C.c_double)]
+
+
+class pg_smooth_result(C.Structure):
+    _fields_ = [("dd", C.POINTER(C.c_int64)), ("xi_ss", C.POINTER(C.c_double)),
+                ("num", C.POINTER(C.c_double)), ("b_pg", C.POINTER(C.c_double)),
+                ("q_eff", C.POINTER(C.c_double)), ("den", C.POINTER(C.c_double)),
+                ("xi_dw", C.POINTER(C.c_double))]
+
+
 class pg_mock(C.Structure):
     _fields_ = [("params", pg_params), ("n_gal", C.c_int64), ("h_pos", C.c_void_p),
                 ("h_vel", C.c_void_p), ("h_w", C.c_void_p), ("out", C.c_void_p)]
@@ -63,7 +74,7 @@ class pg_kernel_stat(C.Structure):
                 ("bytes", C.c_double)]
 
 
-PG_N_FAMILIES = 19
+PG_N_FAMILIES = 20
 
 
 class pg_result(C.Structure):
@@ -82,6 +93,7 @@ def _load():
         "pg_plan_create_shared": (C.c_int, [C.POINTER(pg_params), vp, C.POINTER(vp)]),
         "pg_run_batch": (C.c_int, [vp, i32, vp, vp, vp]),
         "pg_selftest_wait": (C.c_int, [vp, C.c_double, vp]),
+        "pg_forward_smooth": (C.c_int, [vp, vp, i64, vp, vp, vp, vp, vp]),
         "pg_autotune": (C.c_int, [C.POINTER(pg_params), i64, vp, vp, vp, vp, i32, vp, vp, vp]),
         "pg_plan_destroy": (None, [vp]),
         "pg_plan_reserve": (C.c_int, [vp, i64, i64]),
@@ -536,3 +548,28 @@ def pg_selftest_wait(plan: Plan, limit_ms: float, stream=None) -> int:
     """Failure-detection test of the bounded device waits: returns the status
     (PG_ERR_TIMEOUT when the wait gave up, the expected outcome)."""
     return int(_lib.pg_selftest_wait(plan.handle, float(limit_ms), _stream(stream)))
+
+
+# Table tab:weightings: (sigma, r_s, s0, r_cut) for d_p,max = 10 and 30 Mpc/h
+W_DP10 = (30.0, 20.0, 0.8, 10.0)
+W_DP30 = (50.0, 35.0, 0.5, 20.0)
+
+
+def pg_forward_smooth(plan: Plan, w_params, pos, vel=None, w=None, stream=None):
+    """The paper's own smooth-W estimator (pg_forward_smooth) on device
+    tensors; w_params = (sigma, r_s, s0, r_cut). Returns host numpy outputs
+    per (s, mu) pair bin plus den and xi_dw."""
+    n = 0 if pos is None else int(pos.shape[0])
+    P = plan.P
+    arrs = {"dd": np.zeros(P, np.int64), "xi_ss": np.full(P, np.nan), "num": np.full(P, np.nan),
+            "b_pg": np.full(P, np.nan), "q_eff": np.full(P, np.nan), "den": np.full(1, np.nan),
+            "xi_dw": np.full(1, np.nan)}
+    res = pg_smooth_result(*[arrs[k].ctypes.data_as(C.POINTER(C.c_int64 if k == "dd" else C.c_double))
+                             for k, _ in pg_smooth_result._fields_])
+    prm = pg_smooth_params(*[float(v) for v in w_params])
+    _check(_lib.pg_forward_smooth(plan.handle, C.byref(prm), n, _ptr(pos), _ptr(vel), _ptr(w),
+                                  C.byref(res), _stream(stream)), "pg_forward_smooth")
+    out = dict(arrs)
+    out["den"] = float(arrs["den"][0])
+    out["xi_dw"] = float(arrs["xi_dw"][0])
+    return out
