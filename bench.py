@@ -44,6 +44,8 @@ def parse_args():
                     help="timed forward+adjoint steps (0 = skip)")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed steps of the plain per-bin FP64 form (0 = skip)")
+    ap.add_argument("--smooth-steps", type=int, default=3,
+                    help="timed steps of the paper's smooth-W estimator, TSC (0 = skip)")
     ap.add_argument("--many-mocks", type=int, default=64,
                     help="uneven mocks through the batch driver (0 = skip)")
     ap.add_argument("--many-mocks-fp64", type=int, default=3,
@@ -458,6 +460,40 @@ def main():
                  "speedup_of_fp32_batched": plain_ms / value,
                  "fp32_vs_fp64_max_rel": {k: rel(k) for k in ("xi_gg", "xi_pg", "b_pg", "q_eff", "b_pg_agg")}}
 
+    # the paper's own estimator (eq. bpg_final with the Gauss-sigmoid W of
+    # Table tab:weightings, d_p,max = 10 Mpc/h) with TSC assignment, on the same
+    # catalogue: all pair bins from one convolution
+    smooth = None
+    if args.smooth_steps > 0:
+        sp = pg.Plan.of(wl, assign=2, share_with=plan)
+        r = pg.pg_forward_smooth(sp, pg.W_DP10, pos, vel, stream=stream)   # warm-up, W's spectrum
+        pg.pg_forward_smooth(sp, pg.W_DP10, pos, vel, stream=stream)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for _ in range(args.smooth_steps):
+            r = pg.pg_forward_smooth(sp, pg.W_DP10, pos, vel, stream=stream)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        ts = max_over_ranks(d0.elapsed_time(d1), dist, torch, "cuda")
+        sp.set_profiling(True)
+        pg.pg_forward_smooth(sp, pg.W_DP10, pos, vel, stream=stream)
+        sfams, sl = sp.last_stats()
+        sp.set_profiling(False)
+        b = np.asarray(r["b_pg"])
+        smooth = {"ms_per_mock": per_mock(ts / args.smooth_steps, world), "steps": args.smooth_steps,
+                  "assign": "tsc", "w": {"sigma": 30.0, "r_s": 20.0, "s0": 0.8, "r_cut": 10.0},
+                  "xi_dw": r["xi_dw"], "b_pg_range": [float(np.nanmin(b)), float(np.nanmax(b))],
+                  "launches": sl,
+                  "kernels": {k: {"ms": v["ms"],
+                                  "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                              for k, v in sfams.items() if v["launches"] > 0}}
+        sp.close()
+        del sp
+
     many = None
     if args.many_mocks > 0 and rank == 0 and world == 1:
         del plan
@@ -496,7 +532,7 @@ def main():
                        "precision": "fp32 FFT passes, fp64 positions/pairs/reductions/ratios",
                        "l2": "no flush: each step streams ~70 GB of spectra, far above the 129 MB L2",
                        "mocks_per_step": world},
-            "fwd_adj": fwd_adj, "plain_fp64": plain, "many_mocks": many,
+            "fwd_adj": fwd_adj, "plain_fp64": plain, "smooth_w": smooth, "many_mocks": many,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks, "kernels": breakdown,
         }

@@ -17,29 +17,38 @@ constexpr int kPartials = 2048;   // blocks of the W-weighted mesh reduction
 
 // eq. weighting with normalisation 1: W = 0 inside the line-of-sight cylinder
 // r_perp < r_cut, else sigmoid(s0 (r_perp - r_s)) exp(-(r_perp^2 + r_par^2)/(2 sigma^2)).
-__device__ __forceinline__ double w_of(const SmoothW& p, double r_perp, double r_par) {
-  if (!(r_perp >= p.r_cut)) return 0.0;
-  const double sig = 1.0 / (1.0 + exp(-p.s0 * (r_perp - p.r_s)));
-  return sig * exp(-0.5 * (r_perp * r_perp + r_par * r_par) / (p.sigma * p.sigma));
+// Evaluated in the plan's precision R: W only weights the mesh offsets, and
+// FP64 exp at every one of N^3 offsets would cost more than the FFTs.
+__device__ __forceinline__ float ex(float v) { return expf(v); }
+__device__ __forceinline__ double ex(double v) { return exp(v); }
+__device__ __forceinline__ float sq(float v) { return sqrtf(v); }
+__device__ __forceinline__ double sq(double v) { return sqrt(v); }
+
+template <typename R>
+__device__ __forceinline__ R w_of(const SmoothW& p, R r_perp, R r_par) {
+  const R sig = (R)1 / ((R)1 + ex(-(R)p.s0 * (r_perp - (R)p.r_s)));
+  return sig * ex((R)-0.5 * (r_perp * r_perp + r_par * r_par) / (R)(p.sigma * p.sigma));
 }
 
-// Signed minimum-image offset of mesh index i (i <= N/2 positive).
-__device__ __forceinline__ double offset_of(int i, int N, double dx) {
-  return (double)(i <= N / 2 ? i : i - N) * dx;
-}
-
-// W at the mesh offset of node t of a [z][y][x] mesh (line of sight = z).
-__device__ __forceinline__ double w_at(int64_t t, int N, double dx, const SmoothW& p) {
+// W at the mesh offset of node t of a [z][y][x] mesh (line of sight = z);
+// offsets are the signed minimum images i (i <= N/2) or i - N times dx. The
+// cylinder r_perp < r_cut is decided in FP64 on the squared offset.
+template <typename R>
+__device__ __forceinline__ R w_at(int64_t t, int N, double dx, const SmoothW& p) {
   const int x = (int)(t % N), y = (int)((t / N) % N), z = (int)(t / ((int64_t)N * N));
-  const double rx = offset_of(x, N, dx), ry = offset_of(y, N, dx), rz = offset_of(z, N, dx);
-  return w_of(p, sqrt(rx * rx + ry * ry), fabs(rz));
+  const double rx = (double)(x <= N / 2 ? x : x - N) * dx;
+  const double ry = (double)(y <= N / 2 ? y : y - N) * dx;
+  const double rz = (double)(z <= N / 2 ? z : z - N) * dx;
+  const double rp2 = rx * rx + ry * ry;
+  if (!(rp2 >= p.r_cut * p.r_cut)) return (R)0;
+  return w_of<R>(p, sq((R)rp2), (R)fabs(rz));
 }
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_w_mesh(int N, double dx, SmoothW p, R* __restrict__ out) {
   const int64_t n3 = (int64_t)N * N * N;
   for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < n3; t += (int64_t)gridDim.x * kThreads)
-    out[t] = (R)w_at(t, N, dx, p);
+    out[t] = w_at<R>(t, N, dx, p);
 }
 
 // out[kz][ky][kx] (pitch P) = scale * A * B (mode 0) or scale * |B|^2
@@ -136,7 +145,7 @@ k_wc_partial(int N, double dx, SmoothW p, const R* __restrict__ Cm, double* __re
   const int64_t n3 = (int64_t)N * N * N;
   double a = 0.0, b = 0.0;
   for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < n3; t += (int64_t)gridDim.x * kThreads) {
-    const double wv = w_at(t, N, dx, p);
+    const double wv = (double)w_at<R>(t, N, dx, p);
     if (wv != 0.0) {
       const double c = (double)Cm[t];
       a += wv * c * c;

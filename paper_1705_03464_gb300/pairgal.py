@@ -234,6 +234,7 @@ class Plan(Problem):
         if getattr(self, "handle", None):
             _lib.pg_plan_destroy(self.handle)
             self.handle = None
+        self._donor = None
 
     def __del__(self):
         try:
