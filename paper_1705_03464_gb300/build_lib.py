@@ -23,9 +23,10 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 NO_FMA = {"pg_pairs.cu", "pg_mesh.cu"}
-SOURCES = ["pg_api.cu", "pg_pairs.cu", "pg_mesh.cu", "pg_scan.cu", "pg_bin.cu", "pg_tma.cu",
-           "pg_noalloc.cu", "pg_adjoint.cu", "pg_batch.cu", "pg_smooth.cu", "pg_fft_f32.cu",
-           "pg_fft_f64.cu"]
+# the longest compiles first, so the parallel build ends with the short ones
+SOURCES = ["pg_fft_z_f32.cu", "pg_fft_f32.cu", "pg_fft_z_f64.cu", "pg_fft_f64.cu", "pg_api.cu",
+           "pg_pairs.cu", "pg_mesh.cu", "pg_scan.cu", "pg_bin.cu", "pg_tma.cu", "pg_noalloc.cu",
+           "pg_adjoint.cu", "pg_batch.cu", "pg_smooth.cu"]
 
 
 def _nvcc():

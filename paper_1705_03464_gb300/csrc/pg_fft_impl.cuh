@@ -31,13 +31,13 @@ static cudaError_t persistent_grid(K kern, int threads, size_t smem, int64_t ite
 
 // Tensor map over 8-byte elements of nb spectra of the plan layout L (each
 // N*N*P complex), dimensions (kx, y mod K, z, y / K, mesh) with K = 2^L.ks,
-// box (one kx tile, then either bz z rows of one y (by = 1) or by y rows of
-// one z (bz = 1)).
-template <typename R>
+// box (one kx tile of B columns, then either bz z rows of one y (by = 1) or
+// by y rows of one z (bz = 1)).
+template <typename R, int B = ZCols<R>::B>
 static bool spec_map(CUtensorMap* m, const void* base, int N, int P, Lay L, int nb, uint32_t bz,
                      uint32_t by) {
   using C = typename CT<R>::C;
-  constexpr int B = ZCols<R>::B, E = (int)(sizeof(C) / 8);
+  constexpr int E = (int)(sizeof(C) / 8);
   const int K = 1 << L.ks;
   if (K > N || N % K != 0 || (by > 1 && by % K != 0)) return false;
   const uint64_t dims[5] = {(uint64_t)P * E, (uint64_t)K, (uint64_t)N, (uint64_t)(N / K), (uint64_t)nb};
@@ -102,11 +102,12 @@ cudaError_t FftPasses<R>::y_fwd(int N, int nb, const C* spec, int P, const int32
   if (nb <= 0) return cudaSuccess;
   constexpr int B = fft::Cols<R>::B;
   PG_DISPATCH_N(N, {
-    using CP = fft::ColPass<C, NN, B>;
-    auto k = fft::k_y_fwd<C, NN, B>;
-    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
-    dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN, nb);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(spec, P, idx, seg_total, line_base, line_y, S, S_stride, L, tw);
+    using Y = fft::YFwd<C, NN, B>;
+    auto k = fft::k_y_fwd_p<C, NN, B>;
+    PG_CUDA_TRY(set_smem(k, Y::smem_bytes()));
+    unsigned grid = 0;
+    PG_CUDA_TRY(fft::persistent_grid(k, Y::THREADS, Y::smem_bytes(), cdiv(NN / 2 + 1, B) * (int64_t)NN * nb, &grid));
+    k<<<grid, Y::THREADS, Y::smem_bytes(), s>>>(spec, P, nb, idx, seg_total, line_base, line_y, S, S_stride, L, tw);
   });
   return launched();
 }
@@ -120,27 +121,6 @@ cudaError_t FftPasses<R>::z_fwd(int N, C* S, Lay L, const C* tw, cudaStream_t s)
     PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
     dim3 g((unsigned)cdiv(NN / 2 + 1, B), NN);
     k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(S, L, tw);
-  });
-  return launched();
-}
-
-template <typename R>
-cudaError_t FftPasses<R>::z_corr(int N, int nb, const C* S, const C* Fg, bool gg, int w, C* Wz,
-                                 int64_t Wz_stride, int P, Lay L, const C* tw, int* err, cudaStream_t s) {
-  if (nb <= 0) return cudaSuccess;
-  constexpr int B = fft::ZCols<R>::B;
-  const uint32_t zb = N < 256 ? (uint32_t)N : 256u;
-  CUtensorMap mF, mS;
-  if (!fft::spec_map<R>(&mF, Fg, N, P, L, 1, zb, 1) ||
-      !fft::spec_map<R>(&mS, gg ? (const void*)Fg : (const void*)S, N, P, L, gg ? 1 : nb, zb, 1))
-    return cudaErrorInvalidValue;
-  PG_DISPATCH_N(N, {
-    using Z = fft::ZCorr<C, NN, B>;
-    auto k = fft::k_z_corr_tma<C, NN, B>;
-    PG_CUDA_TRY(set_smem(k, Z::smem_bytes()));
-    unsigned grid = 0;
-    PG_CUDA_TRY(fft::persistent_grid(k, Z::THREADS, Z::smem_bytes(), cdiv(NN / 2 + 1, B) * (int64_t)NN, &grid));
-    k<<<grid, Z::THREADS, Z::smem_bytes(), s>>>(mS, mF, nb, gg ? 1 : 0, w, Wz, Wz_stride, P, tw, err);
   });
   return launched();
 }

@@ -88,8 +88,44 @@ __host__ __device__ __forceinline__ C tw32_mul(C v) {
   }
 }
 
-// One radix-2 stage (butterflies of span LEN) of the in-register DFT.
-template <typename C, int RL, bool INV, int LEN>
+__host__ __device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+__host__ __device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+
+// One radix-2 butterfly u, v -> u + t, u - t with t = v * W_32^J (conjugated
+// for the inverse), J known at compile time; TOP / BOT select the outputs that
+// are needed. A general twiddle costs four fused multiply-adds for u + t and
+// two more for u - t = 2u - (u + t): six instructions instead of the eight of
+// a complex product followed by a sum and a difference.
+template <int J, bool INV, bool TOP, bool BOT, typename C>
+__host__ __device__ __forceinline__ void bfly(C& u, C& v) {
+  using T = typename Real<C>::T;
+  constexpr int j = J & 31;
+  constexpr bool triv = j == 0 || j == 8 || j == 16 || j == 24;
+  if constexpr (triv) {
+    const C t = tw32_mul<j, INV>(v);
+    const C x = cadd(u, t), y = csub(u, t);
+    if constexpr (TOP) u = x;
+    if constexpr (BOT) v = y;
+  } else {
+    C w = w32<C>(j);
+    if (INV) w.y = -w.y;
+    if constexpr (TOP) {
+      const C x = make_c<C>(fmadd(w.x, v.x, fmadd(-w.y, v.y, u.x)), fmadd(w.x, v.y, fmadd(w.y, v.x, u.y)));
+      if constexpr (BOT) v = make_c<C>(fmadd((T)2, u.x, -x.x), fmadd((T)2, u.y, -x.y));
+      u = x;
+    } else if constexpr (BOT) {
+      v = make_c<C>(fmadd(-w.x, v.x, fmadd(w.y, v.y, u.x)), fmadd(-w.x, v.y, fmadd(-w.y, v.x, u.y)));
+    }
+  }
+}
+
+// One radix-2 stage (butterflies of span LEN) of the in-register DFT, then
+// the later stages. K prunes the outputs: only X[k] for k < K or k >= RL - K
+// are wanted (all when 2K >= RL). A decimation-in-time stage of span LEN then
+// needs, within each group of LEN, exactly its outputs k < K and k >= LEN - K
+// (the same rule one stage down), so unneeded halves of butterflies are
+// dropped at compile time. Unwanted outputs are left undefined.
+template <typename C, int RL, bool INV, int LEN, int K>
 __host__ __device__ __forceinline__ void dft_stage(C (&a)[RL]) {
   if constexpr (LEN <= RL) {
     constexpr int half = LEN / 2;
@@ -97,19 +133,20 @@ __host__ __device__ __forceinline__ void dft_stage(C (&a)[RL]) {
       constexpr int i = decltype(ii)::value * LEN;
       sfor<0, half>([&](auto kk) {
         constexpr int k = decltype(kk)::value;
-        C u = a[i + k];
-        C v = tw32_mul<k * (32 / LEN), INV>(a[i + k + half]);
-        a[i + k] = cadd(u, v);
-        a[i + k + half] = csub(u, v);
+        constexpr bool all = 2 * K >= LEN;
+        constexpr bool top = all || k < K;
+        constexpr bool bot = all || k + half >= LEN - K;
+        if constexpr (top || bot) bfly<k * (32 / LEN), INV, top, bot>(a[i + k], a[i + k + half]);
       });
     });
-    dft_stage<C, RL, INV, LEN * 2>(a);
+    dft_stage<C, RL, INV, LEN * 2, K>(a);
   }
 }
 
 // In-register DFT of length RL (1..32), forward (exp(-i...)) or inverse:
-// bit-reversal permutation, then radix-2 decimation-in-time stages.
-template <typename C, int RL, bool INV>
+// bit-reversal permutation, then radix-2 decimation-in-time stages. With
+// K < RL / 2 only the outputs k < K and k >= RL - K are computed.
+template <typename C, int RL, bool INV, int K = RL>
 __host__ __device__ __forceinline__ void reg_dft(C (&a)[RL]) {
   if constexpr (RL > 1) {
     constexpr int bits = clog2(RL);
@@ -118,7 +155,7 @@ __host__ __device__ __forceinline__ void reg_dft(C (&a)[RL]) {
       const int j = cbitrev(i, bits);
       if (j > i) { C t = a[i]; a[i] = a[j]; a[j] = t; }
     }
-    dft_stage<C, RL, INV, 2>(a);
+    dft_stage<C, RL, INV, 2, K>(a);
   }
 }
 
@@ -198,12 +235,13 @@ __device__ __forceinline__ void stepA(C* buf, int LD, int c, int k1, C (&a)[N2],
   for (int n2 = 0; n2 < N2; ++n2) buf[prow<X>(n2, k1, N1) * LD + c] = a[n2];
 }
 
-// Step B: task (c, n2) -> out[n1] = x[n2 + N2*n1].
-template <typename C, int N1, int N2, bool INV, int X = 1>
+// Step B: task (c, n2) -> out[n1] = x[n2 + N2*n1]; with K < N1 / 2 only
+// n1 < K and n1 >= N1 - K are computed (see reg_dft).
+template <typename C, int N1, int N2, bool INV, int X = 1, int K = N1>
 __device__ __forceinline__ void stepB(const C* buf, int LD, int c, int n2, C (&a)[N1]) {
 #pragma unroll
   for (int k1 = 0; k1 < N1; ++k1) a[k1] = buf[prow<X>(n2, k1, N1) * LD + c];
-  reg_dft<C, N1, INV>(a);
+  reg_dft<C, N1, INV, K>(a);
 }
 
 template <int N> struct Split {
@@ -319,6 +357,9 @@ template <typename C, int N, int B>
 struct ColPass {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   static constexpr int THREADS = B * N1;
+  // two CTAs per SM (registers capped at 128 for 256 threads): these passes
+  // wait on strided column loads, and a second CTA covers that latency
+  static constexpr int MINB = 2;
   static constexpr size_t smem_bytes() { return sizeof(C) * ((size_t)N * B + N); }
 };
 
@@ -329,55 +370,124 @@ __device__ __forceinline__ void zero_tile(C* buf, int rows) {
   for (int t = threadIdx.x; t < rows * B; t += blockDim.x) buf[t] = z;
 }
 
+// Y pass forward, persistent. A work item is (kx tile, z plane, mesh b), kx
+// tile fastest, so the CTAs running at once gather the same compact lines of
+// one plane. While one item is transformed, the rows of the next are gathered
+// by cp.async into the second buffer (their line numbers were loaded at the
+// start of the item, the plane's line range one item earlier), so the
+// dependent index loads do not stall the pass. Step 2 clears each element it reads, so the rows
+// a sparse plane lacks read as zero the next time the buffer is filled.
+// Sparse path (idx != null): the compact lines of plane z of mesh b are
+// line_base[b] + [idx_b[z][0], idx_b[z+1][0]) with y = line_y[line]; dense
+// path: line z*N + y of one mesh.
 template <typename C, int N, int B>
-__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
-k_y_fwd(const C* __restrict__ spec, int P, const int32_t* __restrict__ idx,
-        const int64_t* __restrict__ seg_total, const int64_t* __restrict__ line_base,
-        const int32_t* __restrict__ line_y, C* __restrict__ S, int64_t S_stride, Lay L,
-        const C* __restrict__ tw) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
-  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
-  using CP = ColPass<C, N, B>;
-  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+struct YFwd {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int THREADS = B * N1;
+  static constexpr int TILE = N * B;
+  static constexpr int RS = THREADS / B;   // rows gathered per round
+  static constexpr int PRE = 4;            // rounds whose line numbers are loaded ahead
+  static constexpr size_t smem_bytes() { return sizeof(C) * (2 * (size_t)TILE + N); }
+};
+
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(YFwd<C, N, B>::THREADS, 1)
+k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__ idx,
+          const int64_t* __restrict__ seg_total, const int64_t* __restrict__ line_base,
+          const int32_t* __restrict__ line_y, C* __restrict__ S, int64_t S_stride, Lay L,
+          const C* __restrict__ tw) {
+  using Y = YFwd<C, N, B>;
+  constexpr int N1 = Y::N1, N2 = Y::N2, TILE = Y::TILE, M1 = N / 2 + 1, RS = Y::RS, PRE = Y::PRE;
   constexpr int XP = xperm<C, N, B>();
-  const int kx0 = blockIdx.x * B;
-  const int z = blockIdx.y;
-  const int b = blockIdx.z;
-  const int ncol = min(B, M1 - kx0);
-  const int c = threadIdx.x % B;
-  if (idx) {
-    const int64_t NN = (int64_t)N * N;
-    const int32_t* ib = idx + (int64_t)b * NN;
-    const int64_t lo = ib[(int64_t)z * N];
-    const int64_t hi = (z + 1 < N) ? ib[(int64_t)(z + 1) * N] : seg_total[b];
-    zero_tile<C, B>(buf, N);
-    __syncthreads();
-    const int64_t base = line_base[b];
-    for (int64_t r = lo + threadIdx.x / B; r < hi; r += blockDim.x / B) {
-      const int64_t l = base + r;
-      const int y = line_y[l];
-      if (c < ncol) buf[y * B + c] = spec[l * P + kx0 + c];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* const tws = reinterpret_cast<C*>(smem_raw);
+  C* const buf0 = tws + N;   // buffers buf0 + k * TILE
+  const int T = (M1 + B - 1) / B;
+  const int64_t n_items = (int64_t)T * N * nb;
+  int64_t item = blockIdx.x;
+  if (item >= n_items) return;   // whole CTA
+  C zc;
+  zc.x = 0; zc.y = 0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
+  for (int i = threadIdx.x; i < 2 * TILE; i += blockDim.x) buf0[i] = zc;
+  const int c = threadIdx.x % B, slot = threadIdx.x / B;
+  struct Item {
+    int kx0, z, b;
+    int64_t lo, hi;   // rows (compact lines, or dense lines) of the item's plane
+  };
+  auto meta = [&](int64_t it, Item& m) {
+    m.kx0 = (int)(it % T) * B;
+    const int64_t r = it / T;
+    m.z = (int)(r % N);
+    m.b = (int)(r / N);
+    if (idx) {
+      const int32_t* ib = idx + (int64_t)m.b * N * N;
+      const int64_t base = line_base[m.b];
+      m.lo = base + ib[(int64_t)m.z * N];
+      m.hi = base + ((m.z + 1 < N) ? (int64_t)ib[(int64_t)(m.z + 1) * N] : seg_total[m.b]);
+    } else {
+      m.lo = (int64_t)m.z * N;
+      m.hi = m.lo + N;
     }
-  } else {
-    for (int y = threadIdx.x / B; y < N; y += blockDim.x / B) {
-      const int64_t l = (int64_t)z * N + y;
-      C v;
-      v.x = 0; v.y = 0;
-      if (c < ncol) v = spec[l * P + kx0 + c];
-      buf[y * B + c] = v;
-    }
-  }
-  __syncthreads();
-  step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
-  __syncthreads();
-  const int k1 = threadIdx.x / B;
-  C a[N2];
-  step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
-  if (c < ncol) {
-    C* out = S + (int64_t)b * S_stride + (int64_t)z * L.zs + kx0 + c;
+  };
+  // rows of item m into buffer dst; y of the first PRE rounds from yv
+  auto gather = [&](const Item& m, C* dst, const int (&yv)[PRE], bool have_yv) {
+    const bool in = c < min(B, M1 - m.kx0);
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) out[yoff(L, k1 + N1 * k2)] = a[k2];
+    for (int p = 0; p < PRE; ++p) {
+      const int64_t r = m.lo + slot + (int64_t)p * RS;
+      if (r < m.hi) {
+        const int y = idx ? (have_yv ? yv[p] : line_y[r]) : (int)(r - m.lo);
+        if (in) tma::cp_async(dst + y * B + c, spec + r * P + m.kx0 + c);
+      }
+    }
+    for (int64_t r = m.lo + slot + (int64_t)PRE * RS; r < m.hi; r += RS) {
+      const int y = idx ? line_y[r] : (int)(r - m.lo);
+      if (in) tma::cp_async(dst + y * B + c, spec + r * P + m.kx0 + c);
+    }
+    tma::cp_async_commit();
+  };
+  Item cur, nxt, nn;
+  meta(item, cur);
+  __syncthreads();   // twiddles staged, buffers cleared
+  {
+    int yv[PRE];
+    gather(cur, buf0, yv, false);
+  }
+  int64_t nitem = item + gridDim.x;
+  if (nitem < n_items) meta(nitem, nxt);
+  for (int64_t job = 0; item < n_items; ++job) {
+    C* buf = buf0 + (job & 1) * TILE;
+    tma::cp_async_wait_all();
+    __syncthreads();   // this item's rows have landed; the other buffer is clear
+    const int64_t nnitem = nitem + gridDim.x;
+    int yv[PRE];
+    if (nitem < n_items) {
+      if (idx) {
+#pragma unroll
+        for (int p = 0; p < PRE; ++p) {
+          const int64_t r = nxt.lo + slot + (int64_t)p * RS;
+          yv[p] = r < nxt.hi ? line_y[r] : 0;
+        }
+      }
+      if (nnitem < n_items) meta(nnitem, nn);
+    }
+    step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
+    __syncthreads();
+    if (nitem < n_items) gather(nxt, buf0 + ((job & 1) ^ 1) * TILE, yv, true);
+    C a[N2];
+    step2<C, N1, N2, false, XP>(buf, B, c, slot, a);
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) buf[prow<XP>(slot, j2, N2) * B + c] = zc;
+    if (c < min(B, M1 - cur.kx0)) {
+      C* out = S + (int64_t)cur.b * S_stride + (int64_t)cur.z * L.zs + cur.kx0 + c;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) out[yoff(L, slot + N1 * k2)] = a[k2];
+    }
+    item = nitem;
+    cur = nxt;
+    nitem = nnitem;
+    nxt = nn;
   }
 }
 
@@ -395,7 +505,7 @@ __device__ __forceinline__ void load_zcol(C* buf, const C* __restrict__ src, int
 
 // Z pass forward in place (galaxy spectrum). CTA = (kx tile, ky).
 template <typename C, int N, int B>
-__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS, ColPass<C, N, B>::MINB)
 k_z_fwd(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
@@ -550,7 +660,7 @@ k_x_c2r_full(const C* __restrict__ S, int P, typename Real<C>::T* __restrict__ o
 
 // Full inverse along z or y in place on a dense half spectrum (stage entry).
 template <typename C, int N, int B, bool ALONG_Z>
-__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS, ColPass<C, N, B>::MINB)
 k_col_inv_full(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw) + N;        // twiddles W_N^j first, then the tile
@@ -585,11 +695,14 @@ k_col_inv_full(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
 
 // ============================================================================
 // Z pass fused, persistent and TMA fed. A work item is (ky, a tile of B kx
-// columns). For each item the CTA loads the galaxy spectrum tile once, then
-// runs every mesh of the batch through forward z -> * conj(F_g) / N^3 ->
-// k = 0 zeroed -> inverse z -> window rows. While one mesh is transformed the
-// next mesh's tile streams into the second shared buffer (TMA + mbarrier), so
-// HBM reads overlap the FFT arithmetic.
+// columns). For each item the CTA loads the galaxy spectrum tile once (and
+// scales it by 1/N^3, a power of two, so exactly), then runs every mesh of the
+// batch through forward z -> * conj(F_g) / N^3 -> k = 0 zeroed -> inverse z
+// -> window rows. While one mesh is transformed the next mesh's tile streams
+// into the second shared buffer (TMA + mbarrier), so HBM reads overlap the FFT
+// arithmetic. The inverse's last DFTs compute only the outputs n1 < K and
+// n1 >= N1 - K, which hold every window row when K > w / N2 (rows
+// n = n2 + N2 n1 with |n| <= w).
 // ============================================================================
 template <typename C, int N, int B>
 struct ZCorr {
@@ -617,7 +730,7 @@ __device__ __forceinline__ void zc_issue(C* dst, const CUtensorMap* map, uint64_
     tma::load_5d_hint(dst + z0 * B, map, bar, kx0 * Z::E, ky & KM, z0, ky >> kYBlockShift, b, pol);
 }
 
-template <typename C, int N, int B>
+template <typename C, int N, int B, int K>
 __global__ void __launch_bounds__(ZCorr<C, N, B>::THREADS, ZCorr<C, N, B>::MINB)
 k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mF,
              int nb, int gg, int w, C* __restrict__ Wz, int64_t Wz_stride, int P,
@@ -657,6 +770,10 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
     const int ncol = min(B, M1 - kx0);
     if (__syncthreads_or(!tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
     ph[2] ^= 1;
+    if (!gg) {   // F_g / N^3 once per item
+      for (int i = threadIdx.x; i < TILE; i += blockDim.x) ftile[i] = cscale(ftile[i], inv_n3);
+      __syncthreads();
+    }
     const bool dc_col = (kx0 + c == 0) && (ky == 0);
     for (int b = 0; b < nb; ++b, ++job) {
       const int cur = (int)(job & 1);
@@ -679,10 +796,7 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
         __syncthreads();
         step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) {
-          const C g = ftile[(k1 + N1 * k2) * B + c];
-          a[k2] = cscale(cmulc(a[k2], g), inv_n3);
-        }
+        for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmulc(a[k2], ftile[(k1 + N1 * k2) * B + c]);
       } else {
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
@@ -706,10 +820,11 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
       for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
         const int cc = t % B, n2 = t / B;
         C x[N1];
-        stepB<C, N1, N2, true, XP>(wbuf, B, cc, n2, x);
+        stepB<C, N1, N2, true, XP, K>(wbuf, B, cc, n2, x);
         if (cc < ncol) {
 #pragma unroll
           for (int n1 = 0; n1 < N1; ++n1) {
+            if (2 * K < N1 && n1 >= K && n1 < N1 - K) continue;   // not computed, not in the window
             const int zw = win_index(n2 + N2 * n1, N, w);
             if (zw >= 0) wout[(int64_t)zw * N * P + cc] = x[n1];
           }
@@ -844,7 +959,7 @@ __device__ __forceinline__ int mesh_of_rank(int r, int N, int w) { return r <= w
 // planes. Window line (b, zr, ry) is spec[((b * W + zr) * W + ry) * P] with
 // y = mesh_of_rank(ry). CTA = (kx tile, zr, mesh b).
 template <typename C, int N, int B>
-__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS)
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS, ColPass<C, N, B>::MINB)
 k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_t Xw_stride, Lay XL,
             const C* __restrict__ tw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];

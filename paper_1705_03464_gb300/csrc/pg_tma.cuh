@@ -140,6 +140,23 @@ __device__ __forceinline__ void st_hint(double2* p, double2 v, uint64_t policy) 
                : "memory");
 }
 
+// Asynchronous 8- or 16-byte copies global -> shared (cp.async), for row
+// gathers that TMA boxes cannot express. Completion is per thread:
+// cp_async_wait_all() waits for the calling thread's own copies, which are
+// loads from valid addresses and always complete.
+__device__ __forceinline__ void cp_async(float2* dst, const float2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async(double2* dst, const double2* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 }  // namespace tma
 
 // Host: a 4D tensor map over 8-byte elements, dims/strides innermost first

@@ -1,7 +1,8 @@
 // Host-side check of the in-register DFT used by every FFT pass: for each
 // length 1..32 and both directions, compares reg_dft against the direct
-// definition sum_j x_j exp(-+2 pi i j k / n) evaluated in double precision.
-// Prints "max_rel_err <value>" and returns 0.
+// definition sum_j x_j exp(-+2 pi i j k / n) evaluated in double precision,
+// and the output-pruned form (only k < K and k >= n - K wanted) on those
+// outputs. Prints "max_rel_err_<type> <value>" and returns 0.
 #include <math.h>
 #include <stdio.h>
 
@@ -11,7 +12,7 @@
 
 using namespace pg::fft;
 
-template <typename C, int RL, bool INV>
+template <typename C, int RL, bool INV, int K = RL>
 double check_one(std::mt19937& rng) {
   std::uniform_real_distribution<double> U(-1.0, 1.0);
   C a[RL];
@@ -24,9 +25,10 @@ double check_one(std::mt19937& rng) {
     xr[j] = a[j].x;
     xi[j] = a[j].y;
   }
-  reg_dft<C, RL, INV>(a);
+  reg_dft<C, RL, INV, K>(a);
   double worst = 0.0, norm = 0.0;
   for (int k = 0; k < RL; ++k) {
+    if (!(2 * K >= RL || k < K || k >= RL - K)) continue;
     double sr = 0.0, si = 0.0;
     for (int j = 0; j < RL; ++j) {
       double ang = (INV ? 2.0 : -2.0) * M_PI * (double)((j * k) % RL) / RL;
@@ -49,6 +51,14 @@ double check_all(std::mt19937& rng) {
     e = fmax(e, check_one<C, 8, INV>(rng));
     e = fmax(e, check_one<C, 16, INV>(rng));
     e = fmax(e, check_one<C, 32, INV>(rng));
+    e = fmax(e, check_one<C, 32, INV, 1>(rng));
+    e = fmax(e, check_one<C, 32, INV, 2>(rng));
+    e = fmax(e, check_one<C, 32, INV, 3>(rng));
+    e = fmax(e, check_one<C, 32, INV, 4>(rng));
+    e = fmax(e, check_one<C, 32, INV, 8>(rng));
+    e = fmax(e, check_one<C, 16, INV, 2>(rng));
+    e = fmax(e, check_one<C, 16, INV, 4>(rng));
+    e = fmax(e, check_one<C, 8, INV, 1>(rng));
   }
   return e;
 }
