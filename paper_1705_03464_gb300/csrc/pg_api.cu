@@ -114,6 +114,7 @@ struct pg_plan {
   PairGeom geom;
   size_t total = 0;
   int64_t n_cells_listed = 0;
+  int n_bin_chunks = 0;           // chunks of the binning pass over all lists
   std::vector<int64_t> h_list_off;
 
   // plan geometry
@@ -128,7 +129,7 @@ struct pg_plan {
   DevBuf &flags, &lidx, &seg_total, &line_base, &n_lines, &stmp, &line_y, &line_bin, &lines_q,
       &qsum, &scale;
   DevBuf &spec, &S, &Fg, &Wz, &Wy, &Cwin, &tmpfft;
-  DevBuf sums_pg, sums_gg, pg_valid;
+  DevBuf sums_pg, sums_gg, pg_valid, bin_part;
   // adjoint: line z, pair galaxy indices, window geometry, spectra X and A,
   // galaxy-window correlation, scalar adjoints, upstream gradients, gathers
   DevBuf &line_z, &wlines, &Xs, &As, &Xw, &cggw;
@@ -331,6 +332,7 @@ cudaError_t ensure_fixed(pg_plan* p) {
   PG_CUDA_TRY(p->sums_pg.ensure(sizeof(double) * 2 * (size_t)p->nPB * p->nL, t));
   PG_CUDA_TRY(p->sums_gg.ensure(sizeof(double) * 2 * (size_t)p->nL, t));
   PG_CUDA_TRY(p->pg_valid.ensure(p->nPB, t));
+  PG_CUDA_TRY(p->bin_part.ensure(sizeof(double) * 2 * (size_t)std::max(p->n_bin_chunks, 1) * p->nbmax, t));
   // outputs: doubles [P*Q]*5 + [P]*6 + [Q]*4 + 4, int64 [P] + [Q] + 1
   const size_t nd = (size_t)p->nPB * p->nQ * 5 + (size_t)p->nPB * 6 + (size_t)p->nQ * 4 + 8;
   const size_t ni = (size_t)p->nPB + p->nQ + 2;
@@ -482,7 +484,7 @@ cudaError_t correlate_window(pg_plan* p, int nb, bool gg, double* sums, cudaStre
   }
   ProfScope ps(p, PG_FAM_BIN, s, nb * (double)p->n_cells_listed * (4.0 + (double)sizeof(R)));
   return launch_bin_sums<R>(nb, p->nL, p->Cwin.as<R>(), Cw_stride, p->cells.as<int32_t>(),
-                            p->list_off.as<int64_t>(), sums, s);
+                            p->list_off.as<int64_t>(), p->n_bin_chunks, p->bin_part.as<double>(), sums, s);
 }
 
 // Galaxy spectrum into Fg from points (SoA), then the galaxy window sums.
@@ -1183,6 +1185,7 @@ pg_status plan_create(const pg_params* prm, const pg_plan* share, pg_plan** out)
   std::vector<int32_t> cells;
   build_cell_lists(p, cells, p->h_list_off);
   p->n_cells_listed = (int64_t)cells.size();
+  p->n_bin_chunks = bin_chunks(p->h_list_off);
   if (e == cudaSuccess) e = build_window_geometry(p, cells);
   if (e == cudaSuccess) e = p->cells.ensure(4 * std::max<size_t>(cells.size(), 1), &p->total);
   if (e == cudaSuccess && !cells.empty())
@@ -1224,7 +1227,7 @@ void pg_plan_destroy(pg_plan* p) {
                    &p->cstart, &p->ccursor, &p->perm, &p->xs, &p->ys, &p->zs, &p->ws, &p->ctmp,
                    &p->ctot, &p->dd, &p->ddq, &p->pcursor, &p->ubin, &p->ui, &p->uj, &p->umx,
                    &p->umy, &p->umz, &p->uwp, &p->pbin, &p->px, &p->py, &p->pz, &p->pw,
-                   &p->bcursor, &p->sums_pg, &p->sums_gg, &p->pg_valid, &p->out, &p->psi,
+                   &p->bcursor, &p->sums_pg, &p->sums_gg, &p->pg_valid, &p->bin_part, &p->out, &p->psi,
                    &p->psj, &p->cell_bin, &p->cell_agg, &p->wl_idx, &p->wl_tot, &p->wl_base,
                    &p->wl_y, &p->adjb, &p->gout, &p->gp, &p->gj, &p->part, &p->Wk, &p->Gs,
                    &p->sm_off, &p->sm_sums, &p->sm_part, &p->sm_out};

@@ -3,8 +3,11 @@
 // Binning (Sec. 2.1, eq. bpg_initial with W the indicator of one shell): every
 // window cell belongs to at most one (r, mu_r) bin, and the plan holds, per
 // bin, the sorted list of its cells plus one extra list for the aggregate
-// support. One CTA sums one list of one mesh in FP64 (sum C and sum C^2) with
-// a fixed warp-shuffle tree, so the sums are deterministic.
+// support. The lists are cut into chunks of kBinChunk cells; one CTA sums one
+// chunk of one mesh in FP64 (sum C and sum C^2) with a fixed warp-shuffle
+// tree, and one thread per list adds its chunks in order, so the sums are
+// deterministic. Chunking spreads the aggregate list (about half of all
+// listed cells) over the whole GPU, whose FP64 rate is low.
 //
 // Ratios (Sec. 2.2 and Sec. 3.4): xi_pg, xi_gg, b_pg = xi_pg / xi_gg,
 // xi(d_w) = sum C_gg^2 / sum C_gg (eq. xi_dw), xi(s, mu) = DD/RR - 1
@@ -19,18 +22,40 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// First chunk index of list l and its chunk count (lists are cut into
+// kBinChunk cells; the chunks of one list are consecutive).
+__device__ __forceinline__ void chunk_of(const int64_t* __restrict__ list_off, int n_lists, int ci, int& l,
+                                         int64_t& lo, int64_t& hi) {
+  int first = 0;
+  for (l = 0; l < n_lists; ++l) {
+    const int64_t a = list_off[l], e = list_off[l + 1];
+    const int nch = (int)((e - a + kBinChunk - 1) / kBinChunk);
+    if (ci < first + nch) {
+      lo = a + (int64_t)(ci - first) * kBinChunk;
+      hi = min(e, lo + kBinChunk);
+      return;
+    }
+    first += nch;
+  }
+  lo = hi = 0;
+}
+
+// One CTA per (chunk, mesh): FP64 sums of C and C^2 over the chunk's cells,
+// reduced by a fixed warp-shuffle tree.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-k_bin_sums(const R* __restrict__ Cwin, int64_t stride, const int32_t* __restrict__ cells,
-           const int64_t* __restrict__ list_off, double* __restrict__ out, int n_lists) {
-  const int l = blockIdx.x, b = blockIdx.y;
+k_bin_chunks(const R* __restrict__ Cwin, int64_t stride, const int32_t* __restrict__ cells,
+             const int64_t* __restrict__ list_off, int n_lists, int n_chunks, double* __restrict__ part) {
+  const int ci = blockIdx.x, b = blockIdx.y;
   const R* cw = Cwin + (int64_t)b * stride;
-  const int64_t lo = list_off[l], hi = list_off[l + 1];
+  int l;
+  int64_t lo, hi;
+  chunk_of(list_off, n_lists, ci, l, lo, hi);
   double s1 = 0.0, s2 = 0.0;
   for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) {
-    double v = (double)cw[cells[i]];
+    const double v = (double)cw[cells[i]];
     s1 += v;
-    s2 += v * v;
+    s2 = fma(v, v, s2);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -50,10 +75,28 @@ k_bin_sums(const R* __restrict__ Cwin, int64_t stride, const int32_t* __restrict
       s2 += __shfl_down_sync(0xffffffffu, s2, o);
     }
     if (lane == 0) {
-      out[((int64_t)b * n_lists + l) * 2] = s1;
-      out[((int64_t)b * n_lists + l) * 2 + 1] = s2;
+      part[((int64_t)b * n_chunks + ci) * 2] = s1;
+      part[((int64_t)b * n_chunks + ci) * 2 + 1] = s2;
     }
   }
+}
+
+// One thread per (list, mesh): the list's chunk partials in chunk order.
+__global__ void k_bin_combine(const int64_t* __restrict__ list_off, int n_lists, int n_chunks, int nb,
+                              const double* __restrict__ part, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_lists * nb) return;
+  const int l = t % n_lists, b = t / n_lists;
+  int first = 0;
+  for (int k = 0; k < l; ++k) first += (int)((list_off[k + 1] - list_off[k] + kBinChunk - 1) / kBinChunk);
+  const int nch = (int)((list_off[l + 1] - list_off[l] + kBinChunk - 1) / kBinChunk);
+  double s1 = 0.0, s2 = 0.0;
+  for (int k = 0; k < nch; ++k) {
+    s1 += part[((int64_t)b * n_chunks + first + k) * 2];
+    s2 += part[((int64_t)b * n_chunks + first + k) * 2 + 1];
+  }
+  out[((int64_t)b * n_lists + l) * 2] = s1;
+  out[((int64_t)b * n_lists + l) * 2 + 1] = s2;
 }
 
 __device__ __forceinline__ double q_notsq(double b, double xi, double xw) {
@@ -136,17 +179,22 @@ __global__ void __launch_bounds__(kThreads) k_ratios(RatioArgs a) {
 
 template <typename R>
 cudaError_t launch_bin_sums(int nb, int n_lists, const R* Cwin, int64_t Cwin_stride,
-                            const int32_t* cells, const int64_t* list_off, double* out,
-                            cudaStream_t s) {
+                            const int32_t* cells, const int64_t* list_off, int n_chunks, double* part,
+                            double* out, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  dim3 g(n_lists, nb);
-  k_bin_sums<R><<<g, kThreads, 0, s>>>(Cwin, Cwin_stride, cells, list_off, out, n_lists);
+  if (n_chunks > 0) {
+    dim3 g(n_chunks, nb);
+    k_bin_chunks<R><<<g, kThreads, 0, s>>>(Cwin, Cwin_stride, cells, list_off, n_lists, n_chunks, part);
+    PG_CUDA_TRY(launched());
+  }
+  const int nt = n_lists * nb;
+  k_bin_combine<<<(unsigned)cdiv(nt, 128), 128, 0, s>>>(list_off, n_lists, n_chunks, nb, part, out);
   return launched();
 }
 template cudaError_t launch_bin_sums<float>(int, int, const float*, int64_t, const int32_t*,
-                                            const int64_t*, double*, cudaStream_t);
+                                            const int64_t*, int, double*, double*, cudaStream_t);
 template cudaError_t launch_bin_sums<double>(int, int, const double*, int64_t, const int32_t*,
-                                             const int64_t*, double*, cudaStream_t);
+                                             const int64_t*, int, double*, double*, cudaStream_t);
 
 cudaError_t launch_ratios(const RatioArgs& a, cudaStream_t s) {
   k_ratios<<<1, kThreads, 0, s>>>(a);

@@ -1135,6 +1135,14 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
       __syncthreads();
       C a[N2];
       step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
+      // the galaxy column is issued here so that its L2 latency overlaps the
+      // window column's forward transform
+      C f[N2];
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        f[k2].x = 0; f[k2].y = 0;
+        if (c < ncol) f[k2] = tma::ld_hint(fcol + (int64_t)(k1 + N1 * k2) * L.zs, pol_keep);
+      }
       __syncthreads();
       step1_win<C, N, B, XP>(buf, xb0 + cur * WS, w, tws);
       __syncthreads();
@@ -1150,12 +1158,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
         *o = v;
       }
 #pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) {
-        C f;
-        f.x = 0; f.y = 0;
-        if (c < ncol) f = tma::ld_hint(fcol + (int64_t)(k1 + N1 * k2) * L.zs, pol_keep);
-        x[k2] = cmul(x[k2], f);
-      }
+      for (int k2 = 0; k2 < N2; ++k2) x[k2] = cmul(x[k2], f[k2]);
       if (dc_col && k1 == 0) { x[0].x = 0; x[0].y = 0; }   // k = 0 mode
       __syncthreads();
       stepA<C, N1, N2, true, XP>(buf, B, c, k1, x, tws, 1);

@@ -1,6 +1,8 @@
 // Internal declarations shared by the libpairgal translation units.
 #pragma once
 
+#include <vector>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -312,10 +314,21 @@ cudaError_t launch_wc_sums(int N, double dx, const SmoothW& p, const R* Cm, doub
 cudaError_t launch_smooth_final(const SmoothArgs& a, cudaStream_t s);
 
 // ---- binning and ratios (pg_bin.cu) -----------------------------------------
+// Cells per chunk of the binning pass: each list is cut into chunks of at
+// most this many cells, summed by one CTA each.
+constexpr int kBinChunk = 4096;
+inline int bin_chunks(const std::vector<int64_t>& list_off) {
+  int64_t n = 0;
+  for (size_t l = 0; l + 1 < list_off.size(); ++l) n += (list_off[l + 1] - list_off[l] + kBinChunk - 1) / kBinChunk;
+  return (int)n;
+}
+// Sums C and C^2 over every list of nb window meshes into out [nb][n_lists][2]
+// (FP64): per-chunk partial sums into part [nb][n_chunks][2], then each list's
+// partials in chunk order, so the result does not depend on scheduling.
 template <typename R>
 cudaError_t launch_bin_sums(int nb, int n_lists, const R* Cwin, int64_t Cwin_stride,
-                            const int32_t* cells, const int64_t* list_off, double* out,
-                            cudaStream_t s);
+                            const int32_t* cells, const int64_t* list_off, int n_chunks, double* part,
+                            double* out, cudaStream_t s);
 
 struct RatioArgs {
   int P, Q;                       // pair bins, (r, mu_r) bins
