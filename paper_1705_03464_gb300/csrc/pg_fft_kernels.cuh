@@ -482,7 +482,7 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
     if (c < min(B, M1 - cur.kx0)) {
       C* out = S + (int64_t)cur.b * S_stride + (int64_t)cur.z * L.zs + cur.kx0 + c;
 #pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) out[yoff(L, slot + N1 * k2)] = a[k2];
+      for (int k2 = 0; k2 < N2; ++k2) tma::st_hint(out + yoff(L, slot + N1 * k2), a[k2], tma::policy_evict_first());
     }
     item = nitem;
     cur = nxt;
