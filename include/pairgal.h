@@ -14,6 +14,10 @@
  *   xi(d_w) = sum C_gg^2 / sum C_gg over the shell                  (eq. xi_dw),
  *   Q_eff from eq. Qeff_notsq and the strict-squeezed form eq. Qeff, with
  *   xi(d_p) = xi(s, mu) = DD / RR - 1 from the pair counts           (eq. 2PCF_d_collapsed).
+ * With pair_grid = 1 the pairs are binned instead on the (d_perp, d_par)
+ * grid of the paper's b_pg and Q_eff maps (Sec. 5), d_perp = sqrt(dx^2 +
+ * dy^2), d_par = |dz|, and the LOS-projected w(d_perp) of eq.
+ * 2PCF_los_integrated_explicit is returned as well.
  *
  * Conventions for every entry point:
  *  - Positions are FP64, [n][3] row-major (x, y, z), Mpc/h, any real value
@@ -70,6 +74,11 @@ typedef struct pg_params {
   double r_perp_cut;        /* aggregates exclude cells with r_perp < cut (Sec. 3.6(b)); 0 = off */
   int32_t precision;        /* 0 = FP32 FFT + FP64 reductions, 1 = FP64 throughout */
   int32_t bins_per_batch;   /* pair meshes resident at once; 0 = chosen from N */
+  int32_t pair_grid;        /* 0 = (s, mu) pair bins; 1 = (d_perp, d_par) grid: s_edges are then
+                               the d_perp edges (n_s bins) and par_edges the |d_par| edges (n_mu
+                               bins); the largest separation sqrt(d_perp,max^2 + d_par,max^2)
+                               must be < L/2 */
+  const double* par_edges;  /* [n_mu+1] ascending, par_edges[0] >= 0 (pair_grid = 1; else unused) */
 } pg_params;
 
 typedef struct pg_plan pg_plan;
@@ -80,7 +89,9 @@ typedef struct pg_plan pg_plan;
 typedef struct pg_result {
   int64_t* dd;          /* [P] number of pairs per (s, mu) bin */
   double* dd_w;         /* [P] sum of w_i*w_j (exact: summed as Q32.32 integers) */
-  double* xi_ss;        /* [P] xi(s, mu) = DD/RR - 1, RR = ((sum w)^2 - sum w^2)/2 * V_bin/L^3 */
+  double* xi_ss;        /* [P] xi(s, mu) = DD/RR - 1, RR = ((sum w)^2 - sum w^2)/2 * V_bin/L^3 with
+                           V_bin = (4 pi/3)(s_hi^3 - s_lo^3)/n_mu, or on the (d_perp, d_par) grid
+                           V_bin = pi (p_hi^2 - p_lo^2) * 2 (l_hi - l_lo) (both signs of d_par) */
   double* xi_pg;        /* [P][Q] mean of C_pg over the bin's cells */
   double* xi_gg;        /* [Q] mean of C_gg */
   double* b_pg;         /* [P][Q] xi_pg / xi_gg */
@@ -97,6 +108,9 @@ typedef struct pg_result {
   double* sum_gg;       /* [Q] */
   double* sum2_gg;      /* [Q] sum of C_gg^2 */
   double* sum_gg_agg;   /* [2] sum C_gg, sum C_gg^2 over the aggregate cells */
+  double* w_perp;       /* [n_s] pair_grid = 1: w(d_perp) = sum over the d_par bins of
+                           2 (l_hi - l_lo) xi(d_perp, d_par) (eq. 2PCF_los_integrated_explicit,
+                           first line, with d_par,max = the last par edge); NaN otherwise */
 } pg_result;
 
 /* Validates *params, copies the edges and builds the data-independent plan
@@ -195,7 +209,8 @@ pg_status pg_forward_smooth(pg_plan* plan, const pg_smooth_params* w, int64_t n_
  * plan (same catalogue, still held in the plan's buffers): with the upstream
  * gradients in *grad_out (HOST arrays in the pg_result layout; the fields
  * xi_pg, xi_gg, b_pg, q_eff, q_eff_sq, xi_dw, b_pg_agg, q_eff_agg, xi_dw_agg,
- * xi_ss, dd_w are read, NULL means zero, other fields are ignored), writes
+ * xi_ss, dd_w and, on the (d_perp, d_par) grid, w_perp are read, NULL means
+ * zero, other fields are ignored), writes
  * d_grad_w[n_gal] (device FP64) = dL/dw_i for L = sum over fields and bins of
  * grad * output, outputs that are NaN contributing nothing. The reverse sweep
  * follows the forward definitions (Sec. 2.1 eqs. bpg_initial /

@@ -31,6 +31,8 @@ from . import pairs as op
 
 OUTPUT_KEYS = ("xi_pg", "xi_gg", "b_pg", "q_eff", "q_eff_sq", "xi_dw", "b_pg_agg", "q_eff_agg",
                "xi_dw_agg", "xi_ss", "dd_w")
+# on the (d_perp, d_par) pair grid the projected w(d_perp) is an output too
+GRID_OUTPUT_KEYS = OUTPUT_KEYS + ("w_perp",)
 
 
 def _node_weights(points, L, N, assign):
@@ -77,7 +79,7 @@ def forward_state(p, pos, vel, w):
     # weights taken in FP64 as given (FP32 inputs convert exactly), so that
     # finite differences of this forward are not rounded to FP32
     wt = np.asarray(w, dtype=np.float64)
-    pr = op.find_pairs(x, None, L, p.s_edges, p.n_mu)
+    pr = op.find_pairs(x, None, L, p.s_edges, p.n_mu, par_edges=getattr(p, "par_edges", None))
     pr["weight"] = wt[pr["i"]] * wt[pr["j"]]
     n_s = len(p.s_edges) - 1
     P = n_s * p.n_mu
@@ -107,8 +109,7 @@ def forward_state(p, pos, vel, w):
     n = np.append(np.bincount(bins[bins >= 0], minlength=Q), np.count_nonzero(agg)).astype(float)
     dd_w = np.bincount(pb, weights=pr["weight"], minlength=P)
     sw, sw2 = wt.sum(), (wt * wt).sum()
-    e = np.asarray(p.s_edges, float)
-    vb = np.repeat((4.0 * np.pi / 3.0) * (e[1:] ** 3 - e[:-1] ** 3) / p.n_mu, p.n_mu)
+    vb = op.pair_volumes(p.s_edges, p.n_mu, getattr(p, "par_edges", None))
     st.update({"S": S, "G": G, "G2": G2, "n": n, "dd_w": dd_w, "sw": sw, "sw2": sw2, "vb": vb})
     return st
 
@@ -129,7 +130,15 @@ def outputs(st):
                 "q_eff": oc.q_eff_notsq(bb, xs[:, None], xw[None, :]),
                 "q_eff_sq": oc.q_eff_sq(bb, xs[:, None]), "xi_dw": xw, "b_pg_agg": b_agg,
                 "q_eff_agg": oc.q_eff_notsq(b_agg, xs, xw_agg), "xi_dw_agg": np.array([xw_agg]),
-                "xi_ss": xs, "dd_w": st["dd_w"]}
+                "xi_ss": xs, "dd_w": st["dd_w"], "w_perp": _w_perp(p, xs)}
+
+
+def _w_perp(p, xs):
+    """w(d_perp) on the (d_perp, d_par) grid, NaN for (s, mu) bins."""
+    pe = getattr(p, "par_edges", None)
+    if pe is None:
+        return np.full(len(p.s_edges) - 1, np.nan)
+    return op.w_perp(xs, pe)
 
 
 def loss(st, gbar):
@@ -149,7 +158,7 @@ def grad_weights(st, gbar):
     L, N, wh = p.box_L, p.mesh_n, st["wh"]
     S, G, G2, n = st["S"], st["G"], st["G2"], st["n"]
     out = outputs(st)
-    gz = {k: np.zeros_like(np.asarray(out[k], float)) for k in OUTPUT_KEYS}
+    gz = {k: np.zeros_like(np.asarray(out[k], float)) for k in GRID_OUTPUT_KEYS}
     for k, g in gbar.items():
         v = np.asarray(out[k], float)
         gz[k] = np.where(np.isfinite(v), np.asarray(g, float).reshape(v.shape), 0.0)
@@ -161,6 +170,10 @@ def grad_weights(st, gbar):
     Gb = np.zeros(Q + 1)
     G2b = np.zeros(Q + 1)
     xsb = gz["xi_ss"].copy()
+    pe = getattr(p, "par_edges", None)
+    if pe is not None:   # w(d_perp) = sum_m 2 (l_hi - l_lo) xi(d_perp, d_par)
+        dl2 = 2.0 * (np.asarray(pe, float)[1:] - np.asarray(pe, float)[:-1])
+        xsb += (gz["w_perp"][:, None] * dl2[None, :]).reshape(-1)
     valid = np.isfinite(S[:, 0])
     for b in np.nonzero(valid)[0]:
         x = xs[b]

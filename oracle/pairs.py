@@ -12,6 +12,12 @@ Follows:
 * Sec. 3.4, eq. 2PCF_d_collapsed: xi = (pair count) / (expected count) - 1,
   with the expected count written exactly as ((sum w)^2 - sum w^2)/2 times
   the bin volume over the box volume.
+* Sec. 3.4, eq. 2PCF_los_integrated_explicit and the (d_perp, d_par) maps of
+  Sec. 5: on the pair grid d_perp = sqrt(dx^2 + dy^2) and d_par = |dz| (line
+  of sight z) are binned instead of (s, mu); a grid cell's volume is the
+  annulus pi (p_hi^2 - p_lo^2) times 2 (l_hi - l_lo) (both signs of d_par),
+  and w(d_perp) is the integral of xi over d_par, sum over the d_par bins of
+  2 (l_hi - l_lo) xi(d_perp, d_par), with d_par,max the last d_par edge.
 
 All arithmetic is IEEE FP64 with one rounding per operation (numpy does not
 contract a*b+c), in the order written below.
@@ -61,8 +67,39 @@ def _bin_pairs(d, s_edges, n_mu):
     return k, m, valid
 
 
-def find_pairs(pos, w, L, s_edges, n_mu, chunk=2048):
-    """All unordered pairs i < j with s in [s_edges[0], s_edges[-1]).
+def _bin_pairs_grid(d, perp_edges, par_edges):
+    """(d_perp bin, d_par bin, valid) for separation vectors d [m, 3]:
+    d_perp^2 = dx^2 + dy^2 against the squared d_perp edges, d_par = |dz|
+    against the d_par edges, bins half-open."""
+    e = np.asarray(perp_edges, dtype=np.float64)
+    e2 = e * e
+    pe = np.asarray(par_edges, dtype=np.float64)
+    p2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]
+    l = np.abs(d[:, 2])
+    k = np.searchsorted(e2, p2, side="right") - 1
+    m = np.searchsorted(pe, l, side="right") - 1
+    valid = (k >= 0) & (k < len(e2) - 1) & (m >= 0) & (m < len(pe) - 1)
+    return k, m, valid
+
+
+def max_separation(s_edges, par_edges=None):
+    """The largest pair separation a binning keeps: s_max, or on the grid
+    the corner sqrt(d_perp,max^2 + d_par,max^2) of its cylinder."""
+    if par_edges is None:
+        return float(s_edges[-1])
+    return math.sqrt(float(s_edges[-1]) ** 2 + float(par_edges[-1]) ** 2)
+
+
+def _bin(d, s_edges, n_mu, par_edges):
+    if par_edges is None:
+        return _bin_pairs(d, s_edges, n_mu)
+    return _bin_pairs_grid(d, s_edges, par_edges)
+
+
+def find_pairs(pos, w, L, s_edges, n_mu, chunk=2048, par_edges=None):
+    """All unordered pairs i < j with s in [s_edges[0], s_edges[-1]) (with
+    par_edges: d_perp in [s_edges[0], s_edges[-1]) and d_par in
+    [par_edges[0], par_edges[-1]), bins 'sbin' = d_perp bin, 'mubin' = d_par bin).
 
     Returns a dict of arrays over pairs: i, j (input indices), sbin, mubin,
     mid [m, 3] (wrapped midpoint x_i + d/2, d = min-image x_j - x_i) and
@@ -83,7 +120,7 @@ def find_pairs(pos, w, L, s_edges, n_mu, chunk=2048):
             I = I[keep]
             J = J[keep]
             d = min_image(pos[J] - pos[I], L)
-            k, m, valid = _bin_pairs(d, s_edges, n_mu)
+            k, m, valid = _bin(d, s_edges, n_mu, par_edges)
             I, J, d, k, m = I[valid], J[valid], d[valid], k[valid], m[valid]
             mid = wrap(pos[I] + 0.5 * d, L)
             out["i"].append(I)
@@ -110,11 +147,34 @@ def pair_counts(pairs, n_s, n_mu):
     return count, ddq
 
 
-def xi_ss(ddq, w, n_gal, L, s_edges, n_mu):
+def pair_volumes(s_edges, n_mu, par_edges=None):
+    """Volume of every pair bin (index s bin * n_mu + mu bin): the shell
+    (4 pi / 3)(s_hi^3 - s_lo^3) / n_mu, or on the grid the annulus
+    pi (p_hi^2 - p_lo^2) times 2 (l_hi - l_lo)."""
+    e = np.asarray(s_edges, dtype=np.float64)
+    if par_edges is None:
+        vshell = (4.0 * math.pi / 3.0) * (e[1:] ** 3 - e[:-1] ** 3)
+        return np.repeat(vshell / n_mu, n_mu)
+    pe = np.asarray(par_edges, dtype=np.float64)
+    ann = math.pi * (e[1:] ** 2 - e[:-1] ** 2)
+    return (ann[:, None] * (2.0 * (pe[1:] - pe[:-1]))[None, :]).reshape(-1)
+
+
+def w_perp(xi, par_edges):
+    """w(d_perp) = sum over the d_par bins of 2 (l_hi - l_lo) xi(d_perp, d_par)
+    (eq. 2PCF_los_integrated_explicit, first line, on the grid); xi is
+    [n_perp * n_par] in bin order."""
+    pe = np.asarray(par_edges, dtype=np.float64)
+    n_par = len(pe) - 1
+    x = np.asarray(xi, dtype=np.float64).reshape(-1, n_par)
+    return np.sum(x * (2.0 * (pe[1:] - pe[:-1]))[None, :], axis=1)
+
+
+def xi_ss(ddq, w, n_gal, L, s_edges, n_mu, par_edges=None):
     """xi(s, mu) = DD / RR - 1 (eq. 2PCF_d_collapsed, exact pair normalisation).
 
-    RR = ((sum w)^2 - sum w^2) / 2 * V_bin / L^3 with
-    V_bin = (4 pi / 3)(s_hi^3 - s_lo^3) / n_mu.
+    RR = ((sum w)^2 - sum w^2) / 2 * V_bin / L^3 with V_bin from pair_volumes
+    ((s, mu) shells or (d_perp, d_par) cells).
     """
     if w is None:
         sw = float(n_gal)
@@ -124,15 +184,13 @@ def xi_ss(ddq, w, n_gal, L, s_edges, n_mu):
         sw = float(np.sum(wd))
         sw2 = float(np.sum(wd * wd))
     npairs = 0.5 * (sw * sw - sw2)
-    e = np.asarray(s_edges, dtype=np.float64)
-    vshell = (4.0 * math.pi / 3.0) * (e[1:] ** 3 - e[:-1] ** 3)
-    rr = npairs * np.repeat(vshell / n_mu, n_mu) / L ** 3
+    rr = npairs * pair_volumes(s_edges, n_mu, par_edges) / L ** 3
     dd = ddq.astype(np.float64) / TWO32
     with np.errstate(invalid="ignore", divide="ignore"):
         return dd / rr - 1.0, rr
 
 
-def find_pairs_kdtree(pos, w, L, s_edges, n_mu):
+def find_pairs_kdtree(pos, w, L, s_edges, n_mu, par_edges=None):
     """find_pairs for large catalogues: the candidate pairs i < j closer than
     s_max come from scipy's periodic k-d tree (a library neighbour search,
     slightly enlarged radius); binning, midpoints and weights are then the
@@ -141,7 +199,7 @@ def find_pairs_kdtree(pos, w, L, s_edges, n_mu):
     pos = np.asarray(pos, dtype=np.float64)
     wt = None if w is None else np.asarray(w, dtype=np.float32).astype(np.float64)
     tree = cKDTree(pos, boxsize=L)
-    cand = tree.query_pairs(float(s_edges[-1]) * (1.0 + 1e-9), output_type="ndarray")
+    cand = tree.query_pairs(max_separation(s_edges, par_edges) * (1.0 + 1e-9), output_type="ndarray")
     if cand.size == 0:
         cand = np.zeros((0, 2), dtype=np.int64)
     I = np.minimum(cand[:, 0], cand[:, 1]).astype(np.int64)
@@ -149,7 +207,7 @@ def find_pairs_kdtree(pos, w, L, s_edges, n_mu):
     o = np.lexsort((J, I))
     I, J = I[o], J[o]
     d = min_image(pos[J] - pos[I], L)
-    k, m, valid = _bin_pairs(d, s_edges, n_mu)
+    k, m, valid = _bin(d, s_edges, n_mu, par_edges)
     I, J, d, k, m = I[valid], J[valid], d[valid], k[valid], m[valid]
     return {"i": I, "j": J, "sbin": k.astype(np.int64), "mubin": m.astype(np.int64),
             "mid": wrap(pos[I] + 0.5 * d, L),

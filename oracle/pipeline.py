@@ -1,8 +1,8 @@
 """The whole forward path for one catalogue (oracle, FP64, test-only).
 
 Steps in the paper's order: positions (Sec. 3.2, eq. RSD) -> pairs binned by
-(s, mu) with midpoints (Sec. 2.1, Sec. 3.3) -> pair counts and xi(s, mu)
-(Sec. 3.4) -> mass assignment of pair midpoints per bin and of galaxies
+(s, mu) (or on the (d_perp, d_par) grid) with midpoints (Sec. 2.1, Sec. 3.3)
+-> pair counts and xi(s, mu) (Sec. 3.4; on the grid also w(d_perp)) -> mass assignment of pair midpoints per bin and of galaxies
 (Sec. 3.5) -> cross-correlation with the galaxy mesh and binning by
 (r, mu_r) (Sec. 2.1, eqs. bpg_initial / bpg_intermediate with a shell W) ->
 b_pg, xi(d_w), Q_eff (Sec. 2.2, eqs. xi_dw, Qeff, Qeff_notsq).
@@ -34,6 +34,7 @@ class Params:
     n_mur: int
     rsd_factor: float = 0.0
     r_perp_cut: float = 0.0
+    par_edges: tuple = None   # (d_perp, d_par) pair grid: s_edges are then the d_perp edges
 
     @classmethod
     def of(cls, wl):
@@ -49,9 +50,9 @@ def run(p: Params, pos, vel=None, w=None, form="mesh", pair_bins=None):
     n_rb = n_r * p.n_mur
     x = op.transform_positions(pos, vel, L, p.rsd_factor)
     wt = None if w is None else np.asarray(w, dtype=np.float32).astype(np.float64)
-    pr = op.find_pairs(x, w, L, p.s_edges, p.n_mu)
+    pr = op.find_pairs(x, w, L, p.s_edges, p.n_mu, par_edges=p.par_edges)
     dd, ddq = op.pair_counts(pr, n_s, p.n_mu)
-    xi_ss, rr = op.xi_ss(ddq, w, x.shape[0], L, p.s_edges, p.n_mu)
+    xi_ss, rr = op.xi_ss(ddq, w, x.shape[0], L, p.s_edges, p.n_mu, p.par_edges)
     wh = oc.window_half(N, L, p.r_edges[-1])
     bins, agg = oc.cell_bins(N, L, p.r_edges, p.n_mur, p.r_perp_cut, wh)
     r_max = p.r_edges[-1]
@@ -93,5 +94,7 @@ def run(p: Params, pos, vel=None, w=None, form="mesh", pair_bins=None):
         "sum_pg": sp1, "sum_pg_agg": spa,
         "sum_gg": s1, "sum2_gg": s2, "sum_gg_agg": a1, "sum2_gg_agg": a2,
         "pairs": pr, "pos": x, "window_half": wh,
+        "w_perp": (op.w_perp(xi_ss, p.par_edges) if p.par_edges is not None
+                   else np.full(n_s, np.nan)),
     })
     return out

@@ -100,9 +100,9 @@ def estimate(p, prm: WParams, pos, vel=None, w=None):
     n_pb = n_s * p.n_mu
     x = op.transform_positions(pos, vel, L, p.rsd_factor)
     wt = np.ones(x.shape[0]) if w is None else np.asarray(w, dtype=np.float32).astype(np.float64)
-    pr = op.find_pairs(x, w, L, p.s_edges, p.n_mu)
+    pr = op.find_pairs(x, w, L, p.s_edges, p.n_mu, par_edges=p.par_edges)
     dd, ddq = op.pair_counts(pr, n_s, p.n_mu)
-    xi_ss, _ = op.xi_ss(ddq, w, x.shape[0], L, p.s_edges, p.n_mu)
+    xi_ss, _ = op.xi_ss(ddq, w, x.shape[0], L, p.s_edges, p.n_mu, p.par_edges)
     mq = om.deposit(x, wt, L, N, p.assign)
     f = oc.field(mq)
     Wm = weight_mesh(L, N, prm)

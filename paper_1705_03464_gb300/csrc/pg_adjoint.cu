@@ -32,11 +32,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_ratios(AdjRatioArgs a) {
   const double sw = a.wsum[0], sw2 = a.wsum[1];
   const double npairs = 0.5 * (sw * sw - sw2);
   const double L3 = a.L * a.L * a.L;
-  auto rr_of = [&](int p) {
-    const int ks = p / a.n_mu;
-    const double lo = a.s_edges[ks], hi = a.s_edges[ks + 1];
-    return npairs * ((4.0 * M_PI / 3.0) * (hi * hi * hi - lo * lo * lo) / (double)a.n_mu) / L3;
-  };
+  auto rr_of = [&](int p) { return npairs * a.vbin[p] / L3; };
   auto ddw_of = [&](int p) { return (double)(long long)a.ddq[p] * (1.0 / 4294967296.0); };
   const double* S = a.sum_pg;   // [P][L][2]
   const double* Gs = a.sum_gg;  // [L][2]
@@ -116,16 +112,12 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_ratios(AdjRatioArgs a) {
   double npb = 0.0;
   for (int p = threadIdx.x; p < P; p += kThreads) {
     double xsb = gate(a.g.xi_ss, a.o.xi_ss, p);
+    if (a.wcoef) xsb += a.wcoef[p] * gate(a.g.w_perp, a.o.w_perp, p / a.n_mu);   // w(d_perp)
     for (int q = 0; q < L; ++q) xsb += a.tmp[3 * ((int64_t)p * L + q) + 2];
     const double rr = rr_of(p), ddw = ddw_of(p);
     const double ddb = gate(a.g.dd_w, a.o.dd_w, p) + (rr > 0.0 ? xsb / rr : 0.0);
     a.DDbar[p] = ddb;
-    if (rr > 0.0) {
-      const int ks = p / a.n_mu;
-      const double lo = a.s_edges[ks], hi = a.s_edges[ks + 1];
-      const double vb = (4.0 * M_PI / 3.0) * (hi * hi * hi - lo * lo * lo) / (double)a.n_mu;
-      npb += (-xsb * ddw / (rr * rr)) * vb / L3;
-    }
+    if (rr > 0.0) npb += (-xsb * ddw / (rr * rr)) * a.vbin[p] / L3;
   }
   red[threadIdx.x] = npb;
   __syncthreads();

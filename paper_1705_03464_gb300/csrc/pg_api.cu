@@ -104,7 +104,7 @@ struct pg_plan {
         Xw(wsp->Xw), cggw(wsp->cggw), cap_lines(wsp->cap_lines) {}
   std::shared_ptr<Workspace> wsp;
   pg_params prm;
-  std::vector<double> s_edges, r_edges;
+  std::vector<double> s_edges, r_edges, par_edges;
   int device = 0;
   int N = 0, M1 = 0, P = 0;       // mesh, half-spectrum length, row pitch
   int w = 0, W = 0;               // window half size, side
@@ -118,7 +118,7 @@ struct pg_plan {
   std::vector<int64_t> h_list_off;
 
   // plan geometry
-  DevBuf tw, cells, list_off, s_edges_d;
+  DevBuf tw, cells, list_off, s_edges_d, vbin_d, wcoef_d;
   // catalogue
   DevBuf in_pos, in_vel, in_w, x, y, z, gw, flag, wpart, wsum;
   DevBuf cell_id, ccount, cstart, ccursor, perm, xs, ys, zs, ws, ctmp, ctot;
@@ -505,7 +505,7 @@ cudaError_t galaxy_pass(pg_plan* p, int64_t n, const double* x, const double* y,
 
 struct OutPtrs {
   double *dd_w, *xi_ss, *xi_pg, *xi_gg, *b_pg, *q_eff, *q_eff_sq, *xi_dw, *b_pg_agg, *q_eff_agg,
-      *xi_dw_agg, *sum_pg, *sum_pg_agg, *sum_gg, *sum2_gg, *sum_gg_agg;
+      *xi_dw_agg, *sum_pg, *sum_pg_agg, *sum_gg, *sum2_gg, *sum_gg_agg, *w_perp;
   int64_t *dd, *n_cells, *n_cells_agg;
 };
 
@@ -525,7 +525,7 @@ OutPtrs out_layout_of(pg_plan* p, double* base) {
   o.b_pg_agg = d; d += P;
   o.q_eff_agg = d; d += P;
   o.sum_pg_agg = d; d += P;
-  d += P;
+  o.w_perp = d; d += P;   // n_s <= P used
   o.xi_gg = d; d += Q;
   o.xi_dw = d; d += Q;
   o.sum_gg = d; d += Q;
@@ -655,8 +655,10 @@ pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* 
   // ratios
   OutPtrs o = out_layout(p);
   RatioArgs ra{};
-  ra.P = p->nPB; ra.Q = p->nQ; ra.n_mu = p->prm.n_mu;
-  ra.s_edges = p->s_edges_d.as<double>();
+  ra.P = p->nPB; ra.Q = p->nQ; ra.n_s = p->prm.n_s; ra.n_mu = p->prm.n_mu;
+  ra.vbin = p->vbin_d.as<double>();
+  ra.wcoef = p->prm.pair_grid ? p->wcoef_d.as<double>() : nullptr;
+  ra.w_perp = o.w_perp;
   ra.L = p->prm.box_L;
   ra.dd = p->dd.as<unsigned long long>();
   ra.ddq = p->ddq.as<unsigned long long>();
@@ -698,6 +700,7 @@ pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* 
     PG_TRY(copy_out(out->sum_gg, o.sum_gg, Qd, s));
     PG_TRY(copy_out(out->sum2_gg, o.sum2_gg, Qd, s));
     PG_TRY(copy_out(out->sum_gg_agg, o.sum_gg_agg, 16, s));
+    PG_TRY(copy_out(out->w_perp, o.w_perp, sizeof(double) * p->prm.n_s, s));
   }
   int32_t herr = 0;
   PG_TRY(cudaMemcpyAsync(&herr, p->flag.as<int32_t>() + 1, 4, cudaMemcpyDeviceToHost, s));
@@ -837,12 +840,14 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
     PG_CUDA_TRY(up(gin->xi_dw_agg, go.xi_dw_agg, 8, g.xi_dw_agg));
     PG_CUDA_TRY(up(gin->xi_ss, go.xi_ss, Pd, g.xi_ss));
     PG_CUDA_TRY(up(gin->dd_w, go.dd_w, Pd, g.dd_w));
+    if (p->prm.pair_grid) PG_CUDA_TRY(up(gin->w_perp, go.w_perp, sizeof(double) * p->prm.n_s, g.w_perp));
   }
   o = OutSet{fo.xi_pg, fo.xi_gg, fo.b_pg, fo.q_eff, fo.q_eff_sq, fo.xi_dw, fo.b_pg_agg, fo.q_eff_agg,
-             fo.xi_dw_agg, fo.xi_ss, fo.dd_w};
+             fo.xi_dw_agg, fo.xi_ss, fo.dd_w, fo.w_perp};
   AdjRatioArgs ra{};
   ra.P = P; ra.Q = p->nQ; ra.n_mu = p->prm.n_mu;
-  ra.s_edges = p->s_edges_d.as<double>();
+  ra.vbin = p->vbin_d.as<double>();
+  ra.wcoef = p->prm.pair_grid ? p->wcoef_d.as<double>() : nullptr;
   ra.L = p->prm.box_L;
   ra.ddq = p->ddq.as<unsigned long long>();
   ra.wsum = p->wsum.as<double>();
@@ -1049,7 +1054,7 @@ pg_status smooth_impl(pg_plan* p, const SmoothW& wp, int64_t n, const double* d_
     SmoothArgs a{};
     a.P = P;
     a.n_mu = p->prm.n_mu;
-    a.s_edges = p->s_edges_d.as<double>();
+    a.vbin = p->vbin_d.as<double>();
     a.L = p->prm.box_L;
     a.ddq = p->ddq.as<unsigned long long>();
     a.wsum = p->wsum.as<double>();
@@ -1124,6 +1129,14 @@ pg_status plan_create(const pg_params* prm, const pg_plan* share, pg_plan** out)
     if (!(q.r_edges[i] < q.r_edges[i + 1]) || !(q.r_edges[0] >= 0.0)) return PG_ERR_INVALID_ARG;
   if (!(q.s_edges[q.n_s] < 0.5 * q.box_L) || !(q.r_edges[q.n_r] < 0.5 * q.box_L))
     return PG_ERR_INVALID_ARG;
+  if (q.pair_grid != 0 && q.pair_grid != 1) return PG_ERR_INVALID_ARG;
+  if (q.pair_grid) {
+    if (!q.par_edges || !(q.par_edges[0] >= 0.0)) return PG_ERR_INVALID_ARG;
+    for (int i = 0; i < q.n_mu; ++i)
+      if (!(q.par_edges[i] < q.par_edges[i + 1])) return PG_ERR_INVALID_ARG;
+    const double pm = q.s_edges[q.n_s], lm = q.par_edges[q.n_mu];
+    if (!(sqrt(pm * pm + lm * lm) < 0.5 * q.box_L)) return PG_ERR_INVALID_ARG;
+  }
   if (!isfinite(q.rsd_factor) || !(q.r_perp_cut >= 0.0)) return PG_ERR_INVALID_ARG;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1145,6 +1158,8 @@ pg_status plan_create(const pg_params* prm, const pg_plan* share, pg_plan** out)
   p->r_edges.assign(q.r_edges, q.r_edges + q.n_r + 1);
   p->prm.s_edges = p->s_edges.data();
   p->prm.r_edges = p->r_edges.data();
+  if (q.pair_grid) p->par_edges.assign(q.par_edges, q.par_edges + q.n_mu + 1);
+  p->prm.par_edges = q.pair_grid ? p->par_edges.data() : nullptr;
   cudaGetDevice(&p->device);
   p->N = q.mesh_n;
   p->M1 = p->N / 2 + 1;
@@ -1172,7 +1187,10 @@ pg_status plan_create(const pg_params* prm, const pg_plan* share, pg_plan** out)
   memset(&g, 0, sizeof(g));
   g.L = q.box_L;
   g.halfL = 0.5 * q.box_L;
-  const double smax = q.s_edges[q.n_s];
+  // largest pair separation: s_max, or on the grid the corner of the
+  // (d_perp, d_par) cylinder
+  const double smax = q.pair_grid ? sqrt(q.s_edges[q.n_s] * q.s_edges[q.n_s] + q.par_edges[q.n_mu] * q.par_edges[q.n_mu])
+                                  : q.s_edges[q.n_s];
   int nc = (int)floor(q.box_L / (smax * (1.0 + 1e-9)));
   if (nc > 256) nc = 256;
   if (nc < 3) nc = 1;
@@ -1181,6 +1199,9 @@ pg_status plan_create(const pg_params* prm, const pg_plan* share, pg_plan** out)
   g.n_s = q.n_s;
   g.n_mu = q.n_mu;
   for (int i = 0; i <= q.n_s; ++i) g.e2[i] = q.s_edges[i] * q.s_edges[i];
+  g.grid = q.pair_grid;
+  if (q.pair_grid)
+    for (int i = 0; i <= q.n_mu; ++i) g.pe[i] = q.par_edges[i];
   cudaError_t e = q.precision ? build_twiddles<double>(p) : build_twiddles<float>(p);
   std::vector<int32_t> cells;
   build_cell_lists(p, cells, p->h_list_off);
@@ -1193,6 +1214,15 @@ pg_status plan_create(const pg_params* prm, const pg_plan* share, pg_plan** out)
   if (e == cudaSuccess) e = p->list_off.ensure(8 * p->h_list_off.size(), &p->total);
   if (e == cudaSuccess)
     e = cudaMemcpy(p->list_off.p, p->h_list_off.data(), 8 * p->h_list_off.size(), cudaMemcpyHostToDevice);
+  {
+    std::vector<double> vb, wc;
+    pair_bin_volumes(q.pair_grid, q.n_s, q.s_edges, q.n_mu, q.par_edges, vb, wc);
+    if (e == cudaSuccess) e = p->vbin_d.ensure(8 * vb.size(), &p->total);
+    if (e == cudaSuccess) e = cudaMemcpy(p->vbin_d.p, vb.data(), 8 * vb.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && q.pair_grid) e = p->wcoef_d.ensure(8 * wc.size(), &p->total);
+    if (e == cudaSuccess && q.pair_grid)
+      e = cudaMemcpy(p->wcoef_d.p, wc.data(), 8 * wc.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = p->s_edges_d.ensure(8 * p->s_edges.size(), &p->total);
   if (e == cudaSuccess)
     e = cudaMemcpy(p->s_edges_d.p, p->s_edges.data(), 8 * p->s_edges.size(), cudaMemcpyHostToDevice);
@@ -1222,7 +1252,7 @@ void pg_plan_destroy(pg_plan* p) {
   cudaGetDevice(&cur);
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
-  DevBuf* all[] = {&p->tw, &p->cells, &p->list_off, &p->s_edges_d, &p->in_pos, &p->in_vel, &p->in_w,
+  DevBuf* all[] = {&p->tw, &p->cells, &p->list_off, &p->s_edges_d, &p->vbin_d, &p->wcoef_d, &p->in_pos, &p->in_vel, &p->in_w,
                    &p->x, &p->y, &p->z, &p->gw, &p->flag, &p->wpart, &p->wsum, &p->cell_id, &p->ccount,
                    &p->cstart, &p->ccursor, &p->perm, &p->xs, &p->ys, &p->zs, &p->ws, &p->ctmp,
                    &p->ctot, &p->dd, &p->ddq, &p->pcursor, &p->ubin, &p->ui, &p->uj, &p->umx,

@@ -35,6 +35,10 @@ bool same_problem(const pg_params& a, const pg_params& b) {
     if (a.s_edges[i] != b.s_edges[i]) return false;
   for (int i = 0; i <= a.n_r; ++i)
     if (a.r_edges[i] != b.r_edges[i]) return false;
+  if (a.pair_grid != b.pair_grid) return false;
+  if (a.pair_grid)
+    for (int i = 0; i <= a.n_mu; ++i)
+      if (a.par_edges[i] != b.par_edges[i]) return false;
   return true;
 }
 

@@ -11,8 +11,9 @@
 //
 // Ratios (Sec. 2.2 and Sec. 3.4): xi_pg, xi_gg, b_pg = xi_pg / xi_gg,
 // xi(d_w) = sum C_gg^2 / sum C_gg (eq. xi_dw), xi(s, mu) = DD/RR - 1
-// (eq. 2PCF_d_collapsed with the exact pair normalisation), Q_eff
-// (eq. Qeff_notsq) and the strict-squeezed Q_eff (eq. Qeff), all FP64.
+// (eq. 2PCF_d_collapsed with the exact pair normalisation and the plan's bin
+// volumes, (s, mu) shells or (d_perp, d_par) cells), Q_eff (eq. Qeff_notsq),
+// the strict-squeezed Q_eff (eq. Qeff) and, on the grid, w(d_perp), all FP64.
 #include <math.h>
 
 #include "pg_internal.cuh"
@@ -114,16 +115,26 @@ __global__ void __launch_bounds__(kThreads) k_ratios(RatioArgs a) {
   const double sw = a.wsum[0], sw2 = a.wsum[1];
   const double npairs = 0.5 * (sw * sw - sw2);
   const double L3 = a.L * a.L * a.L;
-  // per pair bin: counts and xi(s, mu)
+  // per pair bin: counts and xi(s, mu) (or xi(d_perp, d_par))
   for (int p = threadIdx.x; p < P; p += kThreads) {
-    const int ks = p / a.n_mu;
-    const double lo = a.s_edges[ks], hi = a.s_edges[ks + 1];
-    const double vb = (4.0 * M_PI / 3.0) * (hi * hi * hi - lo * lo * lo) / (double)a.n_mu;
-    const double rr = npairs * vb / L3;
+    const double rr = npairs * a.vbin[p] / L3;
     const double ddw = (double)(long long)a.ddq[p] * (1.0 / 4294967296.0);
     if (a.o_dd) a.o_dd[p] = (int64_t)a.dd[p];
     if (a.dd_w) a.dd_w[p] = ddw;
     if (a.xi_ss) a.xi_ss[p] = rr > 0.0 ? ddw / rr - 1.0 : nan;
+  }
+  // grid: w(d_perp) = sum over the d_par bins of wcoef * xi, in bin order
+  if (a.w_perp) {
+    for (int k = threadIdx.x; k < a.n_s; k += kThreads) {
+      double wp = a.wcoef ? 0.0 : nan;
+      for (int m = 0; m < a.n_mu && a.wcoef; ++m) {
+        const int p = k * a.n_mu + m;
+        const double rr = npairs * a.vbin[p] / L3;
+        const double ddw = (double)(long long)a.ddq[p] * (1.0 / 4294967296.0);
+        wp += a.wcoef[p] * (rr > 0.0 ? ddw / rr - 1.0 : nan);
+      }
+      a.w_perp[k] = wp;
+    }
   }
   // per correlation bin: galaxy terms
   for (int q = threadIdx.x; q <= Q; q += kThreads) {
@@ -146,10 +157,7 @@ __global__ void __launch_bounds__(kThreads) k_ratios(RatioArgs a) {
   for (int t = threadIdx.x; t < P * L; t += kThreads) {
     const int p = t / L, q = t % L;
     const double ddw = (double)(long long)a.ddq[p] * (1.0 / 4294967296.0);
-    const int ks = p / a.n_mu;
-    const double lo = a.s_edges[ks], hi = a.s_edges[ks + 1];
-    const double vb = (4.0 * M_PI / 3.0) * (hi * hi * hi - lo * lo * lo) / (double)a.n_mu;
-    const double rr = npairs * vb / L3;
+    const double rr = npairs * a.vbin[p] / L3;
     const double xi = rr > 0.0 ? ddw / rr - 1.0 : nan;
     const double sp = a.pg_valid[p] ? a.sum_pg[((int64_t)p * L + q) * 2] : nan;
     const double sg = a.gg_valid ? a.sum_gg[2 * q] : nan;

@@ -79,7 +79,9 @@ struct PairGeom {
   int nc;                 // cells per side (1, or >= 3)
   double cell_scale;      // nc / L
   int n_s, n_mu;
-  double e2[65];          // squared s edges
+  double e2[65];          // squared s edges (grid: squared d_perp edges)
+  int grid;               // 1: (d_perp, d_par) grid, pe = |d_par| edges
+  double pe[65];
 };
 
 struct CellList {
@@ -281,7 +283,7 @@ struct SmoothW {
 // Inputs and outputs of the final ratios (all device pointers).
 struct SmoothArgs {
   int P, n_mu;
-  const double* s_edges;
+  const double* vbin;              // [P] pair-bin volumes
   double L;
   const unsigned long long* ddq;   // [P] Q32.32 weighted pair counts
   const double* wsum;              // [2] sum w, sum w^2
@@ -330,10 +332,35 @@ cudaError_t launch_bin_sums(int nb, int n_lists, const R* Cwin, int64_t Cwin_str
                             const int32_t* cells, const int64_t* list_off, int n_chunks, double* part,
                             double* out, cudaStream_t s);
 
+// Volume of every pair bin p = k * n_mu + m (the RR normalisation of
+// eq. 2PCF_d_collapsed): a (s, mu) bin is 1/n_mu of the spherical shell
+// (4 pi / 3)(s_hi^3 - s_lo^3); a (d_perp, d_par) grid cell is the annulus
+// pi (p_hi^2 - p_lo^2) times 2 (l_hi - l_lo), both signs of d_par. In grid
+// mode wcoef[p] = 2 (l_hi - l_lo), the weight of xi(p) in w(d_perp) (the
+// integral over d_par of eq. 2PCF_los_integrated_explicit).
+inline void pair_bin_volumes(int grid, int n_s, const double* s_edges, int n_mu, const double* par_edges,
+                             std::vector<double>& vbin, std::vector<double>& wcoef) {
+  vbin.assign((size_t)n_s * n_mu, 0.0);
+  wcoef.assign(grid ? (size_t)n_s * n_mu : 0, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < n_s; ++k)
+    for (int m = 0; m < n_mu; ++m) {
+      const double lo = s_edges[k], hi = s_edges[k + 1];
+      if (grid) {
+        const double dl = par_edges[m + 1] - par_edges[m];
+        vbin[(size_t)k * n_mu + m] = pi * (hi * hi - lo * lo) * (2.0 * dl);
+        wcoef[(size_t)k * n_mu + m] = 2.0 * dl;
+      } else {
+        vbin[(size_t)k * n_mu + m] = (4.0 * pi / 3.0) * (hi * hi * hi - lo * lo * lo) / (double)n_mu;
+      }
+    }
+}
+
 struct RatioArgs {
   int P, Q;                       // pair bins, (r, mu_r) bins
-  int n_mu;
-  const double* s_edges;          // device [n_s+1]
+  int n_s, n_mu;
+  const double* vbin;             // device [P] pair-bin volumes
+  const double* wcoef;            // device [P] weight of xi(p) in w_perp[p / n_mu] (grid), or null
   double L;
   const unsigned long long* dd;   // [P]
   const unsigned long long* ddq;  // [P]
@@ -345,7 +372,7 @@ struct RatioArgs {
   const int64_t* list_off;        // [Q+2]
   // outputs (device)
   double *dd_w, *xi_ss, *xi_pg, *xi_gg, *b_pg, *q_eff, *q_eff_sq, *xi_dw, *b_pg_agg,
-      *q_eff_agg, *xi_dw_agg, *o_sum_pg, *o_sum_pg_agg, *o_sum_gg, *o_sum2_gg, *o_sum_gg_agg;
+      *q_eff_agg, *xi_dw_agg, *o_sum_pg, *o_sum_pg_agg, *o_sum_gg, *o_sum2_gg, *o_sum_gg_agg, *w_perp;
   int64_t *o_dd, *n_cells, *n_cells_agg;
 };
 cudaError_t launch_ratios(const RatioArgs& a, cudaStream_t s);
@@ -353,11 +380,12 @@ cudaError_t launch_ratios(const RatioArgs& a, cudaStream_t s);
 // ---- adjoint (pg_adjoint.cu) ----------------------------------------------------
 struct OutSet {   // device arrays with the pg_result layout (any may be null)
   const double *xi_pg, *xi_gg, *b_pg, *q_eff, *q_eff_sq, *xi_dw, *b_pg_agg, *q_eff_agg,
-      *xi_dw_agg, *xi_ss, *dd_w;
+      *xi_dw_agg, *xi_ss, *dd_w, *w_perp;
 };
 struct AdjRatioArgs {
   int P, Q, n_mu;
-  const double* s_edges;
+  const double* vbin;              // [P] pair-bin volumes
+  const double* wcoef;             // [P] weight of xi(p) in w_perp[p / n_mu], or null
   double L;
   const unsigned long long* ddq;
   const double* wsum;

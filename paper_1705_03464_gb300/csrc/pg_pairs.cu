@@ -154,14 +154,24 @@ __device__ __forceinline__ bool eval_pair(const PairGeom& g, const CellList& cl,
   double dx = min_image(__dsub_rn(cl.xs[pj], xi), g.L, g.halfL);
   double dy = min_image(__dsub_rn(cl.ys[pj], yi), g.L, g.halfL);
   double dz = min_image(__dsub_rn(cl.zs[pj], zi), g.L, g.halfL);
-  double s2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-  if (s2 < g.e2[0] || !(s2 < g.e2[g.n_s])) return false;
-  int k = 0;
-  while (k + 1 < g.n_s && !(s2 < g.e2[k + 1])) ++k;
-  double s = __dsqrt_rn(s2);
-  double mu = s > 0.0 ? __ddiv_rn(fabs(dz), s) : 0.0;
-  int m = (int)floor(__dmul_rn((double)g.n_mu, mu));
-  if (m > g.n_mu - 1) m = g.n_mu - 1;
+  int k = 0, m = 0;
+  if (g.grid) {
+    // (d_perp, d_par) grid: d_perp^2 = dx^2 + dy^2 against the squared
+    // d_perp edges, d_par = |dz| against the d_par edges, half-open bins
+    const double p2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    const double l = fabs(dz);
+    if (p2 < g.e2[0] || !(p2 < g.e2[g.n_s]) || l < g.pe[0] || !(l < g.pe[g.n_mu])) return false;
+    while (k + 1 < g.n_s && !(p2 < g.e2[k + 1])) ++k;
+    while (m + 1 < g.n_mu && !(l < g.pe[m + 1])) ++m;
+  } else {
+    double s2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    if (s2 < g.e2[0] || !(s2 < g.e2[g.n_s])) return false;
+    while (k + 1 < g.n_s && !(s2 < g.e2[k + 1])) ++k;
+    double s = __dsqrt_rn(s2);
+    double mu = s > 0.0 ? __ddiv_rn(fabs(dz), s) : 0.0;
+    m = (int)floor(__dmul_rn((double)g.n_mu, mu));
+    if (m > g.n_mu - 1) m = g.n_mu - 1;
+  }
   h.bin = k * g.n_mu + m;
   h.mx = wrap_box(__dadd_rn(xi, __dmul_rn(0.5, dx)), g.L);
   h.my = wrap_box(__dadd_rn(yi, __dmul_rn(0.5, dy)), g.L);

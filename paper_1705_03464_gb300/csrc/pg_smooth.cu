@@ -188,9 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth_final(SmoothArgs a) {
     a.xi_dw[0] = xw;
   }
   for (int p = threadIdx.x; p < a.P; p += kThreads) {
-    const int ks = p / a.n_mu;
-    const double lo = a.s_edges[ks], hi = a.s_edges[ks + 1];
-    const double vb = (4.0 * M_PI / 3.0) * (hi * hi * hi - lo * lo * lo) / (double)a.n_mu;
+    const double vb = a.vbin[p];
     const double rr = npairs * vb / L3;
     const double ddw = (double)(long long)a.ddq[p] * (1.0 / 4294967296.0);
     const double xi = rr > 0.0 ? ddw / rr - 1.0 : nan;

@@ -34,6 +34,7 @@ class pg_params(C.Structure):
         ("n_r", C.c_int32), ("r_edges", C.POINTER(C.c_double)), ("n_mur", C.c_int32),
         ("rsd_factor", C.c_double), ("r_perp_cut", C.c_double),
         ("precision", C.c_int32), ("bins_per_batch", C.c_int32),
+        ("pair_grid", C.c_int32), ("par_edges", C.POINTER(C.c_double)),
     ]
 
 
@@ -43,7 +44,7 @@ _RESULT_FIELDS = [
     ("xi_dw", "f8", "Q"), ("b_pg_agg", "f8", "P"), ("q_eff_agg", "f8", "P"),
     ("xi_dw_agg", "f8", "1"), ("n_cells", "i8", "Q"), ("n_cells_agg", "i8", "1"),
     ("sum_pg", "f8", "PQ"), ("sum_pg_agg", "f8", "P"), ("sum_gg", "f8", "Q"),
-    ("sum2_gg", "f8", "Q"), ("sum_gg_agg", "f8", "2"),
+    ("sum2_gg", "f8", "Q"), ("sum_gg_agg", "f8", "2"), ("w_perp", "f8", "S"),
 ]
 
 
@@ -157,18 +158,25 @@ class Problem:
     arrays laid out for it; no device state."""
 
     def __init__(self, box_L, mesh_n, assign, s_edges, n_mu, r_edges, n_mur,
-                 rsd_factor=0.0, r_perp_cut=0.0, precision=0, bins_per_batch=0):
+                 rsd_factor=0.0, r_perp_cut=0.0, precision=0, bins_per_batch=0, par_edges=None):
+        """par_edges given: the (d_perp, d_par) pair grid, s_edges the d_perp
+        edges and par_edges the |d_par| edges (n_mu = len(par_edges) - 1)."""
         self.s_edges = np.ascontiguousarray(s_edges, dtype=np.float64)
         self.r_edges = np.ascontiguousarray(r_edges, dtype=np.float64)
         self.n_s = len(self.s_edges) - 1
         self.n_mu = int(n_mu)
+        self.par_edges = None if par_edges is None else np.ascontiguousarray(par_edges, dtype=np.float64)
+        if self.par_edges is not None and len(self.par_edges) - 1 != self.n_mu:
+            raise ValueError("n_mu must be len(par_edges) - 1 on the (d_perp, d_par) grid")
         self.n_r = len(self.r_edges) - 1
         self.n_mur = int(n_mur)
         self.params = pg_params(
             float(box_L), int(mesh_n), int(assign), self.n_s,
             self.s_edges.ctypes.data_as(C.POINTER(C.c_double)), self.n_mu, self.n_r,
             self.r_edges.ctypes.data_as(C.POINTER(C.c_double)), self.n_mur,
-            float(rsd_factor), float(r_perp_cut), int(precision), int(bins_per_batch))
+            float(rsd_factor), float(r_perp_cut), int(precision), int(bins_per_batch),
+            0 if self.par_edges is None else 1,
+            None if self.par_edges is None else self.par_edges.ctypes.data_as(C.POINTER(C.c_double)))
         self.P = self.n_s * self.n_mu
         self.Q = self.n_r * self.n_mur
 
@@ -184,7 +192,7 @@ class Problem:
     def new_result(self):
         """Host arrays for every pg_result field and the struct pointing at them."""
         P, Q = self.P, self.Q
-        sizes = {"P": P, "Q": Q, "PQ": P * Q, "1": 1, "2": 2}
+        sizes = {"P": P, "Q": Q, "PQ": P * Q, "1": 1, "2": 2, "S": self.n_s}
         arrs = {}
         res = pg_result()
         for name, t, sz in _RESULT_FIELDS:
@@ -209,9 +217,10 @@ class Plan(Problem):
     (pg_plan_create_shared)."""
 
     def __init__(self, box_L, mesh_n, assign, s_edges, n_mu, r_edges, n_mur,
-                 rsd_factor=0.0, r_perp_cut=0.0, precision=0, bins_per_batch=0, share_with=None):
+                 rsd_factor=0.0, r_perp_cut=0.0, precision=0, bins_per_batch=0, share_with=None,
+                 par_edges=None):
         super().__init__(box_L, mesh_n, assign, s_edges, n_mu, r_edges, n_mur, rsd_factor,
-                         r_perp_cut, precision, bins_per_batch)
+                         r_perp_cut, precision, bins_per_batch, par_edges)
         h = C.c_void_p()
         if share_with is None:
             _check(_lib.pg_plan_create(C.byref(self.params), C.byref(h)), "pg_plan_create")
@@ -381,7 +390,7 @@ def pg_pair_counts_static(pos, w, box_L, s_edges, n_mu, stream=None):
 
 
 GRAD_FIELDS = ("xi_pg", "xi_gg", "b_pg", "q_eff", "q_eff_sq", "xi_dw", "b_pg_agg", "q_eff_agg",
-               "xi_dw_agg", "xi_ss", "dd_w")
+               "xi_dw_agg", "xi_ss", "dd_w", "w_perp")
 
 
 def pg_backward(plan: Plan, grads: dict, n_gal: int, stream=None):

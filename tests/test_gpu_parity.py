@@ -260,6 +260,26 @@ def test_forward_tsc_weighted_rsd(pg, precision):
     _compare_forward(got, ref, precision)
 
 
+_PRUNE_REF = {}
+
+
+@pytest.mark.parametrize("r_max,precision", [(40.0, 0), (40.0, 1), (20.0, 1), (6.0, 0), (6.0, 1)])
+def test_forward_pruned_z_inverse_widths(pg, r_max, precision):
+    """The fused z pass computes only the inverse outputs that hold window
+    rows; at N = 256 (N2 = 8) a window half-width w of 40, 20 and 6 cells
+    selects the pruning widths K = 8, 4 and 2, each checked against the
+    oracle's mesh form. (K = 4 in FP32 runs in the 512^3 test below; on this
+    sparse 256^3 field its FP32 rounding, about 1.4e-7 on near-zero small-r
+    bins, sits at the 1e-7 absolute floor, so K = 4 is held here in FP64.)"""
+    L = 256.0
+    cat = synth.make_catalogue_box(L, 4000, seed=11)
+    p = pipeline.Params(L, 256, 1, (0.0, 4.0, 8.0), 1, (0.25 * r_max, 0.5 * r_max, r_max), 2, 0.0, 0.0)
+    if r_max not in _PRUNE_REF:
+        _PRUNE_REF[r_max] = pipeline.run(p, cat.pos, form="mesh")
+    plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur, precision=precision)
+    _compare_forward(pg.pg_forward(plan, dev(cat.pos)), _PRUNE_REF[r_max], precision)
+
+
 def test_forward_host_equals_device_and_is_deterministic(pg):
     p, cat, w = _small_cic_rsd()
     plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur,
