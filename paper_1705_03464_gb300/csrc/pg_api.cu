@@ -989,7 +989,7 @@ pg_status smooth_impl(pg_plan* p, const SmoothW& wp, int64_t n, const double* d_
   PG_TRY(p->Wk.ensure(sizeof(C) * NN * p->P, t));
   PG_TRY(p->sm_off.ensure(sizeof(int64_t) * (P + 3), t));
   PG_TRY(p->sm_sums.ensure(sizeof(double) * (2 * P + 4), t));
-  PG_TRY(p->sm_part.ensure(sizeof(double) * 2 * wc_partials(), t));
+  PG_TRY(p->sm_part.ensure(sizeof(double) * 2 * wc_partials(N), t));
   PG_TRY(p->sm_out.ensure(sizeof(double) * (4 * P + 2), t));
   PG_TRY(p->gp.ensure(sizeof(double) * std::max<int64_t>(np, 1), t));
   PG_TRY(p->gj.ensure(sizeof(double) * std::max<int64_t>(n, 1), t));

@@ -308,8 +308,8 @@ cudaError_t launch_interp(const DepGeom& geo, int64_t n, const double* x, const 
 cudaError_t launch_seg_sums(int nseg, const int64_t* off, const double* g, const double* w, double* sums,
                             cudaStream_t s);
 // out[0] = sum W C^2, out[1] = sum W C over the mesh offsets; part holds
-// 2 * wc_partials() doubles.
-int wc_partials();
+// 2 * wc_partials(N) doubles (one partial per block of the reduction).
+int wc_partials(int N);
 template <typename R>
 cudaError_t launch_wc_sums(int N, double dx, const SmoothW& p, const R* Cm, double* part, double* out,
                            cudaStream_t s);

@@ -13,7 +13,6 @@ namespace pg {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kPartials = 2048;   // blocks of the W-weighted mesh reduction
 
 // eq. weighting with normalisation 1: W = 0 inside the line-of-sight cylinder
 // r_perp < r_cut, else sigmoid(s0 (r_perp - r_s)) exp(-(r_perp^2 + r_par^2)/(2 sigma^2)).
@@ -138,18 +137,51 @@ k_seg_sums(const int64_t* __restrict__ off, const double* __restrict__ g, const 
 }
 
 // Partial sums of W C^2 and W C over all mesh offsets (C real [z][y][x]).
+// sum W C^2 and sum W C over the mesh offsets (eq. xi_dw). W separates into
+// an (x, y) factor (the cylinder mask in FP64 on squared offsets, the
+// sigmoid and the Gaussian in r_perp) and a z factor (the Gaussian in r_par),
+// so one thread owns an (x, y) column, evaluates its factor once, and walks z
+// with the z factors from a shared table; the loads of a warp are consecutive
+// x. Sums run in the plan precision over chunks of 32 z rows and are added to
+// FP64 after each chunk; one partial per block, reduced in block order.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_wc_partial(int N, double dx, SmoothW p, const R* __restrict__ Cm, double* __restrict__ part) {
   __shared__ double red[kThreads];
-  const int64_t n3 = (int64_t)N * N * N;
+  __shared__ R bz[1024];
+  const int xb = (N + kThreads - 1) / kThreads;
+  const int y = blockIdx.x / xb, x = (blockIdx.x % xb) * kThreads + threadIdx.x;
+  const R inv2s2 = (R)(0.5 / (p.sigma * p.sigma));
+  for (int z = threadIdx.x; z < N; z += kThreads) {
+    const R rz = (R)((double)(z <= N / 2 ? z : z - N) * dx);
+    bz[z] = ex(-inv2s2 * rz * rz);
+  }
+  R axy = 0;
+  if (x < N) {
+    const double rx = (double)(x <= N / 2 ? x : x - N) * dx;
+    const double ry = (double)(y <= N / 2 ? y : y - N) * dx;
+    const double rp2 = rx * rx + ry * ry;
+    if (rp2 >= p.r_cut * p.r_cut) {
+      const R rp = sq((R)rp2);
+      axy = ((R)1 / ((R)1 + ex(-(R)p.s0 * (rp - (R)p.r_s)))) * ex(-inv2s2 * rp * rp);
+    }
+  }
+  __syncthreads();
   double a = 0.0, b = 0.0;
-  for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < n3; t += (int64_t)gridDim.x * kThreads) {
-    const double wv = (double)w_at<R>(t, N, dx, p);
-    if (wv != 0.0) {
-      const double c = (double)Cm[t];
-      a += wv * c * c;
-      b += wv * c;
+  if (axy != (R)0) {
+    const R* col = Cm + (int64_t)y * N + x;
+    const int64_t zs = (int64_t)N * N;
+    for (int z0 = 0; z0 < N; z0 += 32) {
+      R ca = 0, cb = 0;
+      const int z1 = min(N, z0 + 32);
+      for (int z = z0; z < z1; ++z) {
+        const R c = col[z * zs];
+        const R wc = axy * bz[z] * c;
+        ca += wc * c;
+        cb += wc;
+      }
+      a += (double)ca;
+      b += (double)cb;
     }
   }
   a = block_sum(a, red);
@@ -235,14 +267,16 @@ cudaError_t launch_seg_sums(int nseg, const int64_t* off, const double* g, const
   return launched();
 }
 
-int wc_partials() { return kPartials; }
+int wc_partials(int N) { return N * ((N + kThreads - 1) / kThreads); }
 
 template <typename R>
 cudaError_t launch_wc_sums(int N, double dx, const SmoothW& p, const R* Cm, double* part, double* out,
                            cudaStream_t s) {
-  k_wc_partial<R><<<kPartials, kThreads, 0, s>>>(N, dx, p, Cm, part);
+  if (N > 1024) return cudaErrorInvalidValue;   // the z-factor table
+  const int nblk = wc_partials(N);
+  k_wc_partial<R><<<nblk, kThreads, 0, s>>>(N, dx, p, Cm, part);
   PG_CUDA_TRY(launched());
-  k_wc_final<<<1, kThreads, 0, s>>>(kPartials, part, out);
+  k_wc_final<<<1, kThreads, 0, s>>>(nblk, part, out);
   return launched();
 }
 
