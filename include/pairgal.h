@@ -205,6 +205,27 @@ pg_status pg_forward_smooth(pg_plan* plan, const pg_smooth_params* w, int64_t n_
                             const float* d_vel, const float* d_w, pg_smooth_result* host_out,
                             void* stream);
 
+/* Adjoint of the last successful pg_forward_smooth call on this plan (same
+ * catalogue, still held in the plan's buffers): with the upstream gradients
+ * in *grad_out (HOST arrays in the pg_smooth_result layout; the fields
+ * xi_ss, num, b_pg, q_eff [P], den, xi_dw [1] are read, NULL means zero, dd is
+ * ignored), writes d_grad_w[n_gal] (device FP64) = dL/dw_i for L = sum over
+ * fields and bins of grad * output, outputs that are NaN contributing
+ * nothing. The reverse sweep follows the forward's steps backwards (Sec. 2.1
+ * eq. bpg_final, Sec. 3.6 eq. weighting, eqs. xi_dw, Qeff_notsq,
+ * 2PCF_d_collapsed): ratio outputs -> the bin means and xi -> the adjoint
+ * weights of G = W * delta_g at the pair midpoints and galaxies, deposited on
+ * the mesh (the transpose of the interpolation) -> the W convolution (W is
+ * real and even, so the operator is its own adjoint) together with the xi_w
+ * term delta_bar += (2 / N^3) Cbar * delta (Cbar = d xi_w / d C_gg) in one
+ * k-space combination -> the rho / Q normalisation at the galaxies and the
+ * pair-weight chain w_p = w_i w_j. Without weights in the forward call the
+ * gradient is taken at w = 1. The Q32.32 rounding of the deposit is treated
+ * as exact. Errors: PG_ERR_INVALID_ARG if no smooth forward call preceded
+ * (or another entry point reused the plan since), PG_ERR_UNSUPPORTED,
+ * PG_ERR_OOM, PG_ERR_CUDA, PG_ERR_TIMEOUT. Synchronises the stream. */
+pg_status pg_backward_smooth(pg_plan* plan, const pg_smooth_result* grad_out, double* d_grad_w, void* stream);
+
 /* Adjoint of the last successful pg_forward / pg_forward_host call on this
  * plan (same catalogue, still held in the plan's buffers): with the upstream
  * gradients in *grad_out (HOST arrays in the pg_result layout; the fields

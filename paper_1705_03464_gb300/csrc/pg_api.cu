@@ -140,6 +140,14 @@ struct pg_plan {
   DevBuf Wk, Gs, sm_off, sm_sums, sm_part, sm_out;
   SmoothW wk_key{};
   bool wk_valid = false;
+  // the last successful pg_forward_smooth call, which pg_backward_smooth
+  // differentiates (its G at the points, sums and outputs stay in the plan);
+  // adjoint scratch: upstream gradients, scalar adjoints, point adjoints,
+  // two dense meshes and two spectra
+  bool smooth_ok = false;
+  SmoothW smooth_w{};
+  int64_t smooth_np = 0;
+  DevBuf sa_g, sa_v, sa_gp, sa_gj, sa_fj, sa_mesh, sa_spec;
   // state of the last successful forward call, which pg_backward differentiates
   bool fwd_ok = false, last_has_w = false;
   int64_t last_n = 0;
@@ -615,6 +623,7 @@ pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* 
   int64_t np = 0;
   int nonfinite = 0;
   p->fwd_ok = false;
+  p->smooth_ok = false;
   prof_begin(p);
   const long long launches0 = launch_counter().load();
   PG_TRY(positions_and_pairs(p, n, d_pos, d_vel, d_w, hdd, &np, &nonfinite, s));
@@ -976,6 +985,7 @@ pg_status smooth_impl(pg_plan* p, const SmoothW& wp, int64_t n, const double* d_
   int64_t np = 0;
   int nonfinite = 0;
   p->fwd_ok = false;
+  p->smooth_ok = false;
   prof_begin(p);
   const long long launches0 = launch_counter().load();
   PG_TRY(positions_and_pairs(p, n, d_pos, d_vel, d_w, hdd, &np, &nonfinite, s));
@@ -1083,11 +1093,116 @@ pg_status smooth_impl(pg_plan* p, const SmoothW& wp, int64_t n, const double* d_
   }
   out->den[0] = h[4 * P];
   out->xi_dw[0] = h[4 * P + 1];
+  p->smooth_ok = true;
+  p->smooth_w = wp;
+  p->smooth_np = np;
+  p->last_n = n;
+  p->last_has_w = d_w != nullptr;
   p->last_launches = launch_counter().load() - launches0;
   if (p->prof_on) prof_end(p);
   else
     for (int f = 0; f < PG_N_FAMILIES; ++f) p->stats[f].bytes = p->fam_bytes[f];
   return PG_OK;
+}
+
+// Reverse sweep of the last pg_forward_smooth call (see pg_backward_smooth in
+// pairgal.h): ratio adjoints -> pair terms, their weight chain and the
+// adjoint weights of G at the points -> their deposit -> in k space the
+// W convolution of that mesh plus the xi_w term 2/N^3 Cbar * delta -> fbar ->
+// the rho / Q chain at the galaxies.
+template <typename R>
+cudaError_t smooth_backward_impl(pg_plan* p, const pg_smooth_result* gin, double* wbar, cudaStream_t s) {
+  using C = typename CT<R>::C;
+  const C* tw = p->tw.as<C>();
+  const int N = p->N, P = p->nPB;
+  const int64_t n = p->last_n, np = p->smooth_np;
+  const int64_t NN = (int64_t)N * N, N3 = NN * N, spec = NN * p->P;
+  const double n3 = (double)N3;
+  size_t* t = &p->total;
+  PG_CUDA_TRY(p->sa_g.ensure(sizeof(double) * (4 * P + 2), t));
+  PG_CUDA_TRY(p->sa_v.ensure(sizeof(double) * (3 * P + 5), t));
+  PG_CUDA_TRY(p->sa_gp.ensure(sizeof(double) * std::max<int64_t>(np, 1), t));
+  PG_CUDA_TRY(p->sa_gj.ensure(sizeof(double) * std::max<int64_t>(n, 1), t));
+  PG_CUDA_TRY(p->sa_fj.ensure(sizeof(double) * std::max<int64_t>(n, 1), t));
+  PG_CUDA_TRY(p->sa_mesh.ensure(sizeof(R) * 2 * N3, t));
+  PG_CUDA_TRY(p->sa_spec.ensure(sizeof(C) * 2 * spec, t));
+  // upstream gradients in the forward output layout, zeros where absent
+  std::vector<double> hg(4 * P + 2, 0.0);
+  auto put = [&](const double* src, int off, int cnt) {
+    if (src)
+      for (int i = 0; i < cnt; ++i) hg[off + i] = src[i];
+  };
+  if (gin) {
+    put(gin->xi_ss, 0, P);
+    put(gin->num, P, P);
+    put(gin->b_pg, 2 * P, P);
+    put(gin->q_eff, 3 * P, P);
+    put(gin->den, 4 * P, 1);
+    put(gin->xi_dw, 4 * P + 1, 1);
+  }
+  PG_CUDA_TRY(cudaMemcpyAsync(p->sa_g.p, hg.data(), sizeof(double) * hg.size(), cudaMemcpyHostToDevice, s));
+  const double* wgal = p->last_has_w ? p->gw.as<double>() : nullptr;
+  const double cs = (double)sizeof(C), rs = (double)sizeof(R);
+  ProfScope ps(p, PG_FAM_SMOOTH, s, 14.0 * spec * cs + 8.0 * N3 * rs);
+  // the galaxy spectrum and its Q again: the workspace's F_g and mesh totals
+  // may have served another plan since the forward
+  PG_CUDA_TRY((galaxy_pass<R>(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), wgal, false, s)));
+  double* sa = p->sa_v.as<double>();
+  const double* sums = p->sm_sums.as<double>();   // pairs [P][2], galaxies [2], sum W C^2, sum W C
+  SmoothAdjArgs a{};
+  a.P = P;
+  a.vbin = p->vbin_d.as<double>();
+  a.L = p->prm.box_L;
+  a.ddq = p->ddq.as<unsigned long long>();
+  a.wsum = p->wsum.as<double>();
+  a.out = p->sm_out.as<double>();
+  a.g = p->sa_g.as<double>();
+  a.sa = sa;
+  PG_CUDA_TRY(launch_sadj_ratios(a, s));
+  PG_CUDA_TRY(cudaMemsetAsync(wbar, 0, sizeof(double) * std::max<int64_t>(n, 1), s));
+  PG_CUDA_TRY(launch_sadj_pairs(np, P, p->pbin.as<int32_t>(), p->pw.as<double>(), p->gp.as<double>(),
+                                p->psi.as<int32_t>(), p->psj.as<int32_t>(), wgal, sums, p->sm_out.as<double>(), sa,
+                                p->sa_gp.as<double>(), wbar, s));
+  PG_CUDA_TRY(launch_sadj_gbar(n, P, sa, sums + 2 * P, wgal, p->sa_gj.as<double>(), s));
+  // the adjoint weights of G deposited on the mesh (transpose of the interpolation)
+  R* gbar = p->sa_mesh.as<R>();
+  R* cbar = gbar + N3;
+  PG_CUDA_TRY(cudaMemsetAsync(gbar, 0, sizeof(R) * N3, s));
+  const DepGeom geo{N, p->dx, p->prm.assign};
+  PG_CUDA_TRY(launch_scatter<R>(geo, np, p->px.as<double>(), p->py.as<double>(), p->pz.as<double>(),
+                                p->sa_gp.as<double>(), gbar, s));
+  PG_CUDA_TRY(launch_scatter<R>(geo, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(),
+                                p->sa_gj.as<double>(), gbar, s));
+  // C = N^-6 IDFT[|F_g|^2] (k = 0 zeroed) again, then Cbar over it
+  const Lay L = lay_plan(N, p->P), Z = lay_zy(N, p->P);
+  C* Gs = p->Gs.as<C>();
+  PG_CUDA_TRY(launch_spec_mul<R>(N, p->P, L, nullptr, p->Fg.as<C>(), 1, 1.0 / (n3 * n3), Gs, s));
+  PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, Gs, Z, tw, s));
+  PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, Gs, Z, tw, s));
+  PG_CUDA_TRY(FftPasses<R>::x_c2r_full(N, Gs, p->P, cbar, tw, s));
+  PG_CUDA_TRY(launch_cbar<R>(N, p->dx, p->smooth_w, sums + 2 * P + 2, sa, P, cbar, s));
+  // spectra of Gbar and Cbar in the plan layout
+  C* A = p->sa_spec.as<C>();
+  C* B = A + spec;
+  const R* meshes[2] = {gbar, cbar};
+  C* specs[2] = {A, B};
+  for (int k = 0; k < 2; ++k) {
+    PG_CUDA_TRY(FftPasses<R>::x_r2c_dense(N, meshes[k], Gs, p->P, tw, s));
+    PG_CUDA_TRY(FftPasses<R>::y_fwd(N, 1, Gs, p->P, nullptr, nullptr, nullptr, nullptr, specs[k], 0, L, tw, s));
+    PG_CUDA_TRY(FftPasses<R>::z_fwd(N, specs[k], L, tw, s));
+  }
+  // fbar = N^-3 IDFT[W~ F[Gbar] + (2 / N^3) F[Cbar] F_g], k = 0 zeroed, into the first mesh
+  PG_CUDA_TRY(launch_spec_combine<R>(N, p->P, L, p->Wk.as<C>(), A, B, p->Fg.as<C>(), 2.0 / n3, 1.0 / n3, Gs, s));
+  PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, Gs, Z, tw, s));
+  PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, Gs, Z, tw, s));
+  PG_CUDA_TRY(FftPasses<R>::x_c2r_full(N, Gs, p->P, gbar, tw, s));
+  // fbar at the galaxies, T = sum_j w_j fbar(x_j) (sm_off + P + 1 holds {0, n}), the rho / Q chain
+  PG_CUDA_TRY(launch_interp<R>(geo, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gbar,
+                               p->sa_fj.as<double>(), s));
+  PG_CUDA_TRY(launch_seg_sums(1, p->sm_off.as<int64_t>() + P + 1, p->sa_fj.as<double>(), wgal, sa + 3 * P + 3, s));
+  PG_CUDA_TRY(launch_sadj_gal(n, P, p->sa_fj.as<double>(), sa + 3 * P + 3, p->qsum.as<unsigned long long>(), n3,
+                              p->gj.as<double>(), sums + 2 * P, sa, wgal, wbar, s));
+  return cudaStreamSynchronize(s);   // hg
 }
 
 }  // namespace
@@ -1260,7 +1375,8 @@ void pg_plan_destroy(pg_plan* p) {
                    &p->bcursor, &p->sums_pg, &p->sums_gg, &p->pg_valid, &p->bin_part, &p->out, &p->psi,
                    &p->psj, &p->cell_bin, &p->cell_agg, &p->wl_idx, &p->wl_tot, &p->wl_base,
                    &p->wl_y, &p->adjb, &p->gout, &p->gp, &p->gj, &p->part, &p->Wk, &p->Gs,
-                   &p->sm_off, &p->sm_sums, &p->sm_part, &p->sm_out};
+                   &p->sm_off, &p->sm_sums, &p->sm_part, &p->sm_out, &p->sa_g, &p->sa_v, &p->sa_gp,
+                   &p->sa_gj, &p->sa_fj, &p->sa_mesh, &p->sa_spec};
   for (DevBuf* b : all) b->release(&p->total);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   cudaSetDevice(cur);
@@ -1280,9 +1396,34 @@ pg_status pg_plan_reserve(pg_plan* p, int64_t n_gal_max, int64_t n_pairs_max) {
 
 size_t pg_workspace_bytes(const pg_plan* p) { return p ? p->total + p->wsp->total : 0; }
 
+pg_status pg_backward_smooth(pg_plan* p, const pg_smooth_result* grad_out, double* d_grad_w, void* stream) {
+  if (!p || !d_grad_w) return PG_ERR_INVALID_ARG;
+  if (!p->smooth_ok) return PG_ERR_INVALID_ARG;
+  if (p->N > 1024) return PG_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PG_TRY(ensure_shared(p));
+  prof_begin(p);
+  const long long launches0 = launch_counter().load();
+  PG_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));
+  cudaError_t e = p->prm.precision ? smooth_backward_impl<double>(p, grad_out, d_grad_w, s)
+                                   : smooth_backward_impl<float>(p, grad_out, d_grad_w, s);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return from_cuda(e);
+  }
+  int32_t herr = 0;
+  PG_TRY(cudaMemcpyAsync(&herr, p->flag.as<int32_t>() + 1, 4, cudaMemcpyDeviceToHost, s));
+  PG_TRY(cudaStreamSynchronize(s));
+  p->last_launches = launch_counter().load() - launches0;
+  if (herr) return PG_ERR_TIMEOUT;
+  if (p->prof_on) prof_end(p);
+  return PG_OK;
+}
+
 pg_status pg_backward(pg_plan* p, const pg_result* grad_out, double* d_grad_w, void* stream) {
   if (!p || !d_grad_w) return PG_ERR_INVALID_ARG;
   if (!p->fwd_ok) return PG_ERR_INVALID_ARG;
+  p->smooth_ok = false;   // the backward reuses the plan's point buffers
   const bool fits = p->prm.precision ? FftPasses<double>::adj_fits(p->N, p->w)
                                      : FftPasses<float>::adj_fits(p->N, p->w);
   if (!fits) return PG_ERR_UNSUPPORTED;
@@ -1421,6 +1562,7 @@ pg_status pg_find_pairs(pg_plan* p, int64_t n, const double* d_pos, const float*
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   PG_TRY(ensure_gal(p, n));
   p->fwd_ok = false;   // the plan's pair and position buffers are reused
+  p->smooth_ok = false;
   // positions are taken as given (already wrapped); split them to SoA
   PG_TRY(launch_transform(n, p->prm.box_L, 0.0, d_pos, nullptr, nullptr, p->x.as<double>(),
                           p->y.as<double>(), p->z.as<double>(), s));
@@ -1526,6 +1668,7 @@ pg_status pg_correlate_points(pg_plan* p, int64_t n_a, const double* d_a, const 
   PG_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));
   PG_TRY(ensure_gal(p, nmax));
   p->fwd_ok = false;   // the plan's spectra and sums are reused
+  p->smooth_ok = false;
   // set b -> Fg; set a -> one "pair" mesh in S[0]
   PG_TRY(launch_transform(n_b, p->prm.box_L, 0.0, d_b, nullptr, nullptr, p->x.as<double>(),
                           p->y.as<double>(), p->z.as<double>(), s));

@@ -315,6 +315,37 @@ cudaError_t launch_wc_sums(int N, double dx, const SmoothW& p, const R* Cm, doub
                            cudaStream_t s);
 cudaError_t launch_smooth_final(const SmoothArgs& a, cudaStream_t s);
 
+// ---- adjoint of the smooth-W estimator (pg_smooth_adj.cu) ------------------------
+struct SmoothAdjArgs {
+  int P;
+  const double* vbin;              // [P] pair-bin volumes
+  double L;
+  const unsigned long long* ddq;   // [P] Q32.32 weighted pair counts
+  const double* wsum;              // [2] sum w, sum w^2
+  const double* out;               // forward outputs: xi_ss[P], num[P], b_pg[P], q_eff[P], den, xi_dw
+  const double* g;                 // upstream gradients in the same layout (zeros where absent)
+  double* sa;                      // out: num bar [P], xi bar [P], RR [P], den bar, xi_w bar, npairs bar
+};
+cudaError_t launch_sadj_ratios(const SmoothAdjArgs& a, cudaStream_t s);
+cudaError_t launch_sadj_pairs(int64_t np, int P, const int32_t* pbin, const double* pw, const double* gp,
+                              const int32_t* pi, const int32_t* pj, const double* wgal, const double* psums,
+                              const double* out, const double* sa, double* gpbar, double* wbar, cudaStream_t s);
+cudaError_t launch_sadj_gbar(int64_t n, int P, const double* sa, const double* gal, const double* wgal,
+                             double* gjbar, cudaStream_t s);
+template <typename R>
+cudaError_t launch_scatter(const DepGeom& geo, int64_t n, const double* x, const double* y, const double* z,
+                           const double* v, R* mesh, cudaStream_t s);
+template <typename R>
+cudaError_t launch_cbar(int N, double dx, const SmoothW& p, const double* wc, const double* sa, int P, R* Cm,
+                        cudaStream_t s);
+template <typename R>
+cudaError_t launch_spec_combine(int N, int P, Lay L, const typename CT<R>::C* Wk, const typename CT<R>::C* A,
+                                const typename CT<R>::C* B, const typename CT<R>::C* Fg, double cs, double scale,
+                                typename CT<R>::C* out, cudaStream_t s);
+cudaError_t launch_sadj_gal(int64_t n, int P, const double* fj, const double* Tsum, const unsigned long long* qsum,
+                            double n3, const double* gj, const double* gal, const double* sa, const double* wgal,
+                            double* wbar, cudaStream_t s);
+
 // ---- binning and ratios (pg_bin.cu) -----------------------------------------
 // Cells per chunk of the binning pass: each list is cut into chunks of at
 // most this many cells, summed by one CTA each.

@@ -95,6 +95,7 @@ def _load():
         "pg_run_batch": (C.c_int, [vp, i32, vp, vp, vp]),
         "pg_selftest_wait": (C.c_int, [vp, C.c_double, vp]),
         "pg_forward_smooth": (C.c_int, [vp, vp, i64, vp, vp, vp, vp, vp]),
+        "pg_backward_smooth": (C.c_int, [vp, vp, vp, vp]),
         "pg_autotune": (C.c_int, [C.POINTER(pg_params), i64, vp, vp, vp, vp, i32, vp, vp, vp]),
         "pg_plan_destroy": (None, [vp]),
         "pg_plan_reserve": (C.c_int, [vp, i64, i64]),
@@ -583,3 +584,22 @@ def pg_forward_smooth(plan: Plan, w_params, pos, vel=None, w=None, stream=None):
     out["den"] = float(arrs["den"][0])
     out["xi_dw"] = float(arrs["xi_dw"][0])
     return out
+
+
+SMOOTH_GRAD_FIELDS = ("xi_ss", "num", "b_pg", "q_eff", "den", "xi_dw")
+
+
+def pg_backward_smooth(plan: Plan, grads: dict, n_gal: int, stream=None):
+    """dL/dw (device FP64 tensor [n_gal]) of the last pg_forward_smooth on
+    `plan`, for L = sum over the given fields of grads[field] * output[field]."""
+    import torch
+    res = pg_smooth_result()
+    keep = []
+    for name in SMOOTH_GRAD_FIELDS:
+        if name in grads and grads[name] is not None:
+            a = np.ascontiguousarray(np.asarray(grads[name], dtype=np.float64).reshape(-1))
+            keep.append(a)
+            setattr(res, name, a.ctypes.data_as(C.POINTER(C.c_double)))
+    out = torch.empty(max(int(n_gal), 1), dtype=torch.float64, device="cuda")
+    _check(_lib.pg_backward_smooth(plan.handle, C.byref(res), _ptr(out), _stream(stream)), "pg_backward_smooth")
+    return out[: int(n_gal)]

@@ -1,0 +1,74 @@
+"""GPU adjoint of the smooth-W estimator (pg_backward_smooth) against the
+oracle's reverse-mode gradient (oracle/smooth_adjoint.py, itself pinned by
+finite differences) on the same seeded inputs."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import pipeline  # noqa: E402
+from oracle import smooth as sm  # noqa: E402
+from oracle import smooth_adjoint as sa  # noqa: E402
+from paper_1705_03464_gb300 import synth  # noqa: E402
+
+WPRM = (8.0, 6.0, 0.8, 3.0)
+
+
+@pytest.fixture(scope="module")
+def pg():
+    from paper_1705_03464_gb300 import build_lib
+    build_lib.build(verbose=False)
+    from paper_1705_03464_gb300 import pairgal
+    return pairgal
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _case(assign, rsd, weighted, grid):
+    L, N = 64.0, 32
+    cat = synth.make_catalogue_box(L, 400, seed=3)
+    w = synth.make_weights(cat.n, 3) if weighted else None
+    if grid:
+        p = pipeline.Params(L, N, assign, (0.0, 1.5, 3.0), 2, (6.0, 9.0), 1, rsd, 0.0, (0.0, 1.5, 3.5))
+    else:
+        p = pipeline.Params(L, N, assign, (0.0, 2.0, 4.0), 2, (6.0, 9.0), 1, rsd)
+    return p, cat, w
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("assign,rsd,weighted,grid", [(1, 0.0, False, False), (2, 0.011, True, False),
+                                                      (0, 0.011, True, True)])
+def test_smooth_backward_matches_oracle_gradient(pg, precision, assign, rsd, weighted, grid):
+    p, cat, w = _case(assign, rsd, weighted, grid)
+    plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur,
+                   rsd_factor=rsd, precision=precision, par_edges=p.par_edges)
+    pg.pg_forward_smooth(plan, WPRM, dev(cat.pos), dev(cat.vel) if rsd else None,
+                         None if w is None else dev(w))
+    w64 = np.ones(cat.n) if w is None else w.astype(np.float64)
+    st = sa.forward_state(p, sm.WParams(*WPRM), cat.pos, cat.vel if rsd else None, w64)
+    rng = np.random.default_rng(17)
+    o = sa.outputs(st)
+    gbar = {k: rng.standard_normal(np.asarray(o[k]).shape) for k in sa.OUTPUT_KEYS}
+    ref = sa.grad_weights(st, gbar)
+    got = pg.pg_backward_smooth(plan, gbar, cat.n).cpu().numpy()
+    scale = np.max(np.abs(ref))
+    # FP64: 1e-8 of the largest component (rounding through the ratio and
+    # eq. Qeff_notsq chains reaches 1.4e-9 on these shot-noise boxes)
+    tol = 1e-8 if precision else 2e-4
+    assert np.max(np.abs(got - ref)) <= tol * scale, np.max(np.abs(got - ref)) / scale
+
+
+def test_smooth_backward_needs_a_smooth_forward(pg):
+    p, cat, _ = _case(1, 0.0, False, False)
+    plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur)
+    with pytest.raises(Exception):
+        pg.pg_backward_smooth(plan, {"num": np.ones(plan.P)}, cat.n)
+    pg.pg_forward_smooth(plan, WPRM, dev(cat.pos))
+    pg.pg_backward_smooth(plan, {"num": np.ones(plan.P)}, cat.n)
+    pg.pg_forward(plan, dev(cat.pos))   # a shell-W forward reuses the plan's buffers
+    with pytest.raises(Exception):
+        pg.pg_backward_smooth(plan, {"num": np.ones(plan.P)}, cat.n)
