@@ -483,8 +483,22 @@ def main():
         pg.pg_forward_smooth(sp, pg.W_DP10, pos, vel, stream=stream)
         sfams, sl = sp.last_stats()
         sp.set_profiling(False)
+        # the adjoint (dL/dw for every galaxy, L = sum b_pg + sum q_eff): forward
+        # + backward per step, timed the same way
+        sg = {"b_pg": np.ones(sp.P), "q_eff": np.ones(sp.P)}
+        pg.pg_backward_smooth(sp, sg, int(cat.n), stream=stream)   # warm-up (adjoint scratch)
+        torch.cuda.synchronize()
+        d0.record(stream)
+        for _ in range(args.smooth_steps):
+            pg.pg_forward_smooth(sp, pg.W_DP10, pos, vel, stream=stream)
+            gw = pg.pg_backward_smooth(sp, sg, int(cat.n), stream=stream)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        tsa = max_over_ranks(d0.elapsed_time(d1), dist, torch, "cuda")
         b = np.asarray(r["b_pg"])
         smooth = {"ms_per_mock": per_mock(ts / args.smooth_steps, world), "steps": args.smooth_steps,
+                  "fwd_adj_ms_per_mock": per_mock(tsa / args.smooth_steps, world),
+                  "fwd_adj_ratio": tsa / ts, "grad_finite": bool(torch.isfinite(gw).all().item()),
                   "assign": "tsc", "w": {"sigma": 30.0, "r_s": 20.0, "s0": 0.8, "r_cut": 10.0},
                   "xi_dw": r["xi_dw"], "b_pg_range": [float(np.nanmin(b)), float(np.nanmax(b))],
                   "launches": sl,
