@@ -507,6 +507,30 @@ def main():
                               for k, v in sfams.items() if v["launches"] > 0}}
         sp.close()
         del sp
+        # the paper's redshift-space configuration (d_p,max = 30 Mpc/h, W of
+        # Table tab:weightings row 2) on the (d_perp, d_par) grid of its
+        # redshift-space b_pg / Q_eff maps, positions displaced along z
+        vz = torch.from_numpy(np.ascontiguousarray(cat.vel)).cuda()
+        perp = tuple(np.linspace(0.0, 30.0, 21))
+        par = tuple(np.linspace(0.0, 30.0, 6))
+        sg30 = pg.Plan(wl.box_L, wl.mesh_n, 2, perp, len(par) - 1, wl.r_edges, wl.n_mur,
+                       rsd_factor=synth.RSD_FACTOR_Z05, par_edges=par, share_with=plan)
+        r30 = pg.pg_forward_smooth(sg30, pg.W_DP30, pos, vz, stream=stream)   # warm-up, W's spectrum
+        torch.cuda.synchronize()
+        d0.record(stream)
+        for _ in range(args.smooth_steps):
+            r30 = pg.pg_forward_smooth(sg30, pg.W_DP30, pos, vz, stream=stream)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        t30 = max_over_ranks(d0.elapsed_time(d1), dist, torch, "cuda")
+        b30 = np.asarray(r30["b_pg"])
+        smooth["rsd_dp30_grid"] = {
+            "ms_per_mock": per_mock(t30 / args.smooth_steps, world), "assign": "tsc",
+            "w": {"sigma": 50.0, "r_s": 35.0, "s0": 0.5, "r_cut": 20.0},
+            "pair_grid": "d_perp 0-30 (20) x |d_par| 0-30 (5)", "n_pairs": int(np.sum(r30["dd"])),
+            "xi_dw": r30["xi_dw"], "b_pg_range": [float(np.nanmin(b30)), float(np.nanmax(b30))]}
+        sg30.close()
+        del sg30, vz
 
     many = None
     if args.many_mocks > 0 and rank == 0 and world == 1:

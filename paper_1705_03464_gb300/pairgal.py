@@ -478,6 +478,16 @@ def hod_gradient(plan: Plan, pos, vel, mass, kind, kh, theta, grads, stream=None
     return out, pg_hod_chain(plan, wbar, dw, stream)
 
 
+def hod_gradient_smooth(plan: Plan, w_params, pos, vel, mass, kind, kh, theta, grads, stream=None):
+    """The smooth-W estimator's outputs at HOD parameters theta and dL/dtheta
+    for L = sum grads * outputs: soft weights -> pg_forward_smooth ->
+    pg_backward_smooth -> chain, all on the device."""
+    w, dw = pg_hod_weights(mass, kind, kh, theta, True, stream)
+    out = pg_forward_smooth(plan, w_params, pos, vel, w, stream)
+    wbar = pg_backward_smooth(plan, grads, int(pos.shape[0]), stream)
+    return out, pg_hod_chain(plan, wbar, dw, stream)
+
+
 def _host(a, dtype):
     return None if a is None else np.ascontiguousarray(a, dtype=dtype)
 

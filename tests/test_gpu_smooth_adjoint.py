@@ -72,3 +72,30 @@ def test_smooth_backward_needs_a_smooth_forward(pg):
     pg.pg_forward(plan, dev(cat.pos))   # a shell-W forward reuses the plan's buffers
     with pytest.raises(Exception):
         pg.pg_backward_smooth(plan, {"num": np.ones(plan.P)}, cat.n)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_hod_gradient_through_the_smooth_estimator(pg, precision):
+    """dL/dtheta of the paper's own estimator for the five HOD parameters
+    (Sec. 3.3 eq. hod): soft weights, pg_forward_smooth, pg_backward_smooth and
+    the chain on the device, against the oracle's reverse mode composed with the
+    oracle's dw/dtheta at the FP32 weights the GPU used."""
+    from oracle import hod
+    th = np.array(synth.HOD_Z09)
+    th[3] = 1.1
+    L = 64.0
+    cand = synth.make_candidates(L, 300, seed=4)
+    p = pipeline.Params(L, 32, 2, (0.0, 2.0, 4.0), 2, (6.0, 9.0), 1)
+    plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur, precision=precision)
+    rng = np.random.default_rng(6)
+    gbar = {"b_pg": rng.standard_normal(plan.P), "q_eff": rng.standard_normal(plan.P),
+            "xi_dw": rng.standard_normal(1)}
+    out, g = pg.hod_gradient_smooth(plan, WPRM, dev(cand.pos), None, dev(cand.mass), dev(cand.kind),
+                                    dev(cand.kh), th, gbar)
+    w, _ = pg.pg_hod_weights(dev(cand.mass), dev(cand.kind), dev(cand.kh), th)
+    st = sa.forward_state(p, sm.WParams(*WPRM), cand.pos, None, w.cpu().numpy().astype(np.float64))
+    wbar = sa.grad_weights(st, gbar)
+    ref = hod.grad_theta(th, cand.mass, cand.kind, cand.kh, wbar)
+    cond = np.abs(hod.dweights(th, cand.mass, cand.kind, cand.kh)).T @ np.abs(wbar)
+    tol = 1e-8 if precision else 2e-4
+    assert np.all(np.abs(np.asarray(g) - ref) <= tol * cond), (g, ref, cond)
