@@ -707,7 +707,8 @@ k_col_inv_full(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
 template <typename C, int N, int B>
 struct ZCorr {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
-  static constexpr int THREADS = B * N1;
+  static constexpr int CTHREADS = B * N1;           // transform warpgroups
+  static constexpr int THREADS = CTHREADS + 128;    // + one warpgroup whose first thread issues the loads
   static constexpr int TILE = N * B;
   static constexpr int ZB = N < 256 ? N : 256;   // rows per TMA box
   static constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
@@ -715,6 +716,16 @@ struct ZCorr {
   static constexpr size_t SMEM = sizeof(C) * (3 * (size_t)TILE + N) + 64;
   static constexpr int MINB = SMEM <= 110 * 1024 ? 2 : 1;   // resident CTAs per SM
   static constexpr size_t smem_bytes() { return SMEM; }
+  // Registers per thread: the launch cap of __launch_bounds__(THREADS, MINB);
+  // after the split the load warpgroup keeps RP and the transform warpgroups
+  // take what it frees, RC, so that CTHREADS * RC + 128 * RP <= THREADS * RLAUNCH.
+  static constexpr int RLAUNCH_RAW = (65536 / (THREADS * MINB)) & ~7;
+  static constexpr int RLAUNCH = RLAUNCH_RAW > 248 ? 248 : RLAUNCH_RAW;
+  static constexpr int RP = 24;
+  static constexpr int RC_RAW = ((THREADS * RLAUNCH - 128 * RP) / CTHREADS) & ~7;
+  static constexpr int RC = RC_RAW > 240 ? 240 : RC_RAW;
+  static constexpr bool SPLIT = RC > RLAUNCH;   // else every warp keeps the launch count
+  static_assert(CTHREADS % 128 == 0, "transform threads form whole warpgroups");
 };
 
 template <typename C, int N, int B>
@@ -730,6 +741,46 @@ __device__ __forceinline__ void zc_issue(C* dst, const CUtensorMap* map, uint64_
     tma::load_5d_hint(dst + z0 * B, map, bar, kx0 * Z::E, ky & KM, z0, ky >> kYBlockShift, b, pol);
 }
 
+// The load side of the fused z pass, run by one thread of the extra warp.
+// Barriers: bar[0], bar[1] mesh buffer k loaded; bar[2] galaxy tile loaded;
+// bar[3], bar[4] mesh buffer k free again; bar[5] galaxy tile free again.
+// Per item the order is: first mesh, galaxy tile, remaining meshes, so the
+// first mesh of an item streams in while the previous item's last mesh is
+// still being transformed. Returns 0, or 1 when a wait for a free buffer ran
+// out; copies issued are waited for (bounded) before it returns.
+template <typename C, int N, int B>
+__device__ int zc_produce(const CUtensorMap* mS, const CUtensorMap* mF, C* sbuf0, C* ftile,
+                          uint64_t* bar, int nb, int gg, int64_t n_items, int T, uint64_t limit_ns) {
+  using Z = ZCorr<C, N, B>;
+  uint32_t issued[3] = {0, 0, 0};
+  int64_t job = 0;
+  int failed = 0;
+  auto mesh = [&](int kx0, int ky, int b) {
+    const int s = (int)(job & 1);
+    if (job >= 2 && !tma::mbar_wait(&bar[3 + s], (uint32_t)((job >> 1) - 1) & 1, limit_ns)) return false;
+    tma::fence_async_shared();
+    zc_issue<C, N, B>(sbuf0 + s * Z::TILE, mS, &bar[s], kx0, ky, b);
+    ++issued[s];
+    ++job;
+    return true;
+  };
+  int64_t i = 0;
+  for (int64_t item = blockIdx.x; item < n_items && !failed; item += gridDim.x, ++i) {
+    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
+    if (!gg && !mesh(kx0, ky, 0)) { failed = 1; break; }
+    if (i > 0 && !tma::mbar_wait(&bar[5], (uint32_t)(i - 1) & 1, limit_ns)) { failed = 1; break; }
+    tma::fence_async_shared();
+    zc_issue<C, N, B>(ftile, mF, &bar[2], kx0, ky, 0);
+    ++issued[2];
+    for (int b = 1; b < nb && !gg; ++b)
+      if (!mesh(kx0, ky, b)) { failed = 1; break; }
+  }
+  // every copy issued has landed before the CTA may exit
+  for (int k = 0; k < 3; ++k)
+    if (issued[k]) tma::mbar_wait(&bar[k], (issued[k] - 1) & 1, failed ? 100000000ull : limit_ns);
+  return failed;
+}
+
 template <typename C, int N, int B, int K>
 __global__ void __launch_bounds__(ZCorr<C, N, B>::THREADS, ZCorr<C, N, B>::MINB)
 k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mF,
@@ -737,30 +788,35 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
              const C* __restrict__ tw, int* __restrict__ err) {
   using Z = ZCorr<C, N, B>;
   using RT = typename Real<C>::T;
-  constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1;
+  constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1, CT = Z::CTHREADS;
   constexpr int XP = xperm<C, N, B>();
   constexpr uint64_t kLimitNs = 2000000000ull;   // 2 s per wait
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* const sbuf0 = reinterpret_cast<C*>(smem_raw);   // mesh buffers: sbuf0 + k * TILE
   C* ftile = sbuf0 + 2 * TILE;
   C* tws = ftile + TILE;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);   // [0], [1]: mesh buffers, [2]: F_g
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);   // see zc_produce
   const int T = (M1 + B - 1) / B;
   const int64_t n_items = (int64_t)T * N;
   int64_t item = blockIdx.x;
   if (item >= n_items) return;   // whole CTA
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
-  if (threadIdx.x == 0) {
-    tma::mbar_init(&bar[0], 1);
-    tma::mbar_init(&bar[1], 1);
-    tma::mbar_init(&bar[2], 1);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += blockDim.x) tws[i] = tw[i];
+  if (tid == 0) {
+    for (int k = 0; k < 6; ++k) tma::mbar_init(&bar[k], 1);
     tma::fence_async_shared();
-    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
-    zc_issue<C, N, B>(ftile, &mF, &bar[2], kx0, ky, 0);
-    if (!gg) zc_issue<C, N, B>(sbuf0, &mS, &bar[0], kx0, ky, 0);
   }
   __syncthreads();
-  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  if constexpr (Z::SPLIT) {
+    if (tid >= CT) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Z::RP));
+    else asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(Z::RC));
+  }
+  if (tid >= CT) {   // the load warpgroup; the transform warps sync on named barrier 1 from here
+    if (tid == CT && zc_produce<C, N, B>(&mS, &mF, sbuf0, ftile, bar, nb, gg, n_items, T, kLimitNs))
+      atomicExch(err, tma::kErrTmaTimeout);
+    return;
+  }
+  const int c = tid % B, k1 = tid / B;
   const RT inv_n3 = (RT)(1.0 / ((double)N * (double)N * (double)N));
   uint32_t ph[3] = {0, 0, 0};
   int64_t job = 0;
@@ -768,32 +824,22 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
   for (; item < n_items && !failed; item += gridDim.x) {
     const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
     const int ncol = min(B, M1 - kx0);
-    if (__syncthreads_or(!tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
+    if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
     ph[2] ^= 1;
     if (!gg) {   // F_g / N^3 once per item
-      for (int i = threadIdx.x; i < TILE; i += blockDim.x) ftile[i] = cscale(ftile[i], inv_n3);
-      __syncthreads();
+      for (int i = tid; i < TILE; i += CT) ftile[i] = cscale(ftile[i], inv_n3);
+      tma::bar_sync(1, CT);
     }
     const bool dc_col = (kx0 + c == 0) && (ky == 0);
     for (int b = 0; b < nb; ++b, ++job) {
       const int cur = (int)(job & 1);
       C* buf = sbuf0 + cur * TILE;
-      if (!gg && threadIdx.x == 0) {   // prefetch the next job's tile
-        int nbb = b + 1;
-        int64_t nitem = item;
-        if (nbb == nb) { nbb = 0; nitem = item + gridDim.x; }
-        if (nitem < n_items) {
-          tma::fence_async_shared();
-          zc_issue<C, N, B>(sbuf0 + (cur ^ 1) * TILE, &mS, &bar[cur ^ 1], (int)(nitem % T) * B,
-                            (int)(nitem / T), nbb);
-        }
-      }
       C a[N2];
       if (!gg) {
-        if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
+        if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
         ph[cur] ^= 1;
-        step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
-        __syncthreads();
+        step1<C, N1, N2, B, false, XP>(buf, B, tws, 1, tid, CT);
+        tma::bar_sync(1, CT);
         step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmulc(a[k2], ftile[(k1 + N1 * k2) * B + c]);
@@ -806,18 +852,13 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
         }
       }
       if (dc_col && k1 == 0) { a[0].x = 0; a[0].y = 0; }   // k = 0 mode
-      __syncthreads();
-      // after the last mesh of this item the galaxy tile is free: fetch the next
-      if (b == nb - 1 && threadIdx.x == 0 && item + gridDim.x < n_items) {
-        const int64_t nitem = item + gridDim.x;
-        tma::fence_async_shared();
-        zc_issue<C, N, B>(ftile, &mF, &bar[2], (int)(nitem % T) * B, (int)(nitem / T), 0);
-      }
+      tma::bar_sync(1, CT);
+      if (b == nb - 1 && tid == 0) tma::mbar_arrive(&bar[5]);   // galaxy tile read for this item
       C* wbuf = gg ? sbuf0 : buf;
       stepA<C, N1, N2, true, XP>(wbuf, B, c, k1, a, tws, 1);
-      __syncthreads();
+      tma::bar_sync(1, CT);
       C* wout = Wz + (int64_t)b * Wz_stride + (int64_t)ky * P + kx0;
-      for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+      for (int t = tid; t < B * N2; t += CT) {
         const int cc = t % B, n2 = t / B;
         C x[N1];
         stepB<C, N1, N2, true, XP, K>(wbuf, B, cc, n2, x);
@@ -830,17 +871,11 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
           }
         }
       }
-      __syncthreads();
+      tma::bar_sync(1, CT);
+      if (!gg && tid == 0) tma::mbar_arrive(&bar[3 + cur]);   // mesh buffer free for the next load
     }
   }
-  if (failed) {
-    if (threadIdx.x == 0) {
-      atomicExch(err, tma::kErrTmaTimeout);
-      // let copies still in flight land before the CTA exits (bounded)
-      for (int k = 0; k < 3; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
-    }
-    __syncthreads();
-  }
+  if (failed && tid == 0) atomicExch(err, tma::kErrTmaTimeout);
 }
 
 // ============================================================================
