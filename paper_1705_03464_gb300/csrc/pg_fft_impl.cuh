@@ -29,6 +29,20 @@ static cudaError_t persistent_grid(K kern, int threads, size_t smem, int64_t ite
   return cudaSuccess;
 }
 
+// A kernel that splits its registers (RegSplit) grows its transform
+// warpgroups into the registers its load warpgroup gives back: it may only be
+// launched if it was built with the launch cap the split assumes.
+template <typename RS, typename K>
+static cudaError_t check_reg_split(K kern) {
+  if constexpr (RS::SPLIT) {
+    cudaFuncAttributes fa;
+    PG_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    if ((int64_t)fa.numRegs * RS::THREADS < (int64_t)(RS::THREADS - 128) * RS::RC + 128 * RS::RP)
+      return cudaErrorInvalidConfiguration;
+  }
+  return cudaSuccess;
+}
+
 // Tensor map over 8-byte elements of nb spectra of the plan layout L (each
 // N*N*P complex), dimensions (kx, y mod K, z, y / K, mesh) with K = 2^L.ks,
 // box (one kx tile of B columns, then either bz z rows of one y (by = 1) or
@@ -283,6 +297,7 @@ cudaError_t FftPasses<R>::zadj(int N, int nb, C* S, int64_t S_stride, Lay L, con
     auto k = fft::k_zadj<C, NN, B>;
     const size_t sm = Z::smem(W);
     PG_CUDA_TRY(set_smem(k, sm));
+    PG_CUDA_TRY(fft::check_reg_split<typename Z::Regs>(k));
     unsigned grid = 0;
     PG_CUDA_TRY(fft::persistent_grid(k, Z::THREADS, sm, cdiv(NN / 2 + 1, B) * (int64_t)NN, &grid));
     k<<<grid, Z::THREADS, sm, s>>>(mS, mX, mA, nb, w, S, S_stride, L, Fg, A, tw, err);

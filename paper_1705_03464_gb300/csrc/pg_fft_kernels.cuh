@@ -704,6 +704,33 @@ k_col_inv_full(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
 // n1 >= N1 - K, which hold every window row when K > w / N2 (rows
 // n = n2 + N2 n1 with |n| <= w).
 // ============================================================================
+// Registers per thread for a CTA of CT transform threads (whole warpgroups)
+// plus one load warpgroup, MINB CTAs per SM: RLAUNCH is the cap of
+// __launch_bounds__(CT + 128, MINB); after the split the load warpgroup keeps
+// RP and the transform warpgroups take what it frees, RC, so that
+// CT * RC + 128 * RP <= (CT + 128) * RLAUNCH.
+template <int CT, int MINB>
+struct RegSplit {
+  static constexpr int THREADS = CT + 128;
+  static constexpr int RLAUNCH_RAW = (65536 / (THREADS * MINB)) & ~7;
+  static constexpr int RLAUNCH = RLAUNCH_RAW > 248 ? 248 : RLAUNCH_RAW;
+  static constexpr int RP = 24;
+  static constexpr int RC_RAW = ((THREADS * RLAUNCH - 128 * RP) / CT) & ~7;
+  static constexpr int RC = RC_RAW > 240 ? 240 : RC_RAW;
+  static constexpr bool SPLIT = RC > RLAUNCH;   // else every warp keeps the launch count
+  static_assert(CT % 128 == 0, "transform threads form whole warpgroups");
+};
+
+// Gives the load warpgroup's registers to the transform warpgroups (threads
+// below CT); every thread of the CTA calls it once.
+template <typename RS>
+__device__ __forceinline__ void reg_split(int tid) {
+  if constexpr (RS::SPLIT) {
+    if (tid >= RS::THREADS - 128) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(RS::RP));
+    else asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(RS::RC));
+  }
+}
+
 template <typename C, int N, int B>
 struct ZCorr {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
@@ -716,16 +743,7 @@ struct ZCorr {
   static constexpr size_t SMEM = sizeof(C) * (3 * (size_t)TILE + N) + 64;
   static constexpr int MINB = SMEM <= 110 * 1024 ? 2 : 1;   // resident CTAs per SM
   static constexpr size_t smem_bytes() { return SMEM; }
-  // Registers per thread: the launch cap of __launch_bounds__(THREADS, MINB);
-  // after the split the load warpgroup keeps RP and the transform warpgroups
-  // take what it frees, RC, so that CTHREADS * RC + 128 * RP <= THREADS * RLAUNCH.
-  static constexpr int RLAUNCH_RAW = (65536 / (THREADS * MINB)) & ~7;
-  static constexpr int RLAUNCH = RLAUNCH_RAW > 248 ? 248 : RLAUNCH_RAW;
-  static constexpr int RP = 24;
-  static constexpr int RC_RAW = ((THREADS * RLAUNCH - 128 * RP) / CTHREADS) & ~7;
-  static constexpr int RC = RC_RAW > 240 ? 240 : RC_RAW;
-  static constexpr bool SPLIT = RC > RLAUNCH;   // else every warp keeps the launch count
-  static_assert(CTHREADS % 128 == 0, "transform threads form whole warpgroups");
+  using Regs = RegSplit<CTHREADS, MINB>;
 };
 
 template <typename C, int N, int B>
@@ -807,10 +825,7 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
     tma::fence_async_shared();
   }
   __syncthreads();
-  if constexpr (Z::SPLIT) {
-    if (tid >= CT) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Z::RP));
-    else asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(Z::RC));
-  }
+  reg_split<typename Z::Regs>(tid);
   if (tid >= CT) {   // the load warpgroup; the transform warps sync on named barrier 1 from here
     if (tid == CT && zc_produce<C, N, B>(&mS, &mF, sbuf0, ftile, bar, nb, gg, n_items, T, kLimitNs))
       atomicExch(err, tma::kErrTmaTimeout);
@@ -1028,7 +1043,9 @@ k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_
 template <typename C, int N, int B>
 struct ZAdj {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
-  static constexpr int THREADS = B * N1;
+  static constexpr int CTHREADS = B * N1;           // transform warpgroups
+  static constexpr int THREADS = CTHREADS + 128;    // + one warpgroup whose first thread issues the loads
+  using Regs = RegSplit<CTHREADS, 1>;
   static constexpr int TILE = N * B;
   static constexpr int ZB = N < 256 ? N : 256;   // rows per TMA box of a full column
   static constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
@@ -1067,10 +1084,10 @@ __device__ __forceinline__ void za_issue_win(C* dst, const CUtensorMap* map, uin
 // nonzero rows z <= w and z >= N - w come from the compact slot
 // xc[rank * B + c]: reads the slot directly, writes buf like step1.
 template <typename C, int N, int B, int X>
-__device__ __forceinline__ void step1_win(C* buf, const C* xc, int w, const C* tw) {
+__device__ __forceinline__ void step1_win(C* buf, const C* xc, int w, const C* tw, int tid, int nthr) {
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   const int W = 2 * w + 1;
-  for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+  for (int t = tid; t < B * N2; t += nthr) {
     const int c = t % B, j2 = t / B;
     C a[N1];
 #pragma unroll
@@ -1100,6 +1117,49 @@ __device__ __forceinline__ void step1_win(C* buf, const C* xc, int w, const C* t
 // already read. Persistent and TMA fed; mesh b's S and window tiles share one
 // of two slots so the next mesh streams in during the transforms. F_g is read
 // from global memory (L2: its tile is reused by every mesh of the item).
+// The load side of the adjoint z pass, run by one thread of the load
+// warpgroup (barriers as in k_zadj). Per item the order is: first mesh's slot,
+// A tile, remaining meshes' slots. Returns 0, or 1 when a wait for a free
+// buffer ran out; copies issued are waited for (bounded) before it returns.
+template <typename C, int N, int B>
+__device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CUtensorMap* mA, C* sb0,
+                          C* at, C* xb0, int WS, int W, uint64_t* bar, int nb, int64_t n_items, int T,
+                          uint64_t limit_ns) {
+  using Z = ZAdj<C, N, B>;
+  // S, the window columns and A pass through once: evict first
+  const uint64_t pol = tma::policy_evict_first();
+  const uint32_t slot_bytes = Z::TILE_BYTES + (uint32_t)(W * B * sizeof(C));
+  uint32_t issued[3] = {0, 0, 0};
+  int64_t job = 0;
+  int failed = 0;
+  auto slot = [&](int kx0, int ky, int b) {
+    const int k = (int)(job & 1);
+    if (job >= 2 && !tma::mbar_wait(&bar[3 + k], (uint32_t)((job >> 1) - 1) & 1, limit_ns)) return false;
+    tma::fence_async_shared();
+    tma::mbar_arrive_expect_tx(&bar[k], slot_bytes);
+    za_issue_col<C, N, B>(sb0 + k * Z::TILE, mS, &bar[k], kx0, ky, b, pol);
+    za_issue_win<C, N, B>(xb0 + k * WS, mX, &bar[k], kx0, ky, b, pol);
+    ++issued[k];
+    ++job;
+    return true;
+  };
+  int64_t i = 0;
+  for (int64_t item = blockIdx.x; item < n_items && !failed; item += gridDim.x, ++i) {
+    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
+    if (nb > 0 && !slot(kx0, ky, 0)) { failed = 1; break; }
+    if (i > 0 && !tma::mbar_wait(&bar[5], (uint32_t)(i - 1) & 1, limit_ns)) { failed = 1; break; }
+    tma::fence_async_shared();
+    tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
+    za_issue_col<C, N, B>(at, mA, &bar[2], kx0, ky, 0, pol);
+    ++issued[2];
+    for (int b = 1; b < nb; ++b)
+      if (!slot(kx0, ky, b)) { failed = 1; break; }
+  }
+  for (int k = 0; k < 3; ++k)
+    if (issued[k]) tma::mbar_wait(&bar[k], (issued[k] - 1) & 1, failed ? 100000000ull : limit_ns);
+  return failed;
+}
+
 template <typename C, int N, int B>
 __global__ void __launch_bounds__(ZAdj<C, N, B>::THREADS, 1)
 k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mX,
@@ -1107,7 +1167,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
        Lay L, const C* __restrict__ Fg, C* __restrict__ A, const C* __restrict__ tw,
        int* __restrict__ err) {
   using Z = ZAdj<C, N, B>;
-  constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1;
+  constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1, CT = Z::CTHREADS;
   constexpr int XP = xperm<C, N, B>();
   constexpr uint64_t kLimitNs = 2000000000ull;
   const int W = 2 * w + 1;
@@ -1117,31 +1177,28 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
   const int WS = Z::win_slot(W);
   C* const xb0 = at + TILE;                         // compact window slots: xb0 + k * WS
   C* const tws = xb0 + 2 * WS;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);   // [0], [1]: slots, [2]: A tile
-  const uint32_t slot_bytes = Z::TILE_BYTES + (uint32_t)(W * B * sizeof(C));
+  // [0], [1]: slot k loaded; [2]: A tile loaded; [3], [4]: slot k free; [5]: A tile free
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);
   const int T = (M1 + B - 1) / B;
   const int64_t n_items = (int64_t)T * N;
   int64_t item = blockIdx.x;
   if (item >= n_items) return;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
-  // S, A and Y pass through once: evict first; the item's F_g column is
-  // re-read for every mesh of the batch: evict last
-  const uint64_t pol_stream = tma::policy_evict_first(), pol_keep = tma::policy_evict_last();
-  auto issue_slot = [&](int k, int64_t it, int b) {
-    const int ky = (int)(it / T), kx0 = (int)(it % T) * B;
-    tma::mbar_arrive_expect_tx(&bar[k], slot_bytes);
-    za_issue_col<C, N, B>(sb0 + k * TILE, &mS, &bar[k], kx0, ky, b, pol_stream);
-    za_issue_win<C, N, B>(xb0 + k * WS, &mX, &bar[k], kx0, ky, b, pol_stream);
-  };
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < 3; ++k) tma::mbar_init(&bar[k], 1);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += blockDim.x) tws[i] = tw[i];
+  if (tid == 0) {
+    for (int k = 0; k < 6; ++k) tma::mbar_init(&bar[k], 1);
     tma::fence_async_shared();
-    tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
-    za_issue_col<C, N, B>(at, &mA, &bar[2], (int)(item % T) * B, (int)(item / T), 0, pol_stream);
-    issue_slot(0, item, 0);
   }
   __syncthreads();
-  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  reg_split<typename Z::Regs>(tid);
+  if (tid >= CT) {   // the load warpgroup; the transform warps sync on named barrier 1 from here
+    if (tid == CT && za_produce<C, N, B>(&mS, &mX, &mA, sb0, at, xb0, WS, W, bar, nb, n_items, T, kLimitNs))
+      atomicExch(err, tma::kErrTmaTimeout);
+    return;
+  }
+  // the item's F_g column is re-read for every mesh of the batch: evict last
+  const uint64_t pol_stream = tma::policy_evict_first(), pol_keep = tma::policy_evict_last();
+  const int c = tid % B, k1 = tid / B;
   uint32_t ph[3] = {0, 0, 0};
   int64_t job = 0;
   int failed = 0;
@@ -1150,24 +1207,15 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
     const int ncol = min(B, M1 - kx0);
     const bool dc_col = (kx0 + c == 0) && (ky == 0);
     const C* fcol = Fg + yoff(L, ky) + kx0 + c;
-    if (__syncthreads_or(!tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
+    if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
     ph[2] ^= 1;
     for (int b = 0; b < nb; ++b, ++job) {
       const int cur = (int)(job & 1);
       C* buf = sb0 + cur * TILE;
-      if (threadIdx.x == 0) {   // the next job's tiles into the other slot
-        int nbb = b + 1;
-        int64_t nitem = item;
-        if (nbb == nb) { nbb = 0; nitem = item + gridDim.x; }
-        if (nitem < n_items) {
-          tma::fence_async_shared();
-          issue_slot(cur ^ 1, nitem, nbb);
-        }
-      }
-      if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
+      if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
       ph[cur] ^= 1;
-      step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
-      __syncthreads();
+      step1<C, N1, N2, B, false, XP>(buf, B, tws, 1, tid, CT);
+      tma::bar_sync(1, CT);
       C a[N2];
       step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
       // the galaxy column is issued here so that its L2 latency overlaps the
@@ -1178,9 +1226,9 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
         f[k2].x = 0; f[k2].y = 0;
         if (c < ncol) f[k2] = tma::ld_hint(fcol + (int64_t)(k1 + N1 * k2) * L.zs, pol_keep);
       }
-      __syncthreads();
-      step1_win<C, N, B, XP>(buf, xb0 + cur * WS, w, tws);
-      __syncthreads();
+      tma::bar_sync(1, CT);
+      step1_win<C, N, B, XP>(buf, xb0 + cur * WS, w, tws, tid, CT);
+      tma::bar_sync(1, CT);
       C x[N2];
       step2<C, N1, N2, false, XP>(buf, B, c, k1, x);
 #pragma unroll
@@ -1195,11 +1243,11 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) x[k2] = cmul(x[k2], f[k2]);
       if (dc_col && k1 == 0) { x[0].x = 0; x[0].y = 0; }   // k = 0 mode
-      __syncthreads();
+      tma::bar_sync(1, CT);
       stepA<C, N1, N2, true, XP>(buf, B, c, k1, x, tws, 1);
-      __syncthreads();
+      tma::bar_sync(1, CT);
       C* yout = S + (int64_t)b * S_stride + yoff(L, ky) + kx0;
-      for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+      for (int t = tid; t < B * N2; t += CT) {
         const int cc = t % B, n2 = t / B;
         C v[N1];
         stepB<C, N1, N2, true, XP>(buf, B, cc, n2, v);
@@ -1209,30 +1257,20 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
             tma::st_hint(yout + (int64_t)(n2 + N2 * n1) * L.zs + cc, v[n1], pol_stream);
         }
       }
-      __syncthreads();   // slot free for the job after next
+      tma::bar_sync(1, CT);
+      if (tid == 0) tma::mbar_arrive(&bar[3 + cur]);   // slot free for the next load
     }
     if (failed) break;
-    // the item's A column back to global memory, then the next item's A tile
+    // the item's A column back to global memory; then the tile is free
     C* ag = A + yoff(L, ky) + kx0;
-    for (int t = threadIdx.x; t < TILE; t += blockDim.x) {
+    for (int t = tid; t < TILE; t += CT) {
       const int z = t / B, cc = t % B;
       tma::st_hint(ag + (int64_t)z * L.zs + cc, at[t], pol_stream);
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && item + gridDim.x < n_items) {
-      const int64_t nitem = item + gridDim.x;
-      tma::fence_async_shared();
-      tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
-      za_issue_col<C, N, B>(at, &mA, &bar[2], (int)(nitem % T) * B, (int)(nitem / T), 0, pol_stream);
-    }
+    tma::bar_sync(1, CT);
+    if (tid == 0) tma::mbar_arrive(&bar[5]);
   }
-  if (failed) {
-    if (threadIdx.x == 0) {
-      atomicExch(err, tma::kErrTmaTimeout);
-      for (int k = 0; k < 3; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
-    }
-    __syncthreads();
-  }
+  if (failed && tid == 0) atomicExch(err, tma::kErrTmaTimeout);
 }
 
 // Inverse y of Y_b on the z planes that hold lines of mesh b, stored only at

@@ -25,14 +25,7 @@ static cudaError_t z_corr_launch(const typename CT<R>::C* S, const typename CT<R
     return cudaErrorInvalidValue;
   auto k = k_z_corr_tma<C, N, B, K>;
   PG_CUDA_TRY(set_smem(k, Z::smem_bytes()));
-  if constexpr (Z::SPLIT) {
-    // the transform warpgroups grow into the registers the load warpgroup
-    // gives back: launch only if the kernel was built with the cap assumed
-    cudaFuncAttributes fa;
-    PG_CUDA_TRY(cudaFuncGetAttributes(&fa, k));
-    if ((int64_t)fa.numRegs * Z::THREADS < (int64_t)Z::CTHREADS * Z::RC + 128 * Z::RP)
-      return cudaErrorInvalidConfiguration;
-  }
+  PG_CUDA_TRY(check_reg_split<typename Z::Regs>(k));
   unsigned grid = 0;
   PG_CUDA_TRY(persistent_grid(k, Z::THREADS, Z::smem_bytes(), cdiv(N / 2 + 1, B) * (int64_t)N, &grid));
   k<<<grid, Z::THREADS, Z::smem_bytes(), s>>>(mS, mF, nb, gg ? 1 : 0, w, Wz, Wz_stride, P, tw, err);
