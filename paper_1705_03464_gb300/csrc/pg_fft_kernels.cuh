@@ -244,6 +244,30 @@ __device__ __forceinline__ void stepB(const C* buf, int LD, int c, int n2, C (&a
   reg_dft<C, N1, INV, K>(a);
 }
 
+// Steps A and B with step A writing back into the slots its thread read in
+// step 2: task (c, k1) stores row (n2, k1) at prow<X>(k1, n2, N2), the slot
+// of its own input j2 = n2. No other thread touches those slots between
+// step 2 and step A, so the two need no barrier between them; step B then
+// reads row (n2, k1) for k1 = 0..N1-1 from prow<X>(k1, n2, N2), the access
+// pattern of step 1's stores.
+template <typename C, int N1, int N2, bool INV, int X = 1>
+__device__ __forceinline__ void stepA_own(C* buf, int LD, int c, int k1, C (&a)[N2], const C* tw, int tws) {
+  reg_dft<C, N2, INV>(a);
+  if (N2 > 1 && k1 > 0) {
+#pragma unroll
+    for (int n2 = 1; n2 < N2; ++n2) a[n2] = cmul(a[n2], twid<C, INV>(tw, k1 * n2 * tws));
+  }
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) buf[prow<X>(k1, n2, N2) * LD + c] = a[n2];
+}
+
+template <typename C, int N1, int N2, bool INV, int X = 1, int K = N1>
+__device__ __forceinline__ void stepB_own(const C* buf, int LD, int c, int n2, C (&a)[N1]) {
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) a[k1] = buf[prow<X>(k1, n2, N2) * LD + c];
+  reg_dft<C, N1, INV, K>(a);
+}
+
 template <int N> struct Split {
   static constexpr int N1 = N < 32 ? N : 32;
   static constexpr int N2 = N / N1;
@@ -759,9 +783,10 @@ __device__ __forceinline__ void zc_issue(C* dst, const CUtensorMap* map, uint64_
     tma::load_5d_hint(dst + z0 * B, map, bar, kx0 * Z::E, ky & KM, z0, ky >> kYBlockShift, b, pol);
 }
 
-// The load side of the fused z pass, run by one thread of the extra warp.
-// Barriers: bar[0], bar[1] mesh buffer k loaded; bar[2] galaxy tile loaded;
-// bar[3], bar[4] mesh buffer k free again; bar[5] galaxy tile free again.
+// The load side of the fused z pass, run by one thread of the load
+// warpgroup. Barriers: bar[0], bar[1] mesh buffer k loaded; bar[2] galaxy
+// tile loaded; bar[3], bar[4] mesh buffer k free again; bar[5] galaxy tile
+// free again (an arrival from every transform thread).
 // Per item the order is: first mesh, galaxy tile, remaining meshes, so the
 // first mesh of an item streams in while the previous item's last mesh is
 // still being transformed. Returns 0, or 1 when a wait for a free buffer ran
@@ -821,7 +846,8 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
   const int tid = threadIdx.x;
   for (int i = tid; i < N; i += blockDim.x) tws[i] = tw[i];
   if (tid == 0) {
-    for (int k = 0; k < 6; ++k) tma::mbar_init(&bar[k], 1);
+    for (int k = 0; k < 5; ++k) tma::mbar_init(&bar[k], 1);
+    tma::mbar_init(&bar[5], CT);   // every transform thread reports its last read of the galaxy tile
     tma::fence_async_shared();
   }
   __syncthreads();
@@ -866,17 +892,16 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
           a[k2].y = 0;
         }
       }
+      if (b == nb - 1) tma::mbar_arrive(&bar[5]);   // this thread is done with the galaxy tile
       if (dc_col && k1 == 0) { a[0].x = 0; a[0].y = 0; }   // k = 0 mode
-      tma::bar_sync(1, CT);
-      if (b == nb - 1 && tid == 0) tma::mbar_arrive(&bar[5]);   // galaxy tile read for this item
       C* wbuf = gg ? sbuf0 : buf;
-      stepA<C, N1, N2, true, XP>(wbuf, B, c, k1, a, tws, 1);
+      stepA_own<C, N1, N2, true, XP>(wbuf, B, c, k1, a, tws, 1);
       tma::bar_sync(1, CT);
       C* wout = Wz + (int64_t)b * Wz_stride + (int64_t)ky * P + kx0;
       for (int t = tid; t < B * N2; t += CT) {
         const int cc = t % B, n2 = t / B;
         C x[N1];
-        stepB<C, N1, N2, true, XP, K>(wbuf, B, cc, n2, x);
+        stepB_own<C, N1, N2, true, XP, K>(wbuf, B, cc, n2, x);
         if (cc < ncol) {
 #pragma unroll
           for (int n1 = 0; n1 < N1; ++n1) {
@@ -1243,14 +1268,13 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) x[k2] = cmul(x[k2], f[k2]);
       if (dc_col && k1 == 0) { x[0].x = 0; x[0].y = 0; }   // k = 0 mode
-      tma::bar_sync(1, CT);
-      stepA<C, N1, N2, true, XP>(buf, B, c, k1, x, tws, 1);
+      stepA_own<C, N1, N2, true, XP>(buf, B, c, k1, x, tws, 1);
       tma::bar_sync(1, CT);
       C* yout = S + (int64_t)b * S_stride + yoff(L, ky) + kx0;
       for (int t = tid; t < B * N2; t += CT) {
         const int cc = t % B, n2 = t / B;
         C v[N1];
-        stepB<C, N1, N2, true, XP>(buf, B, cc, n2, v);
+        stepB_own<C, N1, N2, true, XP>(buf, B, cc, n2, v);
         if (cc < ncol) {
 #pragma unroll
           for (int n1 = 0; n1 < N1; ++n1)
