@@ -268,6 +268,41 @@ __device__ __forceinline__ void stepB_own(const C* buf, int LD, int c, int n2, C
   reg_dft<C, N1, INV, K>(a);
 }
 
+// Step 1 and step A (own slots) when every thread runs exactly one task and
+// N1 = N2: task (c, q) of either step multiplies its outputs by W_N^(q m),
+// m < N1, with q = tid / B in both. The caller loads those N1 twiddles into
+// registers once (tq[m] = W_N^(q m); conjugated here for the inverse), which
+// saves 2 (N1 - 1) shared-memory loads per thread and mesh.
+template <typename C, int N1, int N2, int B, bool INV, int X>
+__device__ __forceinline__ void step1_tr(C* buf, int LD, const C (&tq)[N1], int tid) {
+  const int c = tid % B, j2 = tid / B;
+  C a[N1];
+#pragma unroll
+  for (int j1 = 0; j1 < N1; ++j1) a[j1] = buf[(N2 * j1 + j2) * LD + c];
+  reg_dft<C, N1, INV>(a);
+#pragma unroll
+  for (int k1 = 1; k1 < N1; ++k1) {
+    C w = tq[k1];
+    if (INV) w.y = -w.y;
+    a[k1] = cmul(a[k1], w);
+  }
+  if (X > 1) __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) buf[prow<X>(k1, j2, N2) * LD + c] = a[k1];
+}
+template <typename C, int N1, int N2, bool INV, int X>
+__device__ __forceinline__ void stepA_own_tr(C* buf, int LD, int c, int k1, C (&a)[N2], const C (&tq)[N1]) {
+  reg_dft<C, N2, INV>(a);
+#pragma unroll
+  for (int n2 = 1; n2 < N2; ++n2) {
+    C w = tq[n2];
+    if (INV) w.y = -w.y;
+    a[n2] = cmul(a[n2], w);
+  }
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) buf[prow<X>(k1, n2, N2) * LD + c] = a[n2];
+}
+
 template <int N> struct Split {
   static constexpr int N1 = N < 32 ? N : 32;
   static constexpr int N2 = N / N1;
@@ -858,6 +893,12 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
     return;
   }
   const int c = tid % B, k1 = tid / B;
+  constexpr bool TR = (N1 == N2) && (B * N2 == CT);   // twiddles in registers (step1_tr)
+  C tq[N1];
+  if constexpr (TR) {
+#pragma unroll
+    for (int m = 0; m < N1; ++m) tq[m] = tws[(k1 * m) % N];
+  }
   const RT inv_n3 = (RT)(1.0 / ((double)N * (double)N * (double)N));
   uint32_t ph[3] = {0, 0, 0};
   int64_t job = 0;
@@ -879,7 +920,8 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
       if (!gg) {
         if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
         ph[cur] ^= 1;
-        step1<C, N1, N2, B, false, XP>(buf, B, tws, 1, tid, CT);
+        if constexpr (TR) step1_tr<C, N1, N2, B, false, XP>(buf, B, tq, tid);
+        else step1<C, N1, N2, B, false, XP>(buf, B, tws, 1, tid, CT);
         tma::bar_sync(1, CT);
         step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
 #pragma unroll
@@ -895,7 +937,8 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
       if (b == nb - 1) tma::mbar_arrive(&bar[5]);   // this thread is done with the galaxy tile
       if (dc_col && k1 == 0) { a[0].x = 0; a[0].y = 0; }   // k = 0 mode
       C* wbuf = gg ? sbuf0 : buf;
-      stepA_own<C, N1, N2, true, XP>(wbuf, B, c, k1, a, tws, 1);
+      if constexpr (TR) stepA_own_tr<C, N1, N2, true, XP>(wbuf, B, c, k1, a, tq);
+      else stepA_own<C, N1, N2, true, XP>(wbuf, B, c, k1, a, tws, 1);
       tma::bar_sync(1, CT);
       C* wout = Wz + (int64_t)b * Wz_stride + (int64_t)ky * P + kx0;
       for (int t = tid; t < B * N2; t += CT) {
