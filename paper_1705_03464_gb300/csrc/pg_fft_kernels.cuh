@@ -778,6 +778,7 @@ struct RegSplit {
   static constexpr int RC = RC_RAW > 240 ? 240 : RC_RAW;
   static constexpr bool SPLIT = RC > RLAUNCH;   // else every warp keeps the launch count
   static_assert(CT % 128 == 0, "transform threads form whole warpgroups");
+  static_assert(!SPLIT || CT * RC + 128 * RP <= THREADS * RLAUNCH, "split exceeds the registers at launch");
 };
 
 // Gives the load warpgroup's registers to the transform warpgroups (threads
