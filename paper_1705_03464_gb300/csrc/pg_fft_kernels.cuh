@@ -221,35 +221,14 @@ __device__ __forceinline__ void step2(const C* buf, int LD, int c, int k1, C (&a
 }
 
 // Step A (inverse split from registers): a[k2] = X[k1 + N1*k2] of task
-// (c, k1) -> row (n2, k1) = W_N^(-+k1 n2) sum_k2 X W_N2^(-+k2 n2), stored at
-// prow<X>(n2, k1, N1).
-template <typename C, int N1, int N2, bool INV, int X = 1>
-__device__ __forceinline__ void stepA(C* buf, int LD, int c, int k1, C (&a)[N2],
-                                      const C* tw, int tws) {
-  reg_dft<C, N2, INV>(a);
-  if (N2 > 1 && k1 > 0) {
-#pragma unroll
-    for (int n2 = 1; n2 < N2; ++n2) a[n2] = cmul(a[n2], twid<C, INV>(tw, k1 * n2 * tws));
-  }
-#pragma unroll
-  for (int n2 = 0; n2 < N2; ++n2) buf[prow<X>(n2, k1, N1) * LD + c] = a[n2];
-}
-
-// Step B: task (c, n2) -> out[n1] = x[n2 + N2*n1]; with K < N1 / 2 only
-// n1 < K and n1 >= N1 - K are computed (see reg_dft).
-template <typename C, int N1, int N2, bool INV, int X = 1, int K = N1>
-__device__ __forceinline__ void stepB(const C* buf, int LD, int c, int n2, C (&a)[N1]) {
-#pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) a[k1] = buf[prow<X>(n2, k1, N1) * LD + c];
-  reg_dft<C, N1, INV, K>(a);
-}
-
-// Steps A and B with step A writing back into the slots its thread read in
-// step 2: task (c, k1) stores row (n2, k1) at prow<X>(k1, n2, N2), the slot
-// of its own input j2 = n2. No other thread touches those slots between
-// step 2 and step A, so the two need no barrier between them; step B then
-// reads row (n2, k1) for k1 = 0..N1-1 from prow<X>(k1, n2, N2), the access
-// pattern of step 1's stores.
+// (c, k1) -> row (n2, k1) = W_N^(-+k1 n2) sum_k2 X W_N2^(-+k2 n2). The row is
+// written back into the slot its thread read in step 2, prow<X>(k1, n2, N2)
+// (its input j2 = n2). No other thread touches those slots between step 2 and
+// step A, so the two need no barrier between them.
+// Step B: task (c, n2) reads row (n2, k1) for k1 = 0..N1-1 from
+// prow<X>(k1, n2, N2), the access pattern of step 1's stores, and leaves
+// out[n1] = x[n2 + N2*n1]; with K < N1 / 2 only n1 < K and n1 >= N1 - K are
+// computed (see reg_dft).
 template <typename C, int N1, int N2, bool INV, int X = 1>
 __device__ __forceinline__ void stepA_own(C* buf, int LD, int c, int k1, C (&a)[N2], const C* tw, int tws) {
   reg_dft<C, N2, INV>(a);
