@@ -453,20 +453,43 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
     int kx0, z, b;
     int64_t lo, hi;   // rows (compact lines, or dense lines) of the item's plane
   };
-  auto meta = [&](int64_t it, Item& m) {
-    m.kx0 = (int)(it % T) * B;
+  // an item's line range is loaded raw (fetch) one item before its first use
+  // and combined (resolve) after the next barrier, so no arithmetic waits on
+  // the loads while they are in flight
+  struct Raw {
+    int kx0, z, b;
+    int64_t base, last;
+    int32_t i0, i1;
+  };
+  auto fetch = [&](int64_t it, Raw& q) {
+    q.kx0 = (int)(it % T) * B;
     const int64_t r = it / T;
-    m.z = (int)(r % N);
-    m.b = (int)(r / N);
+    q.z = (int)(r % N);
+    q.b = (int)(r / N);
     if (idx) {
-      const int32_t* ib = idx + (int64_t)m.b * N * N;
-      const int64_t base = line_base[m.b];
-      m.lo = base + ib[(int64_t)m.z * N];
-      m.hi = base + ((m.z + 1 < N) ? (int64_t)ib[(int64_t)(m.z + 1) * N] : seg_total[m.b]);
+      const int32_t* ib = idx + (int64_t)q.b * N * N;
+      q.base = line_base[q.b];
+      q.i0 = ib[(int64_t)q.z * N];
+      if (q.z + 1 < N) q.i1 = ib[(int64_t)(q.z + 1) * N];
+      else q.last = seg_total[q.b];
+    }
+  };
+  auto resolve = [&](const Raw& q, Item& m) {
+    m.kx0 = q.kx0;
+    m.z = q.z;
+    m.b = q.b;
+    if (idx) {
+      m.lo = q.base + q.i0;
+      m.hi = q.base + ((q.z + 1 < N) ? (int64_t)q.i1 : q.last);
     } else {
-      m.lo = (int64_t)m.z * N;
+      m.lo = (int64_t)q.z * N;
       m.hi = m.lo + N;
     }
+  };
+  auto meta = [&](int64_t it, Item& m) {
+    Raw q;
+    fetch(it, q);
+    resolve(q, m);
   };
   // rows of item m into buffer dst; y of the first PRE rounds from yv
   auto gather = [&](const Item& m, C* dst, const int (&yv)[PRE], bool have_yv) {
@@ -485,7 +508,8 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
     }
     tma::cp_async_commit();
   };
-  Item cur, nxt, nn;
+  Item cur, nxt;
+  Raw pn;   // raw line range of the item after next, resolved into nxt one item later
   meta(item, cur);
   __syncthreads();   // twiddles staged, buffers cleared
   {
@@ -494,10 +518,12 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
   }
   int64_t nitem = item + gridDim.x;
   if (nitem < n_items) meta(nitem, nxt);
+  bool pend = false;
   for (int64_t job = 0; item < n_items; ++job) {
     C* buf = buf0 + (job & 1) * TILE;
     tma::cp_async_wait_all();
     __syncthreads();   // this item's rows have landed; the other buffer is clear
+    if (pend) resolve(pn, nxt);
     const int64_t nnitem = nitem + gridDim.x;
     int yv[PRE];
     if (nitem < n_items) {
@@ -508,8 +534,9 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
           yv[p] = r < nxt.hi ? line_y[r] : 0;
         }
       }
-      if (nnitem < n_items) meta(nnitem, nn);
     }
+    pend = nitem < n_items && nnitem < n_items;
+    if (pend) fetch(nnitem, pn);
     step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
     __syncthreads();
     if (nitem < n_items) gather(nxt, buf0 + ((job & 1) ^ 1) * TILE, yv, true);
@@ -525,7 +552,6 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
     item = nitem;
     cur = nxt;
     nitem = nnitem;
-    nxt = nn;
   }
 }
 
