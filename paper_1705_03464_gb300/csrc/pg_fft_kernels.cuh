@@ -1381,18 +1381,22 @@ k_y_inv_lines(const __grid_constant__ CUtensorMap mY, int nb, int P, const int32
   int64_t* s_item = reinterpret_cast<int64_t*>(bar + 2);   // [2] item per buffer
   int64_t* s_lo = s_item + 2;                              // [2] line range
   int64_t* s_hi = s_lo + 2;
+  int64_t* s_base = s_hi + 2;                              // [2] the mesh's first line
   const int T = (M1 + B - 1) / B;
   const int64_t NN = (int64_t)N * N;
   const int64_t n_items = (int64_t)T * N * nb;
   // first item at or after `it` (stride gridDim.x) whose plane holds lines
-  auto find = [&](int64_t it, int64_t& lo, int64_t& hi) {
+  auto find = [&](int64_t it, int64_t& lo, int64_t& hi, int64_t& base) {
     for (; it < n_items; it += gridDim.x) {
       const int64_t r = it / T;
       const int z = (int)(r % N), b = (int)(r / N);
       const int32_t* ib = idx + (int64_t)b * NN;
       lo = ib[(int64_t)z * N];
       hi = (z + 1 < N) ? ib[(int64_t)(z + 1) * N] : seg_total[b];
-      if (lo < hi) return it;
+      if (lo < hi) {
+        base = line_base[b];
+        return it;
+      }
     }
     return n_items;
   };
@@ -1411,7 +1415,7 @@ k_y_inv_lines(const __grid_constant__ CUtensorMap mY, int nb, int P, const int32
     tma::mbar_init(&bar[1], 1);
     tma::fence_async_shared();
     for (int k = 0; k < 2; ++k) {
-      const int64_t it = find(k == 0 ? (int64_t)blockIdx.x : s_item[0] + gridDim.x, s_lo[k], s_hi[k]);
+      const int64_t it = find(k == 0 ? (int64_t)blockIdx.x : s_item[0] + gridDim.x, s_lo[k], s_hi[k], s_base[k]);
       s_item[k] = it;
       if (it < n_items) issue(k, it);
       else break;
@@ -1429,36 +1433,45 @@ k_y_inv_lines(const __grid_constant__ CUtensorMap mY, int nb, int P, const int32
     C* buf = buf0 + cur * TILE;
     if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
     ph[cur] ^= 1;
-    const int64_t r = it / T;
-    const int b = (int)(r / N);
     const int kx0 = (int)(it % T) * B;
     const int ncol = min(B, M1 - kx0);
-    const int64_t lo = s_lo[cur], hi = s_hi[cur];
+    const int64_t lo = s_lo[cur], hi = s_hi[cur], base = s_base[cur];
+    // line numbers of the first rounds, loaded while the item is transformed
+    constexpr int RSY = Y::THREADS / B, PRE = 2;
+    int yv[PRE];
+#pragma unroll
+    for (int p = 0; p < PRE; ++p) {
+      const int64_t q = lo + k1 + (int64_t)p * RSY;
+      yv[p] = q < hi ? line_y[base + q] : 0;
+    }
     step1<C, N1, N2, B, true, XP>(buf, B, tws, 1);
-    __syncthreads();
+    __syncthreads();   // every thread has read this buffer's item data
+    // the item after next, looked up now so that its index loads overlap the
+    // transform; its tile is requested once this buffer is free
+    if (threadIdx.x == 0) {
+      const int64_t nx = s_item[cur ^ 1];
+      s_item[cur] = nx < n_items ? find(nx + gridDim.x, s_lo[cur], s_hi[cur], s_base[cur]) : n_items;
+    }
     C a[N2];
     step2<C, N1, N2, true, XP>(buf, B, c, k1, a);
     __syncthreads();
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) buf[(k1 + N1 * k2) * B + c] = a[k2];   // natural row y
     __syncthreads();
-    const int64_t base = line_base[b];
-    for (int64_t q = lo + threadIdx.x / B; q < hi; q += blockDim.x / B) {
+#pragma unroll
+    for (int p = 0; p < PRE; ++p) {
+      const int64_t q = lo + k1 + (int64_t)p * RSY;
+      if (q < hi && c < ncol) hspec[(base + q) * P + kx0 + c] = buf[yv[p] * B + c];
+    }
+    for (int64_t q = lo + k1 + (int64_t)PRE * RSY; q < hi; q += RSY) {
       const int64_t l = base + q;
       if (c < ncol) hspec[l * P + kx0 + c] = buf[line_y[l] * B + c];
     }
     __syncthreads();   // buffer free: stream in the item after the next
-    if (threadIdx.x == 0) {
-      const int64_t nx = s_item[cur ^ 1];
-      int64_t it2 = n_items;
-      if (nx < n_items) it2 = find(nx + gridDim.x, s_lo[cur], s_hi[cur]);
-      s_item[cur] = it2;
-      if (it2 < n_items) {
-        tma::fence_async_shared();
-        issue(cur, it2);
-      }
+    if (threadIdx.x == 0 && s_item[cur] < n_items) {
+      tma::fence_async_shared();
+      issue(cur, s_item[cur]);
     }
-    __syncthreads();
   }
   if (failed) {
     if (threadIdx.x == 0) {
