@@ -763,8 +763,9 @@ k_col_inv_full(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
 // scales it by 1/N^3, a power of two, so exactly), then runs every mesh of the
 // batch through forward z -> * conj(F_g) / N^3 -> k = 0 zeroed -> inverse z
 // -> window rows. While one mesh is transformed the next mesh's tile streams
-// into the second shared buffer (TMA + mbarrier), so HBM reads overlap the FFT
-// arithmetic. The inverse's last DFTs compute only the outputs n1 < K and
+// into the second shared buffer (TMA + mbarrier), issued by a load warpgroup
+// (zc_produce) while the transform warpgroups compute, so HBM reads overlap
+// the FFT arithmetic. The inverse's last DFTs compute only the outputs n1 < K and
 // n1 >= N1 - K, which hold every window row when K > w / N2 (rows
 // n = n2 + N2 n1 with |n| <= w).
 // ============================================================================
@@ -1183,14 +1184,6 @@ __device__ __forceinline__ void step1_win(C* buf, const C* xc, int w, const C* t
   }
 }
 
-// Both sides of the adjoint z pass for every mesh b of the batch, per work
-// item (ky, kx tile): F_b = z transform of S_b, X_b = z transform of the
-// zero-padded window column; A += F_b conj(X_b) accumulates in shared memory
-// over the batch (A read and written once per item); then Y_b = inverse z of
-// X_b F_g (k = 0 set to zero), written over S_b's column, which this CTA has
-// already read. Persistent and TMA fed; mesh b's S and window tiles share one
-// of two slots so the next mesh streams in during the transforms. F_g is read
-// from global memory (L2: its tile is reused by every mesh of the item).
 // The load side of the adjoint z pass, run by one thread of the load
 // warpgroup (barriers as in k_zadj). Per item the order is: first mesh's slot,
 // A tile, remaining meshes' slots. Returns 0, or 1 when a wait for a free
@@ -1234,6 +1227,15 @@ __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CU
   return failed;
 }
 
+// Both sides of the adjoint z pass for every mesh b of the batch, per work
+// item (ky, kx tile): F_b = z transform of S_b, X_b = z transform of the
+// zero-padded window column; A += F_b conj(X_b) accumulates in shared memory
+// over the batch (A read and written once per item); then Y_b = inverse z of
+// X_b F_g (k = 0 set to zero), written over S_b's column, which this CTA has
+// already read. Persistent and TMA fed; mesh b's S and window tiles share one
+// of two slots so the next mesh streams in during the transforms, issued by a
+// load warpgroup (za_produce) while the transform warpgroups compute. F_g is
+// read from global memory (L2: its tile is reused by every mesh of the item).
 template <typename C, int N, int B>
 __global__ void __launch_bounds__(ZAdj<C, N, B>::THREADS, 1)
 k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mX,
