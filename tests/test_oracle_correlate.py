@@ -163,3 +163,98 @@ def test_cell_bins_counts_and_mu():
     assert at(0, 0, 5) == 2 and at(5, 0, 0) == 0 and at(0, 0, 0) == 0
     _, agg2 = oc.cell_bins(N, L, (0.0, 6.0), 3, 2.0, w)
     assert not agg2[((5 + w) * W + w) * W + w] and agg2[(w * W + w) * W + w + 3]
+
+
+def _ngp_node(x, L, N):
+    dx = L / N
+    return tuple(int(math.floor(c / dx + 0.5)) % N for c in x)
+
+
+def _offset_counts(pa, pb, L, N):
+    """Pure-Python D(r) for NGP unit weights: the number of (a, b) point
+    pairs whose node offset node(a) - node(b) is r (mod N), keyed by the
+    signed offset (ox, oy, oz) in (-N/2, N/2]."""
+    D = {}
+    nb = [_ngp_node(q, L, N) for q in pb]
+    for p in pa:
+        a = _ngp_node(p, L, N)
+        for b in nb:
+            o = []
+            for k in range(3):
+                d = (a[k] - b[k]) % N
+                o.append(d - N if d > N // 2 else d)
+            o = tuple(o)
+            D[o] = D.get(o, 0) + 1
+    return D
+
+
+def _shell_sums_brute(D, n_a, n_b, L, N, w, r_edges, n_mur, r_perp_cut):
+    """Per (r, mu_r) bin: sum C, sum C^2, cell count, and the same over the
+    aggregate (r range, r_perp >= cut), with C(r) = N^3 D(r) / (n_a n_b) - 1
+    per window cell, accumulated cell by cell in pure Python."""
+    dx = L / N
+    nrb = (len(r_edges) - 1) * n_mur
+    s1, s2, n = [0.0] * nrb, [0.0] * nrb, [0] * nrb
+    a1 = a2 = 0.0
+    na = 0
+    for oz in range(-w, w + 1):
+        for oy in range(-w, w + 1):
+            for ox in range(-w, w + 1):
+                R2 = ox * ox + oy * oy + oz * oz
+                r2 = R2 * dx * dx
+                k = -1
+                for i in range(len(r_edges) - 1):
+                    if r_edges[i] ** 2 <= r2 < r_edges[i + 1] ** 2:
+                        k = i
+                if k < 0:
+                    continue
+                mu = abs(oz) / math.sqrt(R2) if R2 > 0 else 0.0
+                m = min(n_mur - 1, int(math.floor(n_mur * mu)))
+                c = N ** 3 * D.get((ox, oy, oz), 0) / (n_a * n_b) - 1.0
+                b = k * n_mur + m
+                s1[b] += c
+                s2[b] += c * c
+                n[b] += 1
+                if (ox * ox + oy * oy) * dx * dx >= r_perp_cut ** 2:
+                    a1 += c
+                    a2 += c * c
+                    na += 1
+    return np.array(s1), np.array(s2), np.array(n), a1, a2, na
+
+
+@pytest.mark.parametrize("r_perp_cut", [0.0, 2.0])
+def test_shell_sum_of_squares_and_xi_dw_equal_brute_force(r_perp_cut):
+    """eq. xi_dw with a shell W: xi(d_w) = sum C_gg^2 / sum C_gg over a bin.
+    The squared sums (per bin and over the aggregate support, with and
+    without the r_perp cut) are checked against C summed cell by cell from
+    pure-Python NGP offset counts; the pipeline's xi_dw and xi_dw_agg follow."""
+    L, N = 16.0, 16
+    rng = np.random.default_rng(11)
+    g = rng.random((36, 3)) * L
+    # clustered galaxies, so that C_gg is far from constant inside a shell
+    g[:12] = (g[0] + rng.normal(0.0, 1.2, (12, 3))) % L
+    r_edges = (1.0, 2.5, 4.0, 6.0)
+    n_mur = 2
+    w = oc.window_half(N, L, r_edges[-1])
+    D = _offset_counts(g, g, L, N)
+    b1, b2, bn, ba1, ba2, bna = _shell_sums_brute(D, len(g), len(g), L, N, w, r_edges, n_mur,
+                                                  r_perp_cut)
+    bins, agg = oc.cell_bins(N, L, r_edges, n_mur, r_perp_cut, w)
+    m = om.deposit(g, None, L, N, 0)
+    s1, s2, n, a1, a2, na = oc.bin_sums(oc.window_of(oc.correlate_mesh(m, m), w), bins, agg,
+                                        len(bn))
+    assert n.tolist() == bn.tolist() and na == bna
+    np.testing.assert_allclose(s1, b1, rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(s2, b2, rtol=1e-12, atol=1e-9)
+    assert abs(a1 - ba1) <= 1e-9 * max(1.0, abs(ba1))
+    assert abs(a2 - ba2) <= 1e-12 * abs(ba2)
+    # the shell sum of squares is not the square of the shell sum
+    assert np.max(np.abs(b2 - b1 ** 2 / np.maximum(bn, 1))) > 1.0
+    # through the whole forward path: xi_dw, xi_dw_agg and the raw sums
+    p = pipeline.Params(L, N, 0, (0.0, 1.5, 3.0), 1, r_edges, n_mur, 0.0, r_perp_cut)
+    out = pipeline.run(p, g, form="mesh")
+    np.testing.assert_allclose(out["sum2_gg"], b2, rtol=1e-12, atol=1e-9)
+    assert abs(out["sum2_gg_agg"] - ba2) <= 1e-12 * abs(ba2)
+    np.testing.assert_allclose(out["xi_dw"], b2 / b1, rtol=1e-9)
+    assert abs(out["xi_dw_agg"] - ba2 / ba1) <= 1e-9 * abs(ba2 / ba1)
+    assert out["n_cells_agg"] == bna
