@@ -339,11 +339,16 @@ pg_status pg_fft_c2r_3d(pg_plan* plan, const void* d_in, void* d_out, void* stre
  *   already inside [0, L); d_w [n] FP32 device or NULL; s_edges [n_s+1] host,
  *   ascending, s_edges[n_s] < box_L/2; d_dd, d_ddq [n_s*n_mu] int64 device
  *   outputs (zeroed by the call): pair counts and sums of
- *   llrint(w_i w_j 2^32). Asynchronous on `stream`.
+ *   llrint(w_i w_j 2^32). Positions holding NaN or Inf give
+ *   PG_ERR_INVALID_ARG (as in pg_forward): the call synchronises `stream`
+ *   once to read that check back, then launches the rest asynchronously.
  * The first call on a device looks up the scratch array's device address for
- * that device; make that first call before any stream capture. All calls
- * share the one array, so calls that overlap on the GPU (different streams or
- * host threads) race and must be serialised by the caller. */
+ * that device; make that first call before any stream capture. The address is
+ * kept for the life of the process and does not survive a reset of the
+ * device (cudaDeviceReset): do not call this entry point on a device after
+ * resetting it. All calls share the one array, so calls that overlap on the
+ * GPU (different streams or host threads) race and must be serialised by the
+ * caller. */
 pg_status pg_pair_counts_static(int64_t n, const double* d_pos, const float* d_w,
                                 double box_L, int32_t n_s, const double* s_edges,
                                 int32_t n_mu, int64_t* d_dd, int64_t* d_ddq, void* stream);

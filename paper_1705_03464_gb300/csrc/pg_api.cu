@@ -1306,8 +1306,10 @@ pg_status plan_create(const pg_params* prm, const pg_plan* share, pg_plan** out)
   // (d_perp, d_par) cylinder
   const double smax = q.pair_grid ? sqrt(q.s_edges[q.n_s] * q.s_edges[q.n_s] + q.par_edges[q.n_mu] * q.par_edges[q.n_mu])
                                   : q.s_edges[q.n_s];
-  int nc = (int)floor(q.box_L / (smax * (1.0 + 1e-9)));
-  if (nc > 256) nc = 256;
+  // clamped in FP64 before the conversion: a tiny s_max gives a ratio far
+  // above INT_MAX
+  const double ncr = floor(q.box_L / (smax * (1.0 + 1e-9)));
+  int nc = ncr > 256.0 ? 256 : (int)ncr;
   if (nc < 3) nc = 1;
   g.nc = nc;
   g.cell_scale = (double)nc / q.box_L;

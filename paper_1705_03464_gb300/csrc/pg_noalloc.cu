@@ -30,12 +30,17 @@ constexpr size_t kOffStart = kOffCount + up256(4 * (kMaxCells + 1));
 constexpr size_t kOffCursor = kOffStart + up256(4 * (kMaxCells + 1));
 constexpr size_t kOffTmp = kOffCursor + up256(4 * (kMaxCells + 1));
 constexpr size_t kOffTot = kOffTmp + up256(8 * kScanTmp);
-constexpr size_t kBytes = kOffTot + 256;                         // about 8.4 MB
+constexpr size_t kOffFlag = kOffTot + 256;                       // int32 non-finite flag
+constexpr size_t kBytes = kOffFlag + 256;                        // about 8.4 MB
 
 static __device__ __align__(256) unsigned char g_pair_scratch[kBytes];
 
 // Device address of g_pair_scratch on the current device, looked up once per
-// device (the symbol's host-side name is not a device address).
+// device (the symbol's host-side name is not a device address). The address
+// is kept for the life of the process: it does not survive a reset of the
+// device's primary context (cudaDeviceReset), after which the module and its
+// array are loaded anew, so the entry point is not to be called on a device
+// after a reset.
 pg_status scratch_on_current_device(unsigned char** out) {
   static std::mutex mu;
   static void* addr[256] = {};
@@ -77,8 +82,10 @@ extern "C" pg_status pg_pair_counts_static(int64_t n, const double* d_pos, const
   memset(&g, 0, sizeof(g));
   g.L = box_L;
   g.halfL = 0.5 * box_L;
-  int nc = (int)floor(box_L / (s_edges[n_s] * (1.0 + 1e-9)));
-  if (nc > kMaxCellsPerSide) nc = kMaxCellsPerSide;   // larger cells stay correct
+  // cells per side, clamped in FP64 before the conversion (a tiny s_max
+  // gives a ratio far above INT_MAX); larger cells stay correct
+  const double ncr = floor(box_L / (s_edges[n_s] * (1.0 + 1e-9)));
+  int nc = ncr > (double)kMaxCellsPerSide ? kMaxCellsPerSide : (int)ncr;
   if (nc < 3) nc = 1;
   g.nc = nc;
   g.cell_scale = (double)nc / box_L;
@@ -98,7 +105,16 @@ extern "C" pg_status pg_pair_counts_static(int64_t n, const double* d_pos, const
               reinterpret_cast<int64_t*>(base + kOffTmp),
               reinterpret_cast<int64_t*>(base + kOffTot)};
   const size_t P = (size_t)n_s * n_mu;
-  cudaError_t e = cudaMemsetAsync(d_dd, 0, 8 * P, s);
+  // positions holding NaN or Inf are refused, as in pg_forward: the flag is
+  // read back before anything else is launched (one stream synchronisation)
+  int32_t* flag = reinterpret_cast<int32_t*>(base + kOffFlag);
+  int32_t hflag = 0;
+  cudaError_t e = cudaMemsetAsync(flag, 0, 4, s);
+  if (e == cudaSuccess) e = launch_check_finite(n, d_pos, flag, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && hflag) return PG_ERR_INVALID_ARG;
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_dd, 0, 8 * P, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_ddq, 0, 8 * P, s);
   if (e == cudaSuccess)
     e = launch_transform(n, box_L, 0.0, d_pos, nullptr, nullptr, x, x + kMaxGal, x + 2 * kMaxGal, s);

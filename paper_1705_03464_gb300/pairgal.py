@@ -147,6 +147,67 @@ def _ptr(t):
     return t.data_ptr()
 
 
+_TORCH_DT = {"f64": "float64", "f32": "float32", "i64": "int64", "i32": "int32",
+             "c64": "complex64", "c128": "complex128"}
+
+
+def _dev(t, what, dtype, shape, device=None, optional=False):
+    """Checks a device argument before its address goes to the library: a
+    contiguous CUDA tensor of the given dtype ('f64', 'f32', ...) and shape
+    (a tuple; None entries match any size), on `device` if given. The kernels
+    read exactly the bytes the shape implies, so a wrong dtype, a strided
+    view, a short array or a host tensor would make them read outside the
+    buffer. Raises PairgalError(PG_ERR_INVALID_ARG) otherwise."""
+    if t is None:
+        if optional:
+            return None
+        raise PairgalError(PG_ERR_INVALID_ARG, f"{what} is required")
+    import torch
+    bad = None
+    if not isinstance(t, torch.Tensor):
+        bad = f"a torch tensor, got {type(t).__name__}"
+    elif not t.is_cuda:
+        bad = "a CUDA tensor"
+    elif t.dtype != getattr(torch, _TORCH_DT[dtype]):
+        bad = f"dtype {_TORCH_DT[dtype]}, got {t.dtype}"
+    elif not t.is_contiguous():
+        bad = "contiguous"
+    elif t.dim() != len(shape) or any(w is not None and int(g) != int(w) for g, w in zip(t.shape, shape)):
+        bad = f"shape {tuple('*' if w is None else w for w in shape)}, got {tuple(t.shape)}"
+    elif device is not None and t.device != device:
+        bad = f"on {device}, got {t.device}"
+    if bad:
+        raise PairgalError(PG_ERR_INVALID_ARG, f"{what} must be {bad}")
+    return t
+
+
+def _host_arr(a, what, dtype, shape, optional=False):
+    """Host counterpart of _dev: a C-contiguous numpy array of the dtype (a
+    copy is made if needed) and the given shape (None entries match any)."""
+    if a is None:
+        if optional:
+            return None
+        raise PairgalError(PG_ERR_INVALID_ARG, f"{what} is required")
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if a.ndim != len(shape) or any(w is not None and g != w for g, w in zip(a.shape, shape)):
+        raise PairgalError(PG_ERR_INVALID_ARG,
+                           f"{what} must have shape {tuple('*' if w is None else w for w in shape)}, "
+                           f"got {a.shape}")
+    return a
+
+
+def _catalogue(pos, vel, w):
+    """Device catalogue checks shared by the forward entry points: pos [n, 3]
+    float64, vel [n, 3] float32 or None, w [n] float32 or None, one device."""
+    if pos is None:
+        return 0
+    _dev(pos, "pos", "f64", (None, 3))
+    n = int(pos.shape[0])
+    _dev(vel, "vel", "f32", (n, 3), pos.device, optional=True)
+    _dev(w, "w", "f32", (n,), pos.device, optional=True)
+    return n
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -276,7 +337,7 @@ class Plan(Problem):
 def pg_forward(plan: Plan, pos, vel=None, w=None, stream=None):
     """Full forward path on device tensors: pos [n,3] float64, vel [n,3]
     float32 or None, w [n] float32 or None. Returns host numpy outputs."""
-    n = 0 if pos is None else int(pos.shape[0])
+    n = _catalogue(pos, vel, w)
     res, arrs = plan.new_result()
     st = _lib.pg_forward(plan.handle, n, _ptr(pos), _ptr(vel), _ptr(w), C.byref(res), _stream(stream))
     _check(st, "pg_forward")
@@ -284,9 +345,13 @@ def pg_forward(plan: Plan, pos, vel=None, w=None, stream=None):
 
 
 def pg_forward_host(plan: Plan, pos: np.ndarray, vel=None, w=None, stream=None):
-    """Full forward path from host (preferably pinned) arrays."""
-    pos = np.ascontiguousarray(pos, dtype=np.float64) if isinstance(pos, np.ndarray) else pos
+    """Full forward path from host (preferably pinned) arrays: pos [n, 3]
+    float64, vel [n, 3] float32 or None, w [n] float32 or None (converted
+    to those types if needed)."""
+    pos = _host_arr(pos, "pos", np.float64, (None, 3))
     n = int(pos.shape[0])
+    vel = _host_arr(vel, "vel", np.float32, (n, 3), optional=True)
+    w = _host_arr(w, "w", np.float32, (n,), optional=True)
     res, arrs = plan.new_result()
     st = _lib.pg_forward_host(plan.handle, n, _ptr(pos), _ptr(vel), _ptr(w), C.byref(res), _stream(stream))
     _check(st, "pg_forward_host")
@@ -295,8 +360,11 @@ def pg_forward_host(plan: Plan, pos: np.ndarray, vel=None, w=None, stream=None):
 
 def pg_transform_positions(pos, box_L, rsd_factor=0.0, vel=None, out=None, stream=None):
     import torch
+    _dev(pos, "pos", "f64", (None, 3))
+    _dev(vel, "vel", "f32", (pos.shape[0], 3), pos.device, optional=True)
     if out is None:
         out = torch.empty_like(pos)
+    _dev(out, "out", "f64", tuple(pos.shape), pos.device)
     _check(_lib.pg_transform_positions(int(pos.shape[0]), float(box_L), float(rsd_factor),
                                        _ptr(pos), _ptr(vel), _ptr(out), _stream(stream)),
            "pg_transform_positions")
@@ -306,8 +374,8 @@ def pg_transform_positions(pos, box_L, rsd_factor=0.0, vel=None, out=None, strea
 def pg_find_pairs(plan: Plan, pos, w=None, with_list=True, stream=None):
     """Pairs of wrapped device positions: counts (and the bin-grouped list)."""
     import torch
+    n = _catalogue(pos, None, w)
     dev = pos.device
-    n = int(pos.shape[0])
     dd = torch.zeros(plan.P, dtype=torch.int64, device=dev)
     ddq = torch.zeros(plan.P, dtype=torch.int64, device=dev)
     npairs = C.c_int64(0)
@@ -334,8 +402,11 @@ def pg_find_pairs(plan: Plan, pos, w=None, with_list=True, stream=None):
 
 def pg_deposit_dense(pos, w, box_L, mesh_n, assign, mesh=None, stream=None):
     import torch
+    _dev(pos, "pos", "f64", (None, 3))
+    _dev(w, "w", "f64", (pos.shape[0],), pos.device, optional=True)
     if mesh is None:
         mesh = torch.zeros((mesh_n, mesh_n, mesh_n), dtype=torch.int64, device=pos.device)
+    _dev(mesh, "mesh", "i64", (mesh_n, mesh_n, mesh_n), pos.device)
     _check(_lib.pg_deposit_dense(int(pos.shape[0]), _ptr(pos), _ptr(w), float(box_L), int(mesh_n),
                                  int(assign), _ptr(mesh), _stream(stream)), "pg_deposit_dense")
     return mesh
@@ -343,25 +414,37 @@ def pg_deposit_dense(pos, w, box_L, mesh_n, assign, mesh=None, stream=None):
 
 def pg_fft_r2c_3d(plan: Plan, f, out=None, stream=None):
     import torch
-    N = f.shape[0]
-    cdt = torch.complex128 if f.dtype == torch.float64 else torch.complex64
+    N = int(plan.params.mesh_n)
+    dbl = plan.params.precision == 1
+    _dev(f, "f", "f64" if dbl else "f32", (N, N, N))
+    cdt = torch.complex128 if dbl else torch.complex64
     if out is None:
         out = torch.empty((N, N, N // 2 + 1), dtype=cdt, device=f.device)
+    _dev(out, "out", "c128" if dbl else "c64", (N, N, N // 2 + 1), f.device)
     _check(_lib.pg_fft_r2c_3d(plan.handle, _ptr(f), _ptr(out), _stream(stream)), "pg_fft_r2c_3d")
     return out
 
 
 def pg_fft_c2r_3d(plan: Plan, F, out=None, stream=None):
     import torch
-    N = F.shape[0]
-    rdt = torch.float64 if F.dtype == torch.complex128 else torch.float32
+    N = int(plan.params.mesh_n)
+    dbl = plan.params.precision == 1
+    _dev(F, "F", "c128" if dbl else "c64", (N, N, N // 2 + 1))
+    rdt = torch.float64 if dbl else torch.float32
     if out is None:
         out = torch.empty((N, N, N), dtype=rdt, device=F.device)
+    _dev(out, "out", "f64" if dbl else "f32", (N, N, N), F.device)
     _check(_lib.pg_fft_c2r_3d(plan.handle, _ptr(F), _ptr(out), _stream(stream)), "pg_fft_c2r_3d")
     return out
 
 
 def pg_correlate_points(plan: Plan, pts_a, w_a, pts_b, w_b, stream=None):
+    """Two device point sets [n, 3] float64 (inside [0, L)) with float64
+    weights [n] or None: binned sums of C_ab (pg_correlate_points)."""
+    _dev(pts_a, "pts_a", "f64", (None, 3))
+    _dev(w_a, "w_a", "f64", (pts_a.shape[0],), pts_a.device, optional=True)
+    _dev(pts_b, "pts_b", "f64", (None, 3), pts_a.device)
+    _dev(w_b, "w_b", "f64", (pts_b.shape[0],), pts_a.device, optional=True)
     Q = plan.Q
     s1 = np.zeros(Q)
     s2 = np.zeros(Q)
@@ -379,6 +462,7 @@ def pg_pair_counts_static(pos, w, box_L, s_edges, n_mu, stream=None):
     itself allocates no device memory (the two output tensors are created
     here, by torch, before the call)."""
     import torch
+    _catalogue(pos, None, w)
     edges = np.ascontiguousarray(s_edges, dtype=np.float64)
     P = (len(edges) - 1) * int(n_mu)
     dd = torch.empty(P, dtype=torch.int64, device=pos.device)
@@ -453,8 +537,11 @@ class PairGalFn:
 def pg_hod_weights(mass, kind, kh, theta, with_grad=True, stream=None):
     """Soft HOD weights w [n] FP32 and dw/dtheta [n, 5] FP64 (device tensors)."""
     import torch
+    _dev(mass, "mass", "f64", (None,))
     n = int(mass.shape[0])
-    th = np.ascontiguousarray(theta, dtype=np.float64)
+    _dev(kind, "kind", "i32", (n,), mass.device)
+    _dev(kh, "kh", "f32", (n,), mass.device)
+    th = _host_arr(theta, "theta", np.float64, (5,))
     w = torch.empty(max(n, 1), dtype=torch.float32, device=mass.device)
     dw = torch.empty((max(n, 1), 5), dtype=torch.float64, device=mass.device) if with_grad else None
     _check(_lib.pg_hod_weights(n, _ptr(mass), _ptr(kind), _ptr(kh), _ptr(th), _ptr(w), _ptr(dw),
@@ -463,6 +550,8 @@ def pg_hod_weights(mass, kind, kh, theta, with_grad=True, stream=None):
 
 
 def pg_hod_chain(plan: Plan, wbar, dw, stream=None):
+    _dev(wbar, "wbar", "f64", (None,))
+    _dev(dw, "dw", "f64", (wbar.shape[0], 5), wbar.device)
     out = np.zeros(5)
     _check(_lib.pg_hod_chain(plan.handle, int(wbar.shape[0]), _ptr(wbar), _ptr(dw), _ptr(out),
                              _stream(stream)), "pg_hod_chain")
@@ -580,7 +669,7 @@ def pg_forward_smooth(plan: Plan, w_params, pos, vel=None, w=None, stream=None):
     """The paper's own smooth-W estimator (pg_forward_smooth) on device
     tensors; w_params = (sigma, r_s, s0, r_cut). Returns host numpy outputs
     per (s, mu) pair bin plus den and xi_dw."""
-    n = 0 if pos is None else int(pos.shape[0])
+    n = _catalogue(pos, vel, w)
     P = plan.P
     arrs = {"dd": np.zeros(P, np.int64), "xi_ss": np.full(P, np.nan), "num": np.full(P, np.nan),
             "b_pg": np.full(P, np.nan), "q_eff": np.full(P, np.nan), "den": np.full(1, np.nan),
