@@ -266,6 +266,40 @@ pg_status pg_hod_weights(int64_t n, const double* d_mass, const int32_t* d_kind,
 pg_status pg_hod_chain(pg_plan* plan, int64_t n, const double* d_wbar, const double* d_dw_dtheta,
                        double* h_grad_theta, void* stream);
 
+/* pg_hod_weights with the second derivatives as well: d_d2w_dtheta2 [n][15]
+ * FP64 device, the upper triangle j <= k of d2w/dtheta_j dtheta_k in row
+ * order (00 01 02 03 04 11 12 13 14 22 23 24 33 34 44), from the chain rule
+ * through eq. hod's closed forms. The satellite weight's second derivatives
+ * in log10 M_cut and kappa are unbounded at M = kappa M_cut when alpha < 2
+ * (the weight is not twice differentiable there). All outputs required. */
+pg_status pg_hod_weights2(int64_t n, const double* d_mass, const int32_t* d_kind, const float* d_kh,
+                          const double* h_theta, float* d_w, double* d_dw_dtheta,
+                          double* d_d2w_dtheta2, void* stream);
+
+/* Sec. 5, eqs. 2pf_emulate_1st and 2pf_emulate_2nd: the first and second
+ * derivatives of the pair-count statistics with respect to the HOD
+ * parameters, which the paper solves for from 14 separate evaluations, here
+ * exact from the soft weights' derivatives in one pass over the pairs. The
+ * call enumerates the pairs of the catalogue (positions d_pos [n][3] FP64,
+ * d_vel [n][3] FP32 for RSD plans, else NULL) with the plan's pair binning,
+ * then, with w = d_w [n] FP32 (the weights the forward would use, widened),
+ * dw = d_dw_dtheta [n][5] and d2w = d_d2w_dtheta2 [n][15] (pg_hod_weights2):
+ *   DD_b = sum over the pairs of bin b of w_i w_j (FP64 products), R =
+ *   ((sum w)^2 - sum w^2)/2, xi_b = DD_b / (R V_b / L^3) - 1 (eq.
+ *   2PCF_d_collapsed), and on the (d_perp, d_par) grid w(d_perp)_k =
+ *   sum_m 2 (l_hi - l_lo) xi_{k,m} (eq. 2PCF_los_integrated_explicit),
+ * each with its derivatives by the product and quotient rules. Outputs
+ * (host): h_xi [P][21] per pair bin and h_w_perp [n_s][21] (may be NULL;
+ * NaN unless the plan bins on the grid), each row [value, d/dtheta_j (5),
+ * d2/dtheta_j dtheta_k (15, upper triangle as above)]. Sums are FP64 in a
+ * fixed order. The plan's pair buffers are reused, so a following
+ * pg_backward needs a new pg_forward. Synchronises the stream. Errors:
+ * PG_ERR_INVALID_ARG for NULL arguments, RSD without velocities, or
+ * positions holding NaN or Inf. */
+pg_status pg_hod_pair_derivs(pg_plan* plan, int64_t n, const double* d_pos, const float* d_vel,
+                             const float* d_w, const double* d_dw_dtheta, const double* d_d2w_dtheta2,
+                             double* h_xi, double* h_w_perp, void* stream);
+
 /* Low-level form of the estimator for two arbitrary point sets (Sec. 2.1,
  * eq. bpg_initial): deposits set a and set b, correlates them, and bins
  * C_ab(r) = (1/N^3) sum_x delta_b(x) delta_a(x + r) by (r, mu_r).
@@ -313,6 +347,25 @@ pg_status pg_find_pairs(pg_plan* plan, int64_t n, const double* d_pos,
 pg_status pg_deposit_dense(int64_t n, const double* d_pts, const double* d_w,
                            double box_L, int32_t mesh_n, int32_t assign,
                            int64_t* d_mesh, void* stream);
+
+/* Sec. 3.5 as the estimator itself deposits: the compact-line mass
+ * assignment the forward path runs on each batch of pair meshes (line
+ * flags, their scan, the line numbering and the Q32.32 int64 atomics into
+ * the touched x-lines), with the plan's mesh and assignment, exposed so that
+ * its integer meshes can be compared bit for bit. d_pts [n][3] FP64 device
+ * (inside [0, L)), d_w [n] FP64 device or NULL (= 1); d_bin [n] int32 device,
+ * the mesh of each point in [0, nb), or NULL for one mesh (nb = 1);
+ * 1 <= nb <= the plan's pair meshes per batch. Writes d_mesh[nb][N][N][N]
+ * int64 (device, caller-owned, overwritten): the compact lines scattered
+ * back to dense meshes (untouched lines are zero); h_qsum[nb] (host, may be
+ * NULL): each mesh's total; *h_n_lines (host, may be NULL): the number of
+ * touched lines. Uses the plan's workspace; synchronises the stream.
+ * Errors: PG_ERR_INVALID_ARG for a NULL plan, mesh or points, nb out of
+ * range, d_bin NULL with nb != 1, or a d_bin entry outside [0, nb) (checked
+ * on the device before the deposit). */
+pg_status pg_deposit_lines(pg_plan* plan, int64_t n, const double* d_pts, const double* d_w,
+                           const int32_t* d_bin, int32_t nb, int64_t* d_mesh, int64_t* h_qsum,
+                           int64_t* h_n_lines, void* stream);
 
 /* Sec. 3.6 (the transforms the estimator is built on): forward real-to-
  * complex 3D DFT F(k) = sum_x f(x) exp(-2 pi i k.x / N) of a dense mesh

@@ -135,6 +135,8 @@ struct pg_plan {
   DevBuf &line_z, &wlines, &Xs, &As, &Xw, &cggw;
   DevBuf psi, psj, cell_bin, cell_agg, wl_idx, wl_tot, wl_base, wl_y;
   DevBuf adjb, gout, gp, gj, part;
+  // HOD-parameter derivatives of the pair counts: bin offsets, sums, partials, outputs
+  DevBuf hd;
   // smooth-W estimator: W's spectrum (cached for wk_key), a spectrum of
   // scratch, bin offsets, sums, partial sums and outputs
   DevBuf Wk, Gs, sm_off, sm_sums, sm_part, sm_out;
@@ -1378,7 +1380,7 @@ void pg_plan_destroy(pg_plan* p) {
                    &p->psj, &p->cell_bin, &p->cell_agg, &p->wl_idx, &p->wl_tot, &p->wl_base,
                    &p->wl_y, &p->adjb, &p->gout, &p->gp, &p->gj, &p->part, &p->Wk, &p->Gs,
                    &p->sm_off, &p->sm_sums, &p->sm_part, &p->sm_out, &p->sa_g, &p->sa_v, &p->sa_gp,
-                   &p->sa_gj, &p->sa_fj, &p->sa_mesh, &p->sa_spec};
+                   &p->sa_gj, &p->sa_fj, &p->sa_mesh, &p->sa_spec, &p->hd};
   for (DevBuf* b : all) b->release(&p->total);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   cudaSetDevice(cur);
@@ -1454,8 +1456,75 @@ pg_status pg_hod_weights(int64_t n, const double* d_mass, const int32_t* d_kind,
                          const double* h_theta, float* d_w, double* d_dw_dtheta, void* stream) {
   if (n < 0 || !h_theta || (n > 0 && (!d_mass || !d_kind || !d_kh || !d_w))) return PG_ERR_INVALID_ARG;
   if (!(h_theta[2] > 0.0)) return PG_ERR_INVALID_ARG;
-  PG_TRY(launch_hod_weights(n, d_mass, d_kind, d_kh, h_theta, d_w, d_dw_dtheta,
+  PG_TRY(launch_hod_weights(n, d_mass, d_kind, d_kh, h_theta, d_w, d_dw_dtheta, nullptr,
                             static_cast<cudaStream_t>(stream)));
+  return PG_OK;
+}
+
+pg_status pg_hod_weights2(int64_t n, const double* d_mass, const int32_t* d_kind, const float* d_kh,
+                          const double* h_theta, float* d_w, double* d_dw_dtheta,
+                          double* d_d2w_dtheta2, void* stream) {
+  if (n < 0 || !h_theta || (n > 0 && (!d_mass || !d_kind || !d_kh || !d_w || !d_dw_dtheta || !d_d2w_dtheta2)))
+    return PG_ERR_INVALID_ARG;
+  if (!(h_theta[2] > 0.0)) return PG_ERR_INVALID_ARG;
+  PG_TRY(launch_hod_weights(n, d_mass, d_kind, d_kh, h_theta, d_w, d_dw_dtheta, d_d2w_dtheta2,
+                            static_cast<cudaStream_t>(stream)));
+  return PG_OK;
+}
+
+pg_status pg_hod_pair_derivs(pg_plan* p, int64_t n, const double* d_pos, const float* d_vel,
+                             const float* d_w, const double* d_dw_dtheta, const double* d_d2w_dtheta2,
+                             double* h_xi, double* h_w_perp, void* stream) {
+  if (!p || n < 0 || !h_xi || (n > 0 && (!d_pos || !d_w || !d_dw_dtheta || !d_d2w_dtheta2)))
+    return PG_ERR_INVALID_ARG;
+  if (p->prm.rsd_factor != 0.0 && n > 0 && !d_vel) return PG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->fwd_ok = false;   // the pair buffers are reused
+  p->smooth_ok = false;
+  prof_begin(p);
+  const long long launches0 = launch_counter().load();
+  std::vector<unsigned long long> hdd;
+  int64_t np = 0;
+  int nonfinite = 0;
+  PG_TRY(positions_and_pairs(p, n, d_pos, d_vel, d_w, hdd, &np, &nonfinite, s));
+  if (nonfinite) return PG_ERR_INVALID_ARG;
+  const int P = p->nPB, n_s = p->prm.n_s;
+  std::vector<int64_t> off(P + 1, 0);
+  for (int b = 0; b < P; ++b) off[b + 1] = off[b] + (int64_t)hdd[b];
+  // offsets, pair sums [P][21], weight sums [2][21] and their partials, xi [P][21], w_perp [n_s][21]
+  const size_t n_off = P + 1, n_dd = (size_t)P * kHodVals, n_norm = 2 * kHodVals,
+               n_part = (size_t)kHodNormBlocks * 2 * kHodVals, n_xi = (size_t)P * kHodVals,
+               n_wp = (size_t)n_s * kHodVals;
+  PG_TRY(p->hd.ensure(8 * (n_off + n_dd + n_norm + n_part + n_xi + n_wp), &p->total));
+  int64_t* d_off = p->hd.as<int64_t>();
+  double* d_dd = p->hd.as<double>() + n_off;
+  double* d_norm = d_dd + n_dd;
+  double* d_part = d_norm + n_norm;
+  double* d_xi = d_part + n_part;
+  double* d_wp = d_xi + n_xi;
+  PG_TRY(cudaMemcpyAsync(d_off, off.data(), 8 * n_off, cudaMemcpyHostToDevice, s));
+  {
+    ProfScope ps(p, PG_FAM_PAIRS, s, (8.0 + 4.0 * 2 + 2.0 * (4.0 + 40.0 + 120.0)) * (double)np +
+                                         (4.0 + 40.0 + 120.0) * (double)n);
+    PG_TRY(launch_hod_norm(n, d_w, d_dw_dtheta, d_d2w_dtheta2, d_part, d_norm, s));
+    PG_TRY(launch_hod_pair_sums(P, d_off, p->psi.as<int32_t>(), p->psj.as<int32_t>(), d_w, d_dw_dtheta,
+                                d_d2w_dtheta2, d_dd, s));
+    const double L = p->prm.box_L;
+    PG_TRY(launch_hod_xi(n_s, p->prm.n_mu, d_dd, d_norm, p->vbin_d.as<double>(),
+                         p->prm.pair_grid ? p->wcoef_d.as<double>() : nullptr, 1.0 / (L * L * L), d_xi,
+                         d_wp, s));
+  }
+  PG_TRY(cudaMemcpyAsync(h_xi, d_xi, 8 * n_xi, cudaMemcpyDeviceToHost, s));
+  if (h_w_perp) {
+    if (p->prm.pair_grid) {
+      PG_TRY(cudaMemcpyAsync(h_w_perp, d_wp, 8 * n_wp, cudaMemcpyDeviceToHost, s));
+    } else {
+      for (size_t i = 0; i < n_wp; ++i) h_w_perp[i] = std::numeric_limits<double>::quiet_NaN();
+    }
+  }
+  PG_TRY(cudaStreamSynchronize(s));
+  p->last_launches = launch_counter().load() - launches0;
+  if (p->prof_on) prof_end(p);
   return PG_OK;
 }
 
@@ -1614,6 +1683,40 @@ pg_status pg_deposit_dense(int64_t n, const double* d_pts, const double* d_w, do
   DepGeom g{N, L / (double)N, assign};
   PG_TRY(launch_deposit_dense(g, n, d_pts, d_w, reinterpret_cast<unsigned long long*>(d_mesh),
                               static_cast<cudaStream_t>(stream)));
+  return PG_OK;
+}
+
+pg_status pg_deposit_lines(pg_plan* p, int64_t n, const double* d_pts, const double* d_w,
+                           const int32_t* d_bin, int32_t nb, int64_t* d_mesh, int64_t* h_qsum,
+                           int64_t* h_n_lines, void* stream) {
+  if (!p || n < 0 || (n > 0 && !d_pts) || !d_mesh || nb < 1 || nb > p->nbmax || (!d_bin && nb != 1))
+    return PG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t N = p->N;
+  PG_TRY(ensure_shared(p));
+  PG_TRY(ensure_gal(p, std::max<int64_t>(n, 1)));
+  p->fwd_ok = false;   // the plan's line buffers are reused
+  p->smooth_ok = false;
+  if (d_bin) {   // mesh indices outside [0, nb) would write outside the line flags
+    int32_t bad = 0;
+    PG_TRY(cudaMemsetAsync(p->flag.p, 0, 4, s));
+    PG_TRY(launch_check_bins(n, d_bin, nb, p->flag.as<int32_t>(), s));
+    PG_TRY(cudaMemcpyAsync(&bad, p->flag.p, 4, cudaMemcpyDeviceToHost, s));
+    PG_TRY(cudaStreamSynchronize(s));
+    if (bad) return PG_ERR_INVALID_ARG;
+  }
+  PG_TRY(cudaMemsetAsync(d_mesh, 0, 8 * (size_t)nb * N * N * N, s));
+  PG_TRY(launch_transform(n, p->prm.box_L, 0.0, d_pts, nullptr, nullptr, p->xs.as<double>(),
+                          p->ys.as<double>(), p->zs.as<double>(), s));
+  int64_t nl = 0;
+  PG_TRY(deposit_batch(p, n, p->xs.as<double>(), p->ys.as<double>(), p->zs.as<double>(), d_w,
+                       d_bin, 0, nb, &nl, s));
+  PG_TRY(launch_lines_scatter(p->N, nl, p->lines_q.as<unsigned long long>(), p->line_y.as<int32_t>(),
+                              p->line_z.as<int32_t>(), p->line_bin.as<int32_t>(),
+                              reinterpret_cast<unsigned long long*>(d_mesh), s));
+  if (h_qsum) PG_TRY(cudaMemcpyAsync(h_qsum, p->qsum.p, 8 * (size_t)nb, cudaMemcpyDeviceToHost, s));
+  PG_TRY(cudaStreamSynchronize(s));
+  if (h_n_lines) *h_n_lines = nl;
   return PG_OK;
 }
 

@@ -179,6 +179,11 @@ cudaError_t launch_deposit_lines(const DepGeom& g, int64_t n, const double* x, c
                                  cudaStream_t s);
 cudaError_t launch_deposit_dense(const DepGeom& g, int64_t n, const double* aos,
                                  const double* w, unsigned long long* mesh, cudaStream_t s);
+cudaError_t launch_check_bins(int64_t n, const int32_t* bin, int nb, int32_t* bad, cudaStream_t s);
+cudaError_t launch_lines_scatter(int N, int64_t n_lines, const unsigned long long* lines_q,
+                                const int32_t* line_y, const int32_t* line_z,
+                                const int32_t* line_bin, unsigned long long* mesh,
+                                cudaStream_t s);
 cudaError_t launch_field_scale(int nb, const unsigned long long* qsum, int N, double* scale,
                                cudaStream_t s);
 
@@ -447,7 +452,29 @@ cudaError_t launch_pair_chain(int64_t np, const double* g, const double* T,
                               const int32_t* pi, const int32_t* pj, const double* wgal,
                               double* wbar, cudaStream_t s);
 cudaError_t launch_hod_weights(int64_t n, const double* mass, const int32_t* kind, const float* kh,
-                               const double theta[5], float* w, double* dw, cudaStream_t s);
+                               const double theta[5], float* w, double* dw, double* d2w,
+                               cudaStream_t s);
+
+// ---- HOD-parameter derivatives of the pair-count statistics (pg_hod.cu) ----
+// Per value: [0] the value, [1..5] d/dtheta_j, [6..20] d2/dtheta_j dtheta_k
+// for j <= k in row order (00 01 02 03 04 11 12 13 14 22 23 24 33 34 44).
+constexpr int kHodVals = 21;
+constexpr int kHodNormBlocks = 256;
+// sum w and sum w^2 with their derivatives: partial [kHodNormBlocks][2 * 21]
+// then out[2 * 21] (first sum w, then sum w^2), fixed-order sums
+cudaError_t launch_hod_norm(int64_t n, const float* w, const double* dw, const double* d2w,
+                            double* partial, double* out, cudaStream_t s);
+// DD_b = sum over the pairs of bin b (pi, pj in [off[b], off[b+1])) of
+// w_i w_j with its derivatives: out[P][21]
+cudaError_t launch_hod_pair_sums(int P, const int64_t* off, const int32_t* pi, const int32_t* pj,
+                                 const float* w, const double* dw, const double* d2w,
+                                 double* out, cudaStream_t s);
+// xi_b = DD_b / (R vbin_b / L^3) - 1, R = ((sum w)^2 - sum w^2)/2, with its
+// derivatives (quotient rule): xi[P][21]; with wcoef (the grid), also
+// w(d_perp)_k = sum_m wcoef[k n_mu + m] xi[k n_mu + m]: wp[n_s][21]
+cudaError_t launch_hod_xi(int n_s, int n_mu, const double* dd, const double* norm,
+                          const double* vbin, const double* wcoef, double inv_L3, double* xi,
+                          double* wp, cudaStream_t s);
 cudaError_t launch_hod_chain(int64_t n, const double* wbar, const double* dw, double* partial,
                              double* out5, cudaStream_t s);
 cudaError_t launch_gal_final(int64_t n, const double* g, const double* T,

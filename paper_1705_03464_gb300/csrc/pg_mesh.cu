@@ -128,6 +128,28 @@ k_deposit_dense(DepGeom g, int64_t n, const double* __restrict__ aos, const doub
       }
 }
 
+// Sets *bad when a mesh index lies outside [0, nb) (checked before a deposit
+// that takes caller-supplied indices).
+__global__ void __launch_bounds__(kThreads)
+k_check_bins(int64_t n, const int32_t* __restrict__ bin, int nb, int32_t* bad) {
+  int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (p < n && (bin[p] < 0 || bin[p] >= nb)) atomicOr(bad, 1);
+}
+
+// Compact lines back into dense meshes mesh[bin][z][y][x] (the stage entry
+// point that exposes the deposit's own output); one thread per node.
+__global__ void __launch_bounds__(kThreads)
+k_lines_scatter(int N, int64_t n_lines, const unsigned long long* __restrict__ lines_q,
+                const int32_t* __restrict__ line_y, const int32_t* __restrict__ line_z,
+                const int32_t* __restrict__ line_bin, unsigned long long* __restrict__ mesh) {
+  int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (t >= n_lines * N) return;
+  const int64_t l = t / N;
+  const int x = (int)(t - l * N);
+  const int64_t node = (((int64_t)line_bin[l] * N + line_z[l]) * N + line_y[l]) * N + x;
+  mesh[node] = lines_q[t];
+}
+
 // f = rho / rho_bar = q * N^3 / Q per mesh (FP64); 0 when the mesh is empty.
 __global__ void k_field_scale(int nb, const unsigned long long* __restrict__ qsum, double n3,
                               double* __restrict__ scale) {
@@ -178,6 +200,22 @@ cudaError_t launch_deposit_dense(const DepGeom& g, int64_t n, const double* aos,
                                  unsigned long long* mesh, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_deposit_dense<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(g, n, aos, w, mesh);
+  return launched();
+}
+
+cudaError_t launch_check_bins(int64_t n, const int32_t* bin, int nb, int32_t* bad, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_check_bins<<<(unsigned)cdiv(n, kThreads), kThreads, 0, s>>>(n, bin, nb, bad);
+  return launched();
+}
+
+cudaError_t launch_lines_scatter(int N, int64_t n_lines, const unsigned long long* lines_q,
+                                const int32_t* line_y, const int32_t* line_z,
+                                const int32_t* line_bin, unsigned long long* mesh,
+                                cudaStream_t s) {
+  if (n_lines <= 0) return cudaSuccess;
+  k_lines_scatter<<<(unsigned)cdiv(n_lines * N, kThreads), kThreads, 0, s>>>(
+      N, n_lines, lines_q, line_y, line_z, line_bin, mesh);
   return launched();
 }
 

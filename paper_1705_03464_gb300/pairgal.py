@@ -106,12 +106,15 @@ def _load():
         "pg_transform_positions": (C.c_int, [i64, dbl, dbl, vp, vp, vp, vp]),
         "pg_find_pairs": (C.c_int, [vp, i64, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]),
         "pg_deposit_dense": (C.c_int, [i64, vp, vp, dbl, i32, i32, vp, vp]),
+        "pg_deposit_lines": (C.c_int, [vp, i64, vp, vp, vp, i32, vp, vp, vp, vp]),
         "pg_fft_r2c_3d": (C.c_int, [vp, vp, vp, vp]),
         "pg_fft_c2r_3d": (C.c_int, [vp, vp, vp, vp]),
         "pg_pair_counts_static": (C.c_int, [i64, vp, vp, dbl, i32, vp, i32, vp, vp, vp]),
         "pg_backward": (C.c_int, [vp, C.POINTER(pg_result), vp, vp]),
         "pg_hod_weights": (C.c_int, [i64, vp, vp, vp, vp, vp, vp, vp]),
         "pg_hod_chain": (C.c_int, [vp, i64, vp, vp, vp, vp]),
+        "pg_hod_weights2": (C.c_int, [i64, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "pg_hod_pair_derivs": (C.c_int, [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
         "pg_plan_set_profiling": (C.c_int, [vp, i32]),
         "pg_plan_last_stats": (C.c_int, [vp, vp, vp]),
     }
@@ -412,6 +415,26 @@ def pg_deposit_dense(pos, w, box_L, mesh_n, assign, mesh=None, stream=None):
     return mesh
 
 
+def pg_deposit_lines(plan: Plan, pos, w=None, bins=None, nb=1, stream=None):
+    """The forward path's compact-line deposit (pg_deposit_lines) of device
+    points pos [n, 3] float64 with weights w [n] float64 or None into nb
+    meshes (bins [n] int32 in [0, nb), or None for one mesh). Returns the
+    dense int64 meshes [nb, N, N, N] (device), the totals [nb] and the
+    touched-line count."""
+    import torch
+    _dev(pos, "pos", "f64", (None, 3))
+    n = int(pos.shape[0])
+    _dev(w, "w", "f64", (n,), pos.device, optional=True)
+    _dev(bins, "bins", "i32", (n,), pos.device, optional=True)
+    N = int(plan.params.mesh_n)
+    mesh = torch.empty((int(nb), N, N, N), dtype=torch.int64, device=pos.device)
+    qsum = np.zeros(int(nb), dtype=np.int64)
+    nl = C.c_int64(0)
+    _check(_lib.pg_deposit_lines(plan.handle, n, _ptr(pos), _ptr(w), _ptr(bins), int(nb), _ptr(mesh),
+                                 qsum.ctypes.data, C.byref(nl), _stream(stream)), "pg_deposit_lines")
+    return mesh, qsum, int(nl.value)
+
+
 def pg_fft_r2c_3d(plan: Plan, f, out=None, stream=None):
     import torch
     N = int(plan.params.mesh_n)
@@ -547,6 +570,72 @@ def pg_hod_weights(mass, kind, kh, theta, with_grad=True, stream=None):
     _check(_lib.pg_hod_weights(n, _ptr(mass), _ptr(kind), _ptr(kh), _ptr(th), _ptr(w), _ptr(dw),
                                _stream(stream)), "pg_hod_weights")
     return w[:n], (dw[:n] if dw is not None else None)
+
+
+def pg_hod_weights2(mass, kind, kh, theta, stream=None):
+    """Soft HOD weights w [n] FP32, dw/dtheta [n, 5] and d2w/dtheta2
+    [n, 5, 5] FP64 (device tensors; the last expanded from the library's
+    upper triangle)."""
+    import torch
+    _dev(mass, "mass", "f64", (None,))
+    n = int(mass.shape[0])
+    _dev(kind, "kind", "i32", (n,), mass.device)
+    _dev(kh, "kh", "f32", (n,), mass.device)
+    th = _host_arr(theta, "theta", np.float64, (5,))
+    m = max(n, 1)
+    w = torch.empty(m, dtype=torch.float32, device=mass.device)
+    dw = torch.empty((m, 5), dtype=torch.float64, device=mass.device)
+    d2 = torch.empty((m, 15), dtype=torch.float64, device=mass.device)
+    _check(_lib.pg_hod_weights2(n, _ptr(mass), _ptr(kind), _ptr(kh), _ptr(th), _ptr(w), _ptr(dw),
+                                _ptr(d2), _stream(stream)), "pg_hod_weights2")
+    return w[:n], dw[:n], _tri_to_full(d2[:n])
+
+
+_TRI = [(j, k) for j in range(5) for k in range(j, 5)]
+
+
+def _tri_to_full(t):
+    """[..., 15] upper triangle (row order) -> [..., 5, 5] symmetric."""
+    import torch
+    lib = torch if not isinstance(t, np.ndarray) else np
+    if lib is np:
+        out = np.zeros(t.shape[:-1] + (5, 5))
+    else:
+        out = torch.zeros(tuple(t.shape[:-1]) + (5, 5), dtype=t.dtype, device=t.device)
+    for q, (j, k) in enumerate(_TRI):
+        out[..., j, k] = t[..., q]
+        out[..., k, j] = t[..., q]
+    return out
+
+
+def _full_to_tri(h):
+    import torch
+    idx_j = [j for j, _ in _TRI]
+    idx_k = [k for _, k in _TRI]
+    if isinstance(h, np.ndarray):
+        return np.ascontiguousarray(h[..., idx_j, idx_k])
+    return h[..., idx_j, idx_k].contiguous()
+
+
+def pg_hod_pair_derivs(plan: Plan, pos, vel, w, dw, d2w, stream=None):
+    """Exact HOD-parameter derivatives of xi per pair bin (and of w(d_perp)
+    on the grid): pg_hod_pair_derivs on device tensors pos [n, 3] float64,
+    vel [n, 3] float32 or None, w [n] float32, dw [n, 5] float64 and d2w
+    [n, 5, 5] (or [n, 15]) float64. Returns host arrays xi [P], dxi [P, 5],
+    d2xi [P, 5, 5] and w_perp [n_s], dw_perp [n_s, 5], d2w_perp [n_s, 5, 5]."""
+    n = _catalogue(pos, vel, w)
+    if w is None:
+        raise PairgalError(PG_ERR_INVALID_ARG, "w is required")
+    _dev(dw, "dw", "f64", (n, 5), pos.device)
+    if d2w is not None and d2w.dim() == 3:
+        d2w = _full_to_tri(d2w)
+    _dev(d2w, "d2w", "f64", (n, 15), pos.device)
+    xi = np.zeros((plan.P, 21))
+    wp = np.zeros((plan.n_s, 21))
+    _check(_lib.pg_hod_pair_derivs(plan.handle, n, _ptr(pos), _ptr(vel), _ptr(w), _ptr(dw), _ptr(d2w),
+                                   xi.ctypes.data, wp.ctypes.data, _stream(stream)), "pg_hod_pair_derivs")
+    return {"xi": xi[:, 0], "dxi": xi[:, 1:6], "d2xi": _tri_to_full(xi[:, 6:]),
+            "w_perp": wp[:, 0], "dw_perp": wp[:, 1:6], "d2w_perp": _tri_to_full(wp[:, 6:])}
 
 
 def pg_hod_chain(plan: Plan, wbar, dw, stream=None):

@@ -201,3 +201,45 @@ def test_hod_gradient_finite_differences_512(pg):
     _, g32, _ = _hod_grads(pg, plan32, cand, th, keys, 3)
     cond = np.abs(dw).T @ np.abs(wbar)
     assert np.all(np.abs(g32 - g64) <= 2e-4 * cond), (g32, g64, cond)
+
+
+@pytest.mark.slow
+def test_backward_1024_directional_fd_and_fp32(pg):
+    """The 1024^3 instantiations of the adjoint passes (the window-field x
+    and y passes, the adjoint z pass with register-free twiddle tables at
+    N1 = N2 = 32, the y inverse at the pair lines), on the 12 000-galaxy
+    1024^3 case whose forward is held to the oracle elsewhere. FP64: the
+    backward against central differences of the FP64 forward along a random
+    direction in weight space (a 0.5 % step, exactly representable in FP32).
+    FP32: the backward against the FP64 one, within 2e-4 of the largest
+    component (the bar of the small-box oracle comparison)."""
+    L = 1024.0
+    p = pipeline.Params(L, 1024, 1, (0.0, 6.0, 12.0), 2, (4.0, 8.0, 12.0), 2, 0.0, 0.0)
+    cat = synth.make_catalogue_box(L, 12000, seed=21)
+    w = synth.make_weights(cat.n, 21)
+    pos = dev(cat.pos)
+    keys = ("b_pg", "q_eff", "xi_pg", "xi_gg", "b_pg_agg", "q_eff_agg")
+    plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur, precision=1)
+    rng = np.random.default_rng(23)
+    out = pg.pg_forward(plan, pos, None, dev(w))
+    gbar = {k: rng.standard_normal(np.asarray(out[k]).shape) for k in keys}
+    g64 = pg.pg_backward(plan, gbar, cat.n).cpu().numpy()
+
+    def loss(wv):
+        o = pg.pg_forward(plan, pos, None, dev(wv.astype(np.float32)))
+        return sum(float(np.nansum(gbar[k] * np.asarray(o[k]))) for k in keys)
+
+    v = (rng.standard_normal(cat.n) * 0.005 * w).astype(np.float32).astype(np.float64)
+    wp = (w + v).astype(np.float32).astype(np.float64)
+    wm = (w - v).astype(np.float32).astype(np.float64)
+    fd = (loss(wp) - loss(wm)) / 2.0
+    ad = g64 @ ((wp - wm) / 2.0)
+    print(f"1024^3 shell-W adjoint: directional FD {fd:.9e}, adjoint {ad:.9e}, rel {abs(fd - ad) / abs(fd):.2e}")
+    assert abs(fd - ad) <= 2e-4 * abs(fd)
+    plan.close()
+    plan32 = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur, precision=0)
+    pg.pg_forward(plan32, pos, None, dev(w))
+    g32 = pg.pg_backward(plan32, gbar, cat.n).cpu().numpy()
+    rel = np.max(np.abs(g32 - g64)) / np.max(np.abs(g64))
+    print(f"1024^3 shell-W adjoint: FP32 against FP64, max |diff| / max |g| = {rel:.2e}")
+    assert rel <= 2e-4
