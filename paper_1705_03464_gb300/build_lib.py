@@ -26,7 +26,7 @@ NO_FMA = {"pg_pairs.cu", "pg_mesh.cu"}
 # the longest compiles first, so the parallel build ends with the short ones
 SOURCES = ["pg_fft_z_f32.cu", "pg_fft_f32.cu", "pg_fft_z_f64.cu", "pg_fft_f64.cu", "pg_api.cu",
            "pg_pairs.cu", "pg_mesh.cu", "pg_scan.cu", "pg_bin.cu", "pg_tma.cu", "pg_noalloc.cu",
-           "pg_adjoint.cu", "pg_batch.cu", "pg_smooth.cu", "pg_smooth_adj.cu"]
+           "pg_adjoint.cu", "pg_batch.cu", "pg_smooth.cu", "pg_smooth_adj.cu", "pg_hod.cu"]
 
 
 def _nvcc():

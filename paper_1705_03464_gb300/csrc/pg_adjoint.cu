@@ -329,38 +329,70 @@ cudaError_t launch_pair_chain(int64_t np, const double* g, const double* T,
 //   central:   w = erfc(u)/2, u = ln(M_cut/M) / (sqrt(2) sigma)
 //   satellite: w = ((M - kappa M_cut)/M_1)^alpha / K for M > kappa M_cut, else 0
 // (K: the number of satellite candidates of the halo).
+// With d2w, also the second derivatives, upper triangle j <= k in row order
+// (00 01 02 03 04 11 12 13 14 22 23 24 33 34 44), by the chain rule:
+//   central: g = dv/du = -exp(-u^2)/sqrt(pi), dg/du = -2 u g; u_0 =
+//     ln10/(sqrt(2) sigma), u_2 = -u/sigma, u_02 = -u_0/sigma, u_22 = 2u/sigma^2;
+//     v_jk = -2 u g u_j u_k + g u_jk
+//   satellite: f = x^alpha; x_0 = -kappa M_cut ln10/M_1, x_1 = -x ln10,
+//     x_4 = -M_cut/M_1, x_00 = x_0 ln10, x_01 = -x_0 ln10, x_04 = x_4 ln10,
+//     x_11 = x ln10^2, x_14 = -x_4 ln10; v_jk = (f_xx x_j x_k + f_x x_jk)/K
+//     for j, k in {0, 1, 4}, v_j3 = f_xa x_j / K, v_33 = f_aa / K.
 __global__ void __launch_bounds__(256)
 k_hod_weights(int64_t n, const double* __restrict__ mass, const int32_t* __restrict__ kind,
               const float* __restrict__ kh, double t0, double t1, double sig, double alpha,
-              double kappa, float* __restrict__ w, double* __restrict__ dw) {
+              double kappa, float* __restrict__ w, double* __restrict__ dw, double* __restrict__ d2w) {
   const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (i >= n) return;
   const double ln10 = 2.302585092994045684;
   const double M = mass[i];
   const double mcut = exp(t0 * ln10), m1 = exp(t1 * ln10);
   double v = 0.0, d[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double h[15];
+  for (int k = 0; k < 15; ++k) h[k] = 0.0;
   if (kind[i] == 0) {
     const double u = (t0 * ln10 - log(M)) / (sqrt(2.0) * sig);
     v = 0.5 * erfc(u);
     const double dv_du = -exp(-u * u) / sqrt(M_PI);
-    d[0] = dv_du * ln10 / (sqrt(2.0) * sig);
-    d[2] = dv_du * (-u / sig);
+    const double u0 = ln10 / (sqrt(2.0) * sig), u2 = -u / sig;
+    d[0] = dv_du * u0;
+    d[2] = dv_du * u2;
+    const double gu = -2.0 * u * dv_du;
+    h[0] = gu * u0 * u0;                                   // 00
+    h[2] = gu * u0 * u2 + dv_du * (-u0 / sig);             // 02
+    h[9] = gu * u2 * u2 + dv_du * (2.0 * u / (sig * sig)); // 22
   } else {
     const double x = (M - kappa * mcut) / m1;
     const double K = (double)kh[i];
     if (x > 0.0) {
       const double xa = pow(x, alpha);
+      const double lx = log(x);
       v = xa / K;
-      const double dv_dx = alpha * xa / x / K;
-      d[0] = dv_dx * (-kappa * mcut * ln10 / m1);
-      d[1] = dv_dx * (-x * ln10);
-      d[3] = xa * log(x) / K;
-      d[4] = dv_dx * (-mcut / m1);
+      const double fx = alpha * xa / x;
+      const double x0 = -kappa * mcut * ln10 / m1, x1 = -x * ln10, x4 = -mcut / m1;
+      d[0] = fx * x0 / K;
+      d[1] = fx * x1 / K;
+      d[3] = xa * lx / K;
+      d[4] = fx * x4 / K;
+      const double fxx = alpha * (alpha - 1.0) * xa / (x * x);
+      const double fxa = xa / x * (1.0 + alpha * lx);
+      h[0] = (fxx * x0 * x0 + fx * x0 * ln10) / K;     // 00
+      h[1] = (fxx * x0 * x1 - fx * x0 * ln10) / K;     // 01
+      h[3] = fxa * x0 / K;                             // 03
+      h[4] = (fxx * x0 * x4 + fx * x4 * ln10) / K;     // 04
+      h[5] = (fxx * x1 * x1 + fx * x * ln10 * ln10) / K;   // 11
+      h[7] = fxa * x1 / K;                             // 13
+      h[8] = (fxx * x1 * x4 - fx * x4 * ln10) / K;     // 14
+      h[12] = xa * lx * lx / K;                        // 33
+      h[13] = fxa * x4 / K;                            // 34
+      h[14] = fxx * x4 * x4 / K;                       // 44
     }
   }
   w[i] = (float)v;
   if (dw)
     for (int k = 0; k < 5; ++k) dw[5 * i + k] = d[k];
+  if (d2w)
+    for (int k = 0; k < 15; ++k) d2w[15 * i + k] = h[k];
 }
 
 // dL/dtheta_k = sum_i wbar_i dw_i/dtheta_k, per-block partials then a fixed-order sum.
@@ -387,10 +419,11 @@ __global__ void k_hod_chain_final(int nblk, const double* __restrict__ partial, 
 }
 
 cudaError_t launch_hod_weights(int64_t n, const double* mass, const int32_t* kind, const float* kh,
-                               const double theta[5], float* w, double* dw, cudaStream_t s) {
+                               const double theta[5], float* w, double* dw, double* d2w,
+                               cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_hod_weights<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(n, mass, kind, kh, theta[0], theta[1], theta[2],
-                                                        theta[3], theta[4], w, dw);
+                                                        theta[3], theta[4], w, dw, d2w);
   return launched();
 }
 
