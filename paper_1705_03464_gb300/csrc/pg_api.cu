@@ -1489,26 +1489,46 @@ pg_status pg_hod_pair_derivs(pg_plan* p, int64_t n, const double* d_pos, const f
   PG_TRY(positions_and_pairs(p, n, d_pos, d_vel, d_w, hdd, &np, &nonfinite, s));
   if (nonfinite) return PG_ERR_INVALID_ARG;
   const int P = p->nPB, n_s = p->prm.n_s;
-  std::vector<int64_t> off(P + 1, 0);
-  for (int b = 0; b < P; ++b) off[b + 1] = off[b] + (int64_t)hdd[b];
-  // offsets, pair sums [P][21], weight sums [2][21] and their partials, xi [P][21], w_perp [n_s][21]
-  const size_t n_off = P + 1, n_dd = (size_t)P * kHodVals, n_norm = 2 * kHodVals,
-               n_part = (size_t)kHodNormBlocks * 2 * kHodVals, n_xi = (size_t)P * kHodVals,
-               n_wp = (size_t)n_s * kHodVals;
-  PG_TRY(p->hd.ensure(8 * (n_off + n_dd + n_norm + n_part + n_xi + n_wp), &p->total));
-  int64_t* d_off = p->hd.as<int64_t>();
-  double* d_dd = p->hd.as<double>() + n_off;
-  double* d_norm = d_dd + n_dd;
+  // each bin's pair range [off_b, off_b + hdd_b) cut into chunks of kHodChunk
+  std::vector<int64_t> cstart, cend, cfirst(P + 1, 0);
+  {
+    int64_t o = 0;
+    for (int b = 0; b < P; ++b) {
+      cfirst[b] = (int64_t)cstart.size();
+      for (int64_t q = o; q < o + (int64_t)hdd[b]; q += kHodChunk) {
+        cstart.push_back(q);
+        cend.push_back(std::min<int64_t>(q + kHodChunk, o + (int64_t)hdd[b]));
+      }
+      o += (int64_t)hdd[b];
+    }
+    cfirst[P] = (int64_t)cstart.size();
+  }
+  const int64_t nch = (int64_t)cstart.size();
+  std::vector<int64_t> chunks;
+  chunks.reserve(2 * nch + P + 1);
+  chunks.insert(chunks.end(), cstart.begin(), cstart.end());
+  chunks.insert(chunks.end(), cend.begin(), cend.end());
+  chunks.insert(chunks.end(), cfirst.begin(), cfirst.end());
+  // chunk table, pair sums [P][21], chunk partials [nch][21], weight sums
+  // [2][21] and their partials, xi [P][21], w_perp [n_s][21]
+  const size_t n_ch = chunks.size(), n_dd = (size_t)P * kHodVals, n_pp = (size_t)std::max<int64_t>(nch, 1) * kHodVals,
+               n_norm = 2 * kHodVals, n_part = (size_t)kHodNormBlocks * 2 * kHodVals,
+               n_xi = (size_t)P * kHodVals, n_wp = (size_t)n_s * kHodVals;
+  PG_TRY(p->hd.ensure(8 * (n_ch + n_dd + n_pp + n_norm + n_part + n_xi + n_wp), &p->total));
+  int64_t* d_ch = p->hd.as<int64_t>();
+  double* d_dd = p->hd.as<double>() + n_ch;
+  double* d_pp = d_dd + n_dd;
+  double* d_norm = d_pp + n_pp;
   double* d_part = d_norm + n_norm;
   double* d_xi = d_part + n_part;
   double* d_wp = d_xi + n_xi;
-  PG_TRY(cudaMemcpyAsync(d_off, off.data(), 8 * n_off, cudaMemcpyHostToDevice, s));
+  PG_TRY(cudaMemcpyAsync(d_ch, chunks.data(), 8 * n_ch, cudaMemcpyHostToDevice, s));
   {
     ProfScope ps(p, PG_FAM_PAIRS, s, (8.0 + 4.0 * 2 + 2.0 * (4.0 + 40.0 + 120.0)) * (double)np +
                                          (4.0 + 40.0 + 120.0) * (double)n);
     PG_TRY(launch_hod_norm(n, d_w, d_dw_dtheta, d_d2w_dtheta2, d_part, d_norm, s));
-    PG_TRY(launch_hod_pair_sums(P, d_off, p->psi.as<int32_t>(), p->psj.as<int32_t>(), d_w, d_dw_dtheta,
-                                d_d2w_dtheta2, d_dd, s));
+    PG_TRY(launch_hod_pair_sums(P, nch, d_ch, p->psi.as<int32_t>(), p->psj.as<int32_t>(), d_w, d_dw_dtheta,
+                                d_d2w_dtheta2, d_pp, d_dd, s));
     const double L = p->prm.box_L;
     PG_TRY(launch_hod_xi(n_s, p->prm.n_mu, d_dd, d_norm, p->vbin_d.as<double>(),
                          p->prm.pair_grid ? p->wcoef_d.as<double>() : nullptr, 1.0 / (L * L * L), d_xi,

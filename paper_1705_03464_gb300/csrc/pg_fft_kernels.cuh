@@ -159,6 +159,28 @@ __host__ __device__ __forceinline__ void reg_dft(C (&a)[RL]) {
   }
 }
 
+// Forward DFT of length RL (dividing 32) of an input whose entries m >= NZ
+// are zero: y[k] = sum_{m < NZ} b_m W_RL^(m k), k = 0..RL-1. For
+// k = (RL / NZ) q + r, W_RL^(m k) = W_NZ^(m q) W_RL^(m r), so the outputs
+// with remainder r are the NZ-point DFT of b_m W_RL^(m r) (compile-time
+// twiddles, multiples of a quarter turn free).
+template <typename C, int RL, int NZ>
+__host__ __device__ __forceinline__ void dft_few_inputs(const C (&b)[NZ], C (&y)[RL]) {
+  constexpr int R = RL / NZ;
+  static_assert(R * NZ == RL && 32 % RL == 0, "NZ divides RL, RL divides 32");
+  sfor<0, R>([&](auto rr) {
+    constexpr int r = decltype(rr)::value;
+    C cc[NZ];
+    sfor<0, NZ>([&](auto mm) {
+      constexpr int m = decltype(mm)::value;
+      cc[m] = tw32_mul<m * r * (32 / RL), false>(b[m]);
+    });
+    reg_dft<C, NZ, false>(cc);
+#pragma unroll
+    for (int q = 0; q < NZ; ++q) y[R * q + r] = cc[q];
+  });
+}
+
 // Copies the twiddle table W_N^j (j < n) into shared memory; the caller's
 // next __syncthreads() publishes it.
 template <typename C>
@@ -1184,6 +1206,55 @@ __device__ __forceinline__ void step1_win(C* buf, const C* xc, int w, const C* t
   }
 }
 
+// Step 1 on the same zero-padded window column with the zero inputs pruned.
+// Its nonzero rows, signed z = N2 j1 + j2 with |z| <= w, have j1 in [-J, J),
+// J = floor(w / N2) + 1. With b_m = a[(m - J) mod N1] for m < NZ (NZ >= 2J a
+// power of two, b_m = 0 for m >= 2J):
+//   sum_j1 a_j1 W_N1^(j1 k1) = W_N1^(-J k1) Y[k1],  Y[k] = sum_m b_m W_N1^(m k),
+// and for k = (N1 / NZ) q + r, W_N1^(m k) = W_NZ^(m q) W_N1^(m r), so Y at
+// those k is the NZ-point DFT over m of b_m W_N1^(m r) (compile-time
+// twiddles). The factor W_N1^(-J k1) = W_N^(-J N2 k1) joins step 1's twiddle
+// W_N^(j2 k1): one table entry W_N^((j2 - J N2) k1 mod N). A task reads NZ
+// rows of the compact slot instead of N1, and its DFT costs about half.
+// Compact slot rows: signed z >= 0 at z, z < 0 at z + W.
+template <typename C, int N, int B, int X, int NZ>
+__device__ __forceinline__ void step1_win_p(C* buf, const C* xc, int w, const C* tw, int tid, int nthr) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, R = N1 / NZ;
+  static_assert(R * NZ == N1, "NZ divides N1");
+  const int W = 2 * w + 1;
+  const int J = w / N2 + 1;
+  for (int t = tid; t < B * N2; t += nthr) {
+    const int c = t % B, j2 = t / B;
+    C b[NZ];
+#pragma unroll
+    for (int m = 0; m < NZ; ++m) {
+      const int z = N2 * (m - J) + j2;
+      C v;
+      v.x = 0; v.y = 0;
+      if (m < 2 * J && z >= -w && z <= w) v = xc[(z >= 0 ? z : z + W) * B + c];
+      b[m] = v;
+    }
+    C a[N1];
+    dft_few_inputs<C, N1, NZ>(b, a);
+    const int base = j2 - J * N2;
+#pragma unroll
+    for (int k1 = 1; k1 < N1; ++k1) a[k1] = cmul(a[k1], tw[(base * k1) & (N - 1)]);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) buf[prow<X>(k1, j2, N2) * B + c] = a[k1];
+  }
+}
+
+// Nonzero-input count of the pruned window step 1 for half-width w (a power
+// of two NZ >= 2 (floor(w / N2) + 1)), or 0 where pruning would not pay
+// (NZ > N1 / 4) and the full step runs.
+template <int N>
+__host__ __device__ constexpr int win_nz(int w) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  int nz = 2;
+  while (nz < 2 * (w / N2 + 1)) nz *= 2;
+  return nz <= N1 / 4 ? nz : 0;
+}
+
 // The load side of the adjoint z pass, run by one thread of the load
 // warpgroup (barriers as in k_zadj). Per item the order is: first mesh's slot,
 // A tile, remaining meshes' slots. Returns 0, or 1 when a wait for a free
@@ -1243,6 +1314,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
        Lay L, const C* __restrict__ Fg, C* __restrict__ A, const C* __restrict__ tw,
        int* __restrict__ err) {
   using Z = ZAdj<C, N, B>;
+  const int nz = win_nz<N>(w);
   constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1, CT = Z::CTHREADS;
   constexpr int XP = xperm<C, N, B>();
   constexpr uint64_t kLimitNs = 2000000000ull;
@@ -1294,16 +1366,22 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
       tma::bar_sync(1, CT);
       C a[N2];
       step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
-      // the galaxy column is issued here so that its L2 latency overlaps the
-      // window column's forward transform
+      tma::bar_sync(1, CT);
+      switch (nz) {   // the window column's inputs, pruned to its nonzero rows
+        case 2: step1_win_p<C, N, B, XP, 2>(buf, xb0 + cur * WS, w, tws, tid, CT); break;
+        case 4: step1_win_p<C, N, B, XP, 4>(buf, xb0 + cur * WS, w, tws, tid, CT); break;
+        case 8: step1_win_p<C, N, B, XP, 8>(buf, xb0 + cur * WS, w, tws, tid, CT); break;
+        default: step1_win<C, N, B, XP>(buf, xb0 + cur * WS, w, tws, tid, CT);
+      }
+      // the galaxy column is issued here, after the window transform (which
+      // then has its registers), so that its L2 latency overlaps the barrier
+      // and the window column's step 2
       C f[N2];
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) {
         f[k2].x = 0; f[k2].y = 0;
         if (c < ncol) f[k2] = tma::ld_hint(fcol + (int64_t)(k1 + N1 * k2) * L.zs, pol_keep);
       }
-      tma::bar_sync(1, CT);
-      step1_win<C, N, B, XP>(buf, xb0 + cur * WS, w, tws, tid, CT);
       tma::bar_sync(1, CT);
       C x[N2];
       step2<C, N1, N2, false, XP>(buf, B, c, k1, x);

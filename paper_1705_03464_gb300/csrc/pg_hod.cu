@@ -74,18 +74,21 @@ __global__ void k_hod_norm_final(int nblk, const double* __restrict__ partial, d
   out[v] = s;
 }
 
-// One block per pair bin: DD = sum w_i w_j and its derivatives
-// d_j = w_i' w_j + w_i w_j', d_jk = w_i'' w_j + w_i^j w_j^k + w_i^k w_j^j + w_i w_j''.
+// One block per chunk of a bin's pairs (chunk c covers [cs[c], cs[c] +
+// kHodChunk) clipped to its bin's end ce[c]): partial sums of DD = sum w_i w_j
+// and its derivatives d_j = w_i' w_j + w_i w_j',
+// d_jk = w_i'' w_j + w_i^j w_j^k + w_i^k w_j^j + w_i w_j''.
 __global__ void __launch_bounds__(kThr)
-k_hod_pair_sums(const int64_t* __restrict__ off, const int32_t* __restrict__ pi,
-                const int32_t* __restrict__ pj, const float* __restrict__ w,
-                const double* __restrict__ dw, const double* __restrict__ d2w,
-                double* __restrict__ out) {
+k_hod_pair_sums(const int64_t* __restrict__ cs, const int64_t* __restrict__ ce,
+                const int32_t* __restrict__ pi, const int32_t* __restrict__ pj,
+                const float* __restrict__ w, const double* __restrict__ dw,
+                const double* __restrict__ d2w, double* __restrict__ partial) {
   __shared__ double red[kV][kThr];
-  const int b = blockIdx.x;
+  const int64_t ch = blockIdx.x;
+  const int64_t p0 = cs[ch], p1 = ce[ch];
   double a[kV];
   for (int v = 0; v < kV; ++v) a[v] = 0.0;
-  for (int64_t p = off[b] + threadIdx.x; p < off[b + 1]; p += kThr) {
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += kThr) {
     const int64_t i = pi[p], j = pj[p];
     const double wi = (double)w[i], wj = (double)w[j];
     double di[kT], dj[kT];
@@ -99,7 +102,18 @@ k_hod_pair_sums(const int64_t* __restrict__ off, const int32_t* __restrict__ pi,
       }
   }
   block_sum<kV>(a, red);
-  if (threadIdx.x < kV) out[(int64_t)b * kV + threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x < kV) partial[ch * kV + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Per bin b, the sum of its chunks [c0[b], c0[b+1]) in order: out[P][21].
+__global__ void k_hod_pair_final(int P, const int64_t* __restrict__ c0, const double* __restrict__ partial,
+                                 double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P * kV) return;
+  const int b = t / kV, v = t - b * kV;
+  double s = 0.0;
+  for (int64_t c = c0[b]; c < c0[b + 1]; ++c) s += partial[c * kV + v];
+  out[t] = s;
 }
 
 // One thread per pair bin: q = DD / E, E = R c with c = V_b / L^3,
@@ -154,11 +168,18 @@ cudaError_t launch_hod_norm(int64_t n, const float* w, const double* dw, const d
   return launched();
 }
 
-cudaError_t launch_hod_pair_sums(int P, const int64_t* off, const int32_t* pi, const int32_t* pj,
-                                 const float* w, const double* dw, const double* d2w,
-                                 double* out, cudaStream_t s) {
+cudaError_t launch_hod_pair_sums(int P, int64_t n_chunks, const int64_t* chunks, const int32_t* pi,
+                                 const int32_t* pj, const float* w, const double* dw,
+                                 const double* d2w, double* partial, double* out, cudaStream_t s) {
   if (P <= 0) return cudaSuccess;
-  k_hod_pair_sums<<<P, kThr, 0, s>>>(off, pi, pj, w, dw, d2w, out);
+  const int64_t* cs = chunks;
+  const int64_t* ce = chunks + n_chunks;
+  const int64_t* c0 = chunks + 2 * n_chunks;
+  if (n_chunks > 0) {
+    k_hod_pair_sums<<<(unsigned)n_chunks, kThr, 0, s>>>(cs, ce, pi, pj, w, dw, d2w, partial);
+    PG_CUDA_TRY(launched());
+  }
+  k_hod_pair_final<<<(unsigned)cdiv(P * kV, 128), 128, 0, s>>>(P, c0, partial, out);
   return launched();
 }
 

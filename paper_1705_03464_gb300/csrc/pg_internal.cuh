@@ -464,11 +464,15 @@ constexpr int kHodNormBlocks = 256;
 // then out[2 * 21] (first sum w, then sum w^2), fixed-order sums
 cudaError_t launch_hod_norm(int64_t n, const float* w, const double* dw, const double* d2w,
                             double* partial, double* out, cudaStream_t s);
-// DD_b = sum over the pairs of bin b (pi, pj in [off[b], off[b+1])) of
-// w_i w_j with its derivatives: out[P][21]
-cudaError_t launch_hod_pair_sums(int P, const int64_t* off, const int32_t* pi, const int32_t* pj,
-                                 const float* w, const double* dw, const double* d2w,
-                                 double* out, cudaStream_t s);
+// DD_b = sum over the pairs of bin b of w_i w_j with its derivatives:
+// out[P][21]. The bins' pair ranges are cut into chunks of at most
+// kHodChunk pairs; chunks = [starts (n_chunks) | ends (n_chunks) | first
+// chunk of each bin (P + 1)]; partial [n_chunks][21] scratch. Each bin's
+// chunks are added in order (deterministic).
+constexpr int64_t kHodChunk = 4096;
+cudaError_t launch_hod_pair_sums(int P, int64_t n_chunks, const int64_t* chunks, const int32_t* pi,
+                                 const int32_t* pj, const float* w, const double* dw,
+                                 const double* d2w, double* partial, double* out, cudaStream_t s);
 // xi_b = DD_b / (R vbin_b / L^3) - 1, R = ((sum w)^2 - sum w^2)/2, with its
 // derivatives (quotient rule): xi[P][21]; with wcoef (the grid), also
 // w(d_perp)_k = sum_m wcoef[k n_mu + m] xi[k n_mu + m]: wp[n_s][21]

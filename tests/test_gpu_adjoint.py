@@ -243,3 +243,43 @@ def test_backward_1024_directional_fd_and_fp32(pg):
     rel = np.max(np.abs(g32 - g64)) / np.max(np.abs(g64))
     print(f"1024^3 shell-W adjoint: FP32 against FP64, max |diff| / max |g| = {rel:.2e}")
     assert rel <= 2e-4
+
+
+@pytest.mark.parametrize("r_max", [6.0, 12.0, 20.0])
+def test_backward_pruned_window_transform_256(pg, r_max):
+    """At N = 256 (N2 = 8) the adjoint z pass prunes the window column's z
+    transform to its nonzero inputs: half-widths w = 6, 12 and 20 cells keep
+    2, 4 and 8 of each 32-point DFT's inputs (w < 8, 16 and 32). The FP64
+    backward against directional differences of the FP64 forward. With
+    D(h) = (L(w + h v) - L(w - h v)) / 2 = h g.v + c h^3 + O(h^5), the
+    Richardson combination (8 D(h/2) - D(h)) / 3 removes the h^3 term (on the
+    w = 12 case the loss is curved enough that a plain 0.5 % step leaves a
+    1e-2 truncation error); the adjoint's g.(actual half-steps) is combined
+    the same way."""
+    L = 256.0
+    cat = synth.make_catalogue_box(L, 4000, seed=61)
+    w = synth.make_weights(cat.n, 61)
+    p = pipeline.Params(L, 256, 1, (0.0, 4.0, 8.0), 1, (0.25 * r_max, 0.5 * r_max, r_max), 2, 0.0, 0.0)
+    plan = pg.Plan(p.box_L, p.mesh_n, p.assign, p.s_edges, p.n_mu, p.r_edges, p.n_mur, precision=1)
+    keys = ("b_pg", "q_eff", "xi_pg", "xi_gg", "b_pg_agg")
+    rng = np.random.default_rng(62)
+    pos = dev(cat.pos)
+    out = pg.pg_forward(plan, pos, None, dev(w))
+    gbar = {k: rng.standard_normal(np.asarray(out[k]).shape) for k in keys}
+    g = pg.pg_backward(plan, gbar, cat.n).cpu().numpy()
+
+    def loss(wv):
+        o = pg.pg_forward(plan, pos, None, dev(wv.astype(np.float32)))
+        return sum(float(np.nansum(gbar[k] * np.asarray(o[k]))) for k in keys)
+
+    u = rng.standard_normal(cat.n)
+    fd, ad = [], []
+    for h in (0.005, 0.0025):
+        v = u * h * w
+        wp = (w + v).astype(np.float32).astype(np.float64)
+        wm = (w - v).astype(np.float32).astype(np.float64)
+        fd.append((loss(wp) - loss(wm)) / 2.0)
+        ad.append(g @ ((wp - wm) / 2.0))
+    rf = (8.0 * fd[1] - fd[0]) / 3.0
+    ra = (8.0 * ad[1] - ad[0]) / 3.0
+    assert abs(rf - ra) <= 2e-4 * abs(ra), (rf, ra)
