@@ -50,6 +50,8 @@ def parse_args():
                     help="uneven mocks through the batch driver (0 = skip)")
     ap.add_argument("--many-mocks-fp64", type=int, default=3,
                     help="of those, mocks also run in the plain per-bin FP64 form")
+    ap.add_argument("--hod-study", type=int, default=1,
+                    help="the Sec. 5 HOD-derivative workflow at the paper-scale box (0 = skip)")
     ap.add_argument("--bins-per-batch", type=int, default=0,
                     help="pair meshes resident at once (0 = the plan's default)")
     return ap.parse_args()
@@ -329,7 +331,7 @@ def many_mocks_line(args, pg, np, torch):
     }
 
 
-def summary(value, fwd_adj, plain, smooth, many, cpu, roofline, breakdown, peak):
+def summary(value, fwd_adj, plain, smooth, many, cpu, roofline, breakdown, peak, hod=None):
     """Compact figures of every leg: forward and forward+adjoint ms per
     mock, the FP64 plain form, the smooth-W estimator, the many-mock batch,
     the oracle on one and all cores, and each kernel family's fraction of
@@ -351,6 +353,10 @@ def summary(value, fwd_adj, plain, smooth, many, cpu, roofline, breakdown, peak)
         out["many_mocks_per_s"] = r(many["mocks_per_s"], 2)
         out["many_p50_p99_ms"] = [r(many["p50_ms"]), r(many["p99_ms"])]
         out["plain_loop_mocks_per_s"] = r(many["plain_loop"]["mocks_per_s"], 2)
+    if hod:
+        out["hod_emulator_ms"] = r(hod["emulator_ms"], 2)
+        out["hod_14_evaluations_ms"] = r(hod["fourteen_evaluations_ms"], 2)
+        out["hod_delta_q_eff_ms"] = r(hod["delta_q_eff_ms"])
     if cpu:
         out["oracle_ms"] = {f"{cpu['cores']}_cores": r(cpu["value"], 0),
                             "1_core": r(cpu["one_core"]["value"], 0)}
@@ -358,6 +364,60 @@ def summary(value, fwd_adj, plain, smooth, many, cpu, roofline, breakdown, peak)
     out["hbm_frac"] = {k: r(v["GBps"] / peak, 2) for k, v in breakdown.items()
                        if v.get("GBps") and v["ms_per_step"] >= 0.5}
     return out
+
+
+def hod_study_line(wl, pg, np, torch, share_with):
+    """Sec. 5 at the paper-scale box (L = 1100 Mpc/h, 1024^3): soft HOD
+    candidates around the Z09 design; the emulator of w(d_perp) on a
+    20 x 5 (d_perp, d_par) grid to 30 Mpc/h with exact first and second
+    derivatives in (log10 M_cut, log10 M_1, sigma, alpha), against the 14
+    separate evaluations the paper uses (timed here as 14 evaluations of the
+    same statistic); the alpha = 1.05 and 0.95 fits with the paper's error
+    model; delta Q_eff and delta xi from three redshift-space smooth-W
+    forwards (d_p,max = 30 weighting, TSC) on the same grid."""
+    from paper_1705_03464_gb300 import hod_study as hs, synth
+    th0 = np.array(synth.HOD_Z09, dtype=np.float64)
+    cand = synth.make_candidates(wl.box_L, wl.n_gal, seed=0)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    P, V, M, K, H = dev(cand.pos), dev(cand.vel), dev(cand.mass), dev(cand.kind), dev(cand.kh)
+    perp = tuple(np.linspace(0.0, 30.0, 21))
+    par = tuple(np.linspace(0.0, 30.0, 6))
+    gp = pg.Plan(wl.box_L, wl.mesh_n, 1, perp, len(par) - 1, wl.r_edges, wl.n_mur, par_edges=par,
+                 share_with=share_with)
+    hs.emulator(gp, P, None, M, K, H, th0)   # warm-up
+    em = hs.emulator(gp, P, None, M, K, H, th0)
+    # the paper's route: 14 evaluations of the statistic at distinct HODs,
+    # each its least work on this path (soft weights and weighted pair
+    # counts, from which xi and w(d_perp) follow)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(14):
+        th = th0.copy()
+        th[k % 4] += 0.01 * (1 + k // 4)
+        w, _ = pg.pg_hod_weights(M, K, H, th, with_grad=False)
+        pg.pg_find_pairs(gp, P, w, with_list=False)
+    torch.cuda.synchronize()
+    ms14 = 1e3 * (time.perf_counter() - t0)
+    t1 = time.perf_counter()
+    fits = {a: hs.fit_at_alpha(em, a, perp, 30.0) for a in (1.05, 0.95)}
+    fit_s = time.perf_counter() - t1
+    sp = pg.Plan(wl.box_L, wl.mesh_n, 2, perp, len(par) - 1, wl.r_edges, wl.n_mur,
+                 rsd_factor=synth.RSD_FACTOR_Z05, par_edges=par, share_with=share_with)
+    hs.delta_q_eff(sp, pg.W_DP30, P, V, M, K, H, fits[1.05][0], fits[0.95][0], th0)   # warm-up
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    dq, dx, _ = hs.delta_q_eff(sp, pg.W_DP30, P, V, M, K, H, fits[1.05][0], fits[0.95][0], th0)
+    torch.cuda.synchronize()
+    dq_ms = 1e3 * (time.perf_counter() - t2)
+    sp.close()
+    gp.close()
+    fin = lambda a: np.asarray(a)[np.isfinite(a)]
+    return {"candidates": int(cand.pos.shape[0]), "grid": "d_perp 0-30 (20) x |d_par| 0-30 (5)",
+            "emulator_ms": em["ms"], "fourteen_evaluations_ms": ms14,
+            "fit_s": fit_s, "fits": {str(a): {"theta": [round(float(t), 4) for t in f[0]], "chi2": f[1]}
+                                     for a, f in fits.items()},
+            "delta_q_eff_ms": dq_ms, "max_abs_delta_q_eff": float(np.max(np.abs(fin(dq)))),
+            "max_abs_delta_xi": float(np.max(np.abs(fin(dx))))}
 
 
 # ---------------------------------------------------------------- our path
@@ -586,6 +646,10 @@ def main():
         sg30.close()
         del sg30, vz
 
+    hod = None
+    if args.hod_study > 0:
+        hod = hod_study_line(wl, pg, np, torch, plan)
+
     many = None
     if args.many_mocks > 0 and rank == 0 and world == 1:
         del plan
@@ -629,11 +693,12 @@ def main():
                        "mocks_per_step": world},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks, "kernels": breakdown,
-            "many_mocks": many, "smooth_w": smooth, "plain_fp64": plain, "fwd_adj": fwd_adj,
+            "hod_study": hod, "many_mocks": many, "smooth_w": smooth, "plain_fp64": plain,
+            "fwd_adj": fwd_adj,
         }
         # the line ends with a short summary of every leg, so that a reader
         # who keeps only its last characters still sees the whole metric
-        line["summary"] = summary(value, fwd_adj, plain, smooth, many, cpu, roofline, breakdown, peak)
+        line["summary"] = summary(value, fwd_adj, plain, smooth, many, cpu, roofline, breakdown, peak, hod)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -79,3 +79,34 @@ def test_smooth_rejects_bad_parameters(pg):
         with pytest.raises(pg.PairgalError) as e:
             pg.pg_forward_smooth(plan, bad, pos)
         assert e.value.status == pg.PG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("wset", ["dp30", "dp10"])
+def test_smooth_table_weightings_on_the_redshift_space_grid(pg, precision, wset):
+    """The paper's two weightings of table tab:weightings (d_p,max = 30 Mpc/h:
+    sigma = 50, r_s = 35, s0 = 0.5, r_cut = 20; d_p,max = 10 Mpc/h: 30, 20,
+    0.8, 10) with TSC on redshift-space positions, pairs on a (d_perp, d_par)
+    grid to 30 Mpc/h in each direction (the cylinder corner, 42.4 Mpc/h, stays
+    below L/2), against the oracle's smooth estimator."""
+    L, N = 160.0, 64
+    cat = synth.make_catalogue_box(L, 2500, seed=41)
+    perp = tuple(np.linspace(0.0, 30.0, 7))
+    par = tuple(np.linspace(0.0, 30.0, 4))
+    wprm = pg.W_DP30 if wset == "dp30" else pg.W_DP10
+    p = pipeline.Params(L, N, 2, perp, len(par) - 1, (8.0, 12.0), 1, synth.RSD_FACTOR_Z05, 0.0, par)
+    plan = pg.Plan(L, N, 2, perp, len(par) - 1, (8.0, 12.0), 1, rsd_factor=synth.RSD_FACTOR_Z05,
+                   precision=precision, par_edges=par)
+    got = pg.pg_forward_smooth(plan, wprm, dev(cat.pos), dev(cat.vel))
+    ref = sm.estimate(p, sm.WParams(*wprm), cat.pos, cat.vel)
+    assert got["dd"].tolist() == ref["dd"].tolist()
+    assert int(np.sum(ref["dd"])) > 10000
+    close(got["xi_ss"], ref["xi_ss"], 1e-12, 1e-12)
+    scale = max(abs(ref["den"]), np.nanmax(np.abs(ref["num"])))
+    tol = 1e-9 if precision else 1e-5
+    close(got["num"], ref["num"], tol, tol * scale)
+    close([got["den"]], [ref["den"]], tol, tol * scale)
+    rr = 1e-9 if precision else 1e-4
+    close([got["xi_dw"]], [ref["xi_dw"]], rr, 0.0)
+    close(got["b_pg"], ref["b_pg"], rr, rr * np.nanmax(np.abs(ref["b_pg"])))
+    close(got["q_eff"], ref["q_eff"], rr, rr * np.nanmax(np.abs(ref["q_eff"])))
