@@ -372,11 +372,13 @@ pg_status pg_deposit_lines(pg_plan* plan, int64_t n, const double* d_pts, const 
  * d_in[N][N][N] (FP32 if precision 0, FP64 if 1) into the half spectrum
  * d_out[N][N][N/2+1] (complex64 / complex128 interleaved, kx contiguous),
  * through the same pass kernels as the estimator. Needs a plan with this
- * mesh_n and precision (its workspace is used). */
+ * mesh_n and precision (its workspace is used). Synchronises the stream;
+ * PG_ERR_TIMEOUT if a bounded device wait of a column pass gave up. */
 pg_status pg_fft_r2c_3d(pg_plan* plan, const void* d_in, void* d_out, void* stream);
 
 /* Inverse of the above, unnormalised: f(x) = sum_k F(k) exp(+2 pi i k.x / N)
- * over the Hermitian-completed spectrum. d_in is not modified. */
+ * over the Hermitian-completed spectrum. d_in is not modified. Synchronises
+ * the stream; PG_ERR_TIMEOUT as above. */
 pg_status pg_fft_c2r_3d(pg_plan* plan, const void* d_in, void* d_out, void* stream);
 
 /* Pair counts DD(s, mu) of one catalogue, like the counts of pg_find_pairs,

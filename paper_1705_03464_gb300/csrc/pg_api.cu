@@ -458,7 +458,7 @@ cudaError_t lines_to_S(pg_plan* p, int nb, int64_t nl, typename CT<R>::C* S, int
   ProfScope ps(p, PG_FAM_FFT_Y_FWD, s, (double)nl * M1 * cs + (double)nb * N * N * M1 * cs);
   return FftPasses<R>::y_fwd(p->N, nb, p->spec.as<C>(), p->P, p->lidx.as<int32_t>(),
                              p->seg_total.as<int64_t>(), p->line_base.as<int64_t>(),
-                             p->line_y.as<int32_t>(), S, S_stride, lay_plan(p->N, p->P), tw, s);
+                             p->line_y.as<int32_t>(), S, S_stride, lay_plan<R>(p->N, p->P), tw, s);
 }
 
 // Correlation window of nb meshes against Fg (or Fg with itself) and its bin
@@ -479,7 +479,7 @@ cudaError_t correlate_window(pg_plan* p, int nb, bool gg, double* sums, cudaStre
     ProfScope ps(p, PG_FAM_FFT_Z_CORR, s,
                  (gg ? 0.0 : nb * N * N * M1 * cs) + N * N * M1 * cs + nb * W * N * M1 * cs);
     PG_CUDA_TRY(FftPasses<R>::z_corr(p->N, nb, p->S.as<C>(), p->Fg.as<C>(), gg, p->w,
-                                     p->Wz.as<C>(), Wz_stride, p->P, lay_plan(p->N, p->P), tw,
+                                     p->Wz.as<C>(), Wz_stride, p->P, lay_plan<R>(p->N, p->P), tw,
                                      p->flag.as<int32_t>() + 1, s));
   }
   {
@@ -507,7 +507,8 @@ cudaError_t galaxy_pass(pg_plan* p, int64_t n, const double* x, const double* y,
   PG_CUDA_TRY(lines_to_S<R>(p, 1, nl, p->Fg.as<C>(), 0, s));
   {
     ProfScope ps(p, PG_FAM_FFT_Z_FWD, s, 2.0 * p->N * p->N * p->M1 * (double)sizeof(C));
-    PG_CUDA_TRY(FftPasses<R>::z_fwd(p->N, p->Fg.as<C>(), lay_plan(p->N, p->P), p->tw.as<C>(), s));
+    PG_CUDA_TRY(FftPasses<R>::z_fwd(p->N, p->Fg.as<C>(), p->P, lay_plan<R>(p->N, p->P), p->tw.as<C>(),
+                                    p->flag.as<int32_t>() + 1, s));
   }
   if (do_gg) PG_CUDA_TRY(correlate_window<R>(p, 1, true, p->sums_gg.as<double>(), s));
   return cudaSuccess;
@@ -784,8 +785,8 @@ cudaError_t window_spectrum(pg_plan* p, const double* sbar, const double* gbar,
   PG_CUDA_TRY(FftPasses<R>::x_r2c_real(p->N, p->wlines.as<R>(), nl, p->spec.as<C>(), p->P, tw, s));
   PG_CUDA_TRY(FftPasses<R>::y_fwd(p->N, 1, p->spec.as<C>(), p->P, p->wl_idx.as<int32_t>(),
                                   p->wl_tot.as<int64_t>(), p->wl_base.as<int64_t>(),
-                                  p->wl_y.as<int32_t>(), p->Xs.as<C>(), 0, lay_plan(p->N, p->P), tw, s));
-  return FftPasses<R>::z_fwd(p->N, p->Xs.as<C>(), lay_plan(p->N, p->P), tw, s);
+                                  p->wl_y.as<int32_t>(), p->Xs.as<C>(), 0, lay_plan<R>(p->N, p->P), tw, s));
+  return FftPasses<R>::z_fwd(p->N, p->Xs.as<C>(), p->P, lay_plan<R>(p->N, p->P), tw, p->flag.as<int32_t>() + 1, s);
 }
 
 // Reverse sweep of the last forward call (see pg_backward in pairgal.h).
@@ -808,7 +809,7 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   const int W = p->W, nbmax = p->nbmax;
   const int64_t W2 = (int64_t)W * W;
   const int64_t Xw_stride = (int64_t)W * N * p->P;
-  const Lay L = lay_plan(N, p->P);
+  const Lay L = lay_plan<R>(N, p->P);
   const Lay XL{(int64_t)p->P, 0, (int64_t)W * p->P, 0};   // compact windows [ky][zr][kx]
   PG_CUDA_TRY(ensure_lines(p, nbmax * W2));
   PG_CUDA_TRY(p->Xs.ensure(sizeof(C) * spec_elems, t));
@@ -960,8 +961,8 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   }
   // galaxy side: f_g adjoint = N^-6 IDFT[A] at the galaxy lines
   ProfScope ps(p, PG_FAM_ADJ_GALAXY, s, 4.0 * NN * M1 * cs + 96.0 * (double)n);
-  PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, p->As.as<C>(), L, tw, s));
-  PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, p->As.as<C>(), L, tw, s));
+  PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, p->As.as<C>(), p->P, L, tw, p->flag.as<int32_t>() + 1, s));
+  PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, p->As.as<C>(), p->P, L, tw, p->flag.as<int32_t>() + 1, s));
   int64_t nlg = 0;
   PG_CUDA_TRY(deposit_batch(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, nullptr,
                             0, 1, &nlg, s));
@@ -1019,7 +1020,7 @@ pg_status smooth_impl(pg_plan* p, const SmoothW& wp, int64_t n, const double* d_
     PG_TRY(launch_widen_f32(n, d_w, p->gw.as<double>(), s));
     gw = p->gw.as<double>();
   }
-  const Lay L = lay_plan(N, p->P), Z = lay_zy(N, p->P);
+  const Lay L = lay_plan<R>(N, p->P), Z = lay_zy(N, p->P);
   const C* tw = p->tw.as<C>();
   R* real = reinterpret_cast<R*>(p->S.p);   // shared scratch: at least one spectrum, so N^3 reals
   C* Gs = p->Gs.as<C>();
@@ -1032,14 +1033,14 @@ pg_status smooth_impl(pg_plan* p, const SmoothW& wp, int64_t n, const double* d_
       PG_TRY(launch_w_mesh<R>(N, p->dx, wp, real, s));
       PG_TRY(FftPasses<R>::x_r2c_dense(N, real, Gs, p->P, tw, s));
       PG_TRY(FftPasses<R>::y_fwd(N, 1, Gs, p->P, nullptr, nullptr, nullptr, nullptr, Wk, 0, L, tw, s));
-      PG_TRY(FftPasses<R>::z_fwd(N, Wk, L, tw, s));
+      PG_TRY(FftPasses<R>::z_fwd(N, Wk, p->P, L, tw, p->flag.as<int32_t>() + 1, s));
       p->wk_key = wp;
       p->wk_valid = true;
     }
     // G = W * delta_g = N^-3 IDFT[W~ F_g] (k = 0 zeroed), dense [z][y][x]
     PG_TRY(launch_spec_mul<R>(N, p->P, L, Wk, p->Fg.as<C>(), 0, 1.0 / ((double)NN * N), Gs, s));
-    PG_TRY(FftPasses<R>::z_inv_full(N, Gs, Z, tw, s));
-    PG_TRY(FftPasses<R>::y_inv_full(N, Gs, Z, tw, s));
+    PG_TRY(FftPasses<R>::z_inv_full(N, Gs, p->P, Z, tw, p->flag.as<int32_t>() + 1, s));
+    PG_TRY(FftPasses<R>::y_inv_full(N, Gs, p->P, Z, tw, p->flag.as<int32_t>() + 1, s));
     PG_TRY(FftPasses<R>::x_c2r_full(N, Gs, p->P, real, tw, s));
     // G at the galaxies and at the pair midpoints (grouped by bin)
     const DepGeom geo{N, p->dx, p->prm.assign};
@@ -1058,8 +1059,8 @@ pg_status smooth_impl(pg_plan* p, const SmoothW& wp, int64_t n, const double* d_
     PG_TRY(launch_seg_sums(1, doff + P + 1, p->gj.as<double>(), gw, sums + 2 * P, s));
     // C_gg = N^-6 IDFT[|F_g|^2] (k = 0 zeroed), then sum W C^2 and sum W C
     PG_TRY(launch_spec_mul<R>(N, p->P, L, nullptr, p->Fg.as<C>(), 1, 1.0 / ((double)NN * NN * NN), Gs, s));
-    PG_TRY(FftPasses<R>::z_inv_full(N, Gs, Z, tw, s));
-    PG_TRY(FftPasses<R>::y_inv_full(N, Gs, Z, tw, s));
+    PG_TRY(FftPasses<R>::z_inv_full(N, Gs, p->P, Z, tw, p->flag.as<int32_t>() + 1, s));
+    PG_TRY(FftPasses<R>::y_inv_full(N, Gs, p->P, Z, tw, p->flag.as<int32_t>() + 1, s));
     PG_TRY(FftPasses<R>::x_c2r_full(N, Gs, p->P, real, tw, s));
     PG_TRY(launch_wc_sums<R>(N, p->dx, wp, real, p->sm_part.as<double>(), sums + 2 * P + 2, s));
     double* o = p->sm_out.as<double>();
@@ -1176,11 +1177,11 @@ cudaError_t smooth_backward_impl(pg_plan* p, const pg_smooth_result* gin, double
   PG_CUDA_TRY(launch_scatter<R>(geo, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(),
                                 p->sa_gj.as<double>(), gbar, s));
   // C = N^-6 IDFT[|F_g|^2] (k = 0 zeroed) again, then Cbar over it
-  const Lay L = lay_plan(N, p->P), Z = lay_zy(N, p->P);
+  const Lay L = lay_plan<R>(N, p->P), Z = lay_zy(N, p->P);
   C* Gs = p->Gs.as<C>();
   PG_CUDA_TRY(launch_spec_mul<R>(N, p->P, L, nullptr, p->Fg.as<C>(), 1, 1.0 / (n3 * n3), Gs, s));
-  PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, Gs, Z, tw, s));
-  PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, Gs, Z, tw, s));
+  PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, Gs, p->P, Z, tw, p->flag.as<int32_t>() + 1, s));
+  PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, Gs, p->P, Z, tw, p->flag.as<int32_t>() + 1, s));
   PG_CUDA_TRY(FftPasses<R>::x_c2r_full(N, Gs, p->P, cbar, tw, s));
   PG_CUDA_TRY(launch_cbar<R>(N, p->dx, p->smooth_w, sums + 2 * P + 2, sa, P, cbar, s));
   // spectra of Gbar and Cbar in the plan layout
@@ -1191,12 +1192,12 @@ cudaError_t smooth_backward_impl(pg_plan* p, const pg_smooth_result* gin, double
   for (int k = 0; k < 2; ++k) {
     PG_CUDA_TRY(FftPasses<R>::x_r2c_dense(N, meshes[k], Gs, p->P, tw, s));
     PG_CUDA_TRY(FftPasses<R>::y_fwd(N, 1, Gs, p->P, nullptr, nullptr, nullptr, nullptr, specs[k], 0, L, tw, s));
-    PG_CUDA_TRY(FftPasses<R>::z_fwd(N, specs[k], L, tw, s));
+    PG_CUDA_TRY(FftPasses<R>::z_fwd(N, specs[k], p->P, L, tw, p->flag.as<int32_t>() + 1, s));
   }
   // fbar = N^-3 IDFT[W~ F[Gbar] + (2 / N^3) F[Cbar] F_g], k = 0 zeroed, into the first mesh
   PG_CUDA_TRY(launch_spec_combine<R>(N, p->P, L, p->Wk.as<C>(), A, B, p->Fg.as<C>(), 2.0 / n3, 1.0 / n3, Gs, s));
-  PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, Gs, Z, tw, s));
-  PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, Gs, Z, tw, s));
+  PG_CUDA_TRY(FftPasses<R>::z_inv_full(N, Gs, p->P, Z, tw, p->flag.as<int32_t>() + 1, s));
+  PG_CUDA_TRY(FftPasses<R>::y_inv_full(N, Gs, p->P, Z, tw, p->flag.as<int32_t>() + 1, s));
   PG_CUDA_TRY(FftPasses<R>::x_c2r_full(N, Gs, p->P, gbar, tw, s));
   // fbar at the galaxies, T = sum_j w_j fbar(x_j) (sm_off + P + 1 holds {0, n}), the rho / Q chain
   PG_CUDA_TRY(launch_interp<R>(geo, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gbar,
@@ -1740,29 +1741,40 @@ pg_status pg_deposit_lines(pg_plan* p, int64_t n, const double* d_pts, const dou
   return PG_OK;
 }
 
+// After a stage entry point's passes: synchronises and reports a device
+// wait that gave up (the column passes' bounded TMA waits).
+pg_status stage_status(pg_plan* p, cudaStream_t s) {
+  int32_t herr = 0;
+  PG_TRY(cudaMemcpyAsync(&herr, p->flag.as<int32_t>() + 1, 4, cudaMemcpyDeviceToHost, s));
+  PG_TRY(cudaStreamSynchronize(s));
+  return herr ? PG_ERR_TIMEOUT : PG_OK;
+}
+
 pg_status pg_fft_r2c_3d(pg_plan* p, const void* d_in, void* d_out, void* stream) {
   if (!p || !d_in || !d_out) return PG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PG_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));
   const int N = p->N, P = N / 2 + 1;
   if (p->prm.precision) {
     using C = double2;
     PG_TRY(FftPasses<double>::x_r2c_dense(N, (const double*)d_in, (C*)d_out, P, p->tw.as<C>(), s));
     PG_TRY(FftPasses<double>::y_fwd(N, 1, (C*)d_out, P, nullptr, nullptr, nullptr, nullptr, (C*)d_out, 0,
                                     lay_zy(N, P), p->tw.as<C>(), s));
-    PG_TRY(FftPasses<double>::z_fwd(N, (C*)d_out, lay_zy(N, P), p->tw.as<C>(), s));
+    PG_TRY(FftPasses<double>::z_fwd(N, (C*)d_out, P, lay_zy(N, P), p->tw.as<C>(), p->flag.as<int32_t>() + 1, s));
   } else {
     using C = float2;
     PG_TRY(FftPasses<float>::x_r2c_dense(N, (const float*)d_in, (C*)d_out, P, p->tw.as<C>(), s));
     PG_TRY(FftPasses<float>::y_fwd(N, 1, (C*)d_out, P, nullptr, nullptr, nullptr, nullptr, (C*)d_out, 0,
                                    lay_zy(N, P), p->tw.as<C>(), s));
-    PG_TRY(FftPasses<float>::z_fwd(N, (C*)d_out, lay_zy(N, P), p->tw.as<C>(), s));
+    PG_TRY(FftPasses<float>::z_fwd(N, (C*)d_out, P, lay_zy(N, P), p->tw.as<C>(), p->flag.as<int32_t>() + 1, s));
   }
-  return PG_OK;
+  return stage_status(p, s);
 }
 
 pg_status pg_fft_c2r_3d(pg_plan* p, const void* d_in, void* d_out, void* stream) {
   if (!p || !d_in || !d_out) return PG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PG_TRY(cudaMemsetAsync(p->flag.p, 0, 8, s));
   const int N = p->N, P = N / 2 + 1;
   const size_t bytes = csize(p) * (size_t)N * N * P;
   PG_TRY(p->tmpfft.ensure(bytes, &p->total));
@@ -1770,17 +1782,17 @@ pg_status pg_fft_c2r_3d(pg_plan* p, const void* d_in, void* d_out, void* stream)
   if (p->prm.precision) {
     using C = double2;
     C* t = p->tmpfft.as<C>();
-    PG_TRY(FftPasses<double>::z_inv_full(N, t, lay_zy(N, P), p->tw.as<C>(), s));
-    PG_TRY(FftPasses<double>::y_inv_full(N, t, lay_zy(N, P), p->tw.as<C>(), s));
+    PG_TRY(FftPasses<double>::z_inv_full(N, t, P, lay_zy(N, P), p->tw.as<C>(), p->flag.as<int32_t>() + 1, s));
+    PG_TRY(FftPasses<double>::y_inv_full(N, t, P, lay_zy(N, P), p->tw.as<C>(), p->flag.as<int32_t>() + 1, s));
     PG_TRY(FftPasses<double>::x_c2r_full(N, t, P, (double*)d_out, p->tw.as<C>(), s));
   } else {
     using C = float2;
     C* t = p->tmpfft.as<C>();
-    PG_TRY(FftPasses<float>::z_inv_full(N, t, lay_zy(N, P), p->tw.as<C>(), s));
-    PG_TRY(FftPasses<float>::y_inv_full(N, t, lay_zy(N, P), p->tw.as<C>(), s));
+    PG_TRY(FftPasses<float>::z_inv_full(N, t, P, lay_zy(N, P), p->tw.as<C>(), p->flag.as<int32_t>() + 1, s));
+    PG_TRY(FftPasses<float>::y_inv_full(N, t, P, lay_zy(N, P), p->tw.as<C>(), p->flag.as<int32_t>() + 1, s));
     PG_TRY(FftPasses<float>::x_c2r_full(N, t, P, (float*)d_out, p->tw.as<C>(), s));
   }
-  return PG_OK;
+  return stage_status(p, s);
 }
 
 pg_status pg_correlate_points(pg_plan* p, int64_t n_a, const double* d_a, const double* d_wa,

@@ -6,6 +6,11 @@
 
 namespace pg {
 
+template <typename K>
+static cudaError_t set_smem(K kern, size_t bytes) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 namespace fft {
 template <typename R> struct Cols;
 // 64 KB column tiles, 256 threads: two or three CTAs share an SM, so one
@@ -44,9 +49,11 @@ static cudaError_t check_reg_split(K kern) {
 }
 
 // Tensor map over 8-byte elements of nb spectra of the plan layout L (each
-// N*N*P complex), dimensions (kx, y mod K, z, y / K, mesh) with K = 2^L.ks,
-// box (one kx tile of B columns, then either bz z rows of one y (by = 1) or
-// by y rows of one z (bz = 1)).
+// N*N*P complex, kx in tiles of B = 2^L.txs complex values of 64 bytes, ky in
+// blocks of K = 2^L.ks rows), dimensions (kx mod B, y mod K, kx / B, z,
+// y / K + mesh N / K) (the meshes follow one another, so the last two indices
+// of a mesh's blocks merge into one), box (one kx tile, then either bz z rows
+// of one y (by = 1) or by y rows of one z (bz = 1)).
 template <typename R, int B = ZCols<R>::B>
 static bool spec_map(CUtensorMap* m, const void* base, int N, int P, Lay L, int nb, uint32_t bz,
                      uint32_t by) {
@@ -54,12 +61,58 @@ static bool spec_map(CUtensorMap* m, const void* base, int N, int P, Lay L, int 
   constexpr int E = (int)(sizeof(C) / 8);
   const int K = 1 << L.ks;
   if (K > N || N % K != 0 || (by > 1 && by % K != 0)) return false;
-  const uint64_t dims[5] = {(uint64_t)P * E, (uint64_t)K, (uint64_t)N, (uint64_t)(N / K), (uint64_t)nb};
-  const uint64_t strides[4] = {(uint64_t)L.ys * 8 * E, (uint64_t)L.zs * 8 * E, (uint64_t)L.hs * 8 * E,
-                               (uint64_t)N * N * P * 8 * E};
-  const uint32_t box[5] = {(uint32_t)(B * E), by > 1 ? (uint32_t)K : 1u, bz, by > 1 ? by / (uint32_t)K : 1u,
-                           1u};
+  if ((1 << L.txs) != B || P % B != 0 || L.ys != B || L.ts != (int64_t)K * B ||
+      L.zs != (int64_t)K * P || L.hs != (int64_t)N * K * P)
+    return false;
+  const uint64_t dims[5] = {(uint64_t)B * E, (uint64_t)K, (uint64_t)(P / B), (uint64_t)N,
+                            (uint64_t)(N / K) * nb};
+  const uint64_t strides[4] = {(uint64_t)L.ys * 8 * E, (uint64_t)L.ts * 8 * E, (uint64_t)L.zs * 8 * E,
+                               (uint64_t)L.hs * 8 * E};
+  const uint32_t box[5] = {(uint32_t)(B * E), by > 1 ? (uint32_t)K : 1u, 1u, bz, by > 1 ? by / (uint32_t)K : 1u};
   return encode_map_5d(m, base, dims, strides, box);
+}
+// Tensor map of the persistent column pass over one dense half spectrum in
+// layout L: the plan's tiled layout (*tiled = 1, spec_map), or [z][y][kx]
+// with a pitch of a multiple of 16 bytes (*tiled = 0; dimensions (kx, y, z,
+// 1), box one kx tile by rb rows along the column). False where neither
+// applies (the caller then runs the column pass without TMA).
+template <typename R>
+static bool col_map(CUtensorMap* m, const void* base, int N, int P, Lay L, bool along_z, uint32_t rb,
+                    int* tiled) {
+  using C = typename CT<R>::C;
+  constexpr int B = Cols<R>::B, E = (int)(sizeof(C) / 8);
+  if (L.txs > 0) {
+    *tiled = 1;
+    return spec_map<R, B>(m, base, N, P, L, 1, along_z ? rb : 1u, along_z ? 1u : rb);
+  }
+  if (L.ks < 30 || L.ys != P || L.zs != (int64_t)N * P || ((int64_t)P * (int64_t)sizeof(C)) % 16 != 0)
+    return false;
+  *tiled = 0;
+  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)N, (uint64_t)N, 1u};
+  const uint64_t strides[3] = {(uint64_t)P * 8 * E, (uint64_t)N * P * 8 * E, (uint64_t)N * N * P * 8 * E};
+  const uint32_t box[4] = {(uint32_t)(B * E), along_z ? 1u : rb, along_z ? rb : 1u, 1u};
+  return encode_map_4d(m, base, dims, strides, box);
+}
+
+// Runs the persistent TMA column pass when a map of S can be encoded, else
+// the plain column kernel `plain`; true when the TMA pass was launched.
+template <typename R, int NN, bool INV, bool ALONG_Z>
+static cudaError_t col_pass(typename CT<R>::C* S, int P, Lay L, const typename CT<R>::C* tw, int* err,
+                            cudaStream_t s, bool* used_tma) {
+  using C = typename CT<R>::C;
+  constexpr int B = Cols<R>::B;
+  using Q = ColT<C, NN, B>;
+  CUtensorMap m;
+  int tiled = 0;
+  *used_tma = false;
+  if (!err || !col_map<R>(&m, S, NN, P, L, ALONG_Z, (uint32_t)Q::RB, &tiled)) return cudaSuccess;
+  auto k = k_col_tma<C, NN, B, INV, ALONG_Z>;
+  PG_CUDA_TRY(set_smem(k, Q::smem_bytes()));
+  unsigned grid = 0;
+  PG_CUDA_TRY(persistent_grid(k, Q::THREADS, Q::smem_bytes(), cdiv(NN / 2 + 1, B) * (int64_t)NN, &grid));
+  k<<<grid, Q::THREADS, Q::smem_bytes(), s>>>(m, tiled, S, L, tw, err);
+  *used_tma = true;
+  return cudaSuccess;
 }
 }  // namespace fft
 
@@ -74,10 +127,6 @@ static bool spec_map(CUtensorMap* m, const void* base, int N, int P, Lay L, int 
     default: return cudaErrorInvalidValue;                  \
   }
 
-template <typename K>
-static cudaError_t set_smem(K kern, size_t bytes) {
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 template <typename R>
 int FftPasses<R>::cols() { return fft::Cols<R>::B; }
@@ -127,9 +176,12 @@ cudaError_t FftPasses<R>::y_fwd(int N, int nb, const C* spec, int P, const int32
 }
 
 template <typename R>
-cudaError_t FftPasses<R>::z_fwd(int N, C* S, Lay L, const C* tw, cudaStream_t s) {
+cudaError_t FftPasses<R>::z_fwd(int N, C* S, int P, Lay L, const C* tw, int* err, cudaStream_t s) {
   constexpr int B = fft::Cols<R>::B;
   PG_DISPATCH_N(N, {
+    bool tma_used = false;
+    PG_CUDA_TRY((fft::col_pass<R, NN, false, true>(S, P, L, tw, err, s, &tma_used)));
+    if (tma_used) return launched();
     using CP = fft::ColPass<C, NN, B>;
     auto k = fft::k_z_fwd<C, NN, B>;
     PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
@@ -182,9 +234,12 @@ cudaError_t FftPasses<R>::x_c2r_win(int N, int nb, const C* Wy, int64_t Wy_strid
 }
 
 template <typename R>
-cudaError_t FftPasses<R>::z_inv_full(int N, C* S, Lay L, const C* tw, cudaStream_t s) {
+cudaError_t FftPasses<R>::z_inv_full(int N, C* S, int P, Lay L, const C* tw, int* err, cudaStream_t s) {
   constexpr int B = fft::Cols<R>::B;
   PG_DISPATCH_N(N, {
+    bool tma_used = false;
+    PG_CUDA_TRY((fft::col_pass<R, NN, true, true>(S, P, L, tw, err, s, &tma_used)));
+    if (tma_used) return launched();
     using CP = fft::ColPass<C, NN, B>;
     auto k = fft::k_col_inv_full<C, NN, B, true>;
     PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
@@ -195,9 +250,12 @@ cudaError_t FftPasses<R>::z_inv_full(int N, C* S, Lay L, const C* tw, cudaStream
 }
 
 template <typename R>
-cudaError_t FftPasses<R>::y_inv_full(int N, C* S, Lay L, const C* tw, cudaStream_t s) {
+cudaError_t FftPasses<R>::y_inv_full(int N, C* S, int P, Lay L, const C* tw, int* err, cudaStream_t s) {
   constexpr int B = fft::Cols<R>::B;
   PG_DISPATCH_N(N, {
+    bool tma_used = false;
+    PG_CUDA_TRY((fft::col_pass<R, NN, true, false>(S, P, L, tw, err, s, &tma_used)));
+    if (tma_used) return launched();
     using CP = fft::ColPass<C, NN, B>;
     auto k = fft::k_col_inv_full<C, NN, B, false>;
     PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));

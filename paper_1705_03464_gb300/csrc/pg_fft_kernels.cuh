@@ -318,6 +318,15 @@ __host__ __device__ constexpr int xperm() {
   return (N2 % X == 0 && N1 % X == 0 && (B * N2) % 32 == 0 && B * X <= 32) ? X : 1;
 }
 
+// Work item of a pass over the z columns (ky, kx tile) of the plan's
+// spectra, ordered with the 8 ky rows of a block fastest: the CTAs running at
+// once then read the 8 rows of each 512-byte kx-tile block together.
+__host__ __device__ __forceinline__ void zcol_item(int64_t item, int T, int& ky, int& kx_tile) {
+  const int64_t q = item >> kYBlockShift;
+  kx_tile = (int)(q % T);
+  ky = (int)(q / T) * (1 << kYBlockShift) + (int)(item & ((1 << kYBlockShift) - 1));
+}
+
 __device__ __forceinline__ int win_index(int n, int N, int w) {
   // signed offset of mesh index n in (-N/2, N/2]; returns offset + w, or -1
   if (n <= w) return n + w;
@@ -567,7 +576,7 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) buf[prow<XP>(slot, j2, N2) * B + c] = zc;
     if (c < min(B, M1 - cur.kx0)) {
-      C* out = S + (int64_t)cur.b * S_stride + (int64_t)cur.z * L.zs + cur.kx0 + c;
+      C* out = S + (int64_t)cur.b * S_stride + (int64_t)cur.z * L.zs + xoff(L, cur.kx0) + c;
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) tma::st_hint(out + yoff(L, slot + N1 * k2), a[k2], tma::policy_evict_first());
     }
@@ -599,9 +608,11 @@ k_z_fwd(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
   using CP = ColPass<C, N, B>;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
   constexpr int XP = xperm<C, N, B>();
-  const int kx0 = blockIdx.x * B, ky = blockIdx.y;
+  int ky, kxt;
+  zcol_item((int64_t)blockIdx.y * gridDim.x + blockIdx.x, gridDim.x, ky, kxt);
+  const int kx0 = kxt * B;
   const int ncol = min(B, M1 - kx0);
-  C* col = S + yoff(L, ky) + kx0;
+  C* col = S + yoff(L, ky) + xoff(L, kx0);
   load_zcol<C, N, B>(buf, col, L.zs, ncol);
   __syncthreads();
   step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
@@ -701,7 +712,7 @@ k_x_c2r_lines(const C* __restrict__ S, int P, Lay L, int64_t n_lines, const int3
   x_c2r_core<C, N>(
       buf, l0, n_lines,
       [&](int64_t l, int k) {
-        return line_y ? S[(int64_t)line_z[l] * L.zs + yoff(L, line_y[l]) + k] : S[l * P + k];
+        return line_y ? S[(int64_t)line_z[l] * L.zs + yoff(L, line_y[l]) + xoff(L, k)] : S[l * P + k];
       },
       tws,
       [&](int64_t l, int n, RT v) { out[l * N + n] = v * scale; });
@@ -754,13 +765,15 @@ k_col_inv_full(C* __restrict__ S, Lay L, const C* __restrict__ tw) {
   using CP = ColPass<C, N, B>;
   constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
   constexpr int XP = xperm<C, N, B>();
-  const int kx0 = blockIdx.x * B, other = blockIdx.y;
+  int kxt = blockIdx.x, other = blockIdx.y;
+  if (ALONG_Z) zcol_item((int64_t)blockIdx.y * gridDim.x + blockIdx.x, gridDim.x, other, kxt);
+  const int kx0 = kxt * B;
   const int ncol = min(B, M1 - kx0);
   const int c = threadIdx.x % B;
   // ALONG_Z: column over z at fixed y = other; else over y at fixed z = other
   // row r of the column: z = r (ALONG_Z) or y = r
   auto row = [&](int r) { return ALONG_Z ? (int64_t)r * L.zs : yoff(L, r); };
-  C* col = S + (ALONG_Z ? yoff(L, other) : (int64_t)other * L.zs) + kx0;
+  C* col = S + (ALONG_Z ? yoff(L, other) : (int64_t)other * L.zs) + xoff(L, kx0);
   for (int r = threadIdx.x / B; r < N; r += blockDim.x / B) {
     C v;
     v.x = 0; v.y = 0;
@@ -839,12 +852,13 @@ __device__ __forceinline__ void zc_issue(C* dst, const CUtensorMap* map, uint64_
                                          int ky, int b) {
   using Z = ZCorr<C, N, B>;
   tma::mbar_arrive_expect_tx(bar, Z::TILE_BYTES);
-  // spectra maps are (kx, y mod 8, z, y / 8, mesh)
+  // spectra maps are (kx mod B, y mod 8, kx / B, z, y / 8 + mesh N / 8)
   const uint64_t pol = tma::policy_evict_first();
   constexpr int KM = (1 << kYBlockShift) - 1;
 #pragma unroll
   for (int z0 = 0; z0 < N; z0 += Z::ZB)
-    tma::load_5d_hint(dst + z0 * B, map, bar, kx0 * Z::E, ky & KM, z0, ky >> kYBlockShift, b, pol);
+    tma::load_5d_hint(dst + z0 * B, map, bar, 0, ky & KM, kx0 / B, z0,
+                      (ky >> kYBlockShift) + b * (N >> kYBlockShift), pol);
 }
 
 // The load side of the fused z pass, run by one thread of the load
@@ -873,7 +887,9 @@ __device__ int zc_produce(const CUtensorMap* mS, const CUtensorMap* mF, C* sbuf0
   };
   int64_t i = 0;
   for (int64_t item = blockIdx.x; item < n_items && !failed; item += gridDim.x, ++i) {
-    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
+    int ky, kxt;
+    zcol_item(item, T, ky, kxt);
+    const int kx0 = kxt * B;
     if (!gg && !mesh(kx0, ky, 0)) { failed = 1; break; }
     if (i > 0 && !tma::mbar_wait(&bar[5], (uint32_t)(i - 1) & 1, limit_ns)) { failed = 1; break; }
     tma::fence_async_shared();
@@ -933,7 +949,9 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
   int64_t job = 0;
   int failed = 0;
   for (; item < n_items && !failed; item += gridDim.x) {
-    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
+    int ky, kxt;
+    zcol_item(item, T, ky, kxt);
+    const int kx0 = kxt * B;
     const int ncol = min(B, M1 - kx0);
     if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
     ph[2] ^= 1;
@@ -1094,6 +1112,124 @@ k_y_inv_tma(const __grid_constant__ CUtensorMap mW, int nb, int w, C* __restrict
 
 
 // ============================================================================
+// Full column transform in place, persistent and TMA fed: every column of a
+// dense half spectrum along z (columns (ky, kx tile), rows z) or along y
+// (columns (z, kx tile), rows y), forward or inverse (unnormalised). Items
+// alternate between two shared buffers, so the next column streams in while
+// the current one is transformed; results are stored back in place (each
+// column is read and written by the one CTA that owns its item). The tensor
+// map covers the plan's tiled layout (tiled = 1; dimensions (kx mod B,
+// y mod 8, kx / B, z, y / 8)) or a [z][y][kx] layout whose pitch is a
+// multiple of 16 bytes (tiled = 0; dimensions (kx, y, z, 1)).
+// ============================================================================
+template <typename C, int N, int B>
+struct ColT {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int THREADS = B * N1;
+  static constexpr int TILE = N * B;
+  static constexpr int RB = N < 256 ? N : 256;   // rows per TMA box
+  static constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
+  static constexpr int E = sizeof(C) / 8;
+  static constexpr size_t SMEM = sizeof(C) * (2 * (size_t)TILE + N) + 64;
+  static constexpr int MINB = SMEM <= 74 * 1024 ? 3 : SMEM <= 110 * 1024 ? 2 : 1;
+  static constexpr size_t smem_bytes() { return SMEM; }
+};
+
+template <typename C, int N, int B, bool ALONG_Z>
+__device__ __forceinline__ void colt_issue(C* dst, const CUtensorMap* map, uint64_t* bar, int kxt,
+                                           int other, int tiled) {
+  using Q = ColT<C, N, B>;
+  tma::mbar_arrive_expect_tx(bar, Q::TILE_BYTES);
+  const uint64_t pol = tma::policy_evict_first();
+  constexpr int KM = (1 << kYBlockShift) - 1;
+#pragma unroll
+  for (int r0 = 0; r0 < N; r0 += Q::RB) {
+    if (tiled) {
+      if (ALONG_Z) tma::load_5d_hint(dst + r0 * B, map, bar, 0, other & KM, kxt, r0, other >> kYBlockShift, pol);
+      else tma::load_5d_hint(dst + r0 * B, map, bar, 0, 0, kxt, other, r0 >> kYBlockShift, pol);
+    } else {
+      if (ALONG_Z) tma::load_4d(dst + r0 * B, map, bar, kxt * B * Q::E, other, r0, 0);
+      else tma::load_4d(dst + r0 * B, map, bar, kxt * B * Q::E, r0, other, 0);
+    }
+  }
+}
+
+template <typename C, int N, int B, bool INV, bool ALONG_Z>
+__global__ void __launch_bounds__(ColT<C, N, B>::THREADS, ColT<C, N, B>::MINB)
+k_col_tma(const __grid_constant__ CUtensorMap map, int tiled, C* __restrict__ S, Lay L,
+          const C* __restrict__ tw, int* __restrict__ err) {
+  using Q = ColT<C, N, B>;
+  constexpr int N1 = Q::N1, N2 = Q::N2, TILE = Q::TILE, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
+  constexpr uint64_t kLimitNs = 2000000000ull;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* const buf0 = reinterpret_cast<C*>(smem_raw);   // buffers: buf0 + k * TILE
+  C* tws = buf0 + 2 * TILE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);
+  const int T = (M1 + B - 1) / B;
+  const int64_t n_items = (int64_t)T * N;
+  int64_t item = blockIdx.x;
+  if (item >= n_items) return;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
+  // item -> (kx tile, other): other = ky (along z) or z (along y)
+  auto decode = [&](int64_t it, int& kxt, int& other) {
+    if (ALONG_Z) {
+      zcol_item(it, T, other, kxt);
+    } else {
+      kxt = (int)(it % T);
+      other = (int)(it / T);
+    }
+  };
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::fence_async_shared();
+    int kxt, o;
+    decode(item, kxt, o);
+    colt_issue<C, N, B, ALONG_Z>(buf0, &map, &bar[0], kxt, o, tiled);
+  }
+  __syncthreads();
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  uint32_t ph[2] = {0, 0};
+  int failed = 0;
+  for (int64_t job = 0; item < n_items; item += gridDim.x, ++job) {
+    const int cur = (int)(job & 1);
+    C* buf = buf0 + cur * TILE;
+    if (threadIdx.x == 0 && item + gridDim.x < n_items) {
+      int kxn, on;
+      decode(item + gridDim.x, kxn, on);
+      tma::fence_async_shared();
+      colt_issue<C, N, B, ALONG_Z>(buf0 + (cur ^ 1) * TILE, &map, &bar[cur ^ 1], kxn, on, tiled);
+    }
+    if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
+    ph[cur] ^= 1;
+    int kxt, other;
+    decode(item, kxt, other);
+    const int kx0 = kxt * B, ncol = min(B, M1 - kx0);
+    step1<C, N1, N2, B, INV, XP>(buf, B, tws, 1);
+    __syncthreads();
+    C a[N2];
+    step2<C, N1, N2, INV, XP>(buf, B, c, k1, a);
+    if (c < ncol) {
+      C* col = S + (ALONG_Z ? yoff(L, other) : (int64_t)other * L.zs) + xoff(L, kx0) + c;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int r = k1 + N1 * k2;
+        col[ALONG_Z ? (int64_t)r * L.zs : yoff(L, r)] = a[k2];
+      }
+    }
+    __syncthreads();   // buffer free for the prefetch two items ahead
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, tma::kErrTmaTimeout);
+      for (int k = 0; k < 2; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
+    }
+    __syncthreads();
+  }
+}
+
+// ============================================================================
 // Adjoint passes, batched like the forward (reverse sweep of Sec. 2.1's
 // correlation through FFTs). A window adjoint field is supported on the
 // |r| <= w window, so after its x and y passes only the W = 2w+1 window z
@@ -1131,7 +1267,7 @@ k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_
   C a[N2];
   step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
   if (c < ncol) {
-    C* out = Xw + (int64_t)b * Xw_stride + (int64_t)zr * XL.zs + kx0 + c;
+    C* out = Xw + (int64_t)b * Xw_stride + (int64_t)zr * XL.zs + xoff(XL, kx0) + c;
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) out[yoff(XL, k1 + N1 * k2)] = a[k2];
   }
@@ -1158,15 +1294,15 @@ struct ZAdj {
 };
 
 // Full z column (N rows) of a spectrum array into dst; the tensor map's
-// dimensions are (kx, z, ky, mesh).
+// dimensions are (kx mod B, ky mod 8, kx / B, z, ky / 8 + mesh N / 8).
 template <typename C, int N, int B>
 __device__ __forceinline__ void za_issue_col(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
                                              int ky, int b, uint64_t policy) {
   using Z = ZAdj<C, N, B>;
 #pragma unroll
   for (int z0 = 0; z0 < N; z0 += Z::ZB)
-    tma::load_5d_hint(dst + z0 * B, map, bar, kx0 * Z::E, ky & ((1 << kYBlockShift) - 1), z0,
-                      ky >> kYBlockShift, b, policy);
+    tma::load_5d_hint(dst + z0 * B, map, bar, 0, ky & ((1 << kYBlockShift) - 1), kx0 / B, z0,
+                      (ky >> kYBlockShift) + b * (N >> kYBlockShift), policy);
 }
 
 // Compact window column (W rows) of Xw into dst; the tensor map's
@@ -1283,7 +1419,9 @@ __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CU
   };
   int64_t i = 0;
   for (int64_t item = blockIdx.x; item < n_items && !failed; item += gridDim.x, ++i) {
-    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
+    int ky, kxt;
+    zcol_item(item, T, ky, kxt);
+    const int kx0 = kxt * B;
     if (nb > 0 && !slot(kx0, ky, 0)) { failed = 1; break; }
     if (i > 0 && !tma::mbar_wait(&bar[5], (uint32_t)(i - 1) & 1, limit_ns)) { failed = 1; break; }
     tma::fence_async_shared();
@@ -1351,10 +1489,12 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
   int64_t job = 0;
   int failed = 0;
   for (; item < n_items && !failed; item += gridDim.x) {
-    const int ky = (int)(item / T), kx0 = (int)(item % T) * B;
+    int ky, kxt;
+    zcol_item(item, T, ky, kxt);
+    const int kx0 = kxt * B;
     const int ncol = min(B, M1 - kx0);
     const bool dc_col = (kx0 + c == 0) && (ky == 0);
-    const C* fcol = Fg + yoff(L, ky) + kx0 + c;
+    const C* fcol = Fg + yoff(L, ky) + xoff(L, kx0) + c;
     if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
     ph[2] ^= 1;
     for (int b = 0; b < nb; ++b, ++job) {
@@ -1399,7 +1539,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
       if (dc_col && k1 == 0) { x[0].x = 0; x[0].y = 0; }   // k = 0 mode
       stepA_own<C, N1, N2, true, XP>(buf, B, c, k1, x, tws, 1);
       tma::bar_sync(1, CT);
-      C* yout = S + (int64_t)b * S_stride + yoff(L, ky) + kx0;
+      C* yout = S + (int64_t)b * S_stride + yoff(L, ky) + xoff(L, kx0);
       for (int t = tid; t < B * N2; t += CT) {
         const int cc = t % B, n2 = t / B;
         C v[N1];
@@ -1415,7 +1555,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
     }
     if (failed) break;
     // the item's A column back to global memory; then the tile is free
-    C* ag = A + yoff(L, ky) + kx0;
+    C* ag = A + yoff(L, ky) + xoff(L, kx0);
     for (int t = tid; t < TILE; t += CT) {
       const int z = t / B, cc = t % B;
       tma::st_hint(ag + (int64_t)z * L.zs + cc, at[t], pol_stream);
@@ -1486,8 +1626,8 @@ k_y_inv_lines(const __grid_constant__ CUtensorMap mY, int nb, int P, const int32
     tma::mbar_arrive_expect_tx(&bar[k], Y::TILE_BYTES);
 #pragma unroll
     for (int y0 = 0; y0 < N; y0 += Y::YB)
-      tma::load_5d_hint(buf0 + k * TILE + y0 * B, &mY, &bar[k], (int)(it % T) * B * Y::E, 0, (int)(r % N),
-                        y0 >> kYBlockShift, (int)(r / N), pol_stream);
+      tma::load_5d_hint(buf0 + k * TILE + y0 * B, &mY, &bar[k], 0, 0, (int)(it % T), (int)(r % N),
+                        (y0 >> kYBlockShift) + (int)(r / N) * (N >> kYBlockShift), pol_stream);
   };
   for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
   if (threadIdx.x == 0) {

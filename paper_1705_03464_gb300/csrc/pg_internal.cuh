@@ -188,25 +188,38 @@ cudaError_t launch_field_scale(int nb, const unsigned long long* qsum, int N, do
                                cudaStream_t s);
 
 // ---- FFT passes (pg_fft_f32.cu / pg_fft_f64.cu) -----------------------------
-// Layout of a half-spectrum array, offsets in complex elements (kx has
-// stride 1): element (z, y) at z*zs + (y >> ks)*hs + (y & (2^ks - 1))*ys,
-// i.e. y split into blocks of 2^ks rows. The plan's own spectra are
-// [y / 8][z][y % 8][kx]: a z column of one (ky, kx tile) lies in about 17
-// memory pages and the ky rows one y pass writes fall in 128 blocks, where
-// [z][y][kx] puts each of a z column's N rows in its own page. The stage
-// entry points keep [z][y][kx] (ks large: one block).
+// Layout of a half-spectrum array, offsets in complex elements: element
+// (z, y, kx) at z*zs + yoff(y) + xoff(kx), with
+//   yoff(y)  = (y >> ks)*hs + (y & (2^ks - 1))*ys   (y in blocks of 2^ks rows)
+//   xoff(kx) = (kx >> txs)*ts + (kx & (2^txs - 1))  (kx in tiles of 2^txs)
+// The defaults ts = 1, txs = 0 keep kx contiguous. The plan's own spectra are
+// [y / 8][z][kx / TX][y % 8][kx % TX] with TX = 64 bytes of complex values
+// (8 in FP32, 4 in FP64), the width of every column tile: a y-pass item (one
+// z plane, one kx tile, all ky) writes whole 512-byte blocks, and a z-pass
+// item (one ky, one kx tile, all z) reads one 64-byte row of each block, a
+// z stride of 8 P apart, as in the untiled [y / 8][z][y % 8][kx]. The stage
+// entry points keep [z][y][kx] (ks large: one block; kx contiguous).
 struct Lay {
   int64_t zs, ys, hs;
   int ks;
+  int64_t ts = 1;
+  int txs = 0;
 };
 __host__ __device__ __forceinline__ int64_t yoff(const Lay& L, int y) {
   return (int64_t)(y >> L.ks) * L.hs + (int64_t)(y & ((1 << L.ks) - 1)) * L.ys;
 }
+__host__ __device__ __forceinline__ int64_t xoff(const Lay& L, int kx) {
+  return (int64_t)(kx >> L.txs) * L.ts + (kx & ((1 << L.txs) - 1));
+}
 inline Lay lay_zy(int N, int P) { return {(int64_t)N * P, (int64_t)P, 0, 30}; }
 constexpr int kYBlockShift = 3;   // 8 ky rows per block
+// kx tile shift of the plan layout: 64-byte tiles
+template <typename R> constexpr int tile_shift() { return sizeof(R) == 4 ? 3 : 2; }
+template <typename R>
 inline Lay lay_plan(int N, int P) {
-  const int K = 1 << kYBlockShift;
-  return {(int64_t)K * P, (int64_t)P, (int64_t)N * K * P, kYBlockShift};
+  constexpr int txs = tile_shift<R>();
+  const int K = 1 << kYBlockShift, TX = 1 << txs;
+  return {(int64_t)K * P, (int64_t)TX, (int64_t)N * K * P, kYBlockShift, (int64_t)K * TX, txs};
 }
 
 // Spectra are complex R pairs; P = row pitch in complex elements (>= N/2+1).
@@ -228,7 +241,9 @@ struct FftPasses {
                            const int32_t* line_y, C* S, int64_t S_stride, Lay L, const C* tw,
                            cudaStream_t s);
   // Z pass forward in place: S[z][ky][kx] -> F[kz][ky][kx].
-  static cudaError_t z_fwd(int N, C* S, Lay L, const C* tw, cudaStream_t s);
+  // Dense column passes in place (persistent and TMA fed where the pitch
+  // allows a tensor map; err receives a device wait timeout)
+  static cudaError_t z_fwd(int N, C* S, int P, Lay L, const C* tw, int* err, cudaStream_t s);
   // Z pass fused: for each of nb meshes, forward z, times conj(Fg) / N^3
   // (gg: P = |Fg|^2 / N^3 from Fg itself), k = 0 set to zero, inverse z, and
   // only the |z| <= w rows written: Wz[b] = [2w+1][ky][P]. Persistent and
@@ -245,8 +260,8 @@ struct FftPasses {
                                R* Cwin, int64_t Cwin_stride, int P, double scale,
                                const C* tw, cudaStream_t s);
   // Dense inverse passes for the stage entry point: full y, full x.
-  static cudaError_t z_inv_full(int N, C* S, Lay L, const C* tw, cudaStream_t s);
-  static cudaError_t y_inv_full(int N, C* S, Lay L, const C* tw, cudaStream_t s);
+  static cudaError_t z_inv_full(int N, C* S, int P, Lay L, const C* tw, int* err, cudaStream_t s);
+  static cudaError_t y_inv_full(int N, C* S, int P, Lay L, const C* tw, int* err, cudaStream_t s);
   static cudaError_t x_c2r_full(int N, const C* S, int P, R* out, const C* tw,
                                 cudaStream_t s);
   static cudaError_t set_smem_limits();

@@ -64,7 +64,7 @@ k_spec_mul(int N, int P, Lay L, const C* __restrict__ A, const C* __restrict__ B
     const int kx = (int)(t % M1);
     const int ky = (int)((t / M1) % N);
     const int kz = (int)(t / ((int64_t)M1 * N));
-    const int64_t src = (int64_t)kz * L.zs + yoff(L, ky) + kx;
+    const int64_t src = (int64_t)kz * L.zs + yoff(L, ky) + xoff(L, kx);
     const C b = B[src];
     C v;
     if (mode == 0) {

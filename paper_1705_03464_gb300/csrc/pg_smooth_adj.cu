@@ -189,7 +189,7 @@ k_spec_combine(int N, int P, Lay L, const C* __restrict__ Wk, const C* __restric
     const int kx = (int)(t % M1);
     const int ky = (int)((t / M1) % N);
     const int kz = (int)(t / ((int64_t)M1 * N));
-    const int64_t src = (int64_t)kz * L.zs + yoff(L, ky) + kx;
+    const int64_t src = (int64_t)kz * L.zs + yoff(L, ky) + xoff(L, kx);
     const C w = Wk[src], a = A[src], b = B[src], f = Fg[src];
     C v;
     v.x = (RT)scale * ((w.x * a.x - w.y * a.y) + (RT)cs * (b.x * f.x - b.y * f.y));
