@@ -76,6 +76,10 @@ struct Workspace {
   int device = 0, N = 0, precision = 0;
   size_t total = 0;
   int64_t cap_lines = -1;
+  // count of writes to S (pair spectra, or S used as scratch): a forward
+  // records it after its last batch, and the backward of that forward reuses
+  // the batch's spectra only if nothing has written S since
+  uint64_t s_seq = 0;
   DevBuf flags, lidx, seg_total, line_base, n_lines, stmp, line_y, line_bin, line_z, lines_q, qsum,
       scale, spec, S, Fg, Wz, Wy, Cwin, tmpfft, Xs, As, Xw, wlines, cggw;
   DevBuf* all_bufs[24] = {&flags, &lidx, &seg_total, &line_base, &n_lines, &stmp, &line_y, &line_bin,
@@ -154,6 +158,10 @@ struct pg_plan {
   bool fwd_ok = false, last_has_w = false;
   int64_t last_n = 0;
   std::vector<unsigned long long> last_hdd;
+  // the last forward's final pair batch [reuse_b0, reuse_b1), whose spectra
+  // stay in S while the workspace's write count equals reuse_seq
+  uint64_t reuse_seq = 0;
+  int reuse_b0 = -1, reuse_b1 = -1;
   // outputs
   DevBuf out;
   int64_t cap_gal = -1, cap_pairs = -1;
@@ -313,7 +321,9 @@ cudaError_t ensure_shared(pg_plan* p) {
   PG_CUDA_TRY(p->qsum.ensure(8 * nb, t));
   PG_CUDA_TRY(p->scale.ensure(8 * nb, t));
   const size_t plane = csize(p) * (size_t)NN * p->P;
+  const void* s_before = p->S.p;
   PG_CUDA_TRY(p->S.ensure(plane * nb, t));
+  if (p->S.p != s_before) ++p->wsp->s_seq;   // contents gone
   PG_CUDA_TRY(p->Fg.ensure(plane, t));
   PG_CUDA_TRY(p->Wz.ensure(csize(p) * (size_t)p->W * p->N * p->P * nb, t));
   PG_CUDA_TRY(p->Wy.ensure(csize(p) * (size_t)p->W * p->W * p->P * nb, t));
@@ -448,6 +458,7 @@ template <typename R>
 cudaError_t lines_to_S(pg_plan* p, int nb, int64_t nl, typename CT<R>::C* S, int64_t S_stride,
                        cudaStream_t s) {
   using C = typename CT<R>::C;
+  if (S == p->S.as<C>()) ++p->wsp->s_seq;
   const C* tw = p->tw.as<C>();
   const double cs = (double)sizeof(C), M1 = p->M1, N = p->N;
   {
@@ -619,6 +630,25 @@ cudaError_t positions_and_pairs(pg_plan* p, int64_t n, const double* d_pos, cons
   return cudaStreamSynchronize(s);
 }
 
+// Pair-bin batches of at most nbmax contiguous bins for the forward and the
+// backward: formed from the last nonempty bin down, so that only the first
+// batch can be short (the backward reuses the last, full one), with empty
+// bins trimmed off the ends of each batch. Increasing bin order.
+std::vector<std::pair<int, int>> bin_batches(const std::vector<unsigned long long>& hdd, int nbmax) {
+  std::vector<std::pair<int, int>> out;
+  int b1 = (int)hdd.size();
+  for (;;) {
+    while (b1 > 0 && hdd[b1 - 1] == 0) --b1;
+    if (b1 <= 0) break;
+    int b0 = std::max(0, b1 - nbmax);
+    while (b0 < b1 && hdd[b0] == 0) ++b0;
+    out.push_back({b0, b1});
+    b1 = b0;
+  }
+  std::reverse(out.begin(), out.end());
+  return out;
+}
+
 template <typename R>
 pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* d_vel,
                        const float* d_w, pg_result* out, cudaStream_t s) {
@@ -649,11 +679,10 @@ pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* 
   for (int b = 0; b < p->nPB; ++b) off[b + 1] = off[b] + (int64_t)hdd[b];
   using C = typename CT<R>::C;
   const int64_t S_stride = (int64_t)p->N * p->N * p->P;
-  int b0 = 0;
-  while (have_gal && b0 < p->nPB) {
-    while (b0 < p->nPB && hdd[b0] == 0) ++b0;
-    if (b0 >= p->nPB) break;
-    int b1 = std::min(p->nPB, b0 + p->nbmax);
+  p->reuse_b0 = p->reuse_b1 = -1;
+  const auto batches = have_gal ? bin_batches(hdd, p->nbmax) : std::vector<std::pair<int, int>>{};
+  for (const auto& bb : batches) {
+    const int b0 = bb.first, b1 = bb.second;
     const int nb = b1 - b0;
     const int64_t pn = off[b1] - off[b0];
     int64_t nl = 0;
@@ -662,7 +691,9 @@ pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* 
                          p->pbin.as<int32_t>() + off[b0], b0, nb, &nl, s));
     PG_TRY(lines_to_S<R>(p, nb, nl, p->S.as<C>(), S_stride, s));
     PG_TRY(correlate_window<R>(p, nb, false, p->sums_pg.as<double>() + (size_t)b0 * p->nL * 2, s));
-    b0 = b1;
+    p->reuse_seq = p->wsp->s_seq;   // the correlation only reads S
+    p->reuse_b0 = b0;
+    p->reuse_b1 = b1;
   }
   // ratios
   OutPtrs o = out_layout(p);
@@ -898,12 +929,16 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   R* hl = reinterpret_cast<R*>(p->lines_q.p);   // the deposit's lines are consumed by the x pass
   std::vector<int64_t> off(P + 1, 0), hbase(nbmax, 0);
   for (int b = 0; b < P; ++b) off[b + 1] = off[b] + (int64_t)p->last_hdd[b];
-  int b0 = 0;
-  while (b0 < P) {
-    while (b0 < P && p->last_hdd[b0] == 0) ++b0;
-    if (b0 >= P) break;
-    const int b1 = std::min(P, b0 + nbmax);
+  // the forward's batches, last first (the adjoint z pass takes the meshes
+  // of a batch last first too, so A accumulates in descending bin order for
+  // any batching); the first of them is the forward's final batch, whose
+  // spectra are still in S unless something has written S since
+  const auto batches = bin_batches(p->last_hdd, nbmax);
+  for (auto it = batches.rbegin(); it != batches.rend(); ++it) {
+    const int b0 = it->first, b1 = it->second;
     const int nb = b1 - b0;
+    const bool reuse = it == batches.rbegin() && b0 == p->reuse_b0 && b1 == p->reuse_b1 &&
+                       p->reuse_seq == p->wsp->s_seq;
     int64_t nl = 0;
     PG_CUDA_TRY(deposit_batch(p, off[b1] - off[b0], p->px.as<double>() + off[b0],
                               p->py.as<double>() + off[b0], p->pz.as<double>() + off[b0],
@@ -911,7 +946,7 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
                               &nl, s));
     PG_CUDA_TRY(cudaMemcpyAsync(hbase.data(), p->line_base.p, sizeof(int64_t) * nb,
                                 cudaMemcpyDeviceToHost, s));
-    PG_CUDA_TRY(lines_to_S<R>(p, nb, nl, p->S.as<C>(), S_stride, s));
+    if (!reuse) PG_CUDA_TRY(lines_to_S<R>(p, nb, nl, p->S.as<C>(), S_stride, s));
     const double dnb = nb, Wd = W, spec1 = NN * M1 * cs, win1 = Wd * Nd * M1 * cs;
     {
       ProfScope ps(p, PG_FAM_ADJ_WINDOW, s,
@@ -930,6 +965,7 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
       ProfScope ps(p, PG_FAM_ADJ_Z, s, dnb * (2.0 * spec1 + win1) + 3.0 * spec1);
       PG_CUDA_TRY(FftPasses<R>::zadj(N, nb, p->S.as<C>(), S_stride, L, p->Xw.as<C>(), Xw_stride, XL,
                                      p->Fg.as<C>(), p->As.as<C>(), p->w, p->P, tw, err, s));
+      ++p->wsp->s_seq;   // Y_b written over S
     }
     {
       // Y_b in (planes that hold lines; counted whole), the lines out
@@ -957,7 +993,6 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
                                     n3, DDbar + b, p->psi.as<int32_t>() + o0, p->psj.as<int32_t>() + o0,
                                     gw, wbar, s));
     }
-    b0 = b1;
   }
   // galaxy side: f_g adjoint = N^-6 IDFT[A] at the galaxy lines
   ProfScope ps(p, PG_FAM_ADJ_GALAXY, s, 4.0 * NN * M1 * cs + 96.0 * (double)n);
@@ -1023,6 +1058,7 @@ pg_status smooth_impl(pg_plan* p, const SmoothW& wp, int64_t n, const double* d_
   const Lay L = lay_plan<R>(N, p->P), Z = lay_zy(N, p->P);
   const C* tw = p->tw.as<C>();
   R* real = reinterpret_cast<R*>(p->S.p);   // shared scratch: at least one spectrum, so N^3 reals
+  ++p->wsp->s_seq;
   C* Gs = p->Gs.as<C>();
   C* Wk = p->Wk.as<C>();
   PG_TRY((galaxy_pass<R>(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, false, s)));

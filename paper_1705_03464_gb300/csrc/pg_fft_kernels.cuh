@@ -1422,14 +1422,15 @@ __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CU
     int ky, kxt;
     zcol_item(item, T, ky, kxt);
     const int kx0 = kxt * B;
-    if (nb > 0 && !slot(kx0, ky, 0)) { failed = 1; break; }
+    // meshes in descending order (see k_zadj)
+    if (nb > 0 && !slot(kx0, ky, nb - 1)) { failed = 1; break; }
     if (i > 0 && !tma::mbar_wait(&bar[5], (uint32_t)(i - 1) & 1, limit_ns)) { failed = 1; break; }
     tma::fence_async_shared();
     tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
     za_issue_col<C, N, B>(at, mA, &bar[2], kx0, ky, 0, pol);
     ++issued[2];
-    for (int b = 1; b < nb; ++b)
-      if (!slot(kx0, ky, b)) { failed = 1; break; }
+    for (int j = 1; j < nb; ++j)
+      if (!slot(kx0, ky, nb - 1 - j)) { failed = 1; break; }
   }
   for (int k = 0; k < 3; ++k)
     if (issued[k]) tma::mbar_wait(&bar[k], (issued[k] - 1) & 1, failed ? 100000000ull : limit_ns);
@@ -1497,7 +1498,10 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
     const C* fcol = Fg + yoff(L, ky) + xoff(L, kx0) + c;
     if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
     ph[2] ^= 1;
-    for (int b = 0; b < nb; ++b, ++job) {
+    // meshes in descending order: with the batches also taken last first, A
+    // accumulates the pair meshes in descending bin order for any batching
+    for (int j = 0; j < nb; ++j, ++job) {
+      const int b = nb - 1 - j;
       const int cur = (int)(job & 1);
       C* buf = sb0 + cur * TILE;
       if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
