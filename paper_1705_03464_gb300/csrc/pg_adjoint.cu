@@ -148,8 +148,12 @@ k_window_field(int N, int w, const int32_t* __restrict__ cell_bin, const uint8_t
     const int64_t line = t / N;
     const int x = (int)(t % N);
     const int ox = x <= N / 2 ? x : x - N;
+    if (ox < -w || ox > w) {   // outside the window: no FP64 work (the GPU's FP64 rate is low)
+      lines[t] = R(0);
+      continue;
+    }
     double v = 0.0;
-    if (ox >= -w && ox <= w) {
+    {
       // lines are in mesh order (z, then y): rank r <= w is offset r, rank
       // r > w is offset r - W; window coordinate = offset + w
       const int rz = (int)(line / W), ry = (int)(line % W);

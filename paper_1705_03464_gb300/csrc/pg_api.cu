@@ -841,7 +841,10 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   const int64_t W2 = (int64_t)W * W;
   const int64_t Xw_stride = (int64_t)W * N * p->P;
   const Lay L = lay_plan<R>(N, p->P);
-  const Lay XL{(int64_t)p->P, 0, (int64_t)W * p->P, 0};   // compact windows [ky][zr][kx]
+  // compact window spectra [ky / 8][zr][kx / TX][ky % 8][kx % TX] per mesh
+  constexpr int txs = tile_shift<R>();
+  const Lay XL{(int64_t)8 * p->P, (int64_t)1 << txs, (int64_t)W * 8 * p->P, kYBlockShift,
+               (int64_t)8 << txs, txs};
   PG_CUDA_TRY(ensure_lines(p, nbmax * W2));
   PG_CUDA_TRY(p->Xs.ensure(sizeof(C) * spec_elems, t));
   PG_CUDA_TRY(p->As.ensure(sizeof(C) * spec_elems, t));

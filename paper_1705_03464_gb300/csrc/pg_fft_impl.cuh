@@ -314,26 +314,33 @@ cudaError_t FftPasses<R>::y_fwd_win(int N, int nb, const C* spec, int P, int w, 
   PG_DISPATCH_N(N, {
     using CP = fft::ColPass<C, NN, B>;
     auto k = fft::k_y_fwd_win<C, NN, B>;
-    PG_CUDA_TRY(set_smem(k, CP::smem_bytes()));
+    const size_t sm = CP::smem_bytes() + sizeof(C) * (size_t)(2 * w + 1) * B;   // + the compact slot
+    PG_CUDA_TRY(set_smem(k, sm));
     dim3 g((unsigned)cdiv(NN / 2 + 1, B), (unsigned)(2 * w + 1), (unsigned)nb);
-    k<<<g, CP::THREADS, CP::smem_bytes(), s>>>(spec, P, w, Xw, Xw_stride, XL, tw);
+    k<<<g, CP::THREADS, sm, s>>>(spec, P, w, Xw, Xw_stride, XL, tw);
   });
   return launched();
 }
 
 namespace fft {
-// Tensor map of compact window spectra Xw (layout XL: strides of zr and ky),
-// dimensions (kx, zr, ky, mesh), box (one kx tile, all W rows, one ky, one mesh).
+// Tensor map of compact window spectra Xw in layout XL, [ky / 8][zr][kx / B]
+// [ky % 8][kx % B] per mesh: dimensions (kx mod B, ky mod 8, kx / B, zr,
+// ky / 8 + mesh N / 8), box (one kx tile, one ky, all W rows zr).
 template <typename R>
 static bool adj_win_map(CUtensorMap* m, const void* base, int N, int P, int W, int nb, int64_t stride,
                         Lay XL) {
   using C = typename CT<R>::C;
   constexpr int B = ZCols<R>::B, E = (int)(sizeof(C) / 8);
-  if (XL.ks != 0) return false;   // one ky row per block: ky stride hs
-  const uint64_t dims[4] = {(uint64_t)P * E, (uint64_t)W, (uint64_t)N, (uint64_t)nb};
-  const uint64_t strides[3] = {(uint64_t)XL.zs * 8 * E, (uint64_t)XL.hs * 8 * E, (uint64_t)stride * 8 * E};
-  const uint32_t box[4] = {(uint32_t)(B * E), (uint32_t)W, 1u, 1u};
-  return encode_map_4d(m, base, dims, strides, box);
+  const int K = 1 << kYBlockShift;
+  if (XL.ks != kYBlockShift || (1 << XL.txs) != B || XL.ys != B || XL.ts != (int64_t)K * B ||
+      XL.zs != (int64_t)K * P || XL.hs != (int64_t)W * K * P || stride != (int64_t)W * N * P || P % B != 0)
+    return false;
+  const uint64_t dims[5] = {(uint64_t)B * E, (uint64_t)K, (uint64_t)(P / B), (uint64_t)W,
+                            (uint64_t)(N / K) * nb};
+  const uint64_t strides[4] = {(uint64_t)XL.ys * 8 * E, (uint64_t)XL.ts * 8 * E, (uint64_t)XL.zs * 8 * E,
+                               (uint64_t)XL.hs * 8 * E};
+  const uint32_t box[5] = {(uint32_t)(B * E), 1u, 1u, (uint32_t)W, 1u};
+  return encode_map_5d(m, base, dims, strides, box);
 }
 }  // namespace fft
 

@@ -401,8 +401,16 @@ k_x_r2c_lines(const int64_t* __restrict__ q, const int32_t* __restrict__ line_bi
   const int64_t l0 = (int64_t)blockIdx.x * XPass<C, N>::LB;
   x_r2c_body<C, N>(buf, l0, n_lines, spec, P, tws, [&](int64_t l, int m) {
     const longlong2 qq = reinterpret_cast<const longlong2*>(q + l * N)[m];
-    const double s = scale[line_bin[l]];
-    return make_c<C>((RT)((double)qq.x * s), (RT)((double)qq.y * s));
+    if constexpr (sizeof(RT) == 4) {
+      // FP32 plans convert in FP32: the GPU's FP64 rate would make this
+      // load the x pass's limit; the two extra roundings (of q, and of the
+      // mesh's scale) are far below the FFT's own
+      const float s = (float)scale[line_bin[l]];
+      return make_c<C>(__ll2float_rn(qq.x) * s, __ll2float_rn(qq.y) * s);
+    } else {
+      const double s = scale[line_bin[l]];
+      return make_c<C>((RT)((double)qq.x * s), (RT)((double)qq.y * s));
+    }
   });
 }
 
@@ -1238,81 +1246,6 @@ k_col_tma(const __grid_constant__ CUtensorMap map, int tiled, C* __restrict__ S,
 // ============================================================================
 __device__ __forceinline__ int mesh_of_rank(int r, int N, int w) { return r <= w ? r : r - (2 * w + 1) + N; }
 
-// Y pass forward of the window lines of nb meshes into their W window
-// planes. Window line (b, zr, ry) is spec[((b * W + zr) * W + ry) * P] with
-// y = mesh_of_rank(ry). CTA = (kx tile, zr, mesh b).
-template <typename C, int N, int B>
-__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS, ColPass<C, N, B>::MINB)
-k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_t Xw_stride, Lay XL,
-            const C* __restrict__ tw) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw) + N;
-  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
-  using CP = ColPass<C, N, B>;
-  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
-  constexpr int XP = xperm<C, N, B>();
-  const int W = 2 * w + 1;
-  const int kx0 = blockIdx.x * B, zr = blockIdx.y, b = blockIdx.z;
-  const int ncol = min(B, M1 - kx0);
-  const int c = threadIdx.x % B;
-  zero_tile<C, B>(buf, N);
-  __syncthreads();
-  const int64_t l0 = ((int64_t)b * W + zr) * W;
-  for (int r = threadIdx.x / B; r < W; r += blockDim.x / B)
-    if (c < ncol) buf[mesh_of_rank(r, N, w) * B + c] = spec[(l0 + r) * P + kx0 + c];
-  __syncthreads();
-  step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
-  __syncthreads();
-  const int k1 = threadIdx.x / B;
-  C a[N2];
-  step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
-  if (c < ncol) {
-    C* out = Xw + (int64_t)b * Xw_stride + (int64_t)zr * XL.zs + xoff(XL, kx0) + c;
-#pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) out[yoff(XL, k1 + N1 * k2)] = a[k2];
-  }
-}
-
-template <typename C, int N, int B>
-struct ZAdj {
-  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
-  static constexpr int CTHREADS = B * N1;           // transform warpgroups
-  static constexpr int THREADS = CTHREADS + 128;    // + one warpgroup whose first thread issues the loads
-  using Regs = RegSplit<CTHREADS, 1>;
-  static constexpr int TILE = N * B;
-  static constexpr int ZB = N < 256 ? N : 256;   // rows per TMA box of a full column
-  static constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
-  static constexpr int E = sizeof(C) / 8;
-  // compact window slot in complex elements: W rows of B, rounded up to 128
-  // bytes (a TMA destination in shared memory must be 128-byte aligned)
-  static __host__ __device__ int win_slot(int W) {
-    constexpr int e = 128 / (int)sizeof(C);
-    return (W * B + e - 1) / e * e;
-  }
-  // two mesh tiles, the A tile, two compact window slots
-  static size_t smem(int W) { return sizeof(C) * (3 * (size_t)TILE + 2 * (size_t)win_slot(W) + N) + 64; }
-};
-
-// Full z column (N rows) of a spectrum array into dst; the tensor map's
-// dimensions are (kx mod B, ky mod 8, kx / B, z, ky / 8 + mesh N / 8).
-template <typename C, int N, int B>
-__device__ __forceinline__ void za_issue_col(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
-                                             int ky, int b, uint64_t policy) {
-  using Z = ZAdj<C, N, B>;
-#pragma unroll
-  for (int z0 = 0; z0 < N; z0 += Z::ZB)
-    tma::load_5d_hint(dst + z0 * B, map, bar, 0, ky & ((1 << kYBlockShift) - 1), kx0 / B, z0,
-                      (ky >> kYBlockShift) + b * (N >> kYBlockShift), policy);
-}
-
-// Compact window column (W rows) of Xw into dst; the tensor map's
-// dimensions are (kx, zr, ky, mesh).
-template <typename C, int N, int B>
-__device__ __forceinline__ void za_issue_win(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
-                                             int ky, int b, uint64_t policy) {
-  tma::load_4d_hint(dst, map, bar, kx0 * ZAdj<C, N, B>::E, 0, ky, b, policy);
-}
-
 // Step 1 of the split (see step1) on the zero-padded window column whose
 // nonzero rows z <= w and z >= N - w come from the compact slot
 // xc[rank * B + c]: reads the slot directly, writes buf like step1.
@@ -1389,6 +1322,94 @@ __host__ __device__ constexpr int win_nz(int w) {
   int nz = 2;
   while (nz < 2 * (w / N2 + 1)) nz *= 2;
   return nz <= N1 / 4 ? nz : 0;
+}
+
+// Y pass forward of the window lines of nb meshes into their W window
+// planes. Window line (b, zr, ry) is spec[((b * W + zr) * W + ry) * P] with
+// y = mesh_of_rank(ry): the W rows of a column go to a compact slot in
+// shared memory (rank ry is slot ry: signed y >= 0 at y, y < 0 at y + W),
+// and step 1 reads only them (pruned to its nonzero inputs where that pays).
+// CTA = (kx tile, zr, mesh b). The output Xw is [ky / 8][zr][kx / B][ky % 8]
+// [kx % B] per mesh (layout XL), so a CTA writes whole 512-byte blocks.
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(ColPass<C, N, B>::THREADS, ColPass<C, N, B>::MINB)
+k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_t Xw_stride, Lay XL,
+            const C* __restrict__ tw) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw) + N;
+  const C* tws = stage_tw(reinterpret_cast<C*>(smem_raw), tw, N);
+  C* xc = buf + N * B;   // compact slot of the W window rows
+  using CP = ColPass<C, N, B>;
+  constexpr int N1 = CP::N1, N2 = CP::N2, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
+  const int W = 2 * w + 1;
+  const int kx0 = blockIdx.x * B, zr = blockIdx.y, b = blockIdx.z;
+  const int ncol = min(B, M1 - kx0);
+  const int c = threadIdx.x % B;
+  const int64_t l0 = ((int64_t)b * W + zr) * W;
+  for (int r = threadIdx.x / B; r < W; r += blockDim.x / B) {
+    C v;
+    v.x = 0; v.y = 0;
+    if (c < ncol) v = spec[(l0 + r) * P + kx0 + c];
+    xc[r * B + c] = v;
+  }
+  __syncthreads();
+  switch (win_nz<N>(w)) {
+    case 2: step1_win_p<C, N, B, XP, 2>(buf, xc, w, tws, threadIdx.x, blockDim.x); break;
+    case 4: step1_win_p<C, N, B, XP, 4>(buf, xc, w, tws, threadIdx.x, blockDim.x); break;
+    case 8: step1_win_p<C, N, B, XP, 8>(buf, xc, w, tws, threadIdx.x, blockDim.x); break;
+    default: step1_win<C, N, B, XP>(buf, xc, w, tws, threadIdx.x, blockDim.x);
+  }
+  __syncthreads();
+  const int k1 = threadIdx.x / B;
+  C a[N2];
+  step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
+  if (c < ncol) {
+    C* out = Xw + (int64_t)b * Xw_stride + (int64_t)zr * XL.zs + xoff(XL, kx0) + c;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) out[yoff(XL, k1 + N1 * k2)] = a[k2];
+  }
+}
+
+template <typename C, int N, int B>
+struct ZAdj {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int CTHREADS = B * N1;           // transform warpgroups
+  static constexpr int THREADS = CTHREADS + 128;    // + one warpgroup whose first thread issues the loads
+  using Regs = RegSplit<CTHREADS, 1>;
+  static constexpr int TILE = N * B;
+  static constexpr int ZB = N < 256 ? N : 256;   // rows per TMA box of a full column
+  static constexpr uint32_t TILE_BYTES = TILE * sizeof(C);
+  static constexpr int E = sizeof(C) / 8;
+  // compact window slot in complex elements: W rows of B, rounded up to 128
+  // bytes (a TMA destination in shared memory must be 128-byte aligned)
+  static __host__ __device__ int win_slot(int W) {
+    constexpr int e = 128 / (int)sizeof(C);
+    return (W * B + e - 1) / e * e;
+  }
+  // two mesh tiles, the A tile, two compact window slots
+  static size_t smem(int W) { return sizeof(C) * (3 * (size_t)TILE + 2 * (size_t)win_slot(W) + N) + 64; }
+};
+
+// Full z column (N rows) of a spectrum array into dst; the tensor map's
+// dimensions are (kx mod B, ky mod 8, kx / B, z, ky / 8 + mesh N / 8).
+template <typename C, int N, int B>
+__device__ __forceinline__ void za_issue_col(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
+                                             int ky, int b, uint64_t policy) {
+  using Z = ZAdj<C, N, B>;
+#pragma unroll
+  for (int z0 = 0; z0 < N; z0 += Z::ZB)
+    tma::load_5d_hint(dst + z0 * B, map, bar, 0, ky & ((1 << kYBlockShift) - 1), kx0 / B, z0,
+                      (ky >> kYBlockShift) + b * (N >> kYBlockShift), policy);
+}
+
+// Compact window column (W rows) of Xw into dst; the tensor map's
+// dimensions are (kx mod B, ky mod 8, kx / B, zr, ky / 8 + mesh N / 8).
+template <typename C, int N, int B>
+__device__ __forceinline__ void za_issue_win(C* dst, const CUtensorMap* map, uint64_t* bar, int kx0,
+                                             int ky, int b, uint64_t policy) {
+  tma::load_5d_hint(dst, map, bar, 0, ky & ((1 << kYBlockShift) - 1), kx0 / B, 0,
+                    (ky >> kYBlockShift) + b * (N >> kYBlockShift), policy);
 }
 
 // The load side of the adjoint z pass, run by one thread of the load
