@@ -291,6 +291,24 @@ def many_mocks_line(args, pg, np, torch):
     pg.pg_run_batch(probs[:2], cats[:2], stream=stream)   # warm-up (module load, first plans)
     torch.cuda.synchronize()
     outs, lat, st = pg.pg_run_batch(probs, cats, stream=stream)
+    torch.cuda.synchronize()
+    # the work-queue driver: two runners on their own streams, plans and
+    # scratch; each runner holds its own scratch per mesh size, so its pair
+    # meshes per batch are half the tuned count (at least 8) to fit twice
+    probs2 = [pg.Problem.of(w, bins_per_batch=max(8, tune[w.mesh_n]["bins_per_batch"] // 2)) for w in ws]
+    try:
+        outs2, lat2, st2 = pg.pg_run_batch(probs2, cats, stream=stream, n_streams=2)
+        torch.cuda.synchronize()
+        same2 = all(np.array_equal(np.asarray(a["b_pg"]), np.asarray(b["b_pg"]), equal_nan=True)
+                    for a, b in zip(outs, outs2))
+        del outs2
+        two = {"mocks_per_s": st2["mocks_per_s"], "p50_ms": st2["p50_ms"], "p99_ms": st2["p99_ms"],
+               "wall_s": st2["wall_ms"] / 1e3, "shared_scratch": st2["n_workspaces"],
+               "bins_per_batch": {str(N): max(8, tune[N]["bins_per_batch"] // 2) for N in tune},
+               "outputs_equal_one_stream": bool(same2),
+               "form": "pg_run_batch_streams: two runners claim mocks from one work queue"}
+    except pg.PairgalError as e:
+        two = {"mocks_per_s": None, "error": str(e)}
     # the plain per-mock loop
     loop_ms = []
     t1 = time.perf_counter()
@@ -321,6 +339,7 @@ def many_mocks_line(args, pg, np, torch):
         "mocks_per_s": st["mocks_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
         "wall_s": st["wall_ms"] / 1e3, "plans": st["n_plans"], "shared_scratch": st["n_workspaces"],
         "gpu_launches": st["gpu_launches"], "bins_per_batch": tune,
+        "two_streams": two,
         "plain_loop": {"mocks_per_s": K / loop_wall, "p50_ms": float(np.percentile(loop_ms, 50)),
                        "p99_ms": float(np.percentile(loop_ms, 99)),
                        "form": "a fresh FP32 plan per mock, built, run and freed in turn"},
@@ -351,6 +370,7 @@ def summary(value, fwd_adj, plain, smooth, many, cpu, roofline, breakdown, peak,
             out["smooth_w_rsd_dp30_ms"] = r(smooth["rsd_dp30_grid"]["ms_per_mock"])
     if many:
         out["many_mocks_per_s"] = r(many["mocks_per_s"], 2)
+        out["many_mocks_per_s_two_streams"] = r(many["two_streams"]["mocks_per_s"], 2)
         out["many_p50_p99_ms"] = [r(many["p50_ms"]), r(many["p99_ms"])]
         out["plain_loop_mocks_per_s"] = r(many["plain_loop"]["mocks_per_s"], 2)
     if hod:

@@ -476,6 +476,20 @@ typedef struct pg_batch_stats {
 pg_status pg_run_batch(const pg_mock* mocks, int32_t n_mocks, double* latency_ms,
                        pg_batch_stats* stats, void* stream);
 
+/* pg_run_batch with n_streams runners (1..8; 1 is pg_run_batch): runner
+ * threads, each with its own non-blocking stream, plans and mesh scratch (one
+ * per mesh size and precision: the device holds n_streams times the scratch
+ * of pg_run_batch), claim the next mock from one work queue and run its
+ * forward, so one mock's host work (plan building, the readbacks of pair and
+ * line counts that size its launches) overlaps another's GPU work. The
+ * runners start after the work queued on `stream` and `stream` waits for
+ * them. Outputs, latency and stats as in pg_run_batch (latency from a mock's
+ * claim to its results on the host); a mock that fails leaves the others
+ * running. Errors: those of pg_run_batch, PG_ERR_INVALID_ARG for n_streams
+ * out of range, PG_ERR_CUDA if a stream or event cannot be created. */
+pg_status pg_run_batch_streams(const pg_mock* mocks, int32_t n_mocks, int32_t n_streams, double* latency_ms,
+                               pg_batch_stats* stats, void* stream);
+
 /* Batch-size autotuner: times one forward (after one warm-up) of the given
  * problem and HOST catalogue for each candidate bins_per_batch and writes the
  * fastest to *best (ms_out [n_cand], host, may be NULL: each candidate's

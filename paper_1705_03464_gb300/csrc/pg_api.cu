@@ -179,7 +179,9 @@ struct pg_plan {
 };
 
 std::atomic<long long>& pg::launch_counter() {
-  static std::atomic<long long> c{0};
+  // per host thread: a call counts the launches it issued, also while other
+  // threads drive other plans (the multi-stream batch driver)
+  static thread_local std::atomic<long long> c{0};
   return c;
 }
 

@@ -1,9 +1,13 @@
-// Many-mock driver and batch-size autotuner (host code over the public C
-// ABI). A batch of mocks of uneven size (box, mesh, catalogue) runs its
-// forward calls in order on one stream; a host thread builds the plans of
-// the mocks ahead (cell lists, window geometry, twiddles) while the current
-// mock runs on the GPU, and plans of one mesh size and precision share their
-// mesh scratch, so the device holds one scratch per distinct mesh size.
+// Many-mock drivers and batch-size autotuner (host code over the public C
+// ABI). pg_run_batch: a batch of mocks of uneven size (box, mesh, catalogue)
+// runs its forward calls in order on one stream; a host thread builds the
+// plans of the mocks ahead (cell lists, window geometry, twiddles) while the
+// current mock runs on the GPU, and plans of one mesh size and precision
+// share their mesh scratch, so the device holds one scratch per distinct mesh
+// size. pg_run_batch_streams: several runner threads, each with its own
+// stream, plans and scratch, claim mocks from one work queue, so that one
+// mock's host-side phases (plan building, the pair-count and line-count
+// readbacks that size its launches) overlap another mock's GPU work.
 #include <math.h>
 #include <string.h>
 
@@ -159,6 +163,122 @@ pg_status pg_run_batch(const pg_mock* mocks, int32_t n_mocks, double* latency_ms
     stats->n_plans = n_plans;
     stats->n_workspaces = n_workspaces;
     stats->gpu_launches = launches;
+  }
+  return first_err;
+}
+
+pg_status pg_run_batch_streams(const pg_mock* mocks, int32_t n_mocks, int32_t n_streams, double* latency_ms,
+                               pg_batch_stats* stats, void* stream) {
+  if (n_streams == 1) return pg_run_batch(mocks, n_mocks, latency_ms, stats, stream);
+  if (n_mocks < 0 || (n_mocks > 0 && !mocks) || n_streams < 1 || n_streams > 8) return PG_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < n_mocks; ++i)
+    if (!mocks[i].out || mocks[i].n_gal < 0 || (mocks[i].n_gal > 0 && !mocks[i].h_pos))
+      return PG_ERR_INVALID_ARG;
+  const Clock::time_point t_batch = Clock::now();
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PG_ERR_CUDA;
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  // the runners start after the caller's queued work and the caller's stream
+  // waits for the runners at the end
+  cudaEvent_t start_ev = nullptr;
+  if (cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming) != cudaSuccess) return PG_ERR_CUDA;
+  if (cudaEventRecord(start_ev, caller) != cudaSuccess) {
+    cudaEventDestroy(start_ev);
+    return PG_ERR_CUDA;
+  }
+  std::mutex mu;
+  int32_t next = 0;   // the work queue: the next mock to claim
+  std::vector<pg_status> status(n_mocks, PG_OK);
+  std::vector<double> lat_all(n_mocks, NAN);
+  std::vector<int64_t> launches(n_streams, 0);
+  std::vector<int32_t> n_plans(n_streams, 0), n_ws(n_streams, 0);
+  std::vector<cudaStream_t> streams(n_streams, nullptr);
+  std::vector<cudaEvent_t> done(n_streams, nullptr);
+  pg_status setup = PG_OK;
+  for (int k = 0; k < n_streams && setup == PG_OK; ++k) {
+    if (cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamWaitEvent(streams[k], start_ev, 0) != cudaSuccess)
+      setup = PG_ERR_CUDA;
+  }
+  auto runner = [&](int k) {
+    cudaSetDevice(dev);
+    // this runner's plans (one per distinct problem) and scratch (one per
+    // mesh size and precision): plans are not shared between runners
+    std::vector<std::pair<const pg_params*, pg_plan*>> plans;
+    std::vector<std::pair<std::pair<int32_t, int32_t>, const pg_plan*>> donors;
+    for (;;) {
+      int32_t i;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        i = next++;
+      }
+      if (i >= n_mocks) break;
+      const Clock::time_point t0 = Clock::now();
+      const pg_params& q = mocks[i].params;
+      pg_plan* p = nullptr;
+      for (const auto& e : plans)
+        if (same_problem(*e.first, q)) p = e.second;
+      pg_status st = PG_OK;
+      if (!p) {
+        const pg_plan* donor = nullptr;
+        for (const auto& d : donors)
+          if (d.first.first == q.mesh_n && d.first.second == q.precision) donor = d.second;
+        st = donor ? pg_plan_create_shared(&q, donor, &p) : pg_plan_create(&q, &p);
+        if (st == PG_OK) {
+          plans.push_back({&q, p});
+          if (!donor) {
+            donors.push_back({{q.mesh_n, q.precision}, p});
+            ++n_ws[k];
+          }
+        }
+      }
+      if (st == PG_OK) {
+        const pg_mock& m = mocks[i];
+        st = pg_forward_host(p, m.n_gal, m.h_pos, m.h_vel, m.h_w, m.out, streams[k]);
+        int64_t nl = 0;
+        if (st == PG_OK && pg_plan_last_stats(p, nullptr, &nl) == PG_OK) launches[k] += nl;
+      }
+      status[i] = st;
+      if (st == PG_OK) lat_all[i] = ms_since(t0);
+    }
+    cudaEventRecord(done[k], streams[k]);
+    n_plans[k] = (int32_t)plans.size();
+    for (auto it = plans.rbegin(); it != plans.rend(); ++it) pg_plan_destroy(it->second);
+  };
+  if (setup == PG_OK) {
+    std::vector<std::thread> threads;
+    for (int k = 0; k < n_streams; ++k) threads.emplace_back(runner, k);
+    for (auto& t : threads) t.join();
+    for (int k = 0; k < n_streams; ++k) cudaStreamWaitEvent(caller, done[k], 0);
+  }
+  for (int k = 0; k < n_streams; ++k) {
+    if (done[k]) cudaEventDestroy(done[k]);
+    if (streams[k]) cudaStreamDestroy(streams[k]);
+  }
+  cudaEventDestroy(start_ev);
+  if (setup != PG_OK) return setup;
+  pg_status first_err = PG_OK;
+  std::vector<double> lat;
+  for (int32_t i = 0; i < n_mocks; ++i) {
+    if (latency_ms) latency_ms[i] = lat_all[i];
+    if (status[i] == PG_OK) lat.push_back(lat_all[i]);
+    else if (first_err == PG_OK) first_err = status[i];
+  }
+  const double wall = ms_since(t_batch);
+  if (stats) {
+    stats->wall_ms = wall;
+    stats->mocks_per_s = wall > 0 ? 1e3 * (double)lat.size() / wall : 0.0;
+    stats->p50_ms = quantile(lat, 0.50);
+    stats->p99_ms = quantile(lat, 0.99);
+    stats->n_plans = 0;
+    stats->n_workspaces = 0;
+    stats->gpu_launches = 0;
+    for (int k = 0; k < n_streams; ++k) {
+      stats->n_plans += n_plans[k];
+      stats->n_workspaces += n_ws[k];
+      stats->gpu_launches += launches[k];
+    }
   }
   return first_err;
 }

@@ -44,8 +44,9 @@ __host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_doubl
 __host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 
-// Kernel launches issued by this library (all threads, all plans); a launcher
-// calls launched() right after each <<<...>>> instead of cudaGetLastError().
+// Kernel launches issued by this library from the calling host thread (all
+// plans); a launcher calls launched() right after each <<<...>>> instead of
+// cudaGetLastError() (whose error state is per thread too).
 std::atomic<long long>& launch_counter();
 inline cudaError_t launched() {
   launch_counter().fetch_add(1, std::memory_order_relaxed);

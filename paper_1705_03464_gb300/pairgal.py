@@ -93,6 +93,7 @@ def _load():
         "pg_plan_create": (C.c_int, [C.POINTER(pg_params), C.POINTER(vp)]),
         "pg_plan_create_shared": (C.c_int, [C.POINTER(pg_params), vp, C.POINTER(vp)]),
         "pg_run_batch": (C.c_int, [vp, i32, vp, vp, vp]),
+        "pg_run_batch_streams": (C.c_int, [vp, i32, i32, vp, vp, vp]),
         "pg_selftest_wait": (C.c_int, [vp, C.c_double, vp]),
         "pg_forward_smooth": (C.c_int, [vp, vp, i64, vp, vp, vp, vp, vp]),
         "pg_backward_smooth": (C.c_int, [vp, vp, vp, vp]),
@@ -670,10 +671,12 @@ def _host(a, dtype):
     return None if a is None else np.ascontiguousarray(a, dtype=dtype)
 
 
-def pg_run_batch(problems, catalogues, stream=None):
-    """Many mocks through the forward path (pg_run_batch): problems[i] a
-    Problem (or Plan), catalogues[i] = (pos [n,3] float64, vel [n,3] float32
-    or None, w [n] float32 or None), host arrays. Returns (outputs per mock,
+def pg_run_batch(problems, catalogues, stream=None, n_streams=1):
+    """Many mocks through the forward path: problems[i] a Problem (or Plan),
+    catalogues[i] = (pos [n,3] float64, vel [n,3] float32 or None, w [n]
+    float32 or None), host arrays. n_streams = 1: pg_run_batch (one stream,
+    plans built ahead); > 1: pg_run_batch_streams (runners on their own
+    streams claiming mocks from one work queue). Returns (outputs per mock,
     latency_ms per mock, stats dict)."""
     n = len(problems)
     if len(catalogues) != n:
@@ -695,8 +698,12 @@ def pg_run_batch(problems, catalogues, stream=None):
         m.out = C.addressof(res)
     lat = np.full(max(n, 1), np.nan)
     st = pg_batch_stats()
-    _check(_lib.pg_run_batch(C.addressof(mocks), n, lat.ctypes.data, C.byref(st), _stream(stream)),
-           "pg_run_batch")
+    if n_streams == 1:
+        _check(_lib.pg_run_batch(C.addressof(mocks), n, lat.ctypes.data, C.byref(st), _stream(stream)),
+               "pg_run_batch")
+    else:
+        _check(_lib.pg_run_batch_streams(C.addressof(mocks), n, int(n_streams), lat.ctypes.data, C.byref(st),
+                                         _stream(stream)), "pg_run_batch_streams")
     stats = {k: getattr(st, k) for k, _ in pg_batch_stats._fields_}
     return [pr.shape_result(a) for pr, a in zip(problems, results)], lat[:n], stats
 

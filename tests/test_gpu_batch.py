@@ -80,3 +80,27 @@ def test_autotune_picks_a_candidate(pg):
     best, ms = pg.pg_autotune(pg.Problem.of(w), pos, candidates=(1, 2, 4))
     assert best in (1, 2, 4) and set(ms) == {1, 2, 4}
     assert all(t > 0 for t in ms.values()) and ms[best] == min(ms.values())
+
+
+@pytest.mark.parametrize("n_streams", [2, 3])
+def test_run_batch_streams_matches_standalone_plans(pg, n_streams):
+    """The work-queue driver: runners on their own streams, with their own
+    plans and scratch, claim mocks; every mock's outputs equal its standalone
+    plan's bit for bit, and a mock whose problem is invalid fails alone."""
+    mocks = _small_mocks()
+    problems = [pg.Problem.of(w) for w, _ in mocks]
+    bad = mocks[1][0]
+    problems.insert(2, pg.Problem(bad.box_L, bad.mesh_n, 1, bad.s_edges, bad.n_mu,
+                                  (6.0, 10.0, 0.6 * bad.box_L), 1))   # r_max >= L/2
+    cats = [(p,) for _, p in mocks]
+    cats.insert(2, (mocks[1][1],))
+    with pytest.raises(pg.PairgalError) as e:
+        pg.pg_run_batch(problems, cats, n_streams=n_streams)
+    assert e.value.status == pg.PG_ERR_INVALID_ARG
+    good = [p for i, p in enumerate(problems) if i != 2]
+    gcat = [c for i, c in enumerate(cats) if i != 2]
+    outs, lat, st = pg.pg_run_batch(good, gcat, n_streams=n_streams)
+    assert np.all(np.isfinite(lat)) and st["mocks_per_s"] > 0 and st["gpu_launches"] > 0
+    assert st["n_workspaces"] <= 2 * n_streams
+    for (w, p), o in zip(mocks, outs):
+        _same(o, pg.pg_forward_host(pg.Plan.of(w), p))
