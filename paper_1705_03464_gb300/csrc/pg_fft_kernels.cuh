@@ -1517,6 +1517,14 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
     const int ncol = min(B, M1 - kx0);
     const bool dc_col = (kx0 + c == 0) && (ky == 0);
     const C* fcol = Fg + yoff(L, ky) + xoff(L, kx0) + c;
+    // the item's galaxy column, the same for every mesh: loaded once per item
+    // (its L2 latency overlaps the wait for the item's first tiles)
+    C f[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      f[k2].x = 0; f[k2].y = 0;
+      if (c < ncol) f[k2] = tma::ld_hint(fcol + (int64_t)(k1 + N1 * k2) * L.zs, pol_keep);
+    }
     if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[2], ph[2], kLimitNs))) { failed = 1; break; }
     ph[2] ^= 1;
     // meshes in descending order: with the batches also taken last first, A
@@ -1537,15 +1545,6 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
         case 4: step1_win_p<C, N, B, XP, 4>(buf, xb0 + cur * WS, w, tws, tid, CT); break;
         case 8: step1_win_p<C, N, B, XP, 8>(buf, xb0 + cur * WS, w, tws, tid, CT); break;
         default: step1_win<C, N, B, XP>(buf, xb0 + cur * WS, w, tws, tid, CT);
-      }
-      // the galaxy column is issued here, after the window transform (which
-      // then has its registers), so that its L2 latency overlaps the barrier
-      // and the window column's step 2
-      C f[N2];
-#pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) {
-        f[k2].x = 0; f[k2].y = 0;
-        if (c < ncol) f[k2] = tma::ld_hint(fcol + (int64_t)(k1 + N1 * k2) * L.zs, pol_keep);
       }
       tma::bar_sync(1, CT);
       C x[N2];
