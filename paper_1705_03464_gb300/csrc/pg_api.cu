@@ -80,6 +80,9 @@ struct Workspace {
   // records it after its last batch, and the backward of that forward reuses
   // the batch's spectra only if nothing has written S since
   uint64_t s_seq = 0;
+  // the same for F_g and the galaxy correlation window cggw (written together
+  // by a galaxy pass), which the backward of the last forward reuses
+  uint64_t fg_seq = 0;
   DevBuf flags, lidx, seg_total, line_base, n_lines, stmp, line_y, line_bin, line_z, lines_q, qsum,
       scale, spec, S, Fg, Wz, Wy, Cwin, tmpfft, Xs, As, Xw, wlines, cggw;
   DevBuf* all_bufs[24] = {&flags, &lidx, &seg_total, &line_base, &n_lines, &stmp, &line_y, &line_bin,
@@ -162,6 +165,8 @@ struct pg_plan {
   // stay in S while the workspace's write count equals reuse_seq
   uint64_t reuse_seq = 0;
   int reuse_b0 = -1, reuse_b1 = -1;
+  // the workspace's galaxy-pass count after the last forward's galaxy pass
+  uint64_t fg_seq_fwd = ~0ull;
   // outputs
   DevBuf out;
   int64_t cap_gal = -1, cap_pairs = -1;
@@ -326,7 +331,11 @@ cudaError_t ensure_shared(pg_plan* p) {
   const void* s_before = p->S.p;
   PG_CUDA_TRY(p->S.ensure(plane * nb, t));
   if (p->S.p != s_before) ++p->wsp->s_seq;   // contents gone
+  const void* fg_before = p->Fg.p;
+  const void* cg_before = p->cggw.p;
   PG_CUDA_TRY(p->Fg.ensure(plane, t));
+  PG_CUDA_TRY(p->cggw.ensure(rsize(p) * (size_t)p->W * p->W * p->W, t));
+  if (p->Fg.p != fg_before || p->cggw.p != cg_before) ++p->wsp->fg_seq;   // contents gone
   PG_CUDA_TRY(p->Wz.ensure(csize(p) * (size_t)p->W * p->N * p->P * nb, t));
   PG_CUDA_TRY(p->Wy.ensure(csize(p) * (size_t)p->W * p->W * p->P * nb, t));
   PG_CUDA_TRY(p->Cwin.ensure(rsize(p) * (size_t)p->W * p->W * p->W * nb, t));
@@ -516,6 +525,7 @@ cudaError_t galaxy_pass(pg_plan* p, int64_t n, const double* x, const double* y,
                         const double* w, bool do_gg, cudaStream_t s) {
   using C = typename CT<R>::C;
   int64_t nl = 0;
+  ++p->wsp->fg_seq;
   PG_CUDA_TRY(deposit_batch(p, n, x, y, z, w, nullptr, 0, 1, &nl, s));
   PG_CUDA_TRY(lines_to_S<R>(p, 1, nl, p->Fg.as<C>(), 0, s));
   {
@@ -670,8 +680,13 @@ pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* 
     gw = p->gw.as<double>();
   }
   const bool have_gal = n > 0;
+  p->fg_seq_fwd = ~0ull;
   if (have_gal) {
     PG_TRY((galaxy_pass<R>(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, true, s)));
+    // the galaxy window kept for the backward (Cwin is overwritten by the pair batches)
+    PG_TRY(cudaMemcpyAsync(p->cggw.p, p->Cwin.p, rsize(p) * (size_t)p->W * p->W * p->W,
+                           cudaMemcpyDeviceToDevice, s));
+    p->fg_seq_fwd = p->wsp->fg_seq;
   }
   std::vector<unsigned char> valid(p->nPB, 0);
   for (int b = 0; b < p->nPB; ++b) valid[b] = (have_gal && hdd[b] > 0) ? 1 : 0;
@@ -915,9 +930,13 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   PG_CUDA_TRY(cudaMemsetAsync(wbar, 0, sizeof(double) * std::max<int64_t>(n, 1), s));
   if (n == 0) return cudaSuccess;
   const double* gw = p->last_has_w ? p->gw.as<double>() : nullptr;
-  // galaxy spectrum and galaxy correlation window, recomputed
-  PG_CUDA_TRY((galaxy_pass<R>(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, true, s)));
-  PG_CUDA_TRY(cudaMemcpyAsync(p->cggw.p, p->Cwin.p, sizeof(R) * W3, cudaMemcpyDeviceToDevice, s));
+  // galaxy spectrum and galaxy correlation window: the forward's, unless a
+  // galaxy pass (of any plan sharing the workspace) has run since
+  if (p->fg_seq_fwd != p->wsp->fg_seq) {
+    PG_CUDA_TRY((galaxy_pass<R>(p, n, p->x.as<double>(), p->y.as<double>(), p->z.as<double>(), gw, true, s)));
+    PG_CUDA_TRY(cudaMemcpyAsync(p->cggw.p, p->Cwin.p, sizeof(R) * W3, cudaMemcpyDeviceToDevice, s));
+    p->fg_seq_fwd = p->wsp->fg_seq;
+  }
   const double cs = (double)sizeof(C), rs = (double)sizeof(R), M1 = p->M1, Nd = N;
   {
     // A = 2 Re(F[Cbar_gg]) F_g: dense y and z passes of the gg window field

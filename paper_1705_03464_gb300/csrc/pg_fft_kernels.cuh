@@ -1680,12 +1680,18 @@ k_y_inv_lines(const __grid_constant__ CUtensorMap mY, int nb, int P, const int32
     const int kx0 = (int)(it % T) * B;
     const int ncol = min(B, M1 - kx0);
     const int64_t lo = s_lo[cur], hi = s_hi[cur], base = s_base[cur];
-    // line numbers of the first rounds, loaded while the item is transformed
+    // A plane with few lines (at most two outputs per thread) takes each
+    // needed output y = k1 + N1 k2 straight from step 1's rows as the N2-point
+    // sum over j2 of row (k1, j2) W_N2^(+j2 k2); otherwise step 2 runs whole
+    // and the lines are gathered from it.
     constexpr int RSY = Y::THREADS / B, PRE = 2;
+    const bool direct = (hi - lo) * B <= 2 * Y::THREADS;
+    // line numbers of the first rounds, loaded while the item is transformed
     int yv[PRE];
 #pragma unroll
     for (int p = 0; p < PRE; ++p) {
-      const int64_t q = lo + k1 + (int64_t)p * RSY;
+      const int64_t q = direct ? lo + ((int64_t)threadIdx.x + (int64_t)p * Y::THREADS) / B
+                               : lo + k1 + (int64_t)p * RSY;
       yv[p] = q < hi ? line_y[base + q] : 0;
     }
     step1<C, N1, N2, B, true, XP>(buf, B, tws, 1);
@@ -1696,20 +1702,42 @@ k_y_inv_lines(const __grid_constant__ CUtensorMap mY, int nb, int P, const int32
       const int64_t nx = s_item[cur ^ 1];
       s_item[cur] = nx < n_items ? find(nx + gridDim.x, s_lo[cur], s_hi[cur], s_base[cur]) : n_items;
     }
-    C a[N2];
-    step2<C, N1, N2, true, XP>(buf, B, c, k1, a);
-    __syncthreads();
+    if (direct) {
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) buf[(k1 + N1 * k2) * B + c] = a[k2];   // natural row y
-    __syncthreads();
+      for (int p = 0; p < PRE; ++p) {
+        const int t = threadIdx.x + p * Y::THREADS;
+        const int64_t q = lo + t / B;
+        const int cc = t % B;
+        if (q < hi && cc < ncol) {
+          const int kk1 = yv[p] % N1, kk2 = yv[p] / N1;
+          C acc;
+          acc.x = 0; acc.y = 0;
 #pragma unroll
-    for (int p = 0; p < PRE; ++p) {
-      const int64_t q = lo + k1 + (int64_t)p * RSY;
-      if (q < hi && c < ncol) hspec[(base + q) * P + kx0 + c] = buf[yv[p] * B + c];
-    }
-    for (int64_t q = lo + k1 + (int64_t)PRE * RSY; q < hi; q += RSY) {
-      const int64_t l = base + q;
-      if (c < ncol) hspec[l * P + kx0 + c] = buf[line_y[l] * B + c];
+          for (int j2 = 0; j2 < N2; ++j2) {
+            const C v = buf[prow<XP>(kk1, j2, N2) * B + cc];
+            const C w = twid<C, true>(tws, ((j2 * kk2) % N2) * N1);   // W_N2^(+j2 k2) = W_N^(+N1 j2 k2)
+            acc.x = fmadd(v.x, w.x, fmadd(-v.y, w.y, acc.x));
+            acc.y = fmadd(v.x, w.y, fmadd(v.y, w.x, acc.y));
+          }
+          hspec[(base + q) * P + kx0 + cc] = acc;
+        }
+      }
+    } else {
+      C a[N2];
+      step2<C, N1, N2, true, XP>(buf, B, c, k1, a);
+      __syncthreads();
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) buf[(k1 + N1 * k2) * B + c] = a[k2];   // natural row y
+      __syncthreads();
+#pragma unroll
+      for (int p = 0; p < PRE; ++p) {
+        const int64_t q = lo + k1 + (int64_t)p * RSY;
+        if (q < hi && c < ncol) hspec[(base + q) * P + kx0 + c] = buf[yv[p] * B + c];
+      }
+      for (int64_t q = lo + k1 + (int64_t)PRE * RSY; q < hi; q += RSY) {
+        const int64_t l = base + q;
+        if (c < ncol) hspec[l * P + kx0 + c] = buf[line_y[l] * B + c];
+      }
     }
     __syncthreads();   // buffer free: stream in the item after the next
     if (threadIdx.x == 0 && s_item[cur] < n_items) {
