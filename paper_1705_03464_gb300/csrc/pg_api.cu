@@ -981,7 +981,7 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
                                            p->cggw.as<R>(), p->wlines.as<R>() + j * W2 * N, s));
       PG_CUDA_TRY(FftPasses<R>::x_r2c_real(N, p->wlines.as<R>(), nb * W2, p->spec.as<C>(), p->P, tw, s));
       PG_CUDA_TRY(FftPasses<R>::y_fwd_win(N, nb, p->spec.as<C>(), p->P, p->w, p->Xw.as<C>(), Xw_stride,
-                                          XL, tw, s));
+                                          XL, tw, err, s));
     }
     {
       // S and the compact window spectra of every mesh in, Y_b out; A read

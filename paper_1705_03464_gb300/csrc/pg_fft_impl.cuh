@@ -308,16 +308,36 @@ bool FftPasses<R>::adj_fits(int N, int w) {
 
 template <typename R>
 cudaError_t FftPasses<R>::y_fwd_win(int N, int nb, const C* spec, int P, int w, C* Xw,
-                                    int64_t Xw_stride, Lay XL, const C* tw, cudaStream_t s) {
+                                    int64_t Xw_stride, Lay XL, const C* tw, int* err, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   constexpr int B = fft::ZCols<R>::B;
+  constexpr int E = (int)(sizeof(C) / 8);
+  const int W = 2 * w + 1;
+  // the line spectra as [line][kx] over 8-byte elements, one box = W rows of one kx tile
+  const uint64_t n_lines = (uint64_t)nb * W * W;
+  const uint64_t dims[4] = {(uint64_t)P * E, n_lines, 1u, 1u};
+  const uint64_t strides[3] = {(uint64_t)P * 8 * E, n_lines * P * 8 * E, n_lines * P * 8 * E};
+  const uint32_t box[4] = {(uint32_t)(B * E), (uint32_t)W, 1u, 1u};
+  CUtensorMap mL;
+  const bool tma_ok = err && W <= 256 && (P * 8 * E) % 16 == 0 &&
+                      (int64_t)cdiv(N / 2 + 1, B) * W * nb < INT32_MAX && encode_map_4d(&mL, spec, dims, strides, box);
   PG_DISPATCH_N(N, {
-    using CP = fft::ColPass<C, NN, B>;
-    auto k = fft::k_y_fwd_win<C, NN, B>;
-    const size_t sm = CP::smem_bytes() + sizeof(C) * (size_t)(2 * w + 1) * B;   // + the compact slot
-    PG_CUDA_TRY(set_smem(k, sm));
-    dim3 g((unsigned)cdiv(NN / 2 + 1, B), (unsigned)(2 * w + 1), (unsigned)nb);
-    k<<<g, CP::THREADS, sm, s>>>(spec, P, w, Xw, Xw_stride, XL, tw);
+    if (tma_ok) {
+      using Y = fft::YWin<C, NN, B>;
+      auto k = fft::k_y_fwd_win_p<C, NN, B>;
+      const size_t sm = Y::smem(W);
+      PG_CUDA_TRY(set_smem(k, sm));
+      unsigned grid = 0;
+      PG_CUDA_TRY(fft::persistent_grid(k, Y::THREADS, sm, cdiv(NN / 2 + 1, B) * (int64_t)W * nb, &grid));
+      k<<<grid, Y::THREADS, sm, s>>>(mL, nb, w, Xw, Xw_stride, XL, tw, err);
+    } else {
+      using CP = fft::ColPass<C, NN, B>;
+      auto k = fft::k_y_fwd_win<C, NN, B>;
+      const size_t sm = CP::smem_bytes() + sizeof(C) * (size_t)W * B;   // + the compact slot
+      PG_CUDA_TRY(set_smem(k, sm));
+      dim3 g((unsigned)cdiv(NN / 2 + 1, B), (unsigned)W, (unsigned)nb);
+      k<<<g, CP::THREADS, sm, s>>>(spec, P, w, Xw, Xw_stride, XL, tw);
+    }
   });
   return launched();
 }

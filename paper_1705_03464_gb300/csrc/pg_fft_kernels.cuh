@@ -1371,6 +1371,100 @@ k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_
   }
 }
 
+// The same pass, persistent: a work item is (kx tile, zr, mesh b), kx tile
+// fastest; its W window rows come by one TMA box (the line spectra as a 2D
+// [line][kx] map) into one of two compact slots, so the next item's rows
+// stream in while the current one is transformed, and the twiddles are
+// staged once per CTA instead of once per item.
+template <typename C, int N, int B>
+struct YWin {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int THREADS = B * N1;
+  static constexpr int TILE = N * B;
+  static constexpr int E = sizeof(C) / 8;
+  // a compact slot of W rows of B values, rounded up to 128 bytes (TMA destination)
+  static __host__ __device__ int slot(int W) {
+    constexpr int e = 128 / (int)sizeof(C);
+    return (W * B + e - 1) / e * e;
+  }
+  static size_t smem(int W) { return sizeof(C) * (2 * (size_t)slot(W) + TILE + N) + 64; }
+};
+
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(YWin<C, N, B>::THREADS, 2)
+k_y_fwd_win_p(const __grid_constant__ CUtensorMap mL, int nb, int w, C* __restrict__ Xw, int64_t Xw_stride,
+              Lay XL, const C* __restrict__ tw, int* __restrict__ err) {
+  using Y = YWin<C, N, B>;
+  constexpr int N1 = Y::N1, N2 = Y::N2, TILE = Y::TILE, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
+  constexpr uint64_t kLimitNs = 2000000000ull;
+  const int W = 2 * w + 1, WS = Y::slot(W);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* const slot0 = reinterpret_cast<C*>(smem_raw);   // slots: slot0 + k * WS
+  C* const buf = slot0 + 2 * WS;
+  C* const tws = buf + TILE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);
+  const int T = (M1 + B - 1) / B;
+  const int n_items = T * W * nb;   // the launcher keeps this below 2^31
+  int item = blockIdx.x;
+  if (item >= n_items) return;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
+  const uint32_t slot_bytes = (uint32_t)(W * B * sizeof(C));
+  auto issue = [&](int k, int it) {
+    const int kxt = it % T, r = it / T;   // r = b W + zr: lines (r W + ry)
+    tma::mbar_arrive_expect_tx(&bar[k], slot_bytes);
+    tma::load_4d(slot0 + k * WS, &mL, &bar[k], kxt * B * Y::E, r * W, 0, 0);
+  };
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::fence_async_shared();
+    issue(0, item);
+  }
+  __syncthreads();
+  const int nz = win_nz<N>(w);
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  uint32_t ph[2] = {0, 0};
+  int failed = 0;
+  const int stride = (int)gridDim.x;
+  for (int job = 0; item < n_items; item += stride, ++job) {
+    const int cur = job & 1;
+    if (threadIdx.x == 0 && item < n_items - stride) {
+      tma::fence_async_shared();
+      issue(cur ^ 1, item + stride);
+    }
+    if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
+    ph[cur] ^= 1;
+    const int kx0 = (item % T) * B;
+    const int r = item / T;
+    const int zr = r % W, b = r / W;
+    const int ncol = min(B, M1 - kx0);
+    const C* xc = slot0 + cur * WS;
+    switch (nz) {
+      case 2: step1_win_p<C, N, B, XP, 2>(buf, xc, w, tws, threadIdx.x, blockDim.x); break;
+      case 4: step1_win_p<C, N, B, XP, 4>(buf, xc, w, tws, threadIdx.x, blockDim.x); break;
+      case 8: step1_win_p<C, N, B, XP, 8>(buf, xc, w, tws, threadIdx.x, blockDim.x); break;
+      default: step1_win<C, N, B, XP>(buf, xc, w, tws, threadIdx.x, blockDim.x);
+    }
+    __syncthreads();
+    C a[N2];
+    step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
+    if (c < ncol) {
+      C* out = Xw + (int64_t)b * Xw_stride + (int64_t)zr * XL.zs + xoff(XL, kx0) + c;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) out[yoff(XL, k1 + N1 * k2)] = a[k2];
+    }
+    __syncthreads();   // the tile and this slot are free again
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, tma::kErrTmaTimeout);
+      for (int k = 0; k < 2; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
+    }
+    __syncthreads();
+  }
+}
+
 template <typename C, int N, int B>
 struct ZAdj {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;

@@ -275,7 +275,7 @@ struct FftPasses {
   static bool adj_fits(int N, int w);
   // Y pass of the window lines (spec line (b*W + zr)*W + ry) into Xw.
   static cudaError_t y_fwd_win(int N, int nb, const C* spec, int P, int w, C* Xw,
-                               int64_t Xw_stride, Lay XL, const C* tw, cudaStream_t s);
+                               int64_t Xw_stride, Lay XL, const C* tw, int* err, cudaStream_t s);
   // Both sides of the adjoint z pass: A[kz][ky][kx] += sum_b F_b conj(X_b)
   // (F_b the z transform of S[b], [nb][N][N][P] contiguous; X_b that of
   // Xw[b] zero-padded), and Y_b = inverse z of X_b Fg (k = 0 zeroed) written
