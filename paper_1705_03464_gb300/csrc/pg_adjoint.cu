@@ -175,19 +175,6 @@ k_window_field(int N, int w, const int32_t* __restrict__ cell_bin, const uint8_t
   }
 }
 
-// A = 2 Re(X) F_g over the half spectrum (the galaxy auto-correlation term).
-template <typename C>
-__global__ void __launch_bounds__(kThreads)
-k_acc_gg(int64_t n, const C* __restrict__ X, const C* __restrict__ Fg, C* __restrict__ A) {
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-    const C x = X[i], g = Fg[i];
-    C o;
-    o.x = 2 * x.x * g.x;
-    o.y = 2 * x.x * g.y;
-    A[i] = o;
-  }
-}
-
 // Interpolation of a mesh adjoint held as compact real lines at points, with
 // the deposit's node weights (unrounded): g[k] = sum_nodes K * field(node).
 // Also the partial sums of w[k] * g[k] per block.
@@ -289,16 +276,6 @@ template cudaError_t launch_window_field<float>(int, int, const int32_t*, const 
 template cudaError_t launch_window_field<double>(int, int, const int32_t*, const uint8_t*, int, const double*,
                                                  const double*, const double*, const double*, double*,
                                                  cudaStream_t);
-
-template <typename R>
-cudaError_t launch_acc_gg(int64_t n, const typename CT<R>::C* X, const typename CT<R>::C* Fg,
-                          typename CT<R>::C* A, cudaStream_t s) {
-  const unsigned grid = (unsigned)std::min<int64_t>(cdiv(n, kThreads), 1 << 20);
-  k_acc_gg<typename CT<R>::C><<<grid, kThreads, 0, s>>>(n, X, Fg, A);
-  return launched();
-}
-template cudaError_t launch_acc_gg<float>(int64_t, const float2*, const float2*, float2*, cudaStream_t);
-template cudaError_t launch_acc_gg<double>(int64_t, const double2*, const double2*, double2*, cudaStream_t);
 
 template <typename R>
 cudaError_t launch_gather(const DepGeom& geo, int64_t n, const double* x, const double* y,

@@ -84,10 +84,10 @@ struct Workspace {
   // by a galaxy pass), which the backward of the last forward reuses
   uint64_t fg_seq = 0;
   DevBuf flags, lidx, seg_total, line_base, n_lines, stmp, line_y, line_bin, line_z, lines_q, qsum,
-      scale, spec, S, Fg, Wz, Wy, Cwin, tmpfft, Xs, As, Xw, wlines, cggw;
-  DevBuf* all_bufs[24] = {&flags, &lidx, &seg_total, &line_base, &n_lines, &stmp, &line_y, &line_bin,
+      scale, spec, S, Fg, Wz, Wy, Cwin, tmpfft, As, Xw, wlines, cggw;
+  DevBuf* all_bufs[23] = {&flags, &lidx, &seg_total, &line_base, &n_lines, &stmp, &line_y, &line_bin,
                           &line_z, &lines_q, &qsum, &scale, &spec, &S, &Fg, &Wz, &Wy, &Cwin,
-                          &tmpfft, &Xs, &As, &Xw, &wlines, &cggw};
+                          &tmpfft, &As, &Xw, &wlines, &cggw};
   Workspace() {
     for (DevBuf* b : all_bufs) b->acct = &total;
   }
@@ -107,7 +107,7 @@ struct pg_plan {
         line_base(wsp->line_base), n_lines(wsp->n_lines), stmp(wsp->stmp), line_y(wsp->line_y),
         line_bin(wsp->line_bin), lines_q(wsp->lines_q), qsum(wsp->qsum), scale(wsp->scale),
         spec(wsp->spec), S(wsp->S), Fg(wsp->Fg), Wz(wsp->Wz), Wy(wsp->Wy), Cwin(wsp->Cwin),
-        tmpfft(wsp->tmpfft), line_z(wsp->line_z), wlines(wsp->wlines), Xs(wsp->Xs), As(wsp->As),
+        tmpfft(wsp->tmpfft), line_z(wsp->line_z), wlines(wsp->wlines), As(wsp->As),
         Xw(wsp->Xw), cggw(wsp->cggw), cap_lines(wsp->cap_lines) {}
   std::shared_ptr<Workspace> wsp;
   pg_params prm;
@@ -137,10 +137,11 @@ struct pg_plan {
       &qsum, &scale;
   DevBuf &spec, &S, &Fg, &Wz, &Wy, &Cwin, &tmpfft;
   DevBuf sums_pg, sums_gg, pg_valid, bin_part;
-  // adjoint: line z, pair galaxy indices, window geometry, spectra X and A,
-  // galaxy-window correlation, scalar adjoints, upstream gradients, gathers
-  DevBuf &line_z, &wlines, &Xs, &As, &Xw, &cggw;
-  DevBuf psi, psj, cell_bin, cell_agg, wl_idx, wl_tot, wl_base, wl_y;
+  // adjoint: line z, window lines, spectrum A, compact window spectra,
+  // galaxy-window correlation, pair galaxy indices, window cell bins,
+  // scalar adjoints, upstream gradients, gathers
+  DevBuf &line_z, &wlines, &As, &Xw, &cggw;
+  DevBuf psi, psj, cell_bin, cell_agg;
   DevBuf adjb, gout, gp, gj, part;
   // HOD-parameter derivatives of the pair counts: bin offsets, sums, partials, outputs
   DevBuf hd;
@@ -782,11 +783,10 @@ pg_status forward_impl(pg_plan* p, int64_t n, const double* d_pos, const float* 
 namespace {
 
 // Plan-time geometry of the adjoint: for every window cell its (r, mu_r) bin
-// (-1 if none) and aggregate flag, and the W^2 window x-lines as a compact
-// line set (mesh order of (z, y)) that the y pass can read.
+// (-1 if none) and aggregate flag.
 cudaError_t build_window_geometry(pg_plan* p, const std::vector<int32_t>& cells) {
-  const int N = p->N, w = p->w, W = p->W;
-  const int64_t W3 = (int64_t)W * W * W, NN = (int64_t)N * N;
+  const int W = p->W;
+  const int64_t W3 = (int64_t)W * W * W;
   std::vector<int32_t> cb(W3, -1);
   std::vector<uint8_t> ca(W3, 0);
   for (int q = 0; q <= p->nQ; ++q)
@@ -794,47 +794,32 @@ cudaError_t build_window_geometry(pg_plan* p, const std::vector<int32_t>& cells)
       if (q < p->nQ) cb[cells[i]] = q;
       else ca[cells[i]] = 1;
     }
-  auto mesh_of_rank = [&](int r) { return r <= w ? r : r - W + N; };
-  std::vector<uint8_t> flag(NN, 0);
-  for (int rz = 0; rz < W; ++rz)
-    for (int ry = 0; ry < W; ++ry) flag[(int64_t)mesh_of_rank(rz) * N + mesh_of_rank(ry)] = 1;
-  std::vector<int32_t> idx(NN);
-  int32_t run = 0;
-  for (int64_t i = 0; i < NN; ++i) { idx[i] = run; run += flag[i]; }
-  std::vector<int32_t> ly(W * W);
-  for (int rz = 0; rz < W; ++rz)
-    for (int ry = 0; ry < W; ++ry) ly[rz * W + ry] = mesh_of_rank(ry);
-  const int64_t tot = (int64_t)W * W, zero = 0;
   size_t* t = &p->total;
   PG_CUDA_TRY(p->cell_bin.ensure(4 * W3, t));
   PG_CUDA_TRY(p->cell_agg.ensure(W3, t));
-  PG_CUDA_TRY(p->wl_idx.ensure(4 * NN, t));
-  PG_CUDA_TRY(p->wl_tot.ensure(8, t));
-  PG_CUDA_TRY(p->wl_base.ensure(8, t));
-  PG_CUDA_TRY(p->wl_y.ensure(4 * W * W, t));
   PG_CUDA_TRY(cudaMemcpy(p->cell_bin.p, cb.data(), 4 * W3, cudaMemcpyHostToDevice));
-  PG_CUDA_TRY(cudaMemcpy(p->cell_agg.p, ca.data(), W3, cudaMemcpyHostToDevice));
-  PG_CUDA_TRY(cudaMemcpy(p->wl_idx.p, idx.data(), 4 * NN, cudaMemcpyHostToDevice));
-  PG_CUDA_TRY(cudaMemcpy(p->wl_tot.p, &tot, 8, cudaMemcpyHostToDevice));
-  PG_CUDA_TRY(cudaMemcpy(p->wl_base.p, &zero, 8, cudaMemcpyHostToDevice));
-  return cudaMemcpy(p->wl_y.p, ly.data(), 4 * W * W, cudaMemcpyHostToDevice);
+  return cudaMemcpy(p->cell_agg.p, ca.data(), W3, cudaMemcpyHostToDevice);
 }
 
-// Spectrum X of one window adjoint field (pair mode: sbar of one mesh; gg
-// mode: gbar, g2bar and the galaxy correlation window).
+// The galaxy auto-correlation term of the adjoint, A = 2 Re(X) F_g, X the
+// spectrum of the gg window adjoint field (gbar, g2bar and the galaxy
+// correlation window): its W^2 window lines through the x pass, the window
+// y pass into the compact window spectra (mesh slot 0), and the pruned z
+// transform fused with the product with F_g.
 template <typename R>
-cudaError_t window_spectrum(pg_plan* p, const double* sbar, const double* gbar,
-                            const double* g2bar, cudaStream_t s) {
+cudaError_t galaxy_window_term(pg_plan* p, const double* gbar, const double* g2bar, int64_t Xw_stride,
+                               Lay XL, cudaStream_t s) {
   using C = typename CT<R>::C;
   const C* tw = p->tw.as<C>();
+  int* err = p->flag.as<int32_t>() + 1;
   const int64_t nl = (int64_t)p->W * p->W;
   PG_CUDA_TRY(launch_window_field<R>(p->N, p->w, p->cell_bin.as<int32_t>(), p->cell_agg.as<uint8_t>(),
-                                     p->nQ, sbar, gbar, g2bar, p->cggw.as<R>(), p->wlines.as<R>(), s));
+                                     p->nQ, nullptr, gbar, g2bar, p->cggw.as<R>(), p->wlines.as<R>(), s));
   PG_CUDA_TRY(FftPasses<R>::x_r2c_real(p->N, p->wlines.as<R>(), nl, p->spec.as<C>(), p->P, tw, s));
-  PG_CUDA_TRY(FftPasses<R>::y_fwd(p->N, 1, p->spec.as<C>(), p->P, p->wl_idx.as<int32_t>(),
-                                  p->wl_tot.as<int64_t>(), p->wl_base.as<int64_t>(),
-                                  p->wl_y.as<int32_t>(), p->Xs.as<C>(), 0, lay_plan<R>(p->N, p->P), tw, s));
-  return FftPasses<R>::z_fwd(p->N, p->Xs.as<C>(), p->P, lay_plan<R>(p->N, p->P), tw, p->flag.as<int32_t>() + 1, s);
+  PG_CUDA_TRY(FftPasses<R>::y_fwd_win(p->N, 1, p->spec.as<C>(), p->P, p->w, p->Xw.as<C>(), Xw_stride, XL,
+                                      tw, err, s));
+  return FftPasses<R>::zwin_acc(p->N, p->Xw.as<C>(), Xw_stride, XL, lay_plan<R>(p->N, p->P), p->P, p->w,
+                                p->Fg.as<C>(), p->As.as<C>(), tw, err, s);
 }
 
 // Reverse sweep of the last forward call (see pg_backward in pairgal.h).
@@ -863,7 +848,6 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   const Lay XL{(int64_t)8 * p->P, (int64_t)1 << txs, (int64_t)W * 8 * p->P, kYBlockShift,
                (int64_t)8 << txs, txs};
   PG_CUDA_TRY(ensure_lines(p, nbmax * W2));
-  PG_CUDA_TRY(p->Xs.ensure(sizeof(C) * spec_elems, t));
   PG_CUDA_TRY(p->As.ensure(sizeof(C) * spec_elems, t));
   PG_CUDA_TRY(p->Xw.ensure(sizeof(C) * Xw_stride * nbmax, t));
   PG_CUDA_TRY(p->cggw.ensure(sizeof(R) * W3, t));
@@ -939,10 +923,9 @@ cudaError_t backward_impl(pg_plan* p, const pg_result* gin, double* wbar, cudaSt
   }
   const double cs = (double)sizeof(C), rs = (double)sizeof(R), M1 = p->M1, Nd = N;
   {
-    // A = 2 Re(F[Cbar_gg]) F_g: dense y and z passes of the gg window field
-    ProfScope ps(p, PG_FAM_ADJ_GALAXY, s, 5.0 * NN * M1 * cs);
-    PG_CUDA_TRY(window_spectrum<R>(p, nullptr, Gbar, G2bar, s));
-    PG_CUDA_TRY(launch_acc_gg<R>(spec_elems, p->Xs.as<C>(), p->Fg.as<C>(), p->As.as<C>(), s));
+    // A = 2 Re(F[Cbar_gg]) F_g: F_g read, A written once
+    ProfScope ps(p, PG_FAM_ADJ_GALAXY, s, 2.0 * NN * M1 * cs);
+    PG_CUDA_TRY(galaxy_window_term<R>(p, Gbar, G2bar, Xw_stride, XL, s));
   }
   // the pair meshes in the forward's batches: S_b recomputed, the compact
   // window spectra X_b, A += F_b conj(X_b), Y_b = z-inverse of X_b F_g over
@@ -1438,8 +1421,7 @@ void pg_plan_destroy(pg_plan* p) {
                    &p->ctot, &p->dd, &p->ddq, &p->pcursor, &p->ubin, &p->ui, &p->uj, &p->umx,
                    &p->umy, &p->umz, &p->uwp, &p->pbin, &p->px, &p->py, &p->pz, &p->pw,
                    &p->bcursor, &p->sums_pg, &p->sums_gg, &p->pg_valid, &p->bin_part, &p->out, &p->psi,
-                   &p->psj, &p->cell_bin, &p->cell_agg, &p->wl_idx, &p->wl_tot, &p->wl_base,
-                   &p->wl_y, &p->adjb, &p->gout, &p->gp, &p->gj, &p->part, &p->Wk, &p->Gs,
+                   &p->psj, &p->cell_bin, &p->cell_agg, &p->adjb, &p->gout, &p->gp, &p->gj, &p->part, &p->Wk, &p->Gs,
                    &p->sm_off, &p->sm_sums, &p->sm_part, &p->sm_out, &p->sa_g, &p->sa_v, &p->sa_gp,
                    &p->sa_gj, &p->sa_fj, &p->sa_mesh, &p->sa_spec, &p->hd};
   for (DevBuf* b : all) b->release(&p->total);

@@ -391,6 +391,26 @@ cudaError_t FftPasses<R>::zadj(int N, int nb, C* S, int64_t S_stride, Lay L, con
 }
 
 template <typename R>
+cudaError_t FftPasses<R>::zwin_acc(int N, const C* Xw, int64_t Xw_stride, Lay XL, Lay L, int P, int w,
+                                   const C* Fg, C* A, const C* tw, int* err, cudaStream_t s) {
+  constexpr int B = fft::ZCols<R>::B;
+  const int W = 2 * w + 1;
+  CUtensorMap mX;
+  if (!err || W > 256 || W > N || !fft::adj_win_map<R>(&mX, Xw, N, P, W, 1, Xw_stride, XL))
+    return cudaErrorInvalidValue;
+  PG_DISPATCH_N(N, {
+    using Y = fft::YWin<C, NN, B>;
+    auto k = fft::k_zwin_acc<C, NN, B>;
+    const size_t sm = Y::smem(W);
+    PG_CUDA_TRY(set_smem(k, sm));
+    unsigned grid = 0;
+    PG_CUDA_TRY(fft::persistent_grid(k, Y::THREADS, sm, cdiv(NN / 2 + 1, B) * (int64_t)NN, &grid));
+    k<<<grid, Y::THREADS, sm, s>>>(mX, w, L, Fg, A, tw, err);
+  });
+  return launched();
+}
+
+template <typename R>
 cudaError_t FftPasses<R>::y_inv_lines(int N, int nb, const C* Y, int64_t Y_stride, Lay L, int P,
                                       const int32_t* idx, const int64_t* seg_total,
                                       const int64_t* line_base, const int32_t* line_y, C* hspec,

@@ -1684,6 +1684,102 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
   if (failed && tid == 0) atomicExch(err, tma::kErrTmaTimeout);
 }
 
+// The galaxy auto-correlation term of the adjoint: A = 2 Re(X) F_g, X the
+// z transform of one compact window spectrum (mesh 0 of the window map: the
+// y-transformed window field, W nonzero z rows per column), computed per work
+// item (ky, kx tile) from the W rows alone (pruned step 1) and combined with
+// the F_g column on the way out, so the dense spectrum X never exists.
+// Persistent; the W rows of the next item stream into the other compact slot
+// by TMA while the current item is transformed.
+template <typename C, int N, int B>
+__global__ void __launch_bounds__(YWin<C, N, B>::THREADS, 2)
+k_zwin_acc(const __grid_constant__ CUtensorMap mX, int w, Lay L, const C* __restrict__ Fg,
+           C* __restrict__ A, const C* __restrict__ tw, int* __restrict__ err) {
+  using Y = YWin<C, N, B>;
+  constexpr int N1 = Y::N1, N2 = Y::N2, TILE = Y::TILE, M1 = N / 2 + 1;
+  constexpr int XP = xperm<C, N, B>();
+  constexpr uint64_t kLimitNs = 2000000000ull;
+  const int W = 2 * w + 1, WS = Y::slot(W);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* const slot0 = reinterpret_cast<C*>(smem_raw);   // slots: slot0 + k * WS
+  C* const buf = slot0 + 2 * WS;
+  C* const tws = buf + TILE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);
+  const int T = (M1 + B - 1) / B;
+  const int n_items = T * N;
+  int item = blockIdx.x;
+  if (item >= n_items) return;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
+  const uint32_t slot_bytes = (uint32_t)(W * B * sizeof(C));
+  const uint64_t pol = tma::policy_evict_first();
+  auto issue = [&](int k, int it) {
+    int ky, kxt;
+    zcol_item(it, T, ky, kxt);
+    tma::mbar_arrive_expect_tx(&bar[k], slot_bytes);
+    za_issue_win<C, N, B>(slot0 + k * WS, &mX, &bar[k], kxt * B, ky, 0, pol);
+  };
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::fence_async_shared();
+    issue(0, item);
+  }
+  __syncthreads();
+  const int nz = win_nz<N>(w);
+  const int c = threadIdx.x % B, k1 = threadIdx.x / B;
+  uint32_t ph[2] = {0, 0};
+  int failed = 0;
+  const int stride = (int)gridDim.x;
+  for (int job = 0; item < n_items; item += stride, ++job) {
+    const int cur = job & 1;
+    if (threadIdx.x == 0 && item < n_items - stride) {
+      tma::fence_async_shared();
+      issue(cur ^ 1, item + stride);
+    }
+    if (__syncthreads_or(!tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
+    ph[cur] ^= 1;
+    int ky, kxt;
+    zcol_item(item, T, ky, kxt);
+    const int kx0 = kxt * B;
+    const int ncol = min(B, M1 - kx0);
+    const C* xc = slot0 + cur * WS;
+    switch (nz) {
+      case 2: step1_win_p<C, N, B, XP, 2>(buf, xc, w, tws, threadIdx.x, blockDim.x); break;
+      case 4: step1_win_p<C, N, B, XP, 4>(buf, xc, w, tws, threadIdx.x, blockDim.x); break;
+      case 8: step1_win_p<C, N, B, XP, 8>(buf, xc, w, tws, threadIdx.x, blockDim.x); break;
+      default: step1_win<C, N, B, XP>(buf, xc, w, tws, threadIdx.x, blockDim.x);
+    }
+    __syncthreads();
+    typename Real<C>::T r[N2];
+    {
+      C x[N2];
+      step2<C, N1, N2, false, XP>(buf, B, c, k1, x);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) r[k2] = 2 * x[k2].x;
+    }
+    if (c < ncol) {
+      const int64_t o = yoff(L, ky) + xoff(L, kx0) + c;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int64_t zo = o + (int64_t)(k1 + N1 * k2) * L.zs;
+        const C g = tma::ld_hint(Fg + zo, pol);
+        C v;
+        v.x = r[k2] * g.x;
+        v.y = r[k2] * g.y;
+        tma::st_hint(A + zo, v, pol);
+      }
+    }
+    __syncthreads();   // the tile and this slot are free again
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, tma::kErrTmaTimeout);
+      for (int k = 0; k < 2; ++k) tma::mbar_wait(&bar[k], ph[k], 100000000ull);
+    }
+    __syncthreads();
+  }
+}
+
 // Inverse y of Y_b on the z planes that hold lines of mesh b, stored only at
 // those lines: hspec[line][kx] for the compact lines of the batch (the
 // forward deposit's numbering: idx, seg_total, line_base, line_y). Work item

@@ -283,6 +283,12 @@ struct FftPasses {
   static cudaError_t zadj(int N, int nb, C* S, int64_t S_stride, Lay L, const C* Xw,
                           int64_t Xw_stride, Lay XL, const C* Fg, C* A, int w, int P, const C* tw,
                           int* err, cudaStream_t s);
+  // A = 2 Re(X) F_g over the half spectrum (layout L), X the z transform of
+  // the compact window spectra of mesh 0 of Xw (layout XL, zero outside the
+  // W window planes), taken from the W rows alone. Needs err (a bounded TMA
+  // wait that runs out sets it to PG_ERR_TIMEOUT's device code).
+  static cudaError_t zwin_acc(int N, const C* Xw, int64_t Xw_stride, Lay XL, Lay L, int P, int w,
+                              const C* Fg, C* A, const C* tw, int* err, cudaStream_t s);
   // Inverse y of Y[b] at the compact lines of the batch (numbering of the
   // forward deposit: idx, seg_total, line_base, line_y) into hspec[line][P].
   static cudaError_t y_inv_lines(int N, int nb, const C* Y, int64_t Y_stride, Lay L, int P,
@@ -456,9 +462,6 @@ template <typename R>
 cudaError_t launch_window_field(int N, int w, const int32_t* cell_bin, const uint8_t* cell_agg, int Q,
                                 const double* sbar, const double* gbar, const double* g2bar,
                                 const R* cgg, R* lines, cudaStream_t s);
-template <typename R>
-cudaError_t launch_acc_gg(int64_t n, const typename CT<R>::C* X, const typename CT<R>::C* Fg,
-                          typename CT<R>::C* A, cudaStream_t s);
 template <typename R>
 cudaError_t launch_gather(const DepGeom& geo, int64_t n, const double* x, const double* y,
                           const double* z, const double* wt, const int32_t* idx, const R* lines,
