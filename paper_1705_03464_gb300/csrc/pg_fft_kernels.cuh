@@ -457,6 +457,9 @@ __device__ __forceinline__ void zero_tile(C* buf, int rows) {
 // Sparse path (idx != null): the compact lines of plane z of mesh b are
 // line_base[b] + [idx_b[z][0], idx_b[z+1][0]) with y = line_y[line]; dense
 // path: line z*N + y of one mesh.
+// Two CTAs per SM: two tile buffers where both CTAs' pairs fit in shared
+// memory, else one (the next item's rows are then gathered into it once step
+// 2 has read it, in flight while the item's outputs are stored).
 template <typename C, int N, int B>
 struct YFwd {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
@@ -464,21 +467,24 @@ struct YFwd {
   static constexpr int TILE = N * B;
   static constexpr int RS = THREADS / B;   // rows gathered per round
   static constexpr int PRE = 4;            // rounds whose line numbers are loaded ahead
-  static constexpr size_t smem_bytes() { return sizeof(C) * (2 * (size_t)TILE + N); }
+  static constexpr int MINB = 2;
+  static constexpr int NBUF = 2 * sizeof(C) * (2 * (size_t)TILE + N) <= 220 * 1024 ? 2 : 1;
+  static constexpr size_t smem_bytes() { return sizeof(C) * (NBUF * (size_t)TILE + N); }
 };
 
 template <typename C, int N, int B>
-__global__ void __launch_bounds__(YFwd<C, N, B>::THREADS, 1)
+__global__ void __launch_bounds__(YFwd<C, N, B>::THREADS, YFwd<C, N, B>::MINB)
 k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__ idx,
           const int64_t* __restrict__ seg_total, const int64_t* __restrict__ line_base,
           const int32_t* __restrict__ line_y, C* __restrict__ S, int64_t S_stride, Lay L,
           const C* __restrict__ tw) {
   using Y = YFwd<C, N, B>;
   constexpr int N1 = Y::N1, N2 = Y::N2, TILE = Y::TILE, M1 = N / 2 + 1, RS = Y::RS, PRE = Y::PRE;
+  constexpr int NBUF = Y::NBUF;
   constexpr int XP = xperm<C, N, B>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* const tws = reinterpret_cast<C*>(smem_raw);
-  C* const buf0 = tws + N;   // buffers buf0 + k * TILE
+  C* const buf0 = tws + N;   // buffers buf0 + k * TILE, k < NBUF
   const int T = (M1 + B - 1) / B;
   const int64_t n_items = (int64_t)T * N * nb;
   int64_t item = blockIdx.x;
@@ -486,7 +492,7 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
   C zc;
   zc.x = 0; zc.y = 0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
-  for (int i = threadIdx.x; i < 2 * TILE; i += blockDim.x) buf0[i] = zc;
+  for (int i = threadIdx.x; i < NBUF * TILE; i += blockDim.x) buf0[i] = zc;
   const int c = threadIdx.x % B, slot = threadIdx.x / B;
   struct Item {
     int kx0, z, b;
@@ -559,7 +565,7 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
   if (nitem < n_items) meta(nitem, nxt);
   bool pend = false;
   for (int64_t job = 0; item < n_items; ++job) {
-    C* buf = buf0 + (job & 1) * TILE;
+    C* buf = buf0 + (NBUF == 2 ? (int)(job & 1) : 0) * TILE;
     tma::cp_async_wait_all();
     __syncthreads();   // this item's rows have landed; the other buffer is clear
     if (pend) resolve(pn, nxt);
@@ -578,11 +584,15 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
     if (pend) fetch(nnitem, pn);
     step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
     __syncthreads();
-    if (nitem < n_items) gather(nxt, buf0 + ((job & 1) ^ 1) * TILE, yv, true);
+    if (NBUF == 2 && nitem < n_items) gather(nxt, buf0 + ((job & 1) ^ 1) * TILE, yv, true);
     C a[N2];
     step2<C, N1, N2, false, XP>(buf, B, c, slot, a);
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) buf[prow<XP>(slot, j2, N2) * B + c] = zc;
+    if (NBUF == 1) {
+      __syncthreads();   // the tile is read and clear
+      if (nitem < n_items) gather(nxt, buf, yv, true);
+    }
     if (c < min(B, M1 - cur.kx0)) {
       C* out = S + (int64_t)cur.b * S_stride + (int64_t)cur.z * L.zs + xoff(L, cur.kx0) + c;
 #pragma unroll
@@ -1568,7 +1578,6 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
        Lay L, const C* __restrict__ Fg, C* __restrict__ A, const C* __restrict__ tw,
        int* __restrict__ err) {
   using Z = ZAdj<C, N, B>;
-  const int nz = win_nz<N>(w);
   constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1, CT = Z::CTHREADS;
   constexpr int XP = xperm<C, N, B>();
   constexpr uint64_t kLimitNs = 2000000000ull;
@@ -1634,12 +1643,10 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
       C a[N2];
       step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
       tma::bar_sync(1, CT);
-      switch (nz) {   // the window column's inputs, pruned to its nonzero rows
-        case 2: step1_win_p<C, N, B, XP, 2>(buf, xb0 + cur * WS, w, tws, tid, CT); break;
-        case 4: step1_win_p<C, N, B, XP, 4>(buf, xb0 + cur * WS, w, tws, tid, CT); break;
-        case 8: step1_win_p<C, N, B, XP, 8>(buf, xb0 + cur * WS, w, tws, tid, CT); break;
-        default: step1_win<C, N, B, XP>(buf, xb0 + cur * WS, w, tws, tid, CT);
-      }
+      // the window column's step 1 (its rows from the compact slot); the
+      // pruned form (step1_win_p) needs more registers than this loop has
+      // left and measured slower here
+      step1_win<C, N, B, XP>(buf, xb0 + cur * WS, w, tws, tid, CT);
       tma::bar_sync(1, CT);
       C x[N2];
       step2<C, N1, N2, false, XP>(buf, B, c, k1, x);
