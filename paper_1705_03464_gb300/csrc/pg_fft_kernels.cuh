@@ -1516,28 +1516,55 @@ __device__ __forceinline__ void za_issue_win(C* dst, const CUtensorMap* map, uin
                     (ky >> kYBlockShift) + b * (N >> kYBlockShift), policy);
 }
 
-// The load side of the adjoint z pass, run by one thread of the load
-// warpgroup (barriers as in k_zadj). Per item the order is: first mesh's slot,
-// A tile, remaining meshes' slots. Returns 0, or 1 when a wait for a free
+// Full z column (N rows) from shared memory back to a spectrum array, same
+// tensor map and coordinates as za_issue_col.
+template <typename C, int N, int B>
+__device__ __forceinline__ void za_store_col(const C* src, const CUtensorMap* map, int kx0, int ky, int b,
+                                             uint64_t policy) {
+  using Z = ZAdj<C, N, B>;
+#pragma unroll
+  for (int z0 = 0; z0 < N; z0 += Z::ZB)
+    tma::store_5d_hint(map, src + z0 * B, 0, ky & ((1 << kYBlockShift) - 1), kx0 / B, z0,
+                       (ky >> kYBlockShift) + b * (N >> kYBlockShift), policy);
+}
+
+// The load and store side of the adjoint z pass, run by one thread of the
+// load warpgroup (barriers as in k_zadj). Per item the order is: first mesh's
+// slot, A tile, remaining meshes' slots. Before a slot is refilled, the
+// output column the transform warps left in it (Y_b of the job two back) is
+// stored over that job's S column. Returns 0, or 1 when a wait for a full
 // buffer ran out; copies issued are waited for (bounded) before it returns.
 template <typename C, int N, int B>
 __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CUtensorMap* mA, C* sb0,
                           C* at, C* xb0, int WS, int W, uint64_t* bar, int nb, int64_t n_items, int T,
                           uint64_t limit_ns) {
   using Z = ZAdj<C, N, B>;
-  // S, the window columns and A pass through once: evict first
+  // S, the window columns, A and the outputs pass through once: evict first
   const uint64_t pol = tma::policy_evict_first();
   const uint32_t slot_bytes = Z::TILE_BYTES + (uint32_t)(W * B * sizeof(C));
   uint32_t issued[3] = {0, 0, 0};
+  int pkx[2] = {0, 0}, pky[2] = {0, 0}, pb[2] = {0, 0};   // the job each slot holds
   int64_t job = 0;
   int failed = 0;
+  // the output of job j (in slot j & 1) back to global memory
+  auto put = [&](int64_t j) {
+    const int k = (int)(j & 1);
+    if (!tma::mbar_wait(&bar[3 + k], (uint32_t)(j >> 1) & 1, limit_ns)) return false;
+    za_store_col<C, N, B>(sb0 + k * Z::TILE, mS, pkx[k], pky[k], pb[k], pol);
+    tma::bulk_commit();
+    return true;
+  };
   auto slot = [&](int kx0, int ky, int b) {
     const int k = (int)(job & 1);
-    if (job >= 2 && !tma::mbar_wait(&bar[3 + k], (uint32_t)((job >> 1) - 1) & 1, limit_ns)) return false;
+    if (job >= 2) {
+      if (!put(job - 2)) return false;
+      tma::bulk_wait_read_all();   // the slot's output has left shared memory
+    }
     tma::fence_async_shared();
     tma::mbar_arrive_expect_tx(&bar[k], slot_bytes);
     za_issue_col<C, N, B>(sb0 + k * Z::TILE, mS, &bar[k], kx0, ky, b, pol);
     za_issue_win<C, N, B>(xb0 + k * WS, mX, &bar[k], kx0, ky, b, pol);
+    pkx[k] = kx0; pky[k] = ky; pb[k] = b;
     ++issued[k];
     ++job;
     return true;
@@ -1557,6 +1584,10 @@ __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CU
     for (int j = 1; j < nb; ++j)
       if (!slot(kx0, ky, nb - 1 - j)) { failed = 1; break; }
   }
+  // the last two jobs' outputs
+  for (int64_t j = job >= 2 ? job - 2 : 0; j < job && !failed; ++j)
+    if (!put(j)) failed = 1;
+  tma::bulk_wait_all();
   for (int k = 0; k < 3; ++k)
     if (issued[k]) tma::mbar_wait(&bar[k], (issued[k] - 1) & 1, failed ? 100000000ull : limit_ns);
   return failed;
@@ -1566,18 +1597,19 @@ __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CU
 // item (ky, kx tile): F_b = z transform of S_b, X_b = z transform of the
 // zero-padded window column; A += F_b conj(X_b) accumulates in shared memory
 // over the batch (A read and written once per item); then Y_b = inverse z of
-// X_b F_g (k = 0 set to zero), written over S_b's column, which this CTA has
-// already read. Persistent and TMA fed; mesh b's S and window tiles share one
-// of two slots so the next mesh streams in during the transforms, issued by a
-// load warpgroup (za_produce) while the transform warpgroups compute. F_g is
-// read from global memory (L2: its tile is reused by every mesh of the item).
+// X_b F_g (k = 0 set to zero), left in the slot and stored by TMA over S_b's
+// column, which this CTA has already read. Persistent and TMA fed; mesh b's S
+// and window tiles share one of two slots so the next mesh streams in during
+// the transforms, issued (and the outputs stored) by a load warpgroup
+// (za_produce) while the transform warpgroups compute. F_g's column is read
+// once per item into registers.
 template <typename C, int N, int B>
 __global__ void __launch_bounds__(ZAdj<C, N, B>::THREADS, 1)
 k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mX,
-       const __grid_constant__ CUtensorMap mA, int nb, int w, C* __restrict__ S, int64_t S_stride,
-       Lay L, const C* __restrict__ Fg, C* __restrict__ A, const C* __restrict__ tw,
-       int* __restrict__ err) {
+       const __grid_constant__ CUtensorMap mA, int nb, int w, Lay L, const C* __restrict__ Fg,
+       C* __restrict__ A, const C* __restrict__ tw, int* __restrict__ err) {
   using Z = ZAdj<C, N, B>;
+  static_assert(B * Split<N>::N2 <= Z::CTHREADS, "one step-B task per transform thread");
   constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1, CT = Z::CTHREADS;
   constexpr int XP = xperm<C, N, B>();
   constexpr uint64_t kLimitNs = 2000000000ull;
@@ -1664,19 +1696,23 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
       if (dc_col && k1 == 0) { x[0].x = 0; x[0].y = 0; }   // k = 0 mode
       stepA_own<C, N1, N2, true, XP>(buf, B, c, k1, x, tws, 1);
       tma::bar_sync(1, CT);
-      C* yout = S + (int64_t)b * S_stride + yoff(L, ky) + xoff(L, kx0);
-      for (int t = tid; t < B * N2; t += CT) {
-        const int cc = t % B, n2 = t / B;
+      {
+        // Y_b's column into the slot in natural row order for the TMA store
+        // (za_produce). A lane's output rows n2 + N2 n1 were read in step B
+        // by lanes whose n2 differs in the bits below X, all in its warp.
+        const int cc = tid % B, n2 = tid / B;
+        const bool act = tid < B * N2;
         C v[N1];
-        stepB_own<C, N1, N2, true, XP>(buf, B, cc, n2, v);
-        if (cc < ncol) {
+        if (act) stepB_own<C, N1, N2, true, XP>(buf, B, cc, n2, v);
+        __syncwarp();
+        if (act) {
 #pragma unroll
-          for (int n1 = 0; n1 < N1; ++n1)
-            tma::st_hint(yout + (int64_t)(n2 + N2 * n1) * L.zs + cc, v[n1], pol_stream);
+          for (int n1 = 0; n1 < N1; ++n1) buf[(n2 + N2 * n1) * B + cc] = v[n1];
         }
+        tma::fence_async_shared();
       }
       tma::bar_sync(1, CT);
-      if (tid == 0) tma::mbar_arrive(&bar[3 + cur]);   // slot free for the next load
+      if (tid == 0) tma::mbar_arrive(&bar[3 + cur]);   // output column ready for the store
     }
     if (failed) break;
     // the item's A column back to global memory; then the tile is free

@@ -110,6 +110,27 @@ __device__ __forceinline__ void load_5d_hint(void* dst, const CUtensorMap* map, 
       : "memory");
 }
 
+// 5D tiled store shared -> global, completion tracked by the issuing
+// thread's bulk async groups, with an L2 cache policy. The shared source must
+// be 128-byte aligned (else nothing is stored) and written before the store
+// by threads that then ran fence_async_shared; every coordinate is >= 0.
+__device__ __forceinline__ void store_5d_hint(const CUtensorMap* map, const void* src, int c0, int c1, int c2,
+                                              int c3, int c4, uint64_t policy) {
+  if (smem_addr(src) & 127u) return;
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group.L2::cache_hint"
+      " [%0, {%1, %2, %3, %4, %5}], [%6], %7;" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(src)), "l"(policy)
+      : "memory");
+}
+// Closes the bulk async group of the stores issued so far by this thread.
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until every committed bulk store of this thread has read its shared
+// source (the buffer may then be overwritten).
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Waits until every committed bulk store of this thread is complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // L2 eviction policies for cache-hinted accesses (createpolicy): streamed
 // data that is read or written once is marked evict-first, data that the
 // same CTA re-reads soon is marked evict-last.
