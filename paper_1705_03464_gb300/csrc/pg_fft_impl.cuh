@@ -385,7 +385,7 @@ cudaError_t FftPasses<R>::zadj(int N, int nb, C* S, int64_t S_stride, Lay L, con
     PG_CUDA_TRY(fft::check_reg_split<typename Z::Regs>(k));
     unsigned grid = 0;
     PG_CUDA_TRY(fft::persistent_grid(k, Z::THREADS, sm, cdiv(NN / 2 + 1, B) * (int64_t)NN, &grid));
-    k<<<grid, Z::THREADS, sm, s>>>(mS, mX, mA, nb, w, L, Fg, A, tw, err);
+    k<<<grid, Z::THREADS, sm, s>>>(mS, mX, mA, nb, w, L, Fg, tw, err);
   });
   return launched();
 }

@@ -1532,8 +1532,9 @@ __device__ __forceinline__ void za_store_col(const C* src, const CUtensorMap* ma
 // load warpgroup (barriers as in k_zadj). Per item the order is: first mesh's
 // slot, A tile, remaining meshes' slots. Before a slot is refilled, the
 // output column the transform warps left in it (Y_b of the job two back) is
-// stored over that job's S column. Returns 0, or 1 when a wait for a full
-// buffer ran out; copies issued are waited for (bounded) before it returns.
+// stored over that job's S column; before the A tile is refilled, the
+// previous item's A column is stored. Returns 0, or 1 when a wait ran out;
+// copies issued are waited for (bounded) before it returns.
 template <typename C, int N, int B>
 __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CUtensorMap* mA, C* sb0,
                           C* at, C* xb0, int WS, int W, uint64_t* bar, int nb, int64_t n_items, int T,
@@ -1569,6 +1570,14 @@ __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CU
     ++job;
     return true;
   };
+  // the A column of item number i (tile complete in shared memory) back
+  int akx = 0, aky = 0;
+  auto put_a = [&](int64_t i) {
+    if (!tma::mbar_wait(&bar[5], (uint32_t)i & 1, limit_ns)) return false;
+    za_store_col<C, N, B>(at, mA, akx, aky, 0, pol);
+    tma::bulk_commit();
+    return true;
+  };
   int64_t i = 0;
   for (int64_t item = blockIdx.x; item < n_items && !failed; item += gridDim.x, ++i) {
     int ky, kxt;
@@ -1576,17 +1585,22 @@ __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CU
     const int kx0 = kxt * B;
     // meshes in descending order (see k_zadj)
     if (nb > 0 && !slot(kx0, ky, nb - 1)) { failed = 1; break; }
-    if (i > 0 && !tma::mbar_wait(&bar[5], (uint32_t)(i - 1) & 1, limit_ns)) { failed = 1; break; }
+    if (i > 0) {
+      if (!put_a(i - 1)) { failed = 1; break; }
+      tma::bulk_wait_read_all();   // the previous item's A has left shared memory
+    }
     tma::fence_async_shared();
     tma::mbar_arrive_expect_tx(&bar[2], Z::TILE_BYTES);
     za_issue_col<C, N, B>(at, mA, &bar[2], kx0, ky, 0, pol);
+    akx = kx0; aky = ky;
     ++issued[2];
     for (int j = 1; j < nb; ++j)
       if (!slot(kx0, ky, nb - 1 - j)) { failed = 1; break; }
   }
-  // the last two jobs' outputs
+  // the last two jobs' outputs and the last item's A column
   for (int64_t j = job >= 2 ? job - 2 : 0; j < job && !failed; ++j)
     if (!put(j)) failed = 1;
+  if (i > 0 && !failed && !put_a(i - 1)) failed = 1;
   tma::bulk_wait_all();
   for (int k = 0; k < 3; ++k)
     if (issued[k]) tma::mbar_wait(&bar[k], (issued[k] - 1) & 1, failed ? 100000000ull : limit_ns);
@@ -1607,7 +1621,7 @@ template <typename C, int N, int B>
 __global__ void __launch_bounds__(ZAdj<C, N, B>::THREADS, 1)
 k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mX,
        const __grid_constant__ CUtensorMap mA, int nb, int w, Lay L, const C* __restrict__ Fg,
-       C* __restrict__ A, const C* __restrict__ tw, int* __restrict__ err) {
+       const C* __restrict__ tw, int* __restrict__ err) {
   using Z = ZAdj<C, N, B>;
   static_assert(B * Split<N>::N2 <= Z::CTHREADS, "one step-B task per transform thread");
   constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1, CT = Z::CTHREADS;
@@ -1620,7 +1634,8 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
   const int WS = Z::win_slot(W);
   C* const xb0 = at + TILE;                         // compact window slots: xb0 + k * WS
   C* const tws = xb0 + 2 * WS;
-  // [0], [1]: slot k loaded; [2]: A tile loaded; [3], [4]: slot k free; [5]: A tile free
+  // [0], [1]: slot k loaded; [2]: A tile loaded; [3], [4]: slot k's output
+  // ready (one arrival per transform warp); [5]: A tile complete (the same)
   uint64_t* bar = reinterpret_cast<uint64_t*>(tws + N);
   const int T = (M1 + B - 1) / B;
   const int64_t n_items = (int64_t)T * N;
@@ -1629,7 +1644,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
   const int tid = threadIdx.x;
   for (int i = tid; i < N; i += blockDim.x) tws[i] = tw[i];
   if (tid == 0) {
-    for (int k = 0; k < 6; ++k) tma::mbar_init(&bar[k], 1);
+    for (int k = 0; k < 6; ++k) tma::mbar_init(&bar[k], k < 3 ? 1u : (uint32_t)(CT / 32));
     tma::fence_async_shared();
   }
   __syncthreads();
@@ -1640,7 +1655,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
     return;
   }
   // the item's F_g column is re-read for every mesh of the batch: evict last
-  const uint64_t pol_stream = tma::policy_evict_first(), pol_keep = tma::policy_evict_last();
+  const uint64_t pol_keep = tma::policy_evict_last();
   const int c = tid % B, k1 = tid / B;
   uint32_t ph[3] = {0, 0, 0};
   int64_t job = 0;
@@ -1711,18 +1726,17 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
         }
         tma::fence_async_shared();
       }
-      tma::bar_sync(1, CT);
-      if (tid == 0) tma::mbar_arrive(&bar[3 + cur]);   // output column ready for the store
+      // each warp marks its part of the output column ready for the store
+      // (the next barrier is the next mesh's or item's wait)
+      __syncwarp();
+      if ((tid & 31) == 0) tma::mbar_arrive(&bar[3 + cur]);
     }
     if (failed) break;
-    // the item's A column back to global memory; then the tile is free
-    C* ag = A + yoff(L, ky) + xoff(L, kx0);
-    for (int t = tid; t < TILE; t += CT) {
-      const int z = t / B, cc = t % B;
-      tma::st_hint(ag + (int64_t)z * L.zs + cc, at[t], pol_stream);
-    }
-    tma::bar_sync(1, CT);
-    if (tid == 0) tma::mbar_arrive(&bar[5]);
+    // the item's A column (updated at each task's own positions) is complete:
+    // the load thread stores it before the tile is refilled
+    tma::fence_async_shared();
+    __syncwarp();
+    if ((tid & 31) == 0) tma::mbar_arrive(&bar[5]);
   }
   if (failed && tid == 0) atomicExch(err, tma::kErrTmaTimeout);
 }
