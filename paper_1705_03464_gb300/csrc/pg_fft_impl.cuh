@@ -164,13 +164,26 @@ cudaError_t FftPasses<R>::y_fwd(int N, int nb, const C* spec, int P, const int32
                                 const C* tw, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   constexpr int B = fft::Cols<R>::B;
+  static_assert(fft::Cols<R>::B == fft::ZCols<R>::B, "one tile width for the spectra maps");
+  // TMA stores where the output is the plan's tiled layout with meshes back to back
+  CUtensorMap mO;
+  const bool ts = S_stride == (int64_t)N * N * P && spec != S &&
+                  fft::spec_map<R>(&mO, S, N, P, L, nb, 1, N < 256 ? (uint32_t)N : 256u);
+  if (!ts) memset(&mO, 0, sizeof(mO));
   PG_DISPATCH_N(N, {
-    using Y = fft::YFwd<C, NN, B>;
-    auto k = fft::k_y_fwd_p<C, NN, B>;
-    PG_CUDA_TRY(set_smem(k, Y::smem_bytes()));
-    unsigned grid = 0;
-    PG_CUDA_TRY(fft::persistent_grid(k, Y::THREADS, Y::smem_bytes(), cdiv(NN / 2 + 1, B) * (int64_t)NN * nb, &grid));
-    k<<<grid, Y::THREADS, Y::smem_bytes(), s>>>(spec, P, nb, idx, seg_total, line_base, line_y, S, S_stride, L, tw);
+    auto run = [&](auto tsc) -> cudaError_t {
+      constexpr bool TS = decltype(tsc)::value;
+      using Y = fft::YFwd<C, NN, B, TS>;
+      auto k = fft::k_y_fwd_p<C, NN, B, TS>;
+      PG_CUDA_TRY(set_smem(k, Y::smem_bytes()));
+      unsigned grid = 0;
+      PG_CUDA_TRY(fft::persistent_grid(k, Y::THREADS, Y::smem_bytes(), cdiv(NN / 2 + 1, B) * (int64_t)NN * nb, &grid));
+      k<<<grid, Y::THREADS, Y::smem_bytes(), s>>>(mO, spec, P, nb, idx, seg_total, line_base, line_y, S, S_stride,
+                                                  L, tw);
+      return launched();
+    };
+    if (ts) PG_CUDA_TRY(run(std::true_type{}));
+    else PG_CUDA_TRY(run(std::false_type{}));
   });
   return launched();
 }

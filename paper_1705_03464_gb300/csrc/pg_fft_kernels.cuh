@@ -457,34 +457,43 @@ __device__ __forceinline__ void zero_tile(C* buf, int rows) {
 // Sparse path (idx != null): the compact lines of plane z of mesh b are
 // line_base[b] + [idx_b[z][0], idx_b[z+1][0]) with y = line_y[line]; dense
 // path: line z*N + y of one mesh.
-// Two CTAs per SM: two tile buffers where both CTAs' pairs fit in shared
-// memory, else one (the next item's rows are then gathered into it once step
-// 2 has read it, in flight while the item's outputs are stored).
-template <typename C, int N, int B>
+// Output (TS, the plan's tiled layout): the item's column goes to a staging
+// tile in natural ky order and thread 0 writes it with TMA tensor stores
+// (map mO: the spectra map with boxes of YB ky rows of one z) at the next
+// item's first barrier, and waits for the store to leave shared memory
+// before its second, so the transform threads issue no global stores.
+// Otherwise each thread stores its outputs directly.
+// Buffers: with TS, two gather tiles and the staging tile (two CTAs per SM
+// where that fits); without, two tiles where two CTAs' pairs fit, else one
+// (the next item's rows are then gathered into it once step 2 has read it).
+template <typename C, int N, int B, bool TS>
 struct YFwd {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   static constexpr int THREADS = B * N1;
   static constexpr int TILE = N * B;
   static constexpr int RS = THREADS / B;   // rows gathered per round
   static constexpr int PRE = 4;            // rounds whose line numbers are loaded ahead
-  static constexpr int MINB = 2;
-  static constexpr int NBUF = 2 * sizeof(C) * (2 * (size_t)TILE + N) <= 220 * 1024 ? 2 : 1;
-  static constexpr size_t smem_bytes() { return sizeof(C) * (NBUF * (size_t)TILE + N); }
+  static constexpr int YB = N < 256 ? N : 256;   // ky rows per store box
+  static constexpr int NBUF = TS || 2 * sizeof(C) * (2 * (size_t)TILE + N) <= 220 * 1024 ? 2 : 1;
+  static constexpr size_t SMEM = sizeof(C) * ((NBUF + (TS ? 1 : 0)) * (size_t)TILE + N);
+  static constexpr int MINB = 2 * SMEM <= 220 * 1024 || !TS ? 2 : 1;
+  static constexpr size_t smem_bytes() { return SMEM; }
 };
 
-template <typename C, int N, int B>
-__global__ void __launch_bounds__(YFwd<C, N, B>::THREADS, YFwd<C, N, B>::MINB)
-k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__ idx,
-          const int64_t* __restrict__ seg_total, const int64_t* __restrict__ line_base,
-          const int32_t* __restrict__ line_y, C* __restrict__ S, int64_t S_stride, Lay L,
-          const C* __restrict__ tw) {
-  using Y = YFwd<C, N, B>;
+template <typename C, int N, int B, bool TS>
+__global__ void __launch_bounds__(YFwd<C, N, B, TS>::THREADS, YFwd<C, N, B, TS>::MINB)
+k_y_fwd_p(const __grid_constant__ CUtensorMap mO, const C* __restrict__ spec, int P, int nb,
+          const int32_t* __restrict__ idx, const int64_t* __restrict__ seg_total,
+          const int64_t* __restrict__ line_base, const int32_t* __restrict__ line_y, C* __restrict__ S,
+          int64_t S_stride, Lay L, const C* __restrict__ tw) {
+  using Y = YFwd<C, N, B, TS>;
   constexpr int N1 = Y::N1, N2 = Y::N2, TILE = Y::TILE, M1 = N / 2 + 1, RS = Y::RS, PRE = Y::PRE;
   constexpr int NBUF = Y::NBUF;
   constexpr int XP = xperm<C, N, B>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* const tws = reinterpret_cast<C*>(smem_raw);
   C* const buf0 = tws + N;   // buffers buf0 + k * TILE, k < NBUF
+  C* const stg = buf0 + NBUF * TILE;   // staging tile (TS)
   const int T = (M1 + B - 1) / B;
   const int64_t n_items = (int64_t)T * N * nb;
   int64_t item = blockIdx.x;
@@ -564,10 +573,22 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
   int64_t nitem = item + gridDim.x;
   if (nitem < n_items) meta(nitem, nxt);
   bool pend = false;
+  // TS: the column in the staging tile (item kx0, z, mesh b), if any
+  bool staged = false;
+  int skx = 0, sz = 0, sb = 0;
+  const uint64_t pol_out = tma::policy_evict_first();
+  auto put = [&]() {
+#pragma unroll
+    for (int y0 = 0; y0 < N; y0 += Y::YB)
+      tma::store_5d_hint(&mO, stg + y0 * B, 0, 0, skx / B, sz, (y0 >> kYBlockShift) + sb * (N >> kYBlockShift),
+                         pol_out);
+    tma::bulk_commit();
+  };
   for (int64_t job = 0; item < n_items; ++job) {
     C* buf = buf0 + (NBUF == 2 ? (int)(job & 1) : 0) * TILE;
     tma::cp_async_wait_all();
-    __syncthreads();   // this item's rows have landed; the other buffer is clear
+    __syncthreads();   // this item's rows have landed; the other buffer is clear; [TS] staging written
+    if (TS && staged && threadIdx.x == 0) put();
     if (pend) resolve(pn, nxt);
     const int64_t nnitem = nitem + gridDim.x;
     int yv[PRE];
@@ -583,6 +604,7 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
     pend = nitem < n_items && nnitem < n_items;
     if (pend) fetch(nnitem, pn);
     step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
+    if (TS && staged && threadIdx.x == 0) tma::bulk_wait_read_all();   // staging free again
     __syncthreads();
     if (NBUF == 2 && nitem < n_items) gather(nxt, buf0 + ((job & 1) ^ 1) * TILE, yv, true);
     C a[N2];
@@ -593,7 +615,15 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
       __syncthreads();   // the tile is read and clear
       if (nitem < n_items) gather(nxt, buf, yv, true);
     }
-    if (c < min(B, M1 - cur.kx0)) {
+    if constexpr (TS) {
+      // columns past the half spectrum (kx >= M1, the last tile's padding) get zeros
+      const bool in = c < min(B, M1 - cur.kx0);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) stg[(slot + N1 * k2) * B + c] = in ? a[k2] : zc;
+      tma::fence_async_shared();
+      staged = true;
+      skx = cur.kx0; sz = cur.z; sb = cur.b;
+    } else if (c < min(B, M1 - cur.kx0)) {
       C* out = S + (int64_t)cur.b * S_stride + (int64_t)cur.z * L.zs + xoff(L, cur.kx0) + c;
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) tma::st_hint(out + yoff(L, slot + N1 * k2), a[k2], tma::policy_evict_first());
@@ -601,6 +631,13 @@ k_y_fwd_p(const C* __restrict__ spec, int P, int nb, const int32_t* __restrict__
     item = nitem;
     cur = nxt;
     nitem = nnitem;
+  }
+  if (TS && staged) {
+    __syncthreads();   // the last column is in the staging tile
+    if (threadIdx.x == 0) {
+      put();
+      tma::bulk_wait_all();
+    }
   }
 }
 
@@ -881,8 +918,9 @@ __device__ __forceinline__ void zc_issue(C* dst, const CUtensorMap* map, uint64_
 
 // The load side of the fused z pass, run by one thread of the load
 // warpgroup. Barriers: bar[0], bar[1] mesh buffer k loaded; bar[2] galaxy
-// tile loaded; bar[3], bar[4] mesh buffer k free again; bar[5] galaxy tile
-// free again (an arrival from every transform thread).
+// tile loaded; bar[3], bar[4] mesh buffer k free again (an arrival from every
+// transform warp); bar[5] galaxy tile free again (an arrival from every
+// transform thread).
 // Per item the order is: first mesh, galaxy tile, remaining meshes, so the
 // first mesh of an item streams in while the previous item's last mesh is
 // still being transformed. Returns 0, or 1 when a wait for a free buffer ran
@@ -944,7 +982,8 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
   const int tid = threadIdx.x;
   for (int i = tid; i < N; i += blockDim.x) tws[i] = tw[i];
   if (tid == 0) {
-    for (int k = 0; k < 5; ++k) tma::mbar_init(&bar[k], 1);
+    for (int k = 0; k < 3; ++k) tma::mbar_init(&bar[k], 1);
+    for (int k = 3; k < 5; ++k) tma::mbar_init(&bar[k], CT / 32);   // one arrival per transform warp
     tma::mbar_init(&bar[5], CT);   // every transform thread reports its last read of the galaxy tile
     tma::fence_async_shared();
   }
@@ -1019,8 +1058,11 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
           }
         }
       }
-      tma::bar_sync(1, CT);
-      if (!gg && tid == 0) tma::mbar_arrive(&bar[3 + cur]);   // mesh buffer free for the next load
+      // each warp frees the mesh buffer once its own reads are done; the next
+      // barrier is the next mesh's or item's wait (which also orders the
+      // galaxy-only mode's reuse of its single buffer)
+      __syncwarp();
+      if (!gg && (tid & 31) == 0) tma::mbar_arrive(&bar[3 + cur]);
     }
   }
   if (failed && tid == 0) atomicExch(err, tma::kErrTmaTimeout);

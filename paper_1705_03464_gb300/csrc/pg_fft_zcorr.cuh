@@ -28,7 +28,8 @@ static cudaError_t z_corr_launch(const typename CT<R>::C* S, const typename CT<R
   PG_CUDA_TRY(check_reg_split<typename Z::Regs>(k));
   unsigned grid = 0;
   PG_CUDA_TRY(persistent_grid(k, Z::THREADS, Z::smem_bytes(), cdiv(N / 2 + 1, B) * (int64_t)N, &grid));
-  k<<<grid, Z::THREADS, Z::smem_bytes(), s>>>(mS, mF, nb, gg ? 1 : 0, w, Wz, Wz_stride, P, tw, err);
+  // the galaxy-only mode is one pass over one buffer (the kernel relies on nb = 1 there)
+  k<<<grid, Z::THREADS, Z::smem_bytes(), s>>>(mS, mF, gg ? 1 : nb, gg ? 1 : 0, w, Wz, Wz_stride, P, tw, err);
   return cudaSuccess;
 }
 
