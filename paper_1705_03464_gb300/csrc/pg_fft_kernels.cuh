@@ -916,6 +916,17 @@ __device__ __forceinline__ void zc_issue(C* dst, const CUtensorMap* map, uint64_
                       (ky >> kYBlockShift) + b * (N >> kYBlockShift), pol);
 }
 
+// The same column prefetched into L2 (issued one mesh ahead of its load, so
+// that the load into shared memory finds it there).
+template <typename C, int N, int B>
+__device__ __forceinline__ void zc_prefetch(const CUtensorMap* map, int kx0, int ky, int b) {
+  using Z = ZCorr<C, N, B>;
+  constexpr int KM = (1 << kYBlockShift) - 1;
+#pragma unroll
+  for (int z0 = 0; z0 < N; z0 += Z::ZB)
+    tma::prefetch_5d(map, 0, ky & KM, kx0 / B, z0, (ky >> kYBlockShift) + b * (N >> kYBlockShift));
+}
+
 // The load side of the fused z pass, run by one thread of the load
 // warpgroup. Barriers: bar[0], bar[1] mesh buffer k loaded; bar[2] galaxy
 // tile loaded; bar[3], bar[4] mesh buffer k free again (an arrival from every
@@ -941,18 +952,33 @@ __device__ int zc_produce(const CUtensorMap* mS, const CUtensorMap* mF, C* sbuf0
     ++job;
     return true;
   };
+  // the mesh column after the one just issued (the next item's first mesh
+  // after an item's last) and the next item's galaxy column go to L2 early
+  auto ahead = [&](int64_t item, int kx0, int ky, int b) {
+    if (b + 1 < nb) {
+      zc_prefetch<C, N, B>(mS, kx0, ky, b + 1);
+    } else if (item + gridDim.x < n_items) {
+      int ky2, kxt2;
+      zcol_item(item + gridDim.x, T, ky2, kxt2);
+      zc_prefetch<C, N, B>(mS, kxt2 * B, ky2, 0);
+      zc_prefetch<C, N, B>(mF, kxt2 * B, ky2, 0);
+    }
+  };
   int64_t i = 0;
   for (int64_t item = blockIdx.x; item < n_items && !failed; item += gridDim.x, ++i) {
     int ky, kxt;
     zcol_item(item, T, ky, kxt);
     const int kx0 = kxt * B;
     if (!gg && !mesh(kx0, ky, 0)) { failed = 1; break; }
+    if (!gg) ahead(item, kx0, ky, 0);
     if (i > 0 && !tma::mbar_wait(&bar[5], (uint32_t)(i - 1) & 1, limit_ns)) { failed = 1; break; }
     tma::fence_async_shared();
     zc_issue<C, N, B>(ftile, mF, &bar[2], kx0, ky, 0);
     ++issued[2];
-    for (int b = 1; b < nb && !gg; ++b)
+    for (int b = 1; b < nb && !gg; ++b) {
       if (!mesh(kx0, ky, b)) { failed = 1; break; }
+      ahead(item, kx0, ky, b);
+    }
   }
   // every copy issued has landed before the CTA may exit
   for (int k = 0; k < 3; ++k)
@@ -1558,6 +1584,16 @@ __device__ __forceinline__ void za_issue_win(C* dst, const CUtensorMap* map, uin
                     (ky >> kYBlockShift) + b * (N >> kYBlockShift), policy);
 }
 
+// The same column prefetched into L2.
+template <typename C, int N, int B>
+__device__ __forceinline__ void za_prefetch_col(const CUtensorMap* map, int kx0, int ky, int b) {
+  using Z = ZAdj<C, N, B>;
+#pragma unroll
+  for (int z0 = 0; z0 < N; z0 += Z::ZB)
+    tma::prefetch_5d(map, 0, ky & ((1 << kYBlockShift) - 1), kx0 / B, z0,
+                     (ky >> kYBlockShift) + b * (N >> kYBlockShift));
+}
+
 // Full z column (N rows) from shared memory back to a spectrum array, same
 // tensor map and coordinates as za_issue_col.
 template <typename C, int N, int B>
@@ -1587,7 +1623,7 @@ __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CU
   const uint32_t slot_bytes = Z::TILE_BYTES + (uint32_t)(W * B * sizeof(C));
   uint32_t issued[3] = {0, 0, 0};
   int pkx[2] = {0, 0}, pky[2] = {0, 0}, pb[2] = {0, 0};   // the job each slot holds
-  int64_t job = 0;
+  int64_t job = 0, cur_item = 0;
   int failed = 0;
   // the output of job j (in slot j & 1) back to global memory
   auto put = [&](int64_t j) {
@@ -1607,6 +1643,16 @@ __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CU
     tma::mbar_arrive_expect_tx(&bar[k], slot_bytes);
     za_issue_col<C, N, B>(sb0 + k * Z::TILE, mS, &bar[k], kx0, ky, b, pol);
     za_issue_win<C, N, B>(xb0 + k * WS, mX, &bar[k], kx0, ky, b, pol);
+    // the next job's S column to L2 (meshes descend within an item; after an
+    // item's mesh 0 comes the next item's mesh nb - 1, with its A column)
+    if (b > 0) {
+      za_prefetch_col<C, N, B>(mS, kx0, ky, b - 1);
+    } else if (cur_item + gridDim.x < n_items) {
+      int ky2, kxt2;
+      zcol_item(cur_item + gridDim.x, T, ky2, kxt2);
+      za_prefetch_col<C, N, B>(mS, kxt2 * B, ky2, nb - 1);
+      za_prefetch_col<C, N, B>(mA, kxt2 * B, ky2, 0);
+    }
     pkx[k] = kx0; pky[k] = ky; pb[k] = b;
     ++issued[k];
     ++job;
@@ -1625,6 +1671,7 @@ __device__ int za_produce(const CUtensorMap* mS, const CUtensorMap* mX, const CU
     int ky, kxt;
     zcol_item(item, T, ky, kxt);
     const int kx0 = kxt * B;
+    cur_item = item;
     // meshes in descending order (see k_zadj)
     if (nb > 0 && !slot(kx0, ky, nb - 1)) { failed = 1; break; }
     if (i > 0) {

@@ -131,6 +131,15 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 // Waits until every committed bulk store of this thread is complete.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// 5D tiled prefetch of a box from global memory into L2 (no shared memory,
+// no completion to wait for): a later load of the same box finds it in L2.
+__device__ __forceinline__ void prefetch_5d(const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4) {
+  asm volatile("cp.async.bulk.prefetch.tensor.5d.L2.global.tile [%0, {%1, %2, %3, %4, %5}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+               : "memory");
+}
+
 // L2 eviction policies for cache-hinted accesses (createpolicy): streamed
 // data that is read or written once is marked evict-first, data that the
 // same CTA re-reads soon is marked evict-last.
