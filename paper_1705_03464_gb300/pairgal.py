@@ -671,7 +671,7 @@ def _host(a, dtype):
     return None if a is None else np.ascontiguousarray(a, dtype=dtype)
 
 
-def pg_run_batch(problems, catalogues, stream=None, n_streams=1):
+def pg_run_batch(problems, catalogues, stream=None, n_streams=1, _streams_entry=False):
     """Many mocks through the forward path: problems[i] a Problem (or Plan),
     catalogues[i] = (pos [n,3] float64, vel [n,3] float32 or None, w [n]
     float32 or None), host arrays. n_streams = 1: pg_run_batch (one stream,
@@ -698,7 +698,7 @@ def pg_run_batch(problems, catalogues, stream=None, n_streams=1):
         m.out = C.addressof(res)
     lat = np.full(max(n, 1), np.nan)
     st = pg_batch_stats()
-    if n_streams == 1:
+    if n_streams == 1 and not _streams_entry:
         _check(_lib.pg_run_batch(C.addressof(mocks), n, lat.ctypes.data, C.byref(st), _stream(stream)),
                "pg_run_batch")
     else:
@@ -706,6 +706,13 @@ def pg_run_batch(problems, catalogues, stream=None, n_streams=1):
                                          _stream(stream)), "pg_run_batch_streams")
     stats = {k: getattr(st, k) for k, _ in pg_batch_stats._fields_}
     return [pr.shape_result(a) for pr, a in zip(problems, results)], lat[:n], stats
+
+
+def pg_run_batch_streams(problems, catalogues, n_streams=2, stream=None):
+    """pg_run_batch_streams: the batch through n_streams runner threads, each
+    on its own stream, claiming mocks from one work queue (same returns as
+    pg_run_batch; the outputs are bit-identical to it)."""
+    return pg_run_batch(problems, catalogues, stream=stream, n_streams=int(n_streams), _streams_entry=True)
 
 
 def pg_autotune(problem, pos, vel=None, w=None, candidates=(4, 8, 16, 32), stream=None):
