@@ -319,6 +319,13 @@ bool FftPasses<R>::adj_fits(int N, int w) {
   return need <= (size_t)optin;
 }
 
+namespace fft {
+// Tensor map of compact window spectra (defined below with its layout).
+template <typename R>
+static bool adj_win_map(CUtensorMap* m, const void* base, int N, int P, int W, int nb, int64_t stride, Lay XL,
+                        uint32_t by = 0);
+}  // namespace fft
+
 template <typename R>
 cudaError_t FftPasses<R>::y_fwd_win(int N, int nb, const C* spec, int P, int w, C* Xw,
                                     int64_t Xw_stride, Lay XL, const C* tw, int* err, cudaStream_t s) {
@@ -331,9 +338,12 @@ cudaError_t FftPasses<R>::y_fwd_win(int N, int nb, const C* spec, int P, int w, 
   const uint64_t dims[4] = {(uint64_t)P * E, n_lines, 1u, 1u};
   const uint64_t strides[3] = {(uint64_t)P * 8 * E, n_lines * P * 8 * E, n_lines * P * 8 * E};
   const uint32_t box[4] = {(uint32_t)(B * E), (uint32_t)W, 1u, 1u};
-  CUtensorMap mL;
+  CUtensorMap mL, mO;
   const bool tma_ok = err && W <= 256 && (P * 8 * E) % 16 == 0 &&
                       (int64_t)cdiv(N / 2 + 1, B) * W * nb < INT32_MAX && encode_map_4d(&mL, spec, dims, strides, box);
+  // outputs by TMA store where the compact layout has its tensor map
+  const bool ts = tma_ok && fft::adj_win_map<R>(&mO, Xw, N, P, W, nb, Xw_stride, XL, N < 256 ? (uint32_t)N : 256u);
+  if (!ts) memset(&mO, 0, sizeof(mO));
   PG_DISPATCH_N(N, {
     if (tma_ok) {
       using Y = fft::YWin<C, NN, B>;
@@ -342,7 +352,7 @@ cudaError_t FftPasses<R>::y_fwd_win(int N, int nb, const C* spec, int P, int w, 
       PG_CUDA_TRY(set_smem(k, sm));
       unsigned grid = 0;
       PG_CUDA_TRY(fft::persistent_grid(k, Y::THREADS, sm, cdiv(NN / 2 + 1, B) * (int64_t)W * nb, &grid));
-      k<<<grid, Y::THREADS, sm, s>>>(mL, nb, w, Xw, Xw_stride, XL, tw, err);
+      k<<<grid, Y::THREADS, sm, s>>>(mL, mO, ts ? 1 : 0, nb, w, Xw, Xw_stride, XL, tw, err);
     } else {
       using CP = fft::ColPass<C, NN, B>;
       auto k = fft::k_y_fwd_win<C, NN, B>;
@@ -358,10 +368,11 @@ cudaError_t FftPasses<R>::y_fwd_win(int N, int nb, const C* spec, int P, int w, 
 namespace fft {
 // Tensor map of compact window spectra Xw in layout XL, [ky / 8][zr][kx / B]
 // [ky % 8][kx % B] per mesh: dimensions (kx mod B, ky mod 8, kx / B, zr,
-// ky / 8 + mesh N / 8), box (one kx tile, one ky, all W rows zr).
+// ky / 8 + mesh N / 8), box (one kx tile, one ky, all W rows zr), or with
+// by > 0 (one kx tile, by ky rows, one zr).
 template <typename R>
 static bool adj_win_map(CUtensorMap* m, const void* base, int N, int P, int W, int nb, int64_t stride,
-                        Lay XL) {
+                        Lay XL, uint32_t by) {
   using C = typename CT<R>::C;
   constexpr int B = ZCols<R>::B, E = (int)(sizeof(C) / 8);
   const int K = 1 << kYBlockShift;
@@ -372,7 +383,10 @@ static bool adj_win_map(CUtensorMap* m, const void* base, int N, int P, int W, i
                             (uint64_t)(N / K) * nb};
   const uint64_t strides[4] = {(uint64_t)XL.ys * 8 * E, (uint64_t)XL.ts * 8 * E, (uint64_t)XL.zs * 8 * E,
                                (uint64_t)XL.hs * 8 * E};
-  const uint32_t box[5] = {(uint32_t)(B * E), 1u, 1u, (uint32_t)W, 1u};
+  if (by > 0 && (by % K != 0 || by > 256)) return false;
+  // box: one kx tile and all W rows zr of one ky, or (by > 0) by ky rows of one zr
+  const uint32_t box[5] = {(uint32_t)(B * E), by > 0 ? (uint32_t)K : 1u, 1u, by > 0 ? 1u : (uint32_t)W,
+                           by > 0 ? by / (uint32_t)K : 1u};
   return encode_map_5d(m, base, dims, strides, box);
 }
 }  // namespace fft

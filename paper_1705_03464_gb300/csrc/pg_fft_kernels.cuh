@@ -1453,13 +1453,16 @@ k_y_fwd_win(const C* __restrict__ spec, int P, int w, C* __restrict__ Xw, int64_
 // fastest; its W window rows come by one TMA box (the line spectra as a 2D
 // [line][kx] map) into one of two compact slots, so the next item's rows
 // stream in while the current one is transformed, and the twiddles are
-// staged once per CTA instead of once per item.
+// staged once per CTA instead of once per item. With ts, the item's output
+// column goes back into the tile in natural ky order and thread 0 writes it
+// with TMA stores (map mO: boxes of YB ky rows of one zr plane).
 template <typename C, int N, int B>
 struct YWin {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   static constexpr int THREADS = B * N1;
   static constexpr int TILE = N * B;
   static constexpr int E = sizeof(C) / 8;
+  static constexpr int YB = N < 256 ? N : 256;   // ky rows per store box
   // a compact slot of W rows of B values, rounded up to 128 bytes (TMA destination)
   static __host__ __device__ int slot(int W) {
     constexpr int e = 128 / (int)sizeof(C);
@@ -1470,8 +1473,8 @@ struct YWin {
 
 template <typename C, int N, int B>
 __global__ void __launch_bounds__(YWin<C, N, B>::THREADS, 2)
-k_y_fwd_win_p(const __grid_constant__ CUtensorMap mL, int nb, int w, C* __restrict__ Xw, int64_t Xw_stride,
-              Lay XL, const C* __restrict__ tw, int* __restrict__ err) {
+k_y_fwd_win_p(const __grid_constant__ CUtensorMap mL, const __grid_constant__ CUtensorMap mO, int ts, int nb, int w,
+              C* __restrict__ Xw, int64_t Xw_stride, Lay XL, const C* __restrict__ tw, int* __restrict__ err) {
   using Y = YWin<C, N, B>;
   constexpr int N1 = Y::N1, N2 = Y::N2, TILE = Y::TILE, M1 = N / 2 + 1;
   constexpr int XP = xperm<C, N, B>();
@@ -1500,6 +1503,7 @@ k_y_fwd_win_p(const __grid_constant__ CUtensorMap mL, int nb, int w, C* __restri
     issue(0, item);
   }
   __syncthreads();
+  const uint64_t pol_out = tma::policy_evict_first();
   const int nz = win_nz<N>(w);
   const int c = threadIdx.x % B, k1 = threadIdx.x / B;
   uint32_t ph[2] = {0, 0};
@@ -1527,13 +1531,37 @@ k_y_fwd_win_p(const __grid_constant__ CUtensorMap mL, int nb, int w, C* __restri
     __syncthreads();
     C a[N2];
     step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
-    if (c < ncol) {
-      C* out = Xw + (int64_t)b * Xw_stride + (int64_t)zr * XL.zs + xoff(XL, kx0) + c;
+    if (ts) {
+      __syncthreads();   // every task has read its step-2 rows
+      // the column in natural ky order; past the half spectrum (the last
+      // tile's padding columns) zeros
+      const bool in = c < ncol;
 #pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) out[yoff(XL, k1 + N1 * k2)] = a[k2];
+      for (int k2 = 0; k2 < N2; ++k2) {
+        C v = a[k2];
+        if (!in) { v.x = 0; v.y = 0; }
+        buf[(k1 + N1 * k2) * B + c] = v;
+      }
+      tma::fence_async_shared();
+      __syncthreads();   // the column is written; this slot is free again
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int y0 = 0; y0 < N; y0 += Y::YB)
+          tma::store_5d_hint(&mO, buf + y0 * B, 0, 0, kx0 / B, zr, (y0 >> kYBlockShift) + b * (N >> kYBlockShift),
+                             pol_out);
+        tma::bulk_commit();
+        tma::bulk_wait_read_all();   // the tile may be overwritten after the next barrier
+      }
+    } else {
+      if (c < ncol) {
+        C* out = Xw + (int64_t)b * Xw_stride + (int64_t)zr * XL.zs + xoff(XL, kx0) + c;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) out[yoff(XL, k1 + N1 * k2)] = a[k2];
+      }
+      __syncthreads();   // the tile and this slot are free again
     }
-    __syncthreads();   // the tile and this slot are free again
   }
+  if (ts && threadIdx.x == 0) tma::bulk_wait_all();
   if (failed) {
     if (threadIdx.x == 0) {
       atomicExch(err, tma::kErrTmaTimeout);
