@@ -219,13 +219,23 @@ cudaError_t FftPasses<R>::y_inv_win(int N, int nb, const C* Wz, int64_t Wz_strid
   const uint32_t box[4] = {(uint32_t)(B * E), N < 256 ? (uint32_t)N : 256u, 1u, 1u};
   CUtensorMap mW;
   if (!encode_map_4d(&mW, Wz, dims, strides, box)) return cudaErrorInvalidValue;
+  // outputs y = k1 + N1 k2 with |y| <= w need k2 < K or k2 >= N2 - K, K = floor(w / N1) + 1
+  const int kreq = w / (N < 32 ? N : 32) + 1;
   PG_DISPATCH_N(N, {
-    using Y = fft::YInv<C, NN, B>;
-    auto k = fft::k_y_inv_tma<C, NN, B>;
-    PG_CUDA_TRY(set_smem(k, Y::smem_bytes()));
-    unsigned grid = 0;
-    PG_CUDA_TRY(fft::persistent_grid(k, Y::THREADS, Y::smem_bytes(), cdiv(NN / 2 + 1, B) * (int64_t)W * nb, &grid));
-    k<<<grid, Y::THREADS, Y::smem_bytes(), s>>>(mW, nb, w, Wy, Wy_stride, P, tw, err);
+    auto run = [&](auto kc) -> cudaError_t {
+      constexpr int K = decltype(kc)::value;
+      using Y = fft::YInv<C, NN, B>;
+      auto k = fft::k_y_inv_tma<C, NN, B, K>;
+      PG_CUDA_TRY(set_smem(k, Y::smem_bytes()));
+      unsigned grid = 0;
+      PG_CUDA_TRY(fft::persistent_grid(k, Y::THREADS, Y::smem_bytes(), cdiv(NN / 2 + 1, B) * (int64_t)W * nb, &grid));
+      k<<<grid, Y::THREADS, Y::smem_bytes(), s>>>(mW, nb, w, Wy, Wy_stride, P, tw, err);
+      return launched();
+    };
+    if (kreq <= 2) PG_CUDA_TRY(run(std::integral_constant<int, 2>{}));
+    else if (kreq <= 4) PG_CUDA_TRY(run(std::integral_constant<int, 4>{}));
+    else if (kreq <= 8) PG_CUDA_TRY(run(std::integral_constant<int, 8>{}));
+    else PG_CUDA_TRY(run(std::integral_constant<int, 32>{}));
   });
   return launched();
 }

@@ -234,12 +234,13 @@ __device__ __forceinline__ void step1(C* buf, int LD, const C* tw, int tws) {
   step1<C, N1, N2, B, INV, X>(buf, LD, tw, tws, (int)threadIdx.x, (int)blockDim.x);
 }
 
-// Step 2: task (c, k1) reads its N2 values and leaves X[k1 + N1*k2] in a[k2].
-template <typename C, int N1, int N2, bool INV, int X = 1>
+// Step 2: task (c, k1) reads its N2 values and leaves X[k1 + N1*k2] in a[k2];
+// with K < N2 / 2 only k2 < K and k2 >= N2 - K are computed (see reg_dft).
+template <typename C, int N1, int N2, bool INV, int X = 1, int K = N2>
 __device__ __forceinline__ void step2(const C* buf, int LD, int c, int k1, C (&a)[N2]) {
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) a[j2] = buf[prow<X>(k1, j2, N2) * LD + c];
-  reg_dft<C, N2, INV>(a);
+  reg_dft<C, N2, INV, K>(a);
 }
 
 // Step A (inverse split from registers): a[k2] = X[k1 + N1*k2] of task
@@ -1099,7 +1100,9 @@ k_z_corr_tma(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUt
 // (mesh b, window row zw, tile of B kx columns); its column over ky is
 // Wz[b][zw][0..N)[kx0..kx0+B). Items alternate between two shared buffers so
 // the next column streams in while the current one is transformed; only the
-// |y| <= w outputs are stored, to Wy[b][zw][yw][kx].
+// |y| <= w outputs are stored, to Wy[b][zw][yw][kx]. Those rows y = k1 + N1 k2
+// have k2 < K or k2 >= N2 - K for K > w / N1, so step 2 computes only those
+// outputs (K is dispatched from w; K >= N2 / 2 computes all).
 // ============================================================================
 template <typename C, int N, int B>
 struct YInv {
@@ -1123,7 +1126,7 @@ __device__ __forceinline__ void yi_issue(C* dst, const CUtensorMap* map, uint64_
   for (int y0 = 0; y0 < N; y0 += Y::YB) tma::load_4d(dst + y0 * B, map, bar, kx0 * Y::E, y0, zw, b);
 }
 
-template <typename C, int N, int B>
+template <typename C, int N, int B, int K>
 __global__ void __launch_bounds__(YInv<C, N, B>::THREADS, YInv<C, N, B>::MINB)
 k_y_inv_tma(const __grid_constant__ CUtensorMap mW, int nb, int w, C* __restrict__ Wy,
             int64_t Wy_stride, int P, const C* __restrict__ tw, int* __restrict__ err) {
@@ -1176,7 +1179,7 @@ k_y_inv_tma(const __grid_constant__ CUtensorMap mW, int nb, int w, C* __restrict
     step1<C, N1, N2, B, true, XP>(buf, B, tws, 1);
     __syncthreads();
     C a[N2];
-    step2<C, N1, N2, true, XP>(buf, B, c, k1, a);
+    step2<C, N1, N2, true, XP, K>(buf, B, c, k1, a);
     if (c < ncol) {
       C* out = Wy + (int64_t)b * Wy_stride + (int64_t)zw * W * P + kx0 + c;
 #pragma unroll
@@ -1796,8 +1799,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
     ph[2] ^= 1;
     // meshes in descending order: with the batches also taken last first, A
     // accumulates the pair meshes in descending bin order for any batching
-    for (int j = 0; j < nb; ++j, ++job) {
-      const int b = nb - 1 - j;
+    for (int j = 0; j < nb; ++j, ++job) {   // mesh nb - 1 - j (the load thread's order)
       const int cur = (int)(job & 1);
       C* buf = sb0 + cur * TILE;
       if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
