@@ -96,11 +96,47 @@ __host__ __device__ __forceinline__ double fmadd(double a, double b, double c) {
 // are needed. A general twiddle costs four fused multiply-adds for u + t and
 // two more for u - t = 2u - (u + t): six instructions instead of the eight of
 // a complex product followed by a sum and a difference.
-template <int J, bool INV, bool TOP, bool BOT, typename C>
+//
+// With PK, on sm_100 and later, FP32 butterflies use the packed two-wide FP32
+// arithmetic (__fadd2_rn, __ffma2_rn), which rounds each component exactly as
+// the scalar operation: a twiddle of +-1 takes two packed operations instead
+// of four, a general twiddle three packed fused multiply-adds (each component
+// in the scalar form's order, so the results are bit-identical) instead of six.
+// The operand swaps and paired constants cost registers, so only the kernels
+// where it measured faster ask for it.
+template <int J, bool INV, bool TOP, bool BOT, bool PK, typename C>
 __host__ __device__ __forceinline__ void bfly(C& u, C& v) {
   using T = typename Real<C>::T;
   constexpr int j = J & 31;
   constexpr bool triv = j == 0 || j == 8 || j == 16 || j == 24;
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  if constexpr (PK && sizeof(T) == 4) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    if constexpr (j == 0 || j == 16) {
+      // u + v and u - v (j = 16 swaps them)
+      const float2 s = __fadd2_rn(u, v), d = __ffma2_rn(v, m1, u);
+      if constexpr (TOP) u = j == 0 ? s : d;
+      if constexpr (BOT) v = j == 0 ? d : s;
+      return;
+    } else if constexpr (!triv) {
+      float2 w = w32<float2>(j);
+      if (INV) w.y = -w.y;
+      const float2 vs = make_float2(v.y, v.x);
+      if constexpr (TOP) {
+        // (fma(w.x, v.x, fma(-w.y, v.y, u.x)), fma(w.x, v.y, fma(w.y, v.x, u.y)))
+        const float2 in = __ffma2_rn(make_float2(-w.y, w.y), vs, u);
+        const float2 x = __ffma2_rn(make_float2(w.x, w.x), v, in);
+        if constexpr (BOT) v = __ffma2_rn(make_float2(2.f, 2.f), u, make_float2(-x.x, -x.y));
+        u = x;
+      } else if constexpr (BOT) {
+        // (fma(-w.x, v.x, fma(w.y, v.y, u.x)), fma(-w.x, v.y, fma(-w.y, v.x, u.y)))
+        const float2 in = __ffma2_rn(make_float2(w.y, -w.y), vs, u);
+        v = __ffma2_rn(make_float2(-w.x, -w.x), v, in);
+      }
+      return;
+    }
+  }
+#endif
   if constexpr (triv) {
     const C t = tw32_mul<j, INV>(v);
     const C x = cadd(u, t), y = csub(u, t);
@@ -125,7 +161,7 @@ __host__ __device__ __forceinline__ void bfly(C& u, C& v) {
 // needs, within each group of LEN, exactly its outputs k < K and k >= LEN - K
 // (the same rule one stage down), so unneeded halves of butterflies are
 // dropped at compile time. Unwanted outputs are left undefined.
-template <typename C, int RL, bool INV, int LEN, int K>
+template <typename C, int RL, bool INV, int LEN, int K, bool PK = false>
 __host__ __device__ __forceinline__ void dft_stage(C (&a)[RL]) {
   if constexpr (LEN <= RL) {
     constexpr int half = LEN / 2;
@@ -136,17 +172,17 @@ __host__ __device__ __forceinline__ void dft_stage(C (&a)[RL]) {
         constexpr bool all = 2 * K >= LEN;
         constexpr bool top = all || k < K;
         constexpr bool bot = all || k + half >= LEN - K;
-        if constexpr (top || bot) bfly<k * (32 / LEN), INV, top, bot>(a[i + k], a[i + k + half]);
+        if constexpr (top || bot) bfly<k * (32 / LEN), INV, top, bot, PK>(a[i + k], a[i + k + half]);
       });
     });
-    dft_stage<C, RL, INV, LEN * 2, K>(a);
+    dft_stage<C, RL, INV, LEN * 2, K, PK>(a);
   }
 }
 
 // In-register DFT of length RL (1..32), forward (exp(-i...)) or inverse:
 // bit-reversal permutation, then radix-2 decimation-in-time stages. With
 // K < RL / 2 only the outputs k < K and k >= RL - K are computed.
-template <typename C, int RL, bool INV, int K = RL>
+template <typename C, int RL, bool INV, int K = RL, bool PK = false>
 __host__ __device__ __forceinline__ void reg_dft(C (&a)[RL]) {
   if constexpr (RL > 1) {
     constexpr int bits = clog2(RL);
@@ -155,7 +191,7 @@ __host__ __device__ __forceinline__ void reg_dft(C (&a)[RL]) {
       const int j = cbitrev(i, bits);
       if (j > i) { C t = a[i]; a[i] = a[j]; a[j] = t; }
     }
-    dft_stage<C, RL, INV, 2, K>(a);
+    dft_stage<C, RL, INV, 2, K, PK>(a);
   }
 }
 
@@ -210,7 +246,7 @@ __device__ __forceinline__ int prow(int hi, int lo, int span) { return hi * span
 // warp barrier between its reads and writes makes it safe in place.
 // tid / nthr: this thread's index in, and the size of, the (warp-aligned)
 // group of threads sharing the tile.
-template <typename C, int N1, int N2, int B, bool INV, int X = 1>
+template <typename C, int N1, int N2, int B, bool INV, int X = 1, bool PK = false>
 __device__ __forceinline__ void step1(C* buf, int LD, const C* tw, int tws, int tid, int nthr) {
   static_assert(X == 1 || (B * X <= 32 && N2 % X == 0 && (B * N2) % 32 == 0), "row permutation");
   for (int t = tid; t < B * N2; t += nthr) {
@@ -218,7 +254,7 @@ __device__ __forceinline__ void step1(C* buf, int LD, const C* tw, int tws, int 
     C a[N1];
 #pragma unroll
     for (int j1 = 0; j1 < N1; ++j1) a[j1] = buf[(N2 * j1 + j2) * LD + c];
-    reg_dft<C, N1, INV>(a);
+    reg_dft<C, N1, INV, N1, PK>(a);
     if (N2 > 1 && j2 > 0) {
 #pragma unroll
       for (int k1 = 1; k1 < N1; ++k1) a[k1] = cmul(a[k1], twid<C, INV>(tw, j2 * k1 * tws));
@@ -229,18 +265,18 @@ __device__ __forceinline__ void step1(C* buf, int LD, const C* tw, int tws, int 
   }
 }
 
-template <typename C, int N1, int N2, int B, bool INV, int X = 1>
+template <typename C, int N1, int N2, int B, bool INV, int X = 1, bool PK = false>
 __device__ __forceinline__ void step1(C* buf, int LD, const C* tw, int tws) {
-  step1<C, N1, N2, B, INV, X>(buf, LD, tw, tws, (int)threadIdx.x, (int)blockDim.x);
+  step1<C, N1, N2, B, INV, X, PK>(buf, LD, tw, tws, (int)threadIdx.x, (int)blockDim.x);
 }
 
 // Step 2: task (c, k1) reads its N2 values and leaves X[k1 + N1*k2] in a[k2];
 // with K < N2 / 2 only k2 < K and k2 >= N2 - K are computed (see reg_dft).
-template <typename C, int N1, int N2, bool INV, int X = 1, int K = N2>
+template <typename C, int N1, int N2, bool INV, int X = 1, int K = N2, bool PK = false>
 __device__ __forceinline__ void step2(const C* buf, int LD, int c, int k1, C (&a)[N2]) {
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) a[j2] = buf[prow<X>(k1, j2, N2) * LD + c];
-  reg_dft<C, N2, INV, K>(a);
+  reg_dft<C, N2, INV, K, PK>(a);
 }
 
 // Step A (inverse split from registers): a[k2] = X[k1 + N1*k2] of task
@@ -252,9 +288,9 @@ __device__ __forceinline__ void step2(const C* buf, int LD, int c, int k1, C (&a
 // prow<X>(k1, n2, N2), the access pattern of step 1's stores, and leaves
 // out[n1] = x[n2 + N2*n1]; with K < N1 / 2 only n1 < K and n1 >= N1 - K are
 // computed (see reg_dft).
-template <typename C, int N1, int N2, bool INV, int X = 1>
+template <typename C, int N1, int N2, bool INV, int X = 1, bool PK = false>
 __device__ __forceinline__ void stepA_own(C* buf, int LD, int c, int k1, C (&a)[N2], const C* tw, int tws) {
-  reg_dft<C, N2, INV>(a);
+  reg_dft<C, N2, INV, N2, PK>(a);
   if (N2 > 1 && k1 > 0) {
 #pragma unroll
     for (int n2 = 1; n2 < N2; ++n2) a[n2] = cmul(a[n2], twid<C, INV>(tw, k1 * n2 * tws));
@@ -263,11 +299,11 @@ __device__ __forceinline__ void stepA_own(C* buf, int LD, int c, int k1, C (&a)[
   for (int n2 = 0; n2 < N2; ++n2) buf[prow<X>(k1, n2, N2) * LD + c] = a[n2];
 }
 
-template <typename C, int N1, int N2, bool INV, int X = 1, int K = N1>
+template <typename C, int N1, int N2, bool INV, int X = 1, int K = N1, bool PK = false>
 __device__ __forceinline__ void stepB_own(const C* buf, int LD, int c, int n2, C (&a)[N1]) {
 #pragma unroll
   for (int k1 = 0; k1 < N1; ++k1) a[k1] = buf[prow<X>(k1, n2, N2) * LD + c];
-  reg_dft<C, N1, INV, K>(a);
+  reg_dft<C, N1, INV, K, PK>(a);
 }
 
 // Step 1 and step A (own slots) when every thread runs exactly one task and
@@ -604,12 +640,12 @@ k_y_fwd_p(const __grid_constant__ CUtensorMap mO, const C* __restrict__ spec, in
     }
     pend = nitem < n_items && nnitem < n_items;
     if (pend) fetch(nnitem, pn);
-    step1<C, N1, N2, B, false, XP>(buf, B, tws, 1);
+    step1<C, N1, N2, B, false, XP, true>(buf, B, tws, 1);   // packed FP32 butterflies (see bfly)
     if (TS && staged && threadIdx.x == 0) tma::bulk_wait_read_all();   // staging free again
     __syncthreads();
     if (NBUF == 2 && nitem < n_items) gather(nxt, buf0 + ((job & 1) ^ 1) * TILE, yv, true);
     C a[N2];
-    step2<C, N1, N2, false, XP>(buf, B, c, slot, a);
+    step2<C, N1, N2, false, XP, N2, true>(buf, B, c, slot, a);
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) buf[prow<XP>(slot, j2, N2) * B + c] = zc;
     if (NBUF == 1) {
@@ -1330,7 +1366,7 @@ __device__ __forceinline__ int mesh_of_rank(int r, int N, int w) { return r <= w
 // Step 1 of the split (see step1) on the zero-padded window column whose
 // nonzero rows z <= w and z >= N - w come from the compact slot
 // xc[rank * B + c]: reads the slot directly, writes buf like step1.
-template <typename C, int N, int B, int X>
+template <typename C, int N, int B, int X, bool PK = false>
 __device__ __forceinline__ void step1_win(C* buf, const C* xc, int w, const C* tw, int tid, int nthr) {
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   const int W = 2 * w + 1;
@@ -1346,7 +1382,7 @@ __device__ __forceinline__ void step1_win(C* buf, const C* xc, int w, const C* t
       if (r >= 0) v = xc[r * B + c];
       a[j1] = v;
     }
-    reg_dft<C, N1, false>(a);
+    reg_dft<C, N1, false, N1, PK>(a);
     if (N2 > 1 && j2 > 0) {
 #pragma unroll
       for (int k1 = 1; k1 < N1; ++k1) a[k1] = cmul(a[k1], twid<C, false>(tw, j2 * k1));
@@ -1746,6 +1782,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
   static_assert(B * Split<N>::N2 <= Z::CTHREADS, "one step-B task per transform thread");
   constexpr int N1 = Z::N1, N2 = Z::N2, TILE = Z::TILE, M1 = N / 2 + 1, CT = Z::CTHREADS;
   constexpr int XP = xperm<C, N, B>();
+  constexpr bool PK = true;   // packed FP32 butterflies (see bfly)
   constexpr uint64_t kLimitNs = 2000000000ull;
   const int W = 2 * w + 1;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1804,18 +1841,18 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
       C* buf = sb0 + cur * TILE;
       if (tma::bar_or(1, CT, !tma::mbar_wait(&bar[cur], ph[cur], kLimitNs))) { failed = 1; break; }
       ph[cur] ^= 1;
-      step1<C, N1, N2, B, false, XP>(buf, B, tws, 1, tid, CT);
+      step1<C, N1, N2, B, false, XP, PK>(buf, B, tws, 1, tid, CT);
       tma::bar_sync(1, CT);
       C a[N2];
-      step2<C, N1, N2, false, XP>(buf, B, c, k1, a);
+      step2<C, N1, N2, false, XP, N2, PK>(buf, B, c, k1, a);
       tma::bar_sync(1, CT);
       // the window column's step 1 (its rows from the compact slot); the
       // pruned form (step1_win_p) needs more registers than this loop has
       // left and measured slower here
-      step1_win<C, N, B, XP>(buf, xb0 + cur * WS, w, tws, tid, CT);
+      step1_win<C, N, B, XP, PK>(buf, xb0 + cur * WS, w, tws, tid, CT);
       tma::bar_sync(1, CT);
       C x[N2];
-      step2<C, N1, N2, false, XP>(buf, B, c, k1, x);
+      step2<C, N1, N2, false, XP, N2, PK>(buf, B, c, k1, x);
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) {
         C* o = &at[(k1 + N1 * k2) * B + c];
@@ -1828,7 +1865,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) x[k2] = cmul(x[k2], f[k2]);
       if (dc_col && k1 == 0) { x[0].x = 0; x[0].y = 0; }   // k = 0 mode
-      stepA_own<C, N1, N2, true, XP>(buf, B, c, k1, x, tws, 1);
+      stepA_own<C, N1, N2, true, XP, PK>(buf, B, c, k1, x, tws, 1);
       tma::bar_sync(1, CT);
       {
         // Y_b's column into the slot in natural row order for the TMA store
@@ -1837,7 +1874,7 @@ k_zadj(const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorM
         const int cc = tid % B, n2 = tid / B;
         const bool act = tid < B * N2;
         C v[N1];
-        if (act) stepB_own<C, N1, N2, true, XP>(buf, B, cc, n2, v);
+        if (act) stepB_own<C, N1, N2, true, XP, N1, PK>(buf, B, cc, n2, v);
         __syncwarp();
         if (act) {
 #pragma unroll
