@@ -311,13 +311,13 @@ __device__ __forceinline__ void stepB_own(const C* buf, int LD, int c, int n2, C
 // m < N1, with q = tid / B in both. The caller loads those N1 twiddles into
 // registers once (tq[m] = W_N^(q m); conjugated here for the inverse), which
 // saves 2 (N1 - 1) shared-memory loads per thread and mesh.
-template <typename C, int N1, int N2, int B, bool INV, int X>
+template <typename C, int N1, int N2, int B, bool INV, int X, bool PK = false>
 __device__ __forceinline__ void step1_tr(C* buf, int LD, const C (&tq)[N1], int tid) {
   const int c = tid % B, j2 = tid / B;
   C a[N1];
 #pragma unroll
   for (int j1 = 0; j1 < N1; ++j1) a[j1] = buf[(N2 * j1 + j2) * LD + c];
-  reg_dft<C, N1, INV>(a);
+  reg_dft<C, N1, INV, N1, PK>(a);
 #pragma unroll
   for (int k1 = 1; k1 < N1; ++k1) {
     C w = tq[k1];
@@ -328,9 +328,9 @@ __device__ __forceinline__ void step1_tr(C* buf, int LD, const C (&tq)[N1], int 
 #pragma unroll
   for (int k1 = 0; k1 < N1; ++k1) buf[prow<X>(k1, j2, N2) * LD + c] = a[k1];
 }
-template <typename C, int N1, int N2, bool INV, int X>
+template <typename C, int N1, int N2, bool INV, int X, bool PK = false>
 __device__ __forceinline__ void stepA_own_tr(C* buf, int LD, int c, int k1, C (&a)[N2], const C (&tq)[N1]) {
-  reg_dft<C, N2, INV>(a);
+  reg_dft<C, N2, INV, N2, PK>(a);
 #pragma unroll
   for (int n2 = 1; n2 < N2; ++n2) {
     C w = tq[n2];
