@@ -270,6 +270,33 @@ __device__ __forceinline__ void step1(C* buf, int LD, const C* tw, int tws) {
   step1<C, N1, N2, B, INV, X, PK>(buf, LD, tw, tws, (int)threadIdx.x, (int)blockDim.x);
 }
 
+// Step 1 on a tile whose rows are present only where msk says so: bit j1 of
+// msk[j2] marks row N2 j1 + j2 (msk null: every row). Absent rows are read as
+// zero without touching shared memory, so the tile needs no clearing between
+// sparse fills.
+template <typename C, int N1, int N2, int B, bool INV, int X = 1, bool PK = false>
+__device__ __forceinline__ void step1_m(C* buf, int LD, const C* tw, const uint32_t* msk) {
+  static_assert(N1 <= 32, "one mask word per task");
+  for (int t = threadIdx.x; t < B * N2; t += blockDim.x) {
+    const int c = t % B, j2 = t / B;
+    const uint32_t m = msk ? msk[j2] : 0xffffffffu;
+    C a[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) {
+      a[j1].x = 0; a[j1].y = 0;
+      if ((m >> j1) & 1u) a[j1] = buf[(N2 * j1 + j2) * LD + c];
+    }
+    reg_dft<C, N1, INV, N1, PK>(a);
+    if (N2 > 1 && j2 > 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) a[k1] = cmul(a[k1], twid<C, INV>(tw, j2 * k1));
+    }
+    if (X > 1) __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) buf[prow<X>(k1, j2, N2) * LD + c] = a[k1];
+  }
+}
+
 // Step 2: task (c, k1) reads its N2 values and leaves X[k1 + N1*k2] in a[k2];
 // with K < N2 / 2 only k2 < K and k2 >= N2 - K are computed (see reg_dft).
 template <typename C, int N1, int N2, bool INV, int X = 1, int K = N2, bool PK = false>
@@ -489,8 +516,9 @@ __device__ __forceinline__ void zero_tile(C* buf, int rows) {
 // one plane. While one item is transformed, the rows of the next are gathered
 // by cp.async into the second buffer (their line numbers were loaded at the
 // start of the item, the plane's line range one item earlier), so the
-// dependent index loads do not stall the pass. Step 2 clears each element it reads, so the rows
-// a sparse plane lacks read as zero the next time the buffer is filled.
+// dependent index loads do not stall the pass. The gather marks the rows it
+// fills in the buffer's presence mask, and step 1 reads only those (the rows
+// a sparse plane lacks are zero without being stored).
 // Sparse path (idx != null): the compact lines of plane z of mesh b are
 // line_base[b] + [idx_b[z][0], idx_b[z+1][0]) with y = line_y[line]; dense
 // path: line z*N + y of one mesh.
@@ -512,7 +540,7 @@ struct YFwd {
   static constexpr int PRE = 4;            // rounds whose line numbers are loaded ahead
   static constexpr int YB = N < 256 ? N : 256;   // ky rows per store box
   static constexpr int NBUF = TS || 2 * sizeof(C) * (2 * (size_t)TILE + N) <= 220 * 1024 ? 2 : 1;
-  static constexpr size_t SMEM = sizeof(C) * ((NBUF + (TS ? 1 : 0)) * (size_t)TILE + N);
+  static constexpr size_t SMEM = sizeof(C) * ((NBUF + (TS ? 1 : 0)) * (size_t)TILE + N) + 4 * NBUF * N2;
   static constexpr int MINB = 2 * SMEM <= 220 * 1024 || !TS ? 2 : 1;
   static constexpr size_t smem_bytes() { return SMEM; }
 };
@@ -531,6 +559,8 @@ k_y_fwd_p(const __grid_constant__ CUtensorMap mO, const C* __restrict__ spec, in
   C* const tws = reinterpret_cast<C*>(smem_raw);
   C* const buf0 = tws + N;   // buffers buf0 + k * TILE, k < NBUF
   C* const stg = buf0 + NBUF * TILE;   // staging tile (TS)
+  // row presence of each buffer (sparse path): bit j1 of msk[k * N2 + j2] = row N2 j1 + j2
+  uint32_t* const msk = reinterpret_cast<uint32_t*>(stg + (TS ? TILE : 0));
   const int T = (M1 + B - 1) / B;
   const int64_t n_items = (int64_t)T * N * nb;
   int64_t item = blockIdx.x;
@@ -538,7 +568,7 @@ k_y_fwd_p(const __grid_constant__ CUtensorMap mO, const C* __restrict__ spec, in
   C zc;
   zc.x = 0; zc.y = 0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
-  for (int i = threadIdx.x; i < NBUF * TILE; i += blockDim.x) buf0[i] = zc;
+  for (int i = threadIdx.x; i < NBUF * N2; i += blockDim.x) msk[i] = 0;
   const int c = threadIdx.x % B, slot = threadIdx.x / B;
   struct Item {
     int kx0, z, b;
@@ -585,17 +615,20 @@ k_y_fwd_p(const __grid_constant__ CUtensorMap mO, const C* __restrict__ spec, in
   // rows of item m into buffer dst; y of the first PRE rounds from yv
   auto gather = [&](const Item& m, C* dst, const int (&yv)[PRE], bool have_yv) {
     const bool in = c < min(B, M1 - m.kx0);
+    uint32_t* const mk = msk + (int)((dst - buf0) / TILE) * N2;
 #pragma unroll
     for (int p = 0; p < PRE; ++p) {
       const int64_t r = m.lo + slot + (int64_t)p * RS;
       if (r < m.hi) {
         const int y = idx ? (have_yv ? yv[p] : line_y[r]) : (int)(r - m.lo);
         if (in) tma::cp_async(dst + y * B + c, spec + r * P + m.kx0 + c);
+        if (idx && c == 0) atomicOr(&mk[y % N2], 1u << (y / N2));
       }
     }
     for (int64_t r = m.lo + slot + (int64_t)PRE * RS; r < m.hi; r += RS) {
       const int y = idx ? line_y[r] : (int)(r - m.lo);
       if (in) tma::cp_async(dst + y * B + c, spec + r * P + m.kx0 + c);
+      if (idx && c == 0) atomicOr(&mk[y % N2], 1u << (y / N2));
     }
     tma::cp_async_commit();
   };
@@ -640,16 +673,17 @@ k_y_fwd_p(const __grid_constant__ CUtensorMap mO, const C* __restrict__ spec, in
     }
     pend = nitem < n_items && nnitem < n_items;
     if (pend) fetch(nnitem, pn);
-    step1<C, N1, N2, B, false, XP, true>(buf, B, tws, 1);   // packed FP32 butterflies (see bfly)
+    const int cb = NBUF == 2 ? (int)(job & 1) : 0;
+    // packed FP32 butterflies (see bfly); absent rows of a sparse plane read as zero
+    step1_m<C, N1, N2, B, false, XP, true>(buf, B, tws, idx ? msk + cb * N2 : nullptr);
     if (TS && staged && threadIdx.x == 0) tma::bulk_wait_read_all();   // staging free again
     __syncthreads();
+    if (threadIdx.x < N2) msk[cb * N2 + threadIdx.x] = 0;   // read by step 1; clear for the next fill
     if (NBUF == 2 && nitem < n_items) gather(nxt, buf0 + ((job & 1) ^ 1) * TILE, yv, true);
     C a[N2];
     step2<C, N1, N2, false, XP, N2, true>(buf, B, c, slot, a);
-#pragma unroll
-    for (int j2 = 0; j2 < N2; ++j2) buf[prow<XP>(slot, j2, N2) * B + c] = zc;
     if (NBUF == 1) {
-      __syncthreads();   // the tile is read and clear
+      __syncthreads();   // the tile is read; its mask was cleared after step 1
       if (nitem < n_items) gather(nxt, buf, yv, true);
     }
     if constexpr (TS) {
